@@ -1,0 +1,169 @@
+"""Fractional powers: integer split, improved split and the sinc sum (Sec. 3.4).
+
+Test infrastructure (see ``oracle/__init__``).
+
+With A = kappa^2 M + S and L = M^{-1} A, the field is u = L^{-beta} M^{-1} f.
+
+* Integer part (Sec. 3.4): A w_1 = f, A w_k = M w_{k-1}; then w_n = L^{-n} M^{-1} f.
+* Fractional part beta' in (0,1), Eq. eq:beta-approx rewritten with y = -2t,
+  node step k (the printed step 1/sqrt(K) in t is k = 2/sqrt(K) in y) and the
+  printed "I" read as M (the discrete operator is M^{-1}A):
+      L^{-beta'} v = sum_l c_l (S + sigma_l M)^{-1} M v,
+      y_l = l k,  c_l = (sin(pi beta')/pi) k e^{(1-beta') y_l},  sigma_l = e^{y_l} + kappa^2,
+  for l = l_lo .. l_hi.  The Balakrishnan exponent is read as -beta.
+* Improved split (Sec. 3.4): for beta' in (0, 1/3) and n >= 1 use
+  beta = (n-1) + 2 beta'', beta'' = (beta'+1)/2; for beta' in (2/3, 1) use
+  beta = n + 2 beta'', beta'' = beta'/2; the sinc map for beta'' is applied twice
+  with the same node range, the second time to M times the first result.  At
+  the open interval ends, and for n = 0 with beta' < 1/3, the standard split is used.
+
+Solves are direct sparse LU factorisations (scipy ``splu``), one per shift,
+reused for all samples.
+"""
+import math
+
+import numpy as np
+import scipy.sparse.linalg as spla
+
+STANDARD = "standard"
+IMPROVED = "improved"
+
+
+def split_beta(beta, mode=STANDARD):
+    """Return (n_int, beta_frac, n_passes) of the integer/fractional split."""
+    if beta <= 0:
+        raise ValueError("beta must be positive")
+    n = int(math.floor(beta))
+    bp = beta - n
+    if bp == 0.0:
+        return n, 0.0, 0
+    if mode == IMPROVED:
+        if bp < 1.0 / 3.0 and n >= 1:
+            return n - 1, (bp + 1.0) / 2.0, 2
+        if bp > 2.0 / 3.0:
+            return n, bp / 2.0, 2
+    return n, bp, 1
+
+
+def sinc_rule(beta_frac, k, l_lo, l_hi):
+    """Nodes y_l, weights c_l for l = l_lo..l_hi (Eq. eq:beta-approx in y = -2t)."""
+    l = np.arange(l_lo, l_hi + 1, dtype=np.float64)
+    y = l * k
+    c = math.sin(math.pi * beta_frac) / math.pi * k * np.exp((1.0 - beta_frac) * y)
+    return y, c
+
+
+def scalar_sinc(beta_frac, K, lam):
+    """The paper's scalar u_K(lambda) with K (2K+1 nodes, t_k = k/sqrt(K))."""
+    y, c = sinc_rule(beta_frac, 2.0 / math.sqrt(K), -K, K)
+    return float(np.sum(c / (np.exp(y) + lam)))
+
+
+class Shifted:
+    """Factorisations of S + sigma M, cached per shift."""
+
+    def __init__(self, S, M):
+        self.S = S.tocsc()
+        self.M = M.tocsc()
+        self.cache = {}
+
+    def solve(self, sigma, rhs):
+        key = float(sigma)
+        if key not in self.cache:
+            self.cache[key] = spla.splu((self.S + sigma * self.M).tocsc())
+        return self.cache[key].solve(rhs)
+
+
+def fractional_apply(sh, M, beta_frac, kappa, k, l_lo, l_hi, v, return_terms=False):
+    """L^{-beta'} applied to columns of v ([N, ns]) by the sinc sum."""
+    y, c = sinc_rule(beta_frac, k, l_lo, l_hi)
+    rhs = M @ v
+    u = np.zeros_like(v)
+    terms = []
+    for yl, cl in zip(y, c):
+        x = sh.solve(math.exp(yl) + kappa**2, rhs)
+        u += cl * x
+        if return_terms:
+            terms.append(x)
+    return (u, terms) if return_terms else u
+
+
+def sample_fields(S, M, b, kappa, beta, k, l_lo, l_hi, mode=STANDARD, sh=None):
+    """Fields u_s ([ns, N]) for loads b ([ns, N]) by the split and the sinc sum."""
+    if sh is None:
+        sh = Shifted(S, M)
+    n, bp, passes = split_beta(beta, mode)
+    w = np.asarray(b, dtype=np.float64).T.copy()  # [N, ns]
+    # w_0 := M^{-1} b so that every pass starts from L^{-1} style updates
+    if n >= 1:
+        w = sh.solve(kappa**2, w)
+        for _ in range(n - 1):
+            w = sh.solve(kappa**2, M @ w)
+        v = w
+    else:
+        v = None
+    if passes == 0:
+        return v.T
+    for p_ in range(passes):
+        if v is None:
+            # n = 0: the first pass takes the load itself (M M^{-1} b = b)
+            y, c = sinc_rule(bp, k, l_lo, l_hi)
+            u = np.zeros_like(w)
+            for yl, cl in zip(y, c):
+                u += cl * sh.solve(math.exp(yl) + kappa**2, w)
+            v = u
+        else:
+            v = fractional_apply(sh, M, bp, kappa, k, l_lo, l_hi, v)
+    return v.T
+
+
+def field_loss_grad(S, M, b, g, kappa, beta, k, l_lo, l_hi, mode=STANDARD):
+    """Loss L = sum_s ||u_s - g_s||_M^2 and its gradients by the adjoint identity.
+
+    Returns (L, dL/db [ns, N], dL/dkappa).  Covers the standard split with
+    n = 0 or n >= 1 and one fractional pass.  Derivation: u = sum_l c_l x_l,
+    x_l = A_l^{-1} r, A_l = S + sigma_l M, sigma_l = e^{y_l} + kappa^2, with the
+    symmetric A_l: dL/dr = sum_l c_l z_l, z_l = A_l^{-1} gt, gt = 2 M (u - g);
+    dx_l/dkappa = -A_l^{-1} (2 kappa M) x_l.  The integer chain w_i = A0^{-1} M w_{i-1}
+    (A0 = S + kappa^2 M, w_1 = A0^{-1} b, r = M w_n) is differentiated the same way.
+    """
+    sh = Shifted(S, M)
+    n, bp, passes = split_beta(beta, mode)
+    if passes != 1:
+        raise NotImplementedError("gradient for one fractional pass")
+    y, c = sinc_rule(bp, k, l_lo, l_hi)
+    sig = np.exp(y) + kappa**2
+    B = np.asarray(b, dtype=np.float64).T
+    ws = []
+    if n >= 1:
+        w = sh.solve(kappa**2, B)
+        ws.append(w)
+        for _ in range(n - 1):
+            w = sh.solve(kappa**2, M @ w)
+            ws.append(w)
+        r = M @ w
+    else:
+        r = B
+    xs = [sh.solve(s, r) for s in sig]
+    u = sum(cl * x for cl, x in zip(c, xs))
+    G = np.asarray(g, dtype=np.float64).T
+    d = u - G
+    L = float(np.sum(d * (M @ d)))
+    gt = 2.0 * (M @ d)
+    zs = [sh.solve(s, gt) for s in sig]
+    dLdr = sum(cl * z for cl, z in zip(c, zs))
+    dk = 0.0
+    for cl, x, z in zip(c, xs, zs):
+        dk += -2.0 * kappa * cl * float(np.sum(z * (M @ x)))
+    if n >= 1:
+        # r = M w_n; w_i = A0^{-1} M w_{i-1}; adjoint lambda_n = A0^{-1} M dLdr
+        lam = sh.solve(kappa**2, M @ dLdr)
+        for i in range(n - 1, -1, -1):
+            # w_{i+1} depends on kappa through A0: dw/dkappa = -A0^{-1} 2 kappa M w
+            dk += -2.0 * kappa * float(np.sum(lam * (M @ ws[i])))
+            if i > 0:
+                lam = sh.solve(kappa**2, M @ lam)
+        dLdb = lam
+    else:
+        dLdb = dLdr
+    return L, dLdb.T, dk
