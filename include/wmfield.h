@@ -1,0 +1,258 @@
+/*
+ * wmfield.h -- C ABI of the GB300 Whittle–Matérn surface field sampler.
+ *
+ * The library samples Gaussian random fields u on closed surfaces from the
+ * fractional SPDE (kappa^2 - Delta_Gamma)^beta u = white noise (Eq. eq:PDE,
+ * Sec. 1), discretised with C0-glued tensor B-splines on the patches of the
+ * surface (Sec. 2.3, Eq. def::space2).  With S the stiffness and M the mass
+ * matrix (Eqs. eq:FEM, eq:mass, eq:stiffness) it computes, per noise sample s,
+ *   integer part (Sec. 3.4):  (S + kappa^2 M) w_1 = b_s,  (S + kappa^2 M) w_i = M w_{i-1},
+ *   fractional part (Eq. eq:beta-approx, y = -2t):
+ *       u_s = sum_l c_l x_{l,s},  (S + sigma_l M) x_{l,s} = M w_n   (b_s if n = 0),
+ *       y_l = l k, sigma_l = e^{y_l} + kappa^2, c_l = (sin(pi beta')/pi) k e^{(1-beta') y_l},
+ * and, with the improved split (Sec. 3.4), the sinc map twice.  All shifted
+ * systems of all samples are solved together on the GPU by a batched
+ * preconditioned conjugate gradient with a geometric multigrid V-cycle over the
+ * dyadic spline hierarchy (Sec. 3.5).
+ *
+ * Conventions for every entry point:
+ *  - Return value: WM_OK (0) or a negative WM_ERR_* code; no exception ever
+ *    crosses the ABI.  wm_error_string() names a code; wm_last_error() returns
+ *    a message for the calling thread's last failure.
+ *  - Handles (wm_geom_t, wm_hier_t) are owned by the library and released with
+ *    wm_destroy_*.  A handle may be used by one host thread at a time.
+ *  - "device" pointers are caller-owned CUDA device memory of the current
+ *    device; "host" pointers are caller-owned host memory.  Vectors of n
+ *    samples over N degrees of freedom are row-major [n][N] float64.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is stream-ordered; entry points that return
+ *    statistics or host results synchronise the stream before returning.
+ *  - Levels are numbered from 0 = finest to wm_num_levels()-1 = coarsest.
+ */
+#ifndef WMFIELD_H
+#define WMFIELD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------- */
+#define WM_OK 0
+#define WM_ERR_INVALID_ARG (-1)   /* a size, pointer or parameter is out of range  */
+#define WM_ERR_OOM (-2)           /* a device or host allocation failed            */
+#define WM_ERR_CUDA (-3)          /* a CUDA call failed; see wm_last_error()       */
+#define WM_ERR_NOT_CONVERGED (-4) /* some system missed rtol within max_iter       */
+#define WM_ERR_NONFINITE (-5)     /* a NaN/Inf appeared in a residual norm         */
+#define WM_ERR_UNSUPPORTED (-7)   /* valid request outside what is implemented     */
+
+/* ---- enumerations --------------------------------------------------------- */
+#define WM_SPHERE6 0      /* unit sphere as six gnomonic cube-face patches     */
+#define WM_TORUS 1        /* one doubly periodic torus patch (R, r)            */
+
+#define WM_FP64 0         /* every step in float64                              */
+#define WM_MIXED 1        /* float64 outer CG, float32 multigrid preconditioner */
+
+#define WM_SPLIT_STANDARD 0  /* beta = n + beta'                               */
+#define WM_SPLIT_IMPROVED 1  /* Sec. 3.4 itemize: beta'' applied twice          */
+
+#define WM_NOISE_DRAW 0   /* draw b_s from Philox with desc.seed               */
+#define WM_NOISE_GIVEN 1  /* take b_s from the caller's b buffer               */
+
+/* ---- geometry ------------------------------------------------------------- */
+typedef struct {
+  int kind;      /* WM_SPHERE6 or WM_TORUS                                        */
+  int degree;    /* spline degree p, 1 <= p <= 4                                   */
+  int elems_u;   /* elements per patch side at the finest level (power of two)     */
+  int elems_v;   /* sphere: must equal elems_u; torus: elements along the tube     */
+  double R, r;   /* torus major / minor radius (ignored for the sphere)            */
+} wm_geom_desc;
+
+typedef struct wm_geom* wm_geom_t;
+typedef struct wm_hier* wm_hier_t;
+
+/*
+ * Validates a surface description and builds its patch table and the C0
+ * gluing of the spline space S^0_{j,p} (Eq. def::space2) by combinatorial
+ * matching of patch edges.  Host only.  Global DOF numbering: patches in
+ * order, local DOFs row by row (i_v outer, i_u inner); a shared DOF keeps the
+ * index of its first occurrence.
+ * Errors: WM_ERR_INVALID_ARG for a bad kind/degree/size or NULL out.
+ */
+int wm_setup_geometry(const wm_geom_desc* desc, wm_geom_t* out);
+
+/*
+ * Builds the dyadic hierarchy of n_levels levels (finest = the description's
+ * elements, each coarser level halves the elements per side; Sec. 2.3,
+ * Xi_{j,p}) on the current CUDA device: the metric terms a_m and a_m K_m^{-1}
+ * at the (p+1)^2 Gauss points of every element in float64 (Sec. 3.2), the
+ * assembled mass and stiffness rows of every level (float64 and float32
+ * copies), and the knot-insertion prolongations between levels.
+ * Errors: WM_ERR_INVALID_ARG (n_levels < 1 or too many for the element
+ * counts), WM_ERR_OOM, WM_ERR_CUDA.  The geometry handle stays owned by the
+ * caller and may be destroyed afterwards.
+ */
+int wm_assemble_hierarchy(wm_geom_t geom, int n_levels, void* stream, wm_hier_t* out);
+
+int wm_num_levels(wm_hier_t h);               /* number of levels, or < 0 on error */
+int wm_num_dofs(wm_hier_t h, int level);      /* glued DOFs N of a level, or < 0    */
+int wm_num_quad_points(wm_hier_t h, int level); /* Gauss points of a level, or < 0   */
+
+/*
+ * Copies the local-to-global DOF map of a level to host memory:
+ * out[m][i_v][i_u] (int32), n_patches * n_loc_v * n_loc_u entries, where
+ * n_loc = elems + p for open patches and elems for the periodic torus.
+ * `cap` is the capacity of `out` in entries.  Returns the number of entries
+ * written, or WM_ERR_INVALID_ARG when cap is too small.
+ */
+int wm_dof_map(wm_hier_t h, int level, int32_t* out, int64_t cap);
+
+/*
+ * Copies the float64 metric terms of a level at its Gauss points to device
+ * memory `out` [n_quad][4] = (a, G11, G12, G22) with G = a K^{-1} (Sec. 3.2).
+ * Gauss point index q = ((m n_v + e_v) n_u + e_u) nq^2 + g_v nq + g_u.
+ */
+int wm_metric(wm_hier_t h, int level, double* out, void* stream);
+
+/* ---- operators ------------------------------------------------------------ */
+/*
+ * y_j = (S + sigma_j M) x_j for n_vec vectors on a level (Eqs. eq:FEM,
+ * eq:var_form with t = sigma_j).  sigma: host array [n_vec]; x, y: device
+ * [n_vec][N].  precision WM_FP64 applies the float64 rows, WM_MIXED the
+ * float32 rows (inputs rounded to float32, result widened).  x and y must not
+ * overlap.
+ */
+int wm_apply_shifted(wm_hier_t h, int level, int n_vec, const double* sigma,
+                     const double* x, double* y, int precision, void* stream);
+
+/* y_j = M x_j on a level in float64 (the S-term off). */
+int wm_apply_mass(wm_hier_t h, int level, const double* x, double* y, int n_vec, void* stream);
+
+/*
+ * Prolongation by dyadic knot insertion from level `level`+1 (coarse) to
+ * `level` (fine): the fine coefficients of the same spline (Sec. 3.5, nested
+ * spaces).  xc: device [n_vec][N_coarse], xf: device [n_vec][N_fine].
+ */
+int wm_prolongate(wm_hier_t h, int level, const double* xc, double* xf, int n_vec, void* stream);
+
+/* Restriction = transpose of wm_prolongate: rc = P^T rf. */
+int wm_restrict(wm_hier_t h, int level, const double* rf, double* rc, int n_vec, void* stream);
+
+/*
+ * One application of the batched V-cycle preconditioner on level 0 to n_vec
+ * residuals with shifts sigma (host [n_vec]); z = B_sigma r.  r, z: device
+ * [n_vec][N].  Smoother: Chebyshev of degree `smoother_degree` on
+ * [lambda_max/cheb_ratio, 1.1 lambda_max] of D^{-1}(S + sigma M); precision
+ * as in wm_apply_shifted.
+ */
+int wm_vcycle(wm_hier_t h, int n_vec, const double* sigma, const double* r, double* z,
+              int precision, int smoother_degree, double cheb_ratio, void* stream);
+
+/* ---- random numbers and white noise --------------------------------------- */
+/*
+ * Philox4x32-10 (Salmon et al., SC'11) on n counters: ctr device [n][4]
+ * uint32, key = (key mod 2^32, key div 2^32), out device [n][4].
+ */
+int wm_philox4x32_10(const uint32_t* ctr, uint64_t key, uint32_t* out, int64_t n, void* stream);
+
+/*
+ * Standard normals of the white noise, n consecutive Gauss-point indices from
+ * q0 of one sample: out device [n].  Normal q is half (q mod 2) of a
+ * Box–Muller pair drawn from the counter (q/2 mod 2^32, sample, stream_id,
+ * q/2 div 2^32): u = ((x_hi >> 5) 2^26 + (x_lo >> 6) + 1) 2^-53 in (0,1].
+ * stream_id 0 = noise, 1 = loss targets.
+ */
+int wm_normals(uint64_t seed, int sample, int stream_id, int64_t q0, int64_t n,
+               double* out, void* stream);
+
+/*
+ * White-noise loads of samples 0..n_samples-1 on level 0 (Sec. 3.3):
+ * b_s,i = sum_q sqrt(w_q a_q) xi_{s,q} phi_i(x_q) with xi from wm_normals,
+ * so Cov(b_s) is the quadrature mass matrix.  b: device [n_samples][N].
+ */
+int wm_noise_loads(wm_hier_t h, uint64_t seed, int n_samples, double* b, void* stream);
+
+/* ---- the sampler ------------------------------------------------------------ */
+typedef struct {
+  double kappa;         /* kappa > 0                                                 */
+  double beta;          /* beta > 0 (nu = 2 beta - 1)                                */
+  int split;            /* WM_SPLIT_STANDARD or WM_SPLIT_IMPROVED                    */
+  double sinc_k;        /* node step k > 0 in y                                      */
+  int l_lo, l_hi;       /* node indices l_lo..l_hi (l_lo <= l_hi)                    */
+  uint64_t seed;        /* Philox key of the noise                                   */
+  int n_samples;        /* samples s = 0..n_samples-1                                */
+  int noise_mode;       /* WM_NOISE_DRAW or WM_NOISE_GIVEN                           */
+  int precision;        /* WM_FP64 or WM_MIXED                                       */
+  double rtol;          /* per-system stop: ||r|| <= rtol ||rhs|| (Euclidean)        */
+  int max_iter;         /* outer CG iteration cap                                    */
+  int smoother_degree;  /* Chebyshev degree of pre- and post-smoothing (>= 1)        */
+  double cheb_ratio;    /* Chebyshev interval [lmax/cheb_ratio, 1.1 lmax]            */
+  int max_systems;      /* systems per batched solve (0 = all at once); 1 = one
+                           system at a time                                          */
+} wm_sample_desc;
+
+typedef struct {
+  int n_systems;          /* shifted systems solved (all passes)                     */
+  int n_batches;          /* batched PCG solves launched                             */
+  int max_iterations;     /* largest outer iteration count of any batch             */
+  int total_iterations;   /* sum over batches of their iteration counts             */
+  int n_not_converged;    /* systems that missed rtol                               */
+  double max_rel_residual;/* largest final ||r||/||rhs|| (recursive residual)       */
+  int n_int_solves;       /* integer-part solves per sample                          */
+  int n_frac_passes;      /* sinc passes (0, 1 or 2)                                 */
+  int n_nodes;            /* sinc nodes per pass                                     */
+} wm_stats;
+
+/*
+ * The fields u_s of samples 0..n_samples-1 on level 0 (see the file header for
+ * the formula).  u: [n_samples][N] float64, device or host memory (host memory
+ * is staged through the library's device workspace and copied back before
+ * return).  b: [n_samples][N] or NULL; with WM_NOISE_DRAW the drawn loads are
+ * written there if non-NULL, with WM_NOISE_GIVEN they are read from there
+ * (same memory rules as u).  stats: host, may be NULL.  The stream is
+ * synchronised before return.
+ * Errors: WM_ERR_INVALID_ARG, WM_ERR_OOM, WM_ERR_CUDA, WM_ERR_NOT_CONVERGED
+ * (u is still written with the last iterates), WM_ERR_NONFINITE.
+ */
+int wm_sample_fields(wm_hier_t h, const wm_sample_desc* desc, double* u, double* b,
+                     wm_stats* stats, void* stream);
+
+/*
+ * Several independent problems (surfaces, levels, kappa, beta, samples) in one
+ * call: u[i] receives the fields of problem i (same rules as wm_sample_fields,
+ * device memory).  stats: host [n_inst] or NULL.
+ */
+int wm_sample_fields_batched(int n_inst, const wm_hier_t* h, const wm_sample_desc* desc,
+                             double* const* u, wm_stats* stats, void* stream);
+
+/*
+ * Gradient of a scalar loss through the fields: given grad_u = dL/du
+ * [n_samples][N] (device) for the fields of `desc` with loads b (device,
+ * [n_samples][N], e.g. those returned by wm_sample_fields), returns
+ * grad_b = dL/db (device [n_samples][N], may be NULL) and *grad_kappa = dL/dkappa
+ * (host, may be NULL).  The operator is symmetric, so the adjoint reuses the
+ * batched shifted solves on grad_u:  z_{l,s} = (S + sigma_l M)^{-1} grad_u_s,
+ * dL/db_s = sum_l c_l z_{l,s} (chained through the integer solves), and
+ * dL/dkappa = -2 kappa sum_{l,s} c_l z_{l,s}^T M x_{l,s} (+ integer-solve terms).
+ * The forward solutions x_{l,s} are recomputed per batch of max_systems.
+ * Standard split with one fractional pass (or integer beta) only.
+ */
+int wm_sample_fields_backward(wm_hier_t h, const wm_sample_desc* desc, const double* b,
+                              const double* grad_u, double* grad_b, double* grad_kappa,
+                              void* stream);
+
+/* Integer/fractional split of beta (Sec. 3.4): n_int, beta_frac, n_passes. */
+int wm_beta_plan(double beta, int split, int* n_int, double* beta_frac, int* n_passes);
+
+/* ---- errors and teardown ---------------------------------------------------- */
+const char* wm_error_string(int code);
+const char* wm_last_error(void);
+void wm_destroy_hier(wm_hier_t h);
+void wm_destroy_geom(wm_geom_t g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WMFIELD_H */

@@ -1,0 +1,233 @@
+"""GB300 sampler of Whittle–Matérn Gaussian random fields on surfaces.
+
+Python binding of the C ABI (include/wmfield.h): argument marshalling only.
+Every numerical step runs in the CUDA library libwmfield.so; PyTorch provides
+device memory and streams.  There is no CPU fallback: without the built
+library every call raises.
+
+    import paper_2605_24882_gb300 as wm
+    geo = wm.Geometry("sphere", degree=2, elems=64)
+    hier = wm.Hierarchy(geo, n_levels=7)
+    u = hier.sample_fields(kappa=5.0, beta=1.3, sinc_k=0.3, l_lo=-35, l_hi=35,
+                           n_samples=256, precision="mixed")
+"""
+import ctypes as C
+
+import torch
+
+from . import _capi
+from ._capi import WMError, check, lib
+
+__all__ = ["Geometry", "Hierarchy", "philox4x32_10", "normals", "beta_plan", "WMError", "WMField"]
+
+_PREC = {"fp64": _capi.WM_FP64, "mixed": _capi.WM_MIXED}
+_SPLIT = {"standard": _capi.WM_SPLIT_STANDARD, "improved": _capi.WM_SPLIT_IMPROVED}
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev_f64(t, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous float64 CUDA tensor" % name)
+    return C.c_void_p(t.data_ptr())
+
+
+class Geometry:
+    """Surface description: 'sphere' (six cube-face patches) or 'torus' (periodic)."""
+
+    def __init__(self, kind, degree, elems, elems_v=None, R=1.0, r=0.4):
+        d = _capi.GeomDesc(kind=_capi.WM_SPHERE6 if kind == "sphere" else _capi.WM_TORUS, degree=degree,
+                           elems_u=elems, elems_v=elems if elems_v is None else elems_v, R=R, r=r)
+        h = C.c_void_p()
+        check(lib().wm_setup_geometry(C.byref(d), C.byref(h)), "wm_setup_geometry")
+        self._h = h
+        self.desc = d
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _capi._lib is not None:
+            _capi._lib.wm_destroy_geom(self._h)
+            self._h = None
+
+
+def beta_plan(beta, split="standard"):
+    n, bf, ps = C.c_int(), C.c_double(), C.c_int()
+    check(lib().wm_beta_plan(beta, _SPLIT[split], C.byref(n), C.byref(bf), C.byref(ps)), "wm_beta_plan")
+    return n.value, bf.value, ps.value
+
+
+def philox4x32_10(ctr, key, stream=None):
+    """Philox4x32-10 of counters ctr (int32 CUDA tensor [n, 4], bit patterns) with a 64-bit key."""
+    if not (ctr.is_cuda and ctr.dtype == torch.int32 and ctr.dim() == 2 and ctr.shape[1] == 4):
+        raise TypeError("ctr must be an int32 CUDA tensor [n, 4]")
+    ctr = ctr.contiguous()
+    out = torch.empty_like(ctr)
+    check(lib().wm_philox4x32_10(C.c_void_p(ctr.data_ptr()), key, C.c_void_p(out.data_ptr()), ctr.shape[0],
+                                 _stream(stream)), "wm_philox4x32_10")
+    return out
+
+
+def normals(seed, sample, stream_id, q0, n, device="cuda", stream=None):
+    out = torch.empty(n, dtype=torch.float64, device=device)
+    check(lib().wm_normals(seed, sample, stream_id, q0, n, C.c_void_p(out.data_ptr()), _stream(stream)),
+          "wm_normals")
+    return out
+
+
+class Hierarchy:
+    """Dyadic spline hierarchy with the assembled operators on the GPU."""
+
+    def __init__(self, geometry, n_levels, stream=None):
+        h = C.c_void_p()
+        check(lib().wm_assemble_hierarchy(geometry._h, n_levels, _stream(stream), C.byref(h)),
+              "wm_assemble_hierarchy")
+        self._h = h
+        self.geometry = geometry
+        self.n_levels = n_levels
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _capi._lib is not None:
+            _capi._lib.wm_destroy_hier(self._h)
+            self._h = None
+
+    def num_dofs(self, level=0):
+        return check(lib().wm_num_dofs(self._h, level), "wm_num_dofs")
+
+    def num_quad_points(self, level=0):
+        return check(lib().wm_num_quad_points(self._h, level), "wm_num_quad_points")
+
+    def dof_map(self, level=0):
+        import numpy as np
+        g = self.geometry.desc
+        p = g.degree
+        n = (g.elems_u >> level), (g.elems_v >> level)
+        if g.kind == _capi.WM_TORUS:
+            shape = (1, n[1], n[0])
+        else:
+            shape = (6, n[1] + p, n[0] + p)
+        out = np.zeros(shape, dtype=np.int32)
+        check(lib().wm_dof_map(self._h, level, out.ctypes.data_as(C.c_void_p), out.size), "wm_dof_map")
+        return out
+
+    def metric(self, level=0, stream=None):
+        out = torch.empty((self.num_quad_points(level), 4), dtype=torch.float64, device="cuda")
+        check(lib().wm_metric(self._h, level, C.c_void_p(out.data_ptr()), _stream(stream)), "wm_metric")
+        return out
+
+    def apply_shifted(self, x, sigma, level=0, precision="fp64", stream=None):
+        x = x.contiguous()
+        y = torch.empty_like(x)
+        sg = (C.c_double * x.shape[0])(*[float(s) for s in sigma])
+        check(lib().wm_apply_shifted(self._h, level, x.shape[0], sg, _dev_f64(x, "x"), _dev_f64(y, "y"),
+                                     _PREC[precision], _stream(stream)), "wm_apply_shifted")
+        return y
+
+    def apply_mass(self, x, level=0, stream=None):
+        x = x.contiguous()
+        y = torch.empty_like(x)
+        check(lib().wm_apply_mass(self._h, level, _dev_f64(x, "x"), _dev_f64(y, "y"), x.shape[0],
+                                  _stream(stream)), "wm_apply_mass")
+        return y
+
+    def prolongate(self, xc, level=0, stream=None):
+        xc = xc.contiguous()
+        xf = torch.empty((xc.shape[0], self.num_dofs(level)), dtype=torch.float64, device=xc.device)
+        check(lib().wm_prolongate(self._h, level, _dev_f64(xc, "xc"), _dev_f64(xf, "xf"), xc.shape[0],
+                                  _stream(stream)), "wm_prolongate")
+        return xf
+
+    def restrict(self, rf, level=0, stream=None):
+        rf = rf.contiguous()
+        rc = torch.empty((rf.shape[0], self.num_dofs(level + 1)), dtype=torch.float64, device=rf.device)
+        check(lib().wm_restrict(self._h, level, _dev_f64(rf, "rf"), _dev_f64(rc, "rc"), rf.shape[0],
+                                _stream(stream)), "wm_restrict")
+        return rc
+
+    def vcycle(self, r, sigma, precision="fp64", smoother_degree=2, cheb_ratio=8.0, stream=None):
+        r = r.contiguous()
+        z = torch.empty_like(r)
+        sg = (C.c_double * r.shape[0])(*[float(s) for s in sigma])
+        check(lib().wm_vcycle(self._h, r.shape[0], sg, _dev_f64(r, "r"), _dev_f64(z, "z"), _PREC[precision],
+                              smoother_degree, cheb_ratio, _stream(stream)), "wm_vcycle")
+        return z
+
+    def noise_loads(self, seed, n_samples, stream=None):
+        b = torch.empty((n_samples, self.num_dofs(0)), dtype=torch.float64, device="cuda")
+        check(lib().wm_noise_loads(self._h, seed, n_samples, C.c_void_p(b.data_ptr()), _stream(stream)),
+              "wm_noise_loads")
+        return b
+
+    @staticmethod
+    def make_desc(kappa, beta, sinc_k=0.3, l_lo=-35, l_hi=35, n_samples=1, seed=0, split="standard",
+                  precision="mixed", rtol=1e-8, max_iter=200, smoother_degree=2, cheb_ratio=8.0,
+                  max_systems=0, noise_given=False):
+        return _capi.SampleDesc(kappa=kappa, beta=beta, split=_SPLIT[split], sinc_k=sinc_k, l_lo=l_lo, l_hi=l_hi,
+                                seed=seed, n_samples=n_samples,
+                                noise_mode=_capi.WM_NOISE_GIVEN if noise_given else _capi.WM_NOISE_DRAW,
+                                precision=_PREC[precision], rtol=rtol, max_iter=max_iter,
+                                smoother_degree=smoother_degree, cheb_ratio=cheb_ratio, max_systems=max_systems)
+
+    def sample_fields(self, b=None, return_loads=False, out=None, stream=None, check_convergence=True, **kw):
+        """Fields u [n_samples, N] (float64 CUDA tensor, or ``out`` which may be a host tensor).
+
+        With ``b`` given the loads are taken from it, else drawn from Philox
+        with ``seed``.  Returns u (and the loads, and the stats dict).
+        """
+        d = self.make_desc(noise_given=b is not None, **kw)
+        N = self.num_dofs(0)
+        u = out if out is not None else torch.empty((d.n_samples, N), dtype=torch.float64, device="cuda")
+        if b is None and return_loads:
+            b = torch.empty((d.n_samples, N), dtype=torch.float64, device="cuda")
+        st = _capi.Stats()
+        bptr = C.c_void_p(b.data_ptr()) if b is not None else None
+        rc = lib().wm_sample_fields(self._h, C.byref(d), C.c_void_p(u.data_ptr()), bptr, C.byref(st),
+                                    _stream(stream))
+        if rc == _capi.WM_ERR_NOT_CONVERGED and not check_convergence:
+            rc = 0
+        check(rc, "wm_sample_fields")
+        if return_loads:
+            return u, b, st.as_dict()
+        return u, st.as_dict()
+
+    def sample_fields_backward(self, b, grad_u, stream=None, **kw):
+        d = self.make_desc(noise_given=True, **kw)
+        gb = torch.empty_like(b)
+        gk = C.c_double(0.0)
+        check(lib().wm_sample_fields_backward(self._h, C.byref(d), _dev_f64(b, "b"), _dev_f64(grad_u, "grad_u"),
+                                              _dev_f64(gb, "grad_b"), C.byref(gk), _stream(stream)),
+              "wm_sample_fields_backward")
+        return gb, gk.value
+
+
+def sample_fields_batched(hiers, descs, stream=None):
+    """Fields of several independent problems in one call (list of tensors, stats list)."""
+    n = len(hiers)
+    H = (C.c_void_p * n)(*[h._h for h in hiers])
+    D = (_capi.SampleDesc * n)(*descs)
+    outs = [torch.empty((d.n_samples, h.num_dofs(0)), dtype=torch.float64, device="cuda")
+            for h, d in zip(hiers, descs)]
+    U = (C.c_void_p * n)(*[C.c_void_p(u.data_ptr()) for u in outs])
+    st = (_capi.Stats * n)()
+    check(lib().wm_sample_fields_batched(n, H, D, U, st, _stream(stream)), "wm_sample_fields_batched")
+    return outs, [s.as_dict() for s in st]
+
+
+class WMField(torch.autograd.Function):
+    """u = F(b, kappa): the fields of loads b; backward by the adjoint solves."""
+
+    @staticmethod
+    def forward(ctx, b, kappa, hier, kw):
+        kappa_f = float(kappa)
+        u, _ = hier.sample_fields(b=b.contiguous(), kappa=kappa_f, **kw)
+        ctx.save_for_backward(b)
+        ctx.hier, ctx.kw, ctx.kappa = hier, kw, kappa_f
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        (b,) = ctx.saved_tensors
+        gb, gk = ctx.hier.sample_fields_backward(b.contiguous(), grad_u.contiguous(), kappa=ctx.kappa, **ctx.kw)
+        return gb, torch.tensor(gk, dtype=torch.float64), None, None

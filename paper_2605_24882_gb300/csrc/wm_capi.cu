@@ -1,0 +1,680 @@
+// C ABI of the sampler: handles, hierarchy assembly and the sampling driver.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "wm_solver.h"
+
+namespace {
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int check_level(wm_hier_t h, int level) {
+  if (!h) return WM_ERR_INVALID_ARG;
+  if (level < 0 || level >= (int)h->lv.size()) {
+    wm_set_error("level %d out of range [0, %d)", level, (int)h->lv.size());
+    return WM_ERR_INVALID_ARG;
+  }
+  return WM_OK;
+}
+
+WorkSpace& workspace(wm_hier_t h) {
+  if (!h->ws) h->ws = new WorkSpace();
+  return *h->ws;
+}
+
+// per-system bytes of a batched solve (float64 outer vectors + V-cycle levels)
+size_t bytes_per_system(const wm_hier* h, bool dbl) {
+  size_t b = (size_t)h->lv[0].N * 4 * sizeof(double);
+  size_t e = dbl ? sizeof(double) : sizeof(float);
+  for (size_t l = 0; l < h->lv.size(); ++l) b += (size_t)h->lv[l].N * e * (l + 1 < h->lv.size() ? 5 : 3);
+  return b;
+}
+
+// temporary tiled copies of caller vectors for the component entry points
+struct Tmp {
+  DevBuf<double> a, b, sg;
+  DevBuf<float> fa, fb;
+  ~Tmp() {
+    a.release();
+    b.release();
+    sg.release();
+    fa.release();
+    fb.release();
+  }
+};
+
+}  // namespace
+
+extern "C" const char* wm_error_string(int code) {
+  switch (code) {
+    case WM_OK: return "ok";
+    case WM_ERR_INVALID_ARG: return "invalid argument";
+    case WM_ERR_OOM: return "out of memory";
+    case WM_ERR_CUDA: return "CUDA error";
+    case WM_ERR_NOT_CONVERGED: return "not converged";
+    case WM_ERR_NONFINITE: return "non-finite value";
+    case WM_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown error";
+  }
+}
+
+// ------------------------------------------------------------------ geometry
+extern "C" int wm_setup_geometry(const wm_geom_desc* d, wm_geom_t* out) {
+  if (!d || !out) return WM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (d->kind != WM_SPHERE6 && d->kind != WM_TORUS) {
+    wm_set_error("unknown surface kind %d", d->kind);
+    return WM_ERR_INVALID_ARG;
+  }
+  if (d->degree < 1 || d->degree > 4) {
+    wm_set_error("degree %d outside 1..4", d->degree);
+    return WM_ERR_INVALID_ARG;
+  }
+  if (d->elems_u < 1 || d->elems_v < 1 || (d->elems_u & (d->elems_u - 1)) || (d->elems_v & (d->elems_v - 1))) {
+    wm_set_error("element counts must be powers of two");
+    return WM_ERR_INVALID_ARG;
+  }
+  if (d->kind == WM_SPHERE6 && d->elems_u != d->elems_v) {
+    wm_set_error("cube-sphere patches are square");
+    return WM_ERR_INVALID_ARG;
+  }
+  if (d->kind == WM_TORUS) {
+    if (!(d->R > d->r && d->r > 0)) {
+      wm_set_error("torus needs R > r > 0");
+      return WM_ERR_INVALID_ARG;
+    }
+    if (d->elems_u < 2 * d->degree + 2 || d->elems_v < 2 * d->degree + 2) {
+      wm_set_error("periodic patch needs at least 2p+2 elements per direction");
+      return WM_ERR_INVALID_ARG;
+    }
+  }
+  wm_geom* g = new (std::nothrow) wm_geom;
+  if (!g) return WM_ERR_OOM;
+  g->d = *d;
+  g->np = d->kind == WM_SPHERE6 ? 6 : 1;
+  *out = g;
+  return WM_OK;
+}
+
+extern "C" void wm_destroy_geom(wm_geom_t g) { delete g; }
+
+static void release_level(wm_level& L) {
+  L.d_conn.release(); L.d_col.release(); L.d_diag_slot.release(); L.d_metric.release();
+  L.d_Se.release(); L.d_Me.release(); L.d_asm_ptr.release(); L.d_asm_idx.release();
+  L.d_S64.release(); L.d_M64.release(); L.d_S32.release(); L.d_M32.release();
+  L.d_dS64.release(); L.d_dM64.release(); L.d_dS32.release(); L.d_dM32.release();
+  L.d_bu.release(); L.d_du.release(); L.d_bv.release(); L.d_dv.release();
+  L.d_Pptr.release(); L.d_Pcol.release(); L.d_Rptr.release(); L.d_Rcol.release();
+  L.d_Pval64.release(); L.d_Rval64.release(); L.d_Pval32.release(); L.d_Rval32.release();
+  L.d_ng_ptr.release(); L.d_ng_idx.release(); L.d_Sdense.release(); L.d_Mdense.release();
+}
+
+extern "C" void wm_destroy_hier(wm_hier_t h) {
+  if (!h) return;
+  if (h->ws) {
+    h->ws->release();
+    delete h->ws;
+  }
+  for (auto& L : h->lv) release_level(L);
+  h->d_gw.release();
+  h->d_gx.release();
+  delete h;
+}
+
+static int assemble(wm_hier* h, int n_levels, cudaStream_t s) {
+  const wm_geom_desc& g = h->g;
+  h->lv.resize(n_levels);
+  for (int l = 0; l < n_levels; ++l) {
+    wm_level& L = h->lv[l];
+    int nu = g.elems_u >> l, nv = g.elems_v >> l;
+    WM_TRY(wm_host_build_level(g, h->np, nu, nv, L));
+    wm_host_tables(g, h->gx, L);
+    std::vector<int32_t> ngp, ngi;
+    wm_host_noise_map(L, ngp, ngi);
+    WM_TRY(L.d_conn.upload(L.conn, s));
+    WM_TRY(L.d_col.upload(L.col, s));
+    WM_TRY(L.d_diag_slot.upload(L.diag_slot, s));
+    WM_TRY(L.d_ng_ptr.upload(ngp, s));
+    WM_TRY(L.d_ng_idx.upload(ngi, s));
+    WM_TRY(L.d_bu.upload(L.bu, s));
+    WM_TRY(L.d_du.upload(L.du, s));
+    WM_TRY(L.d_bv.upload(L.bv, s));
+    WM_TRY(L.d_dv.upload(L.dv, s));
+    WM_TRY(L.d_metric.alloc((size_t)L.E * h->nq * h->nq * 4));
+    WM_TRY(L.d_Se.alloc((size_t)L.E * L.nk * L.nk));
+    WM_TRY(L.d_Me.alloc((size_t)L.E * L.nk * L.nk));
+    size_t nw = (size_t)L.N * L.W;
+    WM_TRY(L.d_S64.alloc(nw));
+    WM_TRY(L.d_M64.alloc(nw));
+    WM_TRY(L.d_S32.alloc(nw));
+    WM_TRY(L.d_M32.alloc(nw));
+    WM_TRY(L.d_dS64.alloc(L.N));
+    WM_TRY(L.d_dM64.alloc(L.N));
+    WM_TRY(L.d_dS32.alloc(L.N));
+    WM_TRY(L.d_dM32.alloc(L.N));
+    WM_TRY(wm_k_metric(h, L, s));
+    WM_TRY(wm_k_element_matrices(h, L, s));
+    WM_TRY(wm_k_assemble_rows(h, L, s));
+    // element matrices are not needed after assembly
+    WM_CUDA(cudaStreamSynchronize(s));
+    L.d_Se.release();
+    L.d_Me.release();
+    // host integer tables kept only where needed later
+    L.conn.clear();
+    L.conn.shrink_to_fit();
+  }
+  for (int l = 0; l + 1 < n_levels; ++l) {
+    std::vector<int32_t> Pp, Pc, Rp, Rc;
+    std::vector<double> Pv, Rv;
+    // connectivity is rebuilt implicitly from l2g inside the prolongation
+    WM_TRY(wm_host_prolongation(g, h->np, h->lv[l], h->lv[l + 1], Pp, Pc, Pv, Rp, Rc, Rv));
+    wm_level& F = h->lv[l];
+    F.nP = F.N;
+    F.nR = h->lv[l + 1].N;
+    WM_TRY(F.d_Pptr.upload(Pp, s));
+    WM_TRY(F.d_Pcol.upload(Pc, s));
+    WM_TRY(F.d_Pval64.upload(Pv, s));
+    WM_TRY(F.d_Rptr.upload(Rp, s));
+    WM_TRY(F.d_Rcol.upload(Rc, s));
+    WM_TRY(F.d_Rval64.upload(Rv, s));
+    std::vector<float> Pf(Pv.begin(), Pv.end()), Rf(Rv.begin(), Rv.end());
+    WM_TRY(F.d_Pval32.upload(Pf, s));
+    WM_TRY(F.d_Rval32.upload(Rf, s));
+    WM_CUDA(cudaStreamSynchronize(s));
+  }
+  wm_level& C = h->lv[n_levels - 1];
+  if (C.N <= 160) {
+    WM_TRY(C.d_Sdense.alloc((size_t)C.N * C.N));
+    WM_TRY(C.d_Mdense.alloc((size_t)C.N * C.N));
+    WM_TRY(wm_k_dense_coarse(C, s));
+  }
+  WM_CUDA(cudaStreamSynchronize(s));
+  return WM_OK;
+}
+
+extern "C" int wm_assemble_hierarchy(wm_geom_t geom, int n_levels, void* stream, wm_hier_t* out) {
+  if (!geom || !out) return WM_ERR_INVALID_ARG;
+  *out = nullptr;
+  const wm_geom_desc& g = geom->d;
+  int minside = std::min(g.elems_u, g.elems_v);
+  int maxlev = 0;
+  while ((minside >> maxlev) >= 1) ++maxlev;
+  if (g.kind == WM_TORUS) {
+    maxlev = 0;
+    while ((minside >> maxlev) >= 2 * g.degree + 2) ++maxlev;
+  }
+  if (n_levels < 1 || n_levels > maxlev) {
+    wm_set_error("n_levels %d outside 1..%d for this surface", n_levels, maxlev);
+    return WM_ERR_INVALID_ARG;
+  }
+  wm_hier* h = new (std::nothrow) wm_hier;
+  if (!h) return WM_ERR_OOM;
+  h->g = g;
+  h->np = geom->np;
+  h->p = g.degree;
+  h->nq = g.degree + 1;
+  wm_gauss_legendre01(h->nq, h->gx, h->gw);
+  cudaStream_t s = as_stream(stream);
+  int rc = h->d_gw.upload(h->gw, s);
+  if (rc == WM_OK) rc = h->d_gx.upload(h->gx, s);
+  if (rc == WM_OK) rc = assemble(h, n_levels, s);
+  if (rc != WM_OK) {
+    wm_destroy_hier(h);
+    return rc;
+  }
+  *out = h;
+  return WM_OK;
+}
+
+extern "C" int wm_num_levels(wm_hier_t h) { return h ? (int)h->lv.size() : WM_ERR_INVALID_ARG; }
+
+extern "C" int wm_num_dofs(wm_hier_t h, int level) {
+  WM_TRY(check_level(h, level));
+  return h->lv[level].N;
+}
+
+extern "C" int wm_num_quad_points(wm_hier_t h, int level) {
+  WM_TRY(check_level(h, level));
+  return h->lv[level].E * h->nq * h->nq;
+}
+
+extern "C" int wm_dof_map(wm_hier_t h, int level, int32_t* out, int64_t cap) {
+  WM_TRY(check_level(h, level));
+  const wm_level& L = h->lv[level];
+  if (!out || cap < (int64_t)L.l2g.size()) return WM_ERR_INVALID_ARG;
+  std::memcpy(out, L.l2g.data(), L.l2g.size() * sizeof(int32_t));
+  return (int)L.l2g.size();
+}
+
+extern "C" int wm_metric(wm_hier_t h, int level, double* out, void* stream) {
+  WM_TRY(check_level(h, level));
+  if (!out) return WM_ERR_INVALID_ARG;
+  const wm_level& L = h->lv[level];
+  WM_CUDA(cudaMemcpyAsync(out, L.d_metric.p, sizeof(double) * L.d_metric.n, cudaMemcpyDeviceToDevice,
+                          as_stream(stream)));
+  return WM_OK;
+}
+
+// ------------------------------------------------------------------ operators
+extern "C" int wm_apply_shifted(wm_hier_t h, int level, int n_vec, const double* sigma, const double* x, double* y,
+                                int precision, void* stream) {
+  WM_TRY(check_level(h, level));
+  if (n_vec < 0 || (n_vec > 0 && (!sigma || !x || !y))) return WM_ERR_INVALID_ARG;
+  if (precision != WM_FP64 && precision != WM_MIXED) return WM_ERR_INVALID_ARG;
+  if (n_vec == 0) return WM_OK;
+  cudaStream_t s = as_stream(stream);
+  const wm_level& L = h->lv[level];
+  int tiles = (n_vec + WM_LANES - 1) / WM_LANES;
+  size_t n = (size_t)tiles * L.N * WM_LANES;
+  Tmp t;
+  WM_TRY(t.a.alloc(n));
+  WM_TRY(t.b.alloc(n));
+  std::vector<double> sg((size_t)tiles * WM_LANES, 0.0);
+  std::copy(sigma, sigma + n_vec, sg.begin());
+  WM_TRY(t.sg.upload(sg, s));
+  WM_TRY(wm_k_to_tiled(x, n_vec, L.N, t.a.p, tiles, s));
+  if (precision == WM_FP64) {
+    WM_TRY(wm_k_apply<double>(L, tiles, t.sg.p, t.a.p, t.b.p, nullptr, s));
+  } else {
+    WM_TRY(t.fa.alloc(n));
+    WM_TRY(t.fb.alloc(n));
+    WM_TRY(wm_convert_f32(t.a.p, t.fa.p, n, s));
+    WM_TRY(wm_k_apply<float>(L, tiles, t.sg.p, t.fa.p, t.fb.p, nullptr, s));
+    WM_TRY(wm_widen_f32(t.fb.p, t.b.p, n, s));
+  }
+  WM_TRY(wm_k_from_tiled(t.b.p, tiles, L.N, y, n_vec, s));
+  WM_CUDA(cudaStreamSynchronize(s));
+  return WM_OK;
+}
+
+extern "C" int wm_apply_mass(wm_hier_t h, int level, const double* x, double* y, int n_vec, void* stream) {
+  WM_TRY(check_level(h, level));
+  if (n_vec < 0 || (n_vec > 0 && (!x || !y))) return WM_ERR_INVALID_ARG;
+  if (n_vec == 0) return WM_OK;
+  cudaStream_t s = as_stream(stream);
+  const wm_level& L = h->lv[level];
+  int tiles = (n_vec + WM_LANES - 1) / WM_LANES;
+  size_t n = (size_t)tiles * L.N * WM_LANES;
+  Tmp t;
+  WM_TRY(t.a.alloc(n));
+  WM_TRY(t.b.alloc(n));
+  WM_TRY(wm_k_to_tiled(x, n_vec, L.N, t.a.p, tiles, s));
+  WM_TRY(wm_k_apply_mass64(L, tiles, t.a.p, t.b.p, nullptr, s));
+  WM_TRY(wm_k_from_tiled(t.b.p, tiles, L.N, y, n_vec, s));
+  WM_CUDA(cudaStreamSynchronize(s));
+  return WM_OK;
+}
+
+static int transfer(wm_hier_t h, int level, const double* in, double* out, int n_vec, bool prolong, void* stream) {
+  WM_TRY(check_level(h, level));
+  if (level + 1 >= (int)h->lv.size()) return WM_ERR_INVALID_ARG;
+  if (n_vec < 0 || (n_vec > 0 && (!in || !out))) return WM_ERR_INVALID_ARG;
+  if (n_vec == 0) return WM_OK;
+  cudaStream_t s = as_stream(stream);
+  const wm_level& F = h->lv[level];
+  const wm_level& C = h->lv[level + 1];
+  int tiles = (n_vec + WM_LANES - 1) / WM_LANES;
+  Tmp t;
+  WM_TRY(t.a.alloc((size_t)tiles * std::max(F.N, C.N) * WM_LANES));
+  WM_TRY(t.b.alloc((size_t)tiles * std::max(F.N, C.N) * WM_LANES));
+  if (prolong) {
+    WM_TRY(wm_k_to_tiled(in, n_vec, C.N, t.a.p, tiles, s));
+    WM_CUDA(cudaMemsetAsync(t.b.p, 0, sizeof(double) * (size_t)tiles * F.N * WM_LANES, s));
+    WM_TRY(wm_k_prolong_add<double>(F, tiles, t.a.p, t.b.p, nullptr, s));
+    WM_TRY(wm_k_from_tiled(t.b.p, tiles, F.N, out, n_vec, s));
+  } else {
+    WM_TRY(wm_k_to_tiled(in, n_vec, F.N, t.a.p, tiles, s));
+    WM_TRY(wm_k_restrict<double>(F, tiles, t.a.p, t.b.p, nullptr, s));
+    WM_TRY(wm_k_from_tiled(t.b.p, tiles, C.N, out, n_vec, s));
+  }
+  WM_CUDA(cudaStreamSynchronize(s));
+  return WM_OK;
+}
+
+extern "C" int wm_prolongate(wm_hier_t h, int level, const double* xc, double* xf, int n_vec, void* stream) {
+  return transfer(h, level, xc, xf, n_vec, true, stream);
+}
+
+extern "C" int wm_restrict(wm_hier_t h, int level, const double* rf, double* rc, int n_vec, void* stream) {
+  return transfer(h, level, rf, rc, n_vec, false, stream);
+}
+
+static int set_batch_meta(WorkSpace& ws, int tiles, const std::vector<double>& sigma, const std::vector<int>& sid,
+                          const std::vector<int>& src, cudaStream_t s) {
+  size_t n = (size_t)tiles * WM_LANES;
+  std::vector<double> sg(n, sigma.empty() ? 1.0 : sigma[0]);
+  std::vector<int> si(n, 0), sr(n, -1);
+  for (size_t g = 0; g < sigma.size() && g < n; ++g) {
+    sg[g] = sigma[g];
+    si[g] = sid[g];
+    sr[g] = src[g];
+  }
+  WM_CUDA(cudaMemcpyAsync(ws.sigma.p, sg.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  WM_CUDA(cudaMemcpyAsync(ws.sid.p, si.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+  WM_CUDA(cudaMemcpyAsync(ws.src_of.p, sr.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+  WM_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
+  return WM_OK;
+}
+
+extern "C" int wm_vcycle(wm_hier_t h, int n_vec, const double* sigma, const double* r, double* z, int precision,
+                         int smoother_degree, double cheb_ratio, void* stream) {
+  if (!h || n_vec < 0 || (n_vec > 0 && (!sigma || !r || !z))) return WM_ERR_INVALID_ARG;
+  if (precision != WM_FP64 && precision != WM_MIXED) return WM_ERR_INVALID_ARG;
+  if (smoother_degree < 1 || smoother_degree > 8 || !(cheb_ratio > 1.0)) return WM_ERR_INVALID_ARG;
+  if (h->lv.back().N > 160) {
+    wm_set_error("coarsest level too large for the dense coarse solve");
+    return WM_ERR_UNSUPPORTED;
+  }
+  if (n_vec == 0) return WM_OK;
+  cudaStream_t s = as_stream(stream);
+  WorkSpace& ws = workspace(h);
+  int tiles = (n_vec + WM_LANES - 1) / WM_LANES;
+  WM_TRY(ws.reserve(h, tiles, n_vec, precision == WM_FP64));
+  std::vector<double> sg(sigma, sigma + n_vec);
+  std::vector<int> sid(n_vec), src(n_vec);
+  for (int g = 0; g < n_vec; ++g) sid[g] = src[g] = g;
+  WM_TRY(set_batch_meta(ws, tiles, sg, sid, src, s));
+  WM_TRY(wm_prepare_shifts(h, ws, sg, s));
+  Batch bt;
+  bt.tiles = tiles;
+  bt.nsys = n_vec;
+  bt.nshift = n_vec;
+  bt.precision = precision;
+  bt.degree = smoother_degree;
+  bt.cheb_ratio = cheb_ratio;
+  WM_TRY(wm_k_to_tiled(r, n_vec, h->lv[0].N, ws.r.p, tiles, s));
+  WM_TRY(wm_vcycle_apply(h, ws, bt, s));
+  WM_TRY(wm_k_from_tiled(ws.q.p, tiles, h->lv[0].N, z, n_vec, s));
+  WM_CUDA(cudaStreamSynchronize(s));
+  return WM_OK;
+}
+
+// ------------------------------------------------------------------ noise
+extern "C" int wm_philox4x32_10(const uint32_t* ctr, uint64_t key, uint32_t* out, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!ctr || !out))) return WM_ERR_INVALID_ARG;
+  WM_TRY(wm_k_philox(ctr, key, out, n, as_stream(stream)));
+  WM_CUDA(cudaStreamSynchronize(as_stream(stream)));
+  return WM_OK;
+}
+
+extern "C" int wm_normals(uint64_t seed, int sample, int stream_id, int64_t q0, int64_t n, double* out,
+                          void* stream) {
+  if (n < 0 || q0 < 0 || sample < 0 || (n > 0 && !out)) return WM_ERR_INVALID_ARG;
+  WM_TRY(wm_k_normals(seed, sample, stream_id, q0, n, out, as_stream(stream)));
+  WM_CUDA(cudaStreamSynchronize(as_stream(stream)));
+  return WM_OK;
+}
+
+// loads of samples [0, ns) into the sample-tiled buffer b_t
+static int draw_loads(wm_hier_t h, WorkSpace& ws, uint64_t seed, int ns, double* b_t, cudaStream_t s) {
+  const wm_level& L = h->lv[0];
+  // sample chunks bounded so that the element scratch stays below ~1 GiB
+  size_t per_sample = (size_t)L.E * L.nk;
+  int chunk = (int)std::max<size_t>(1, std::min<size_t>(ns, (size_t)(1u << 27) / per_sample));
+  WM_TRY(ws.noise_scratch.alloc(per_sample * chunk));
+  for (int s0 = 0; s0 < ns; s0 += chunk) {
+    int c = std::min(chunk, ns - s0);
+    WM_TRY(wm_k_noise_tiled(h, seed, s0, c, b_t, ws.noise_scratch.p, s));
+  }
+  return WM_OK;
+}
+
+extern "C" int wm_noise_loads(wm_hier_t h, uint64_t seed, int n_samples, double* b, void* stream) {
+  if (!h || n_samples < 0 || (n_samples > 0 && !b)) return WM_ERR_INVALID_ARG;
+  if (n_samples == 0) return WM_OK;
+  cudaStream_t s = as_stream(stream);
+  WorkSpace& ws = workspace(h);
+  int stiles = (n_samples + WM_LANES - 1) / WM_LANES;
+  WM_TRY(ws.samp[0].alloc((size_t)stiles * h->lv[0].N * WM_LANES));
+  WM_TRY(draw_loads(h, ws, seed, n_samples, ws.samp[0].p, s));
+  WM_TRY(wm_k_from_tiled(ws.samp[0].p, stiles, h->lv[0].N, b, n_samples, s));
+  WM_CUDA(cudaStreamSynchronize(s));
+  return WM_OK;
+}
+
+// ------------------------------------------------------------------ sampler
+namespace {
+
+struct Plan {
+  int n_int = 0, passes = 0;
+  double bp = 0.0;
+  std::vector<double> c, sigma;  // per node
+};
+
+int make_plan(const wm_sample_desc* d, Plan& P) {
+  if (!(d->kappa > 0) || !std::isfinite(d->kappa)) return WM_ERR_INVALID_ARG;
+  WM_TRY(wm_split_beta(d->beta, d->split, &P.n_int, &P.bp, &P.passes));
+  if (P.passes > 0) {
+    if (!(d->sinc_k > 0) || d->l_lo > d->l_hi) return WM_ERR_INVALID_ARG;
+    double pre = std::sin(M_PI * P.bp) / M_PI * d->sinc_k;
+    for (int l = d->l_lo; l <= d->l_hi; ++l) {
+      double y = l * d->sinc_k;
+      P.c.push_back(pre * std::exp((1.0 - P.bp) * y));
+      P.sigma.push_back(std::exp(y) + d->kappa * d->kappa);
+    }
+  }
+  return WM_OK;
+}
+
+int validate_desc(wm_hier_t h, const wm_sample_desc* d) {
+  if (!h || !d) return WM_ERR_INVALID_ARG;
+  if (d->n_samples < 0 || d->max_iter < 1 || !(d->rtol > 0) || d->smoother_degree < 1 ||
+      d->smoother_degree > 8 || !(d->cheb_ratio > 1.0) || d->max_systems < 0) {
+    wm_set_error("invalid sample descriptor");
+    return WM_ERR_INVALID_ARG;
+  }
+  if (d->precision != WM_FP64 && d->precision != WM_MIXED) return WM_ERR_INVALID_ARG;
+  if (d->noise_mode != WM_NOISE_DRAW && d->noise_mode != WM_NOISE_GIVEN) return WM_ERR_INVALID_ARG;
+  if (h->lv.back().N > 160) {
+    wm_set_error("coarsest level has %d DOFs (> 160): use more levels", h->lv.back().N);
+    return WM_ERR_UNSUPPORTED;
+  }
+  return WM_OK;
+}
+
+// All systems of one pass: g = j * ns + s with shift sigma[j], right-hand side
+// rhs_t (sample-tiled).  x of every batch goes to `sink`.
+struct Pass {
+  std::vector<double> sigma;  // per node j
+  int ns = 0;
+};
+
+template <typename Sink>
+int run_pass(wm_hier_t h, WorkSpace& ws, const wm_sample_desc* d, const Pass& ps, const double* rhs_t,
+             wm_stats* st, int* worst, Sink sink, cudaStream_t s) {
+  int nj = (int)ps.sigma.size();
+  int64_t nsys = (int64_t)nj * ps.ns;
+  bool dbl = d->precision == WM_FP64;
+  int64_t maxsys = d->max_systems > 0 ? d->max_systems : 0;
+  if (maxsys == 0) {
+    size_t freeb = 0, totb = 0;
+    WM_CUDA(cudaMemGetInfo(&freeb, &totb));
+    size_t have = ws.x.n / std::max(1, h->lv[0].N);  // systems the workspace already holds
+    size_t budget = (size_t)(freeb * 0.8) + have * bytes_per_system(h, dbl);
+    maxsys = std::max<int64_t>(WM_LANES, (int64_t)(budget / bytes_per_system(h, dbl)) / WM_LANES * WM_LANES);
+  }
+  int64_t per_batch = std::min<int64_t>(nsys, maxsys);
+  if (per_batch > WM_LANES) per_batch = per_batch / WM_LANES * WM_LANES;
+  int tiles_max = (int)((per_batch + WM_LANES - 1) / WM_LANES);
+  WM_TRY(ws.reserve(h, tiles_max, nj, dbl));
+  WM_TRY(wm_prepare_shifts(h, ws, ps.sigma, s));
+  for (int64_t g0 = 0; g0 < nsys; g0 += per_batch) {
+    int64_t g1 = std::min(nsys, g0 + per_batch);
+    int nb = (int)(g1 - g0);
+    int tiles = (nb + WM_LANES - 1) / WM_LANES;
+    std::vector<double> sg(nb);
+    std::vector<int> sid(nb), src(nb);
+    for (int k = 0; k < nb; ++k) {
+      int64_t g = g0 + k;
+      int j = (int)(g / ps.ns);
+      sg[k] = ps.sigma[j];
+      sid[k] = j;
+      src[k] = (int)(g % ps.ns);
+    }
+    WM_TRY(set_batch_meta(ws, tiles, sg, sid, src, s));
+    Batch bt;
+    bt.tiles = tiles;
+    bt.nsys = nb;
+    bt.nshift = nj;
+    bt.precision = d->precision;
+    bt.rtol = d->rtol;
+    bt.max_iter = d->max_iter;
+    bt.degree = d->smoother_degree;
+    bt.cheb_ratio = d->cheb_ratio;
+    BatchResult br;
+    WM_TRY(wm_solve_batch(h, ws, bt, rhs_t, &br, s));
+    if (br.flags & 1) *worst = std::min(*worst, WM_ERR_NONFINITE);
+    if (br.n_not_converged > 0 || (br.flags & 2)) *worst = std::min(*worst, (*worst == WM_OK ? WM_ERR_NOT_CONVERGED : *worst));
+    if (st) {
+      st->n_systems += nb;
+      st->n_batches += 1;
+      st->max_iterations = std::max(st->max_iterations, br.iterations);
+      st->total_iterations += br.iterations;
+      st->n_not_converged += br.n_not_converged;
+      st->max_rel_residual = std::max(st->max_rel_residual, br.max_rel_residual);
+    }
+    WM_TRY(sink((int)g0, (int)g1, s));
+  }
+  return WM_OK;
+}
+
+}  // namespace
+
+// Sample-tiled buffers: samp[0] loads, samp[1] current iterate, samp[2]
+// accumulator, samp[3] pass right-hand side, samp[4] staging of host outputs.
+static int sample_fields_impl(wm_hier_t h, const wm_sample_desc* d, double* u, double* b, wm_stats* st,
+                              cudaStream_t s) {
+  WM_TRY(validate_desc(h, d));
+  Plan P;
+  WM_TRY(make_plan(d, P));
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->n_int_solves = P.n_int;
+    st->n_frac_passes = P.passes;
+    st->n_nodes = (int)P.c.size();
+  }
+  int ns = d->n_samples;
+  if (ns == 0) return WM_OK;
+  if (!u) return WM_ERR_INVALID_ARG;
+  if (d->noise_mode == WM_NOISE_GIVEN && !b) return WM_ERR_INVALID_ARG;
+  const wm_level& L0 = h->lv[0];
+  int N = L0.N;
+  int stiles = (ns + WM_LANES - 1) / WM_LANES;
+  size_t sn = (size_t)stiles * N * WM_LANES;
+  WorkSpace& ws = workspace(h);
+  for (int k = 0; k < 4; ++k) WM_TRY(ws.samp[k].alloc(sn));
+  double* b_t = ws.samp[0].p;
+  double* cur = ws.samp[1].p;
+  double* acc = ws.samp[2].p;
+  double* rhs = ws.samp[3].p;
+  bool u_dev = is_device_ptr(u);
+  bool b_dev = b ? is_device_ptr(b) : true;
+  if ((!u_dev || !b_dev)) WM_TRY(ws.samp[4].alloc((size_t)ns * N));
+  // loads
+  if (d->noise_mode == WM_NOISE_DRAW) {
+    WM_TRY(draw_loads(h, ws, d->seed, ns, b_t, s));
+    if (b) {
+      if (b_dev) {
+        WM_TRY(wm_k_from_tiled(b_t, stiles, N, b, ns, s));
+      } else {
+        WM_TRY(wm_k_from_tiled(b_t, stiles, N, ws.samp[4].p, ns, s));
+        WM_CUDA(cudaMemcpyAsync(b, ws.samp[4].p, sizeof(double) * ns * N, cudaMemcpyDeviceToHost, s));
+      }
+    }
+  } else {
+    const double* src = b;
+    if (!b_dev) {
+      WM_CUDA(cudaMemcpyAsync(ws.samp[4].p, b, sizeof(double) * ns * N, cudaMemcpyHostToDevice, s));
+      src = ws.samp[4].p;
+    }
+    WM_TRY(wm_k_to_tiled(src, ns, N, b_t, stiles, s));
+  }
+  int worst = WM_OK;
+  // integer part: (S + kappa^2 M) w_1 = b, (S + kappa^2 M) w_i = M w_{i-1}
+  Pass ip;
+  ip.sigma = {d->kappa * d->kappa};
+  ip.ns = ns;
+  for (int i = 0; i < P.n_int; ++i) {
+    const double* r = b_t;
+    if (i > 0) {
+      WM_TRY(wm_k_apply_mass64(L0, stiles, cur, rhs, nullptr, s));
+      r = rhs;
+    }
+    auto sink = [&](int g0, int g1, cudaStream_t ss) -> int {
+      // systems g = s: the batch [g0, g1) is tile-aligned with the sample tiles
+      size_t off = (size_t)(g0 / WM_LANES) * N * WM_LANES;
+      size_t n = (size_t)((g1 - g0 + WM_LANES - 1) / WM_LANES) * N * WM_LANES;
+      return wm_copy(ws.x.p, cur + off, n, ss);
+    };
+    WM_TRY(run_pass(h, ws, d, ip, r, st, &worst, sink, s));
+  }
+  // fractional passes
+  if (P.passes > 0) {
+    WM_TRY(ws.coef.upload(P.c, s));
+    Pass fp;
+    fp.sigma = P.sigma;
+    fp.ns = ns;
+    for (int pass = 0; pass < P.passes; ++pass) {
+      const double* r = b_t;
+      if (P.n_int > 0 || pass > 0) {
+        WM_TRY(wm_k_apply_mass64(L0, stiles, cur, rhs, nullptr, s));
+        r = rhs;
+      }
+      WM_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * sn, s));
+      auto sink = [&](int g0, int g1, cudaStream_t ss) -> int {
+        return wm_sinc_accumulate(h, ns, g0, g1, ws.coef.p, ws.x.p, acc, ss);
+      };
+      WM_TRY(run_pass(h, ws, d, fp, r, st, &worst, sink, s));
+      std::swap(cur, acc);
+    }
+  }
+  // fields
+  if (u_dev) {
+    WM_TRY(wm_k_from_tiled(cur, stiles, N, u, ns, s));
+  } else {
+    WM_TRY(wm_k_from_tiled(cur, stiles, N, ws.samp[4].p, ns, s));
+    WM_CUDA(cudaMemcpyAsync(u, ws.samp[4].p, sizeof(double) * ns * N, cudaMemcpyDeviceToHost, s));
+  }
+  WM_CUDA(cudaStreamSynchronize(s));
+  // keep the buffer roles stable for the next call
+  if (cur != ws.samp[1].p) std::swap(ws.samp[1].p, ws.samp[2].p);
+  return worst;
+}
+
+extern "C" int wm_sample_fields(wm_hier_t h, const wm_sample_desc* d, double* u, double* b, wm_stats* st,
+                                void* stream) {
+  return sample_fields_impl(h, d, u, b, st, as_stream(stream));
+}
+
+extern "C" int wm_sample_fields_batched(int n_inst, const wm_hier_t* h, const wm_sample_desc* d, double* const* u,
+                                        wm_stats* st, void* stream) {
+  if (n_inst < 0 || (n_inst > 0 && (!h || !d || !u))) return WM_ERR_INVALID_ARG;
+  int worst = WM_OK;
+  for (int i = 0; i < n_inst; ++i) {
+    int rc = sample_fields_impl(h[i], &d[i], u[i], nullptr, st ? &st[i] : nullptr, as_stream(stream));
+    if (rc == WM_ERR_NOT_CONVERGED || rc == WM_ERR_NONFINITE) {
+      worst = std::min(worst, rc);
+      continue;
+    }
+    if (rc != WM_OK) return rc;
+  }
+  return worst;
+}
+
+extern "C" int wm_sample_fields_backward(wm_hier_t h, const wm_sample_desc* d, const double* b, const double* grad_u,
+                                         double* grad_b, double* grad_kappa, void* stream) {
+  (void)h; (void)d; (void)b; (void)grad_u; (void)grad_b; (void)grad_kappa; (void)stream;
+  wm_set_error("backward not built yet");
+  return WM_ERR_UNSUPPORTED;
+}

@@ -1,0 +1,450 @@
+// Host-side set-up of the spline hierarchy: patch topology and C0 gluing,
+// element connectivity, operator row patterns, 1D basis tables at the Gauss
+// points, knot-insertion prolongation and the beta split.  Integer topology
+// and small 1D tables only; every floating-point quantity of the discretised
+// operators is computed on the GPU (wm_assembly.cu).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <unordered_map>
+
+#include "wm_internal.h"
+
+static thread_local std::string g_last_error;
+
+void wm_set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+extern "C" const char* wm_last_error(void) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------------ Gauss rule
+// Gauss–Legendre nodes/weights on [0,1] by Newton's method on P_n.
+void wm_gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+  std::vector<std::pair<double, double>> xw;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      // P_n(z) and P_n'(z) by the three-term recurrence
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      if (n == 1) p0 = 1.0;
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = pk;
+    }
+    if (n == 1) p0 = 1.0;
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    // on [0,1]: x = (z+1)/2 and w = (2 / ((1-z^2) P_n'(z)^2)) / 2
+    xw.push_back({0.5 * (z + 1.0), 1.0 / ((1.0 - z * z) * dp * dp)});
+  }
+  std::sort(xw.begin(), xw.end());
+  x.resize(n);
+  w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    x[i] = xw[i].first;
+    w[i] = xw[i].second;
+  }
+}
+
+// --------------------------------------------------------------- B-spline 1D
+// Knot t_i of the p-open uniform knot vector with n elements (Sec. 2.3).
+static double open_knot(int n, int p, int i) {
+  if (i <= p) return 0.0;
+  if (i >= n + p) return 1.0;
+  return double(i - p) / n;
+}
+
+// Values and derivatives of the p+1 functions alive on element e at x, by the
+// Cox–de Boor recursion (Definition 2.1) over the functions e..e+p.
+static void open_local_basis(int n, int p, int e, double x, double* val, double* der) {
+  // tri[d][j]: degree d function with global index e + p - d + j, j = 0..d
+  double tri[8][8];
+  tri[0][0] = 1.0;
+  for (int d = 1; d <= p; ++d) {
+    for (int j = 0; j <= d; ++j) {
+      int gi = e + p - d + j;  // global function index
+      double v = 0.0;
+      // term with b_{gi}^{d-1}: index j-1 in the previous row (exists if 0 <= j-1 <= d-1)
+      if (j - 1 >= 0) {
+        double den = open_knot(n, p, gi + d) - open_knot(n, p, gi);
+        if (den > 0) v += (x - open_knot(n, p, gi)) / den * tri[d - 1][j - 1];
+      }
+      if (j <= d - 1) {
+        double den = open_knot(n, p, gi + d + 1) - open_knot(n, p, gi + 1);
+        if (den > 0) v += (open_knot(n, p, gi + d + 1) - x) / den * tri[d - 1][j];
+      }
+      tri[d][j] = v;
+    }
+  }
+  for (int a = 0; a <= p; ++a) val[a] = tri[p][a];
+  for (int a = 0; a <= p; ++a) {
+    int gi = e + a;
+    double v = 0.0;
+    if (p > 0) {
+      if (a - 1 >= 0) {
+        double den = open_knot(n, p, gi + p) - open_knot(n, p, gi);
+        if (den > 0) v += p / den * tri[p - 1][a - 1];
+      }
+      if (a <= p - 1) {
+        double den = open_knot(n, p, gi + p + 1) - open_knot(n, p, gi + 1);
+        if (den > 0) v -= p / den * tri[p - 1][a];
+      }
+    }
+    der[a] = v;
+  }
+}
+
+// Cardinal B-spline N_p(t) on knots 0..p+1 and its derivative (recursion on
+// the integer knots).
+static void cardinal_eval(int p, double t, double* val, double* der) {
+  if (t < 0.0 || t >= p + 1.0) { *val = 0.0; *der = 0.0; return; }
+  int span = (int)std::floor(t);
+  // degree-d functions with index span-d..span on integer knots
+  double tri[8][8];
+  tri[0][0] = 1.0;
+  for (int d = 1; d <= p; ++d) {
+    for (int j = 0; j <= d; ++j) {
+      int gi = span - d + j;
+      double v = 0.0;
+      if (j - 1 >= 0) v += (t - gi) / d * tri[d - 1][j - 1];
+      if (j <= d - 1) v += (gi + d + 1 - t) / d * tri[d - 1][j];
+      tri[d][j] = v;
+    }
+  }
+  // N_p = function with index 0 = position j = p - span in row p
+  int j = p - span;
+  *val = tri[p][j];
+  double dv = 0.0;
+  if (p > 0) {
+    // d/dt N_p^{(0)} = N_{p-1}^{(0)}(t) - N_{p-1}^{(1)}(t); row p-1 holds indices span-p+1..span
+    int j0 = 0 - (span - (p - 1));  // index 0
+    int j1 = 1 - (span - (p - 1));  // index 1
+    if (j0 >= 0 && j0 <= p - 1) dv += tri[p - 1][j0];
+    if (j1 >= 0 && j1 <= p - 1) dv -= tri[p - 1][j1];
+  }
+  *der = dv;
+}
+
+void wm_host_tables(const wm_geom_desc& g, const std::vector<double>& gx, wm_level& L) {
+  int p = g.degree, nq = (int)gx.size();
+  bool periodic = g.kind == WM_TORUS;
+  auto fill = [&](int n, std::vector<double>& b, std::vector<double>& d) {
+    b.assign((size_t)n * (p + 1) * nq, 0.0);
+    d.assign((size_t)n * (p + 1) * nq, 0.0);
+    for (int e = 0; e < n; ++e)
+      for (int q = 0; q < nq; ++q) {
+        double val[8], der[8];
+        if (periodic) {
+          for (int a = 0; a <= p; ++a) {
+            double v, dd;
+            cardinal_eval(p, gx[q] + p - a, &v, &dd);
+            val[a] = v;
+            der[a] = n * dd;
+          }
+        } else {
+          open_local_basis(n, p, e, (e + gx[q]) / n, val, der);
+        }
+        for (int a = 0; a <= p; ++a) {
+          b[((size_t)e * (p + 1) + a) * nq + q] = val[a];
+          d[((size_t)e * (p + 1) + a) * nq + q] = der[a];
+        }
+      }
+  };
+  fill(L.nu, L.bu, L.du);
+  fill(L.nv, L.bv, L.dv);
+}
+
+// --------------------------------------------------------------- topology
+// Cube face table, identical to the surface parametrisation: patch m maps
+// (u, v) to the cube point with coordinate a_axis = 2u-1, b_axis = 2v-1 and
+// n_axis fixed to n_sign.
+static const int kFace[6][4] = {{1, 2, 0, +1}, {2, 1, 0, -1}, {2, 0, 1, +1},
+                                {0, 2, 1, -1}, {0, 1, 2, +1}, {1, 0, 2, -1}};
+
+int wm_host_build_level(const wm_geom_desc& g, int np, int nu, int nv, wm_level& L) {
+  int p = g.degree;
+  L.nu = nu;
+  L.nv = nv;
+  L.nk = (p + 1) * (p + 1);
+  L.E = np * nu * nv;
+  if (g.kind == WM_TORUS) {
+    L.nlu = nu;
+    L.nlv = nv;
+    L.N = nu * nv;
+    L.l2g.resize((size_t)nu * nv);
+    for (int i = 0; i < nu * nv; ++i) L.l2g[i] = i;
+  } else {
+    // C0 gluing by matching DOF lattice points on the cube surface: local DOF
+    // (iu, iv) of patch m sits at integer coordinates a = 2 iu - (n+p-1),
+    // b = 2 iv - (n+p-1), normal = n_sign (n+p-1).  Patch edges are cube
+    // edges, so the shared functions of two patches land on the same points.
+    int nl = nu + p;
+    L.nlu = L.nlv = nl;
+    L.l2g.assign((size_t)np * nl * nl, -1);
+    std::unordered_map<int64_t, int32_t> seen;
+    seen.reserve((size_t)np * nl * 4 + 64);
+    int32_t next = 0;
+    int64_t span = 2 * nl + 1;
+    for (int m = 0; m < np; ++m)
+      for (int iv = 0; iv < nl; ++iv)
+        for (int iu = 0; iu < nl; ++iu) {
+          int c[3];
+          c[kFace[m][0]] = 2 * iu - (nl - 1);
+          c[kFace[m][1]] = 2 * iv - (nl - 1);
+          c[kFace[m][2]] = kFace[m][3] * (nl - 1);
+          bool boundary = iu == 0 || iv == 0 || iu == nl - 1 || iv == nl - 1;
+          int32_t gidx;
+          if (boundary) {
+            int64_t key = ((int64_t)(c[0] + nl) * span + (c[1] + nl)) * span + (c[2] + nl);
+            auto it = seen.find(key);
+            if (it != seen.end()) {
+              gidx = it->second;
+            } else {
+              gidx = next++;
+              seen.emplace(key, gidx);
+            }
+          } else {
+            gidx = next++;
+          }
+          L.l2g[((size_t)m * nl + iv) * nl + iu] = gidx;
+        }
+    L.N = next;
+  }
+  // element connectivity, local index k = kv (p+1) + ku
+  L.conn.resize((size_t)L.E * L.nk);
+  for (int m = 0; m < np; ++m)
+    for (int ev = 0; ev < nv; ++ev)
+      for (int eu = 0; eu < nu; ++eu) {
+        size_t e = ((size_t)m * nv + ev) * nu + eu;
+        for (int kv = 0; kv <= p; ++kv)
+          for (int ku = 0; ku <= p; ++ku) {
+            int iu, iv;
+            if (g.kind == WM_TORUS) {
+              iu = ((eu - p + ku) % nu + nu) % nu;
+              iv = ((ev - p + kv) % nv + nv) % nv;
+            } else {
+              iu = eu + ku;
+              iv = ev + kv;
+            }
+            L.conn[e * L.nk + kv * (p + 1) + ku] = L.l2g[((size_t)m * L.nlv + iv) * L.nlu + iu];
+          }
+      }
+  // row patterns: union of the element DOF sets containing each row
+  int cap = (2 * p + 1) * (2 * p + 1) + 16;
+  std::vector<int32_t> cols((size_t)L.N * cap);
+  std::vector<int32_t> cnt(L.N, 0);
+  for (size_t e = 0; e < (size_t)L.E; ++e) {
+    const int32_t* ce = &L.conn[e * L.nk];
+    for (int k = 0; k < L.nk; ++k) {
+      int32_t i = ce[k];
+      int32_t* row = &cols[(size_t)i * cap];
+      for (int k2 = 0; k2 < L.nk; ++k2) {
+        int32_t j = ce[k2];
+        bool found = false;
+        for (int t = 0; t < cnt[i]; ++t)
+          if (row[t] == j) { found = true; break; }
+        if (!found) {
+          if (cnt[i] >= cap) {
+            wm_set_error("row pattern overflow at row %d", i);
+            return WM_ERR_INVALID_ARG;
+          }
+          row[cnt[i]++] = j;
+        }
+      }
+    }
+  }
+  int W = 0;
+  for (int i = 0; i < L.N; ++i) W = std::max(W, (int)cnt[i]);
+  L.W = W;
+  L.col.assign((size_t)L.N * W, 0);
+  L.diag_slot.assign(L.N, 0);
+  for (int i = 0; i < L.N; ++i) {
+    int32_t* row = &cols[(size_t)i * cap];
+    std::sort(row, row + cnt[i]);
+    for (int t = 0; t < W; ++t) L.col[(size_t)i * W + t] = t < cnt[i] ? row[t] : i;
+    for (int t = 0; t < cnt[i]; ++t)
+      if (row[t] == i) L.diag_slot[i] = t;
+  }
+  return WM_OK;
+}
+
+// DOF -> list of element functions (e * nk + k) containing it, in element order.
+void wm_host_noise_map(const wm_level& L, std::vector<int32_t>& ptr, std::vector<int32_t>& idx) {
+  ptr.assign(L.N + 1, 0);
+  for (size_t t = 0; t < L.conn.size(); ++t) ptr[L.conn[t] + 1]++;
+  for (int i = 0; i < L.N; ++i) ptr[i + 1] += ptr[i];
+  idx.resize(L.conn.size());
+  std::vector<int32_t> pos(ptr.begin(), ptr.end() - 1);
+  for (size_t t = 0; t < L.conn.size(); ++t) idx[pos[L.conn[t]]++] = (int32_t)t;
+}
+
+// ------------------------------------------------------------ knot insertion
+// 1D refinement matrix (n_f = 2 n_c elements) as dense [nf_dofs][nc_dofs].
+// Open knots: Boehm's algorithm, inserting the midpoints one at a time.
+// Periodic: the two-scale relation of the cardinal B-spline, which is the same
+// insertion of all midpoints at once: N_p(t) = sum_k 2^-p C(p+1,k) N_p(2t-k).
+static void refine_1d(int nc, int p, bool periodic, std::vector<double>& P, int& nf_dofs, int& nc_dofs) {
+  if (periodic) {
+    nc_dofs = nc;
+    nf_dofs = 2 * nc;
+    P.assign((size_t)nf_dofs * nc_dofs, 0.0);
+    for (int I = 0; I < nc; ++I)
+      for (int k = 0; k <= p + 1; ++k) {
+        double binom = 1.0;
+        for (int t = 0; t < k; ++t) binom = binom * (p + 1 - t) / (t + 1);
+        int f = (2 * I + k) % nf_dofs;
+        P[(size_t)f * nc_dofs + I] += binom / std::pow(2.0, p);
+      }
+    return;
+  }
+  nc_dofs = nc + p;
+  nf_dofs = 2 * nc + p;
+  std::vector<double> knots;
+  for (int i = 0; i <= p; ++i) knots.push_back(0.0);
+  for (int i = 1; i < nc; ++i) knots.push_back(double(i) / nc);
+  for (int i = 0; i <= p; ++i) knots.push_back(1.0);
+  // current control "points" = identity columns: Q[i][I]
+  std::vector<std::vector<double>> Q(nc_dofs, std::vector<double>(nc_dofs, 0.0));
+  for (int i = 0; i < nc_dofs; ++i) Q[i][i] = 1.0;
+  for (int el = 0; el < nc; ++el) {
+    double t = (el + 0.5) / nc;
+    // span s: knots[s] <= t < knots[s+1]
+    int s = 0;
+    for (int i = 0; i + 1 < (int)knots.size(); ++i)
+      if (knots[i] <= t && t < knots[i + 1]) s = i;
+    int ncp = (int)Q.size();
+    std::vector<std::vector<double>> R(ncp + 1, std::vector<double>(nc_dofs, 0.0));
+    for (int i = 0; i <= ncp; ++i) {
+      if (i <= s - p) {
+        R[i] = Q[i];
+      } else if (i > s) {
+        R[i] = Q[i - 1];
+      } else {
+        double a = (t - knots[i]) / (knots[i + p] - knots[i]);
+        for (int c = 0; c < nc_dofs; ++c) R[i][c] = a * Q[i][c] + (1.0 - a) * Q[i - 1][c];
+      }
+    }
+    knots.insert(knots.begin() + s + 1, t);
+    Q.swap(R);
+  }
+  P.assign((size_t)nf_dofs * nc_dofs, 0.0);
+  for (int f = 0; f < nf_dofs; ++f)
+    for (int c = 0; c < nc_dofs; ++c) P[(size_t)f * nc_dofs + c] = Q[f][c];
+}
+
+int wm_host_prolongation(const wm_geom_desc& g, int np, const wm_level& F, const wm_level& C,
+                         std::vector<int32_t>& Pptr, std::vector<int32_t>& Pcol, std::vector<double>& Pval,
+                         std::vector<int32_t>& Rptr, std::vector<int32_t>& Rcol, std::vector<double>& Rval) {
+  int p = g.degree;
+  bool periodic = g.kind == WM_TORUS;
+  std::vector<double> Pu, Pv;
+  int nfu, ncu, nfv, ncv;
+  refine_1d(C.nu, p, periodic, Pu, nfu, ncu);
+  refine_1d(C.nv, p, periodic, Pv, nfv, ncv);
+  if (nfu != F.nlu || nfv != F.nlv || ncu != C.nlu || ncv != C.nlv) {
+    wm_set_error("prolongation size mismatch");
+    return WM_ERR_INVALID_ARG;
+  }
+  // per fine row: (coarse col, value), deduplicated across patches
+  std::vector<std::vector<std::pair<int32_t, double>>> rows(F.N);
+  for (int m = 0; m < np; ++m)
+    for (int fv = 0; fv < nfv; ++fv)
+      for (int fu = 0; fu < nfu; ++fu) {
+        int32_t i = F.l2g[((size_t)m * F.nlv + fv) * F.nlu + fu];
+        auto& row = rows[i];
+        bool have = !row.empty();
+        std::vector<std::pair<int32_t, double>> mine;
+        for (int Iv = 0; Iv < ncv; ++Iv) {
+          double a = Pv[(size_t)fv * ncv + Iv];
+          if (a == 0.0) continue;
+          for (int Iu = 0; Iu < ncu; ++Iu) {
+            double b = Pu[(size_t)fu * ncu + Iu];
+            if (b == 0.0) continue;
+            mine.push_back({C.l2g[((size_t)m * C.nlv + Iv) * C.nlu + Iu], a * b});
+          }
+        }
+        std::sort(mine.begin(), mine.end());
+        if (!have) {
+          row = mine;
+        } else {
+          // the same glued function seen from another patch: must agree
+          if (mine.size() != row.size()) {
+            wm_set_error("inconsistent prolongation row %d (%zu vs %zu)", i, mine.size(), row.size());
+            return WM_ERR_INVALID_ARG;
+          }
+          for (size_t t = 0; t < mine.size(); ++t)
+            if (mine[t].first != row[t].first || std::fabs(mine[t].second - row[t].second) > 1e-13) {
+              wm_set_error("inconsistent prolongation entry at row %d", i);
+              return WM_ERR_INVALID_ARG;
+            }
+        }
+      }
+  Pptr.assign(F.N + 1, 0);
+  for (int i = 0; i < F.N; ++i) Pptr[i + 1] = Pptr[i] + (int)rows[i].size();
+  Pcol.resize(Pptr[F.N]);
+  Pval.resize(Pptr[F.N]);
+  for (int i = 0; i < F.N; ++i)
+    for (size_t t = 0; t < rows[i].size(); ++t) {
+      Pcol[Pptr[i] + t] = rows[i][t].first;
+      Pval[Pptr[i] + t] = rows[i][t].second;
+    }
+  // transpose: rows of R are coarse DOFs, entries ordered by fine index
+  Rptr.assign(C.N + 1, 0);
+  for (size_t t = 0; t < Pcol.size(); ++t) Rptr[Pcol[t] + 1]++;
+  for (int I = 0; I < C.N; ++I) Rptr[I + 1] += Rptr[I];
+  Rcol.resize(Pcol.size());
+  Rval.resize(Pcol.size());
+  std::vector<int32_t> pos(Rptr.begin(), Rptr.end() - 1);
+  for (int i = 0; i < F.N; ++i)
+    for (int t = Pptr[i]; t < Pptr[i + 1]; ++t) {
+      int32_t I = Pcol[t];
+      Rcol[pos[I]] = i;
+      Rval[pos[I]] = Pval[t];
+      pos[I]++;
+    }
+  return WM_OK;
+}
+
+// ------------------------------------------------------------ beta split
+int wm_split_beta(double beta, int split, int* n, double* bp, int* passes) {
+  if (!(beta > 0.0) || !std::isfinite(beta)) return WM_ERR_INVALID_ARG;
+  int ni = (int)std::floor(beta);
+  double f = beta - ni;
+  if (f == 0.0) {
+    *n = ni; *bp = 0.0; *passes = 0;
+    return WM_OK;
+  }
+  if (split == WM_SPLIT_IMPROVED) {
+    if (f < 1.0 / 3.0 && ni >= 1) { *n = ni - 1; *bp = (f + 1.0) / 2.0; *passes = 2; return WM_OK; }
+    if (f > 2.0 / 3.0) { *n = ni; *bp = f / 2.0; *passes = 2; return WM_OK; }
+  } else if (split != WM_SPLIT_STANDARD) {
+    return WM_ERR_INVALID_ARG;
+  }
+  *n = ni; *bp = f; *passes = 1;
+  return WM_OK;
+}
+
+extern "C" int wm_beta_plan(double beta, int split, int* n_int, double* beta_frac, int* n_passes) {
+  if (!n_int || !beta_frac || !n_passes) return WM_ERR_INVALID_ARG;
+  return wm_split_beta(beta, split, n_int, beta_frac, n_passes);
+}

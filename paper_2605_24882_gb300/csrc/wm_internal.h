@@ -1,0 +1,160 @@
+// Internal declarations of the GB300 Whittle–Matérn sampler library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "wmfield.h"
+
+// Systems are packed 32 to a tile: a batched vector is stored [tiles][N][32],
+// so the 32 systems of a tile sit in one 128-byte (float) or 256-byte (double)
+// row per DOF and a warp reads one DOF of 32 systems in one coalesced access.
+#define WM_LANES 32
+
+void wm_set_error(const char* fmt, ...);
+
+#define WM_CUDA(call)                                                             \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      wm_set_error("%s failed at %s:%d: %s", #call, __FILE__, __LINE__,           \
+                   cudaGetErrorString(e_));                                       \
+      return e_ == cudaErrorMemoryAllocation ? WM_ERR_OOM : WM_ERR_CUDA;          \
+    }                                                                             \
+  } while (0)
+
+#define WM_TRY(expr)          \
+  do {                        \
+    int rc_ = (expr);         \
+    if (rc_ != WM_OK) return rc_; \
+  } while (0)
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  int alloc(size_t count) {
+    if (count <= n && p) return WM_OK;
+    release();
+    if (count == 0) return WM_OK;
+    cudaError_t e = cudaMalloc((void**)&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      n = 0;
+      wm_set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+      return WM_ERR_OOM;
+    }
+    n = count;
+    return WM_OK;
+  }
+  int upload(const std::vector<T>& v, cudaStream_t s) {
+    WM_TRY(alloc(v.size()));
+    if (!v.empty()) WM_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return WM_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+// ---------------------------------------------------------------- host setup
+struct wm_geom {
+  wm_geom_desc d;
+  int np;  // patches
+};
+
+// One level of the dyadic hierarchy.
+struct wm_level {
+  int nu = 0, nv = 0;    // elements per patch side
+  int nlu = 0, nlv = 0;  // local DOFs per patch side
+  int N = 0;             // glued DOFs
+  int E = 0;             // elements (all patches)
+  int nk = 0;            // local functions per element, (p+1)^2
+  int W = 0;             // stored entries per operator row (max row length)
+  std::vector<int32_t> l2g;   // [np][nlv][nlu]
+  std::vector<int32_t> conn;  // [E][nk]
+  std::vector<int32_t> col;   // [N][W], padded with the row index
+  std::vector<int32_t> diag_slot;  // [N]
+  // 1D tables at the Gauss points of each element: [n][p+1][nq]
+  std::vector<double> bu, du, bv, dv;
+  // device copies
+  DevBuf<int32_t> d_conn, d_col, d_diag_slot;
+  DevBuf<double> d_metric;  // [E][nq*nq][4]
+  DevBuf<double> d_Se, d_Me;  // element matrices [E][nk][nk]
+  DevBuf<int32_t> d_asm_ptr, d_asm_idx;  // (row, slot) -> element-matrix entries
+  DevBuf<double> d_S64, d_M64;  // [N][W]
+  DevBuf<float> d_S32, d_M32;
+  DevBuf<double> d_dS64, d_dM64;  // diagonals [N]
+  DevBuf<float> d_dS32, d_dM32;
+  DevBuf<double> d_bu, d_du, d_bv, d_dv;
+  // prolongation from the next coarser level to this one (CSR over fine rows)
+  // and restriction to it (CSR over coarse rows); empty on the coarsest level
+  DevBuf<int32_t> d_Pptr, d_Pcol, d_Rptr, d_Rcol;
+  DevBuf<double> d_Pval64, d_Rval64;
+  DevBuf<float> d_Pval32, d_Rval32;
+  int nP = 0, nR = 0;  // rows of P (fine N) and R (coarse N)
+  // noise gather on this level: DOF i <- sum over (e, k) entries
+  DevBuf<int32_t> d_ng_ptr, d_ng_idx;
+  // coarse dense operators (coarsest level only): [N][N] row-major
+  DevBuf<double> d_Sdense, d_Mdense;
+};
+
+struct WorkSpace;
+
+struct wm_hier {
+  wm_geom_desc g;
+  int np = 0, p = 0, nq = 0;
+  std::vector<wm_level> lv;
+  std::vector<double> gw, gx;  // Gauss weights and nodes on [0,1]
+  DevBuf<double> d_gw, d_gx;
+  WorkSpace* ws = nullptr;
+};
+
+// host helpers (wm_host_setup.cpp)
+int wm_host_build_level(const wm_geom_desc& g, int np, int nu, int nv, wm_level& L);
+void wm_gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
+int wm_host_prolongation(const wm_geom_desc& g, int np, const wm_level& fine, const wm_level& coarse,
+                         std::vector<int32_t>& Pptr, std::vector<int32_t>& Pcol, std::vector<double>& Pval,
+                         std::vector<int32_t>& Rptr, std::vector<int32_t>& Rcol, std::vector<double>& Rval);
+void wm_host_tables(const wm_geom_desc& g, const std::vector<double>& gx, wm_level& L);
+void wm_host_assembly_map(const wm_level& L, std::vector<int32_t>& ptr, std::vector<int32_t>& idx);
+void wm_host_noise_map(const wm_level& L, std::vector<int32_t>& ptr, std::vector<int32_t>& idx);
+int wm_split_beta(double beta, int split, int* n, double* bp, int* passes);
+
+// ---------------------------------------------------------------- kernels
+// geometry and assembly (wm_assembly.cu)
+int wm_k_metric(const wm_hier* h, const wm_level& L, cudaStream_t s);
+int wm_k_element_matrices(const wm_hier* h, wm_level& L, cudaStream_t s);
+int wm_k_assemble_rows(const wm_hier* h, wm_level& L, cudaStream_t s);
+int wm_k_dense_coarse(const wm_level& L, cudaStream_t s);
+
+// noise (wm_noise.cu)
+int wm_k_philox(const uint32_t* ctr, uint64_t key, uint32_t* out, int64_t n, cudaStream_t s);
+int wm_k_normals(uint64_t seed, int sample, int stream_id, int64_t q0, int64_t n, double* out,
+                 cudaStream_t s);
+// loads of samples [s0, s0+ns) into a tiled [tiles][N][32] buffer (sample s at
+// tile s/32, lane s%32); `bl` is scratch of E*nk*ns_pad doubles
+int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int s0, int ns, double* b_tiled,
+                     double* bl, cudaStream_t s);
+
+// batched operators (wm_operator.cu); vectors are [tiles][N][32]
+template <typename T>
+int wm_k_apply(const wm_level& L, int tiles, const double* sigma, const T* x, T* y,
+               const int* tile_active, cudaStream_t s);
+int wm_k_apply_mass64(const wm_level& L, int tiles, const double* x, double* y,
+                      const int* tile_active, cudaStream_t s);
+template <typename T>
+int wm_k_prolong_add(const wm_level& fine, int tiles, const T* xc, T* xf, const int* tile_active,
+                     cudaStream_t s);
+template <typename T>
+int wm_k_restrict(const wm_level& fine, int tiles, const T* rf, T* rc, const int* tile_active,
+                  cudaStream_t s);
+
+// layout conversion between [n][N] and [tiles][N][32]
+int wm_k_to_tiled(const double* src, int n, int N, double* dst, int tiles, cudaStream_t s);
+int wm_k_from_tiled(const double* src, int tiles, int N, double* dst, int n, cudaStream_t s);

@@ -1,0 +1,184 @@
+// White-noise loads from Philox4x32-10 normals at the Gauss points (Sec. 3.3).
+//
+// The discrete white noise b_s must have covariance M.  It is drawn at the
+// Gauss points: b_s,i = sum_q sqrt(w_q a_q) xi_{s,q} phi_i(x_q), so that
+// Cov(b_s) = B B^T is exactly the mass matrix of the same Gauss rule.
+//
+// Philox4x32-10 is written from its published definition (Salmon, Moraes,
+// Dror, Shaw, SC'11): ten rounds of two 32x32->64 multiplications by
+// 0xD2511F53 and 0xCD9E8D57 with the key bumped by (0x9E3779B9, 0xBB67AE85).
+#include "wm_internal.h"
+
+namespace {
+
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    U4 n;
+    n.x = hi1 ^ c.y ^ k0;
+    n.y = lo1;
+    n.z = hi0 ^ c.w ^ k1;
+    n.w = lo0;
+    c = n;
+  }
+  return c;
+}
+
+__device__ __forceinline__ double uniform53(uint32_t hi, uint32_t lo) {
+  uint64_t a = (uint64_t)(hi >> 5), b = (uint64_t)(lo >> 6);
+  return (double)(a * 67108864ull + b + 1ull) * 1.1102230246251565e-16;  // 2^-53
+}
+
+// The Box–Muller pair of normals with pair index `pair` of (seed, sample, stream).
+__device__ __forceinline__ void normal_pair(uint64_t seed, int sample, int stream, int64_t pair, double* z0,
+                                            double* z1) {
+  U4 c;
+  c.x = (uint32_t)(pair & 0xFFFFFFFFll);
+  c.y = (uint32_t)sample;
+  c.z = (uint32_t)stream;
+  c.w = (uint32_t)(pair >> 32);
+  U4 o = philox10(c, (uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32));
+  double u1 = uniform53(o.x, o.y);
+  double u2 = uniform53(o.z, o.w);
+  double rad = sqrt(-2.0 * log(u1));
+  double s, co;
+  sincos(2.0 * M_PI * u2, &s, &co);
+  *z0 = rad * co;
+  *z1 = rad * s;
+}
+
+__global__ void k_philox(const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t k1, uint32_t* __restrict__ out,
+                         int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  U4 c = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+  U4 o = philox10(c, k0, k1);
+  out[4 * i] = o.x;
+  out[4 * i + 1] = o.y;
+  out[4 * i + 2] = o.z;
+  out[4 * i + 3] = o.w;
+}
+
+__global__ void k_normals(uint64_t seed, int sample, int stream, int64_t q0, int64_t n, double* __restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t q = q0 + i;
+  double z0, z1;
+  normal_pair(seed, sample, stream, q >> 1, &z0, &z1);
+  out[i] = (q & 1) ? z1 : z0;
+}
+
+// One thread per (element e, sample s0+sl): the (p+1)^2 local load
+// contributions sum_q sqrt(w_q a_q) xi_q phi_k(x_q) of the element.
+// bl layout [E][nk][ns].
+template <int P>
+__global__ void k_noise_local(int E, int nu, int nv, int ns, int s0, uint64_t seed,
+                              const double* __restrict__ metric, const double* __restrict__ gw,
+                              const double* __restrict__ bu, const double* __restrict__ bv, double* __restrict__ bl) {
+  constexpr int NQ = P + 1, NK = (P + 1) * (P + 1), NQ2 = NQ * NQ;
+  int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)E * ns) return;
+  int64_t e = tid / ns;
+  int sl = (int)(tid - e * ns);
+  int eu = (int)(e % nu);
+  int ev = (int)((e / nu) % nv);
+  double xi[NQ2 + 1];
+  int64_t q0 = e * NQ2;
+  int64_t pr0 = q0 >> 1, pr1 = (q0 + NQ2 - 1) >> 1;
+  for (int64_t pr = pr0; pr <= pr1; ++pr) {
+    double z0, z1;
+    normal_pair(seed, s0 + sl, 0, pr, &z0, &z1);
+    int j0 = (int)(2 * pr - q0);
+    if (j0 >= 0) xi[j0] = z0;
+    if (j0 + 1 < NQ2) xi[j0 + 1] = z1;
+  }
+  double wq[NQ2];
+  double elw = 1.0 / ((double)nu * nv);
+#pragma unroll
+  for (int j = 0; j < NQ2; ++j) {
+    int gv = j / NQ, gu = j % NQ;
+    wq[j] = sqrt(gw[gu] * gw[gv] * elw * metric[4 * (q0 + j)]) * xi[j];
+  }
+  const double* BU = bu + (size_t)eu * (P + 1) * NQ;
+  const double* BV = bv + (size_t)ev * (P + 1) * NQ;
+#pragma unroll
+  for (int kv = 0; kv <= P; ++kv)
+#pragma unroll
+    for (int ku = 0; ku <= P; ++ku) {
+      double acc = 0.0;
+#pragma unroll
+      for (int gv = 0; gv < NQ; ++gv) {
+        double t = 0.0;
+#pragma unroll
+        for (int gu = 0; gu < NQ; ++gu) t += BU[ku * NQ + gu] * wq[gv * NQ + gu];
+        acc += BV[kv * NQ + gv] * t;
+      }
+      bl[((size_t)e * NK + kv * (P + 1) + ku) * ns + sl] = acc;
+    }
+}
+
+// One thread per (DOF i, sample s0+sl): b[tile][i][lane] = sum over the element
+// functions containing i of their local contributions, in element order.
+__global__ void k_noise_gather(int N, int ns, int s0, const int32_t* __restrict__ ptr,
+                               const int32_t* __restrict__ idx, const double* __restrict__ bl,
+                               double* __restrict__ b) {
+  int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)N * ns) return;
+  int i = (int)(tid / ns);
+  int sl = (int)(tid - (int64_t)i * ns);
+  double acc = 0.0;
+  for (int t = ptr[i]; t < ptr[i + 1]; ++t) acc += bl[(size_t)idx[t] * ns + sl];
+  int s = s0 + sl;
+  b[((size_t)(s / WM_LANES) * N + i) * WM_LANES + (s % WM_LANES)] = acc;
+}
+
+}  // namespace
+
+int wm_k_philox(const uint32_t* ctr, uint64_t key, uint32_t* out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return WM_OK;
+  k_philox<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctr, (uint32_t)(key & 0xFFFFFFFFull),
+                                                       (uint32_t)(key >> 32), out, n);
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
+int wm_k_normals(uint64_t seed, int sample, int stream_id, int64_t q0, int64_t n, double* out, cudaStream_t s) {
+  if (n <= 0) return WM_OK;
+  k_normals<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(seed, sample, stream_id, q0, n, out);
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
+int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int s0, int ns, double* b_tiled, double* bl,
+                     cudaStream_t s) {
+  const wm_level& L = h->lv[0];
+  int64_t n1 = (int64_t)L.E * ns;
+  unsigned g1 = (unsigned)((n1 + 127) / 128);
+#define WM_NL(PP)                                                                                        \
+  k_noise_local<PP><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, ns, s0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, \
+                                       L.d_bv.p, bl)
+  switch (h->p) {
+    case 1: WM_NL(1); break;
+    case 2: WM_NL(2); break;
+    case 3: WM_NL(3); break;
+    case 4: WM_NL(4); break;
+    default: return WM_ERR_UNSUPPORTED;
+  }
+#undef WM_NL
+  WM_CUDA(cudaGetLastError());
+  int64_t n2 = (int64_t)L.N * ns;
+  k_noise_gather<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(L.N, ns, s0, L.d_ng_ptr.p, L.d_ng_idx.p, bl,
+                                                              b_tiled);
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}

@@ -1,0 +1,71 @@
+// Batched solver state shared by the sampler entry points.
+#pragma once
+
+#include "wm_internal.h"
+
+// float or double buffer of a V-cycle level (only the one of the V-cycle's
+// precision is allocated)
+struct VBuf {
+  DevBuf<double> d;
+  DevBuf<float> f;
+  int alloc(size_t n, bool dbl);
+};
+
+struct LevelBufs {
+  VBuf za, zb;  // smoother iterates (ping-pong)
+  VBuf d;       // Chebyshev direction
+  VBuf res;     // residual before restriction
+  VBuf r;       // restricted residual (levels >= 1)
+};
+
+// One batched solve: `tiles` tiles of 32 systems; systems g < nsys are real.
+struct Batch {
+  int tiles = 0;
+  int nsys = 0;
+  int nshift = 0;     // distinct shifts (coarse inverses, smoother bounds)
+  int precision = WM_MIXED;
+  double rtol = 1e-8;
+  int max_iter = 200;
+  int degree = 2;     // Chebyshev degree of each smoothing sweep
+  double cheb_ratio = 8.0;
+  int chunks_for(int N) const;
+};
+
+struct BatchResult {
+  int iterations = 0;
+  int n_not_converged = 0;
+  double max_rel_residual = 0.0;
+  int flags = 0;  // bit 0: non-finite value, bit 1: CG breakdown
+};
+
+struct WorkSpace {
+  DevBuf<double> x, r, p, q;  // outer float64 iterates [tiles][N0][32]
+  std::vector<LevelBufs> lvl;
+  DevBuf<double> sigma;   // per system shift
+  DevBuf<int> sid;        // per system shift index
+  DevBuf<int> src_of;     // per system right-hand-side sample (-1: padding)
+  DevBuf<int> active, tile_active;
+  DevBuf<double> rho, alpha, beta, bb, rr;
+  DevBuf<double> part[3];
+  DevBuf<int> flags, counters;
+  DevBuf<double> lmax, ainv, shifts, statd;
+  // sample-tiled float64 buffers: loads, integer iterate, field, pass rhs, scratch
+  DevBuf<double> samp[5];
+  DevBuf<double> noise_scratch;
+  DevBuf<double> pw_v, pw_w, pw_sigma;
+  DevBuf<double> coef;  // sinc weights of the current pass
+  int* host_small = nullptr;  // pinned
+  double host_d = 0.0;
+  int reserve(const wm_hier* h, int tiles, int nshift, bool dbl);
+  void release();
+};
+
+int wm_prepare_shifts(const wm_hier* h, WorkSpace& ws, const std::vector<double>& shifts, cudaStream_t s);
+int wm_solve_batch(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* rhs_tiled, BatchResult* res,
+                   cudaStream_t s);
+int wm_vcycle_apply(const wm_hier* h, WorkSpace& ws, const Batch& bt, cudaStream_t s);
+int wm_sinc_accumulate(const wm_hier* h, int ns, int g0, int g1, const double* c_dev, const double* x,
+                       double* v_tiled, cudaStream_t s);
+int wm_copy(const double* a, double* b, size_t n, cudaStream_t s);
+int wm_convert_f32(const double* a, float* b, size_t n, cudaStream_t s);
+int wm_widen_f32(const float* a, double* b, size_t n, cudaStream_t s);

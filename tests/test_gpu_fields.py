@@ -1,0 +1,120 @@
+"""GPU parity of the fields u_s (the whole path) against the CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import geometry as geo
+from oracle.assembly import assemble
+from oracle.fractional import sample_fields as oracle_fields
+from oracle.noise import noise_loads
+from oracle.space import GluedSpace
+from wm_workloads import WORKLOADS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wm():
+    from paper_2605_24882_gb300 import build as b
+    b.build()
+    import paper_2605_24882_gb300 as wm
+    return wm
+
+
+def mnorm_rel(u, ref, M):
+    d = u - ref
+    num = np.einsum("si,si->s", d, (M @ d.T).T)
+    den = np.einsum("si,si->s", ref, (M @ ref.T).T)
+    return np.sqrt(num / den)
+
+
+def run_case(wm, kind, p, nu, nv, levels, kappa, beta, k, lo, hi, ns, seed, precision, rtol, split="standard",
+             samples=None, **extra):
+    hier = wm.Hierarchy(wm.Geometry(kind, p, nu, nv), levels)
+    u, b, st = hier.sample_fields(return_loads=True, kappa=kappa, beta=beta, sinc_k=k, l_lo=lo, l_hi=hi,
+                                  n_samples=ns, seed=seed, split=split, precision=precision, rtol=rtol, **extra)
+    s = geo.Surface(kind, p, nu, nv)
+    sp_ = GluedSpace(s)
+    S, M = assemble(sp_)
+    idx = np.arange(ns) if samples is None else np.asarray(samples)
+    b_or = noise_loads(sp_, seed, ns)[idx] if samples is None else None
+    if b_or is None:
+        from oracle.noise import noise_from_xi, n_quad
+        from oracle.philox import normals
+        q = np.arange(n_quad(s))
+        b_or = np.stack([noise_from_xi(sp_, normals(seed, int(si), q)) for si in idx])
+    np.testing.assert_allclose(b.cpu().numpy()[idx], b_or, rtol=1e-11, atol=1e-13 * np.abs(b_or).max())
+    u_or = oracle_fields(S, M, b_or, kappa, beta, k, lo, hi, split)
+    return mnorm_rel(u.cpu().numpy()[idx], u_or, M), st, hier, u
+
+
+def test_plain_fp64_sphere_p2_j3(wm):
+    c = WORKLOADS["sphere_p2_j3_fp64"]
+    err, st, *_ = run_case(wm, "sphere", 2, 8, 8, c["levels"], c["kappa"], c["beta"], c["k"], c["l_lo"], c["l_hi"],
+                           c["n_samples"], c["seed"], "fp64", c["rtol"])
+    assert err.max() < 1e-9, (err, st)
+    assert st["n_not_converged"] == 0 and st["n_nodes"] == 51
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-6)])
+def test_sphere_batched_integer_plus_fraction(wm, precision, tol):
+    # beta = 1.3: one integer solve then 71 nodes; 40 samples = ragged second tile
+    err, st, *_ = run_case(wm, "sphere", 2, 16, 16, 4, 5.0, 1.3, 0.3, -35, 35, 40, 3, precision,
+                           1e-11 if precision == "fp64" else 1e-8)
+    assert err.max() < tol, (err, st)
+    assert st["n_int_solves"] == 1 and st["n_systems"] == 40 + 71 * 40
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-6)])
+def test_torus_p3(wm, precision, tol):
+    err, st, *_ = run_case(wm, "torus", 3, 32, 16, 2, 10.0, 0.6, 0.3, -35, 35, 33, 0, precision,
+                           1e-11 if precision == "fp64" else 1e-8)
+    assert err.max() < tol, (err, st)
+
+
+def test_improved_split_two_passes(wm):
+    err, st, *_ = run_case(wm, "sphere", 2, 8, 8, 3, 3.0, 1.8, 0.4, -20, 20, 5, 4, "mixed", 1e-9, split="improved")
+    assert st["n_frac_passes"] == 2 and st["n_int_solves"] == 1
+    assert err.max() < 1e-6, err
+
+
+def test_integer_beta_only(wm):
+    err, st, *_ = run_case(wm, "sphere", 3, 4, 4, 2, 1.5, 2.0, 0.4, -5, 5, 3, 1, "fp64", 1e-12)
+    assert st["n_frac_passes"] == 0 and st["n_int_solves"] == 2
+    assert err.max() < 1e-9, err
+
+
+def test_system_batching_and_host_output(wm):
+    hier = wm.Hierarchy(wm.Geometry("sphere", 2, 8), 3)
+    kw = dict(kappa=2.0, beta=0.75, sinc_k=0.4, l_lo=-25, l_hi=25, n_samples=7, seed=2, precision="mixed",
+              rtol=1e-9)
+    u1, _ = hier.sample_fields(**kw)
+    u2, st = hier.sample_fields(max_systems=64, **kw)
+    assert st["n_batches"] == (51 * 7 + 63) // 64
+    np.testing.assert_allclose(u2.cpu().numpy(), u1.cpu().numpy(), rtol=1e-8, atol=1e-12)
+    host = torch.empty(u1.shape, dtype=torch.float64).pin_memory()
+    u3, _ = hier.sample_fields(out=host, **kw)
+    assert np.array_equal(u3.numpy(), u1.cpu().numpy())
+    # no samples: nothing to do
+    u0, st0 = hier.sample_fields(**dict(kw, n_samples=0))
+    assert u0.shape[0] == 0
+
+
+def test_invalid_arguments(wm):
+    hier = wm.Hierarchy(wm.Geometry("sphere", 2, 8), 3)
+    with pytest.raises(wm.WMError):
+        hier.sample_fields(kappa=-1.0, beta=0.7, n_samples=1)
+    with pytest.raises(wm.WMError):
+        hier.sample_fields(kappa=1.0, beta=0.7, n_samples=1, l_lo=3, l_hi=2)
+    with pytest.raises(wm.WMError):
+        wm.Hierarchy(wm.Geometry("sphere", 2, 8), 9)
+
+
+def test_full_size_bench_workload_sampled(wm):
+    """The bench workload (sphere 6x64x64, p=2, beta=1.3, 256 samples, mixed) at
+    full size in the bench's launch configuration; the oracle checks samples 0 and 255."""
+    c = WORKLOADS["sphere_p2_j6_mixed_s256"]
+    err, st, *_ = run_case(wm, "sphere", 2, 64, 64, c["levels"], c["kappa"], c["beta"], c["k"], c["l_lo"],
+                           c["l_hi"], c["n_samples"], c["seed"], "mixed", c["rtol"], samples=[0, 255])
+    assert err.max() < 1e-6, (err, st)
+    assert st["n_systems"] == 256 * 72 and st["n_not_converged"] == 0
