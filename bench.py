@@ -1,0 +1,341 @@
+"""Throughput of batched Whittle–Matérn field sampling on GB300.
+
+One step = one call of the sampler (the whole hot path): Philox white-noise
+loads for 256 samples, the integer-part solve and the 71 shifted solves of
+every sample (18,432 systems of 25,352 DOFs, batched PCG with the float32
+multigrid V-cycle, float64 outer iteration), and the float64 sinc sum, on the
+six-patch unit sphere with 64 x 64 bi-quadratic elements per patch.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank samples its own 256 fields (independent seeds, no
+collective on the data path: weak scaling); rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from wm_workloads import WORKLOADS  # noqa: E402
+
+METRIC = "field samples/s & DOF-solves/s at ≤1e-6 rel err: batched mixed vs plain FP64"
+WORKLOAD = "sphere_p2_j6_mixed_s256"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# CUDA-core peaks of GB300 from unit counts and the 2070 MHz maximum SM clock:
+# FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64: the recipe's nominal 1.25 TFLOP/s
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "wm_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for name, val in zip(names[1:], f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", rank=rank, world_size=world, device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_estimate(c, n_shifts=4, n_sub=2):
+    """Oracle cost of the workload from a bounded sample, extrapolated linearly.
+
+    Times the oracle's assembly, its loads for n_sub samples, and the sparse LU
+    factorisation plus n_sub solves for n_shifts of the shifted matrices; the
+    full workload is n_nodes + n_int shifted matrices, each solved for every sample.
+    """
+    import numpy as np
+    from oracle import geometry as geo
+    from oracle.assembly import assemble
+    from oracle.fractional import Shifted, sinc_rule, split_beta
+    from oracle.noise import noise_loads
+    from oracle.space import GluedSpace
+
+    t0 = time.perf_counter()
+    s = geo.Surface(c["kind"], c["p"], c["n_u"], c["n_v"], c.get("R", 1.0), c.get("r", 0.4))
+    sp_ = GluedSpace(s)
+    S, M = assemble(sp_)
+    t_asm = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b = noise_loads(sp_, c["seed"], n_sub)
+    t_noise = (time.perf_counter() - t0) / n_sub
+    n, bp, passes = split_beta(c["beta"], c["split"])
+    y, _ = sinc_rule(bp, c["k"], c["l_lo"], c["l_hi"])
+    sig = np.exp(y) + c["kappa"] ** 2
+    n_mats = len(y) + (1 if n > 0 else 0)
+    sh = Shifted(S, M)
+    t_fact, t_solve = 0.0, 0.0
+    for k in range(n_shifts):
+        sg = float(sig[(k * 17) % len(sig)])
+        t0 = time.perf_counter()
+        sh.solve(sg, b[:1].T)
+        t1 = time.perf_counter()
+        sh.solve(sg, b.T)
+        t2 = time.perf_counter()
+        t_fact += (t1 - t0) - (t2 - t1) / n_sub
+        t_solve += (t2 - t1) / n_sub
+    t_fact /= n_shifts
+    t_solve /= n_shifts
+    ns = c["n_samples"]
+    total = t_asm + ns * t_noise + n_mats * t_fact + n_mats * passes * ns * t_solve
+    sample = ("assembly, loads of %d samples, LU factorisation of %d of the %d shifted matrices with %d solves "
+              "each; extrapolated linearly to %d matrices x %d samples" % (n_sub, n_shifts, n_mats, n_sub, n_mats, ns))
+    return ns / total, total, sample, sp_.N
+
+
+def reference_arm(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    c = WORKLOADS[args.workload]
+    vals, times = [], []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        v, _, sample, N = oracle_estimate(c, n_shifts=1, n_sub=2)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            vals.append(v)
+            times.append(dt)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "dofs": N},
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                             "sample": "per step: " + sample},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def roofline(prof, pk, pk_kind):
+    """Dominant kernel category by device time; achieved vs peak of its bound."""
+    name, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    sec = d["ms"] / 1e3
+    if sec <= 0 or d["timed"] == 0:
+        return None, name
+    gbs = d["bytes"] / sec / 1e9
+    tfl = d["flops"] / sec / 1e12
+    is64 = name in ("apply_f64_outer", "cg_vectors")
+    alu_peak = FP64_PEAK_TFLOPS if is64 else FP32_PEAK_TFLOPS
+    t_alu = d["flops"] / (alu_peak * 1e12)
+    t_hbm = d["bytes"] / (pk["hbm_gbs"] * 1e9)
+    per_launch = d["bytes"] / d["timed"]
+    if t_hbm >= t_alu:
+        r = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+             "peak_kind": pk_kind + " (MEASURED_PEAKS.json hbm_gbs)" if pk_kind == "measured" else pk_kind}
+    else:
+        r = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfl / alu_peak,
+             "peak_kind": ("nominal FP64 1.25 TFLOP/s" if is64 else
+                           "FP32 CUDA cores 152 SMs x 128 lanes x 2 x 2.07 GHz")}
+    r.update({"kernel": name, "launches": d["timed"], "avg_launch_ms": d["ms"] / d["timed"],
+              "alg_bytes_per_launch": per_launch, "alg_flops_per_launch": d["flops"] / d["timed"],
+              "traffic": traffic_for(name)})
+    return r, name
+
+
+def traffic_for(name):
+    """DRAM bytes per launch of category `name` from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(name)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_2605_24882_gb300", "csrc", e["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != e["source_sha"]:
+        return None
+    return e["dram_bytes_per_launch"]
+
+
+def our_arm(args):
+    import torch
+
+    import paper_2605_24882_gb300 as wm
+
+    world, rank, local = dist_setup(args.gpus)
+    c = WORKLOADS[args.workload]
+    pk, pk_kind = peaks()
+    hier = wm.Hierarchy(wm.Geometry(c["kind"], c["p"], c["n_u"], c["n_v"], c.get("R", 1.0), c.get("r", 0.4)),
+                        c["levels"])
+    N = hier.num_dofs(0)
+    ns = c["n_samples"]
+    kw = dict(kappa=c["kappa"], beta=c["beta"], sinc_k=c["k"], l_lo=c["l_lo"], l_hi=c["l_hi"], n_samples=ns,
+              seed=c["seed"] + 1000003 * rank, split=c["split"], precision=c["precision"], rtol=c["rtol"],
+              smoother_degree=args.smoother_degree, cheb_ratio=args.cheb_ratio)
+    u = torch.empty((ns, N), dtype=torch.float64, device="cuda")
+    stats = None
+    for _ in range(args.warmup):
+        _, stats = hier.sample_fields(out=u, **kw)
+    torch.cuda.synchronize()
+    wm.profile_enable(args.profile)
+    before = wm.profile_read()
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, stats = hier.sample_fields(out=u, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    prof = wm.profile_read()
+    wm.profile_enable(False)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    launches = sum(prof[k]["launches"] - before[k]["launches"] for k in prof)
+    value = world * ns / (ms / 1e3)
+    n_int, bf, passes = wm.beta_plan(c["beta"], c["split"])
+    n_nodes = c["l_hi"] - c["l_lo"] + 1
+    dof_solves = world * N * (n_int + passes * n_nodes) * ns / (ms / 1e3)
+    # end to end through the C ABI with a pinned host output buffer: the
+    # device->host copy of every step's fields is inside the timed region
+    host = torch.empty((ns, N), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        hier.sample_fields(out=host, **kw)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / max(1, args.e2e_steps), world)
+    rl, dominant = roofline(prof, pk, pk_kind) if args.profile else (None, None)
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": args.workload, "surface": "unit sphere, 6 patches x 64 x 64 elements, p = 2",
+                       "dofs": N, "samples_per_gpu": ns, "integer_solves": n_int, "sinc_nodes": n_nodes,
+                       "systems_per_step": ns * (n_int + passes * n_nodes), "rtol": c["rtol"],
+                       "precision": c["precision"], "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2: the batch working set is about 25 GB per step"},
+            "dof_solves_per_s": dof_solves,
+            "solver": {k: stats[k] for k in ("max_iterations", "total_iterations", "n_not_converged",
+                                             "max_rel_residual", "n_systems", "n_batches")},
+            "e2e": {"value": world * ns / (e2e_ms / 1e3) if args.e2e_steps else None, "unit": "samples/s",
+                    "h2d_bytes_per_step": 120, "d2h_bytes_per_step": ns * N * 8},
+            "gpu_launches": launches,
+            "roofline": rl,
+            "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["ms"] > 0},
+            "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, total, sample, _ = oracle_estimate(c)
+        line["cpu_baseline"] = {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle", "sample": sample,
+                                "extrapolated_seconds_per_step": total}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--smoother-degree", type=int, default=2)
+    ap.add_argument("--cheb-ratio", type=float, default=8.0)
+    ap.add_argument("--no-profile", dest="profile", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        our_arm(args)
+
+
+if __name__ == "__main__":
+    main()

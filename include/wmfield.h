@@ -246,6 +246,26 @@ int wm_sample_fields_backward(wm_hier_t h, const wm_sample_desc* desc, const dou
 /* Integer/fractional split of beta (Sec. 3.4): n_int, beta_frac, n_passes. */
 int wm_beta_plan(double beta, int split, int* n_int, double* beta_frac, int* n_passes);
 
+/* ---- live profiling --------------------------------------------------------- */
+/*
+ * Launch counting is always on.  wm_profile_enable(1) resets the per-category
+ * timers and starts recording a CUDA event pair on the launching stream around
+ * every kernel launch of the library (a diagnostic aid: about a microsecond
+ * of host time per launch); wm_profile_enable(0) stops.  wm_profile_read()
+ * waits for the recorded events and returns, for category c in
+ * [0, wm_profile_categories()), the summed device time of its timed launches,
+ * their number, the number of launches since the library was loaded, the
+ * algorithmic bytes and flops of the timed launches (the minimum traffic and
+ * arithmetic of each launch: every vector stream of the active systems read
+ * or written once, operator rows counted per stored nonzero), and a static
+ * name.  Returns 1 instead of WM_OK when the event pool (65536 pairs)
+ * overflowed, after which further launches were counted but not timed.
+ */
+int wm_profile_enable(int on);
+int wm_profile_read(int c, double* total_ms, int64_t* timed_launches, int64_t* all_launches,
+                    double* alg_bytes, double* alg_flops, const char** name);
+int wm_profile_categories(void);
+
 /* ---- errors and teardown ---------------------------------------------------- */
 const char* wm_error_string(int code);
 const char* wm_last_error(void);

@@ -215,6 +215,23 @@ def sample_fields_batched(hiers, descs, stream=None):
     return outs, [s.as_dict() for s in st]
 
 
+def profile_enable(on=True):
+    """Start (reset) or stop live per-kernel event timing inside the library."""
+    check(lib().wm_profile_enable(1 if on else 0), "wm_profile_enable")
+
+
+def profile_read():
+    """{category: dict(ms, timed, launches, bytes, flops)} since profile_enable(True)."""
+    out = {}
+    for c in range(lib().wm_profile_categories()):
+        ms, nt, na, by, fl, name = C.c_double(), C.c_int64(), C.c_int64(), C.c_double(), C.c_double(), C.c_char_p()
+        check(lib().wm_profile_read(c, C.byref(ms), C.byref(nt), C.byref(na), C.byref(by), C.byref(fl),
+                                    C.byref(name)), "wm_profile_read")
+        out[name.value.decode()] = dict(ms=ms.value, timed=nt.value, launches=na.value, bytes=by.value,
+                                        flops=fl.value)
+    return out
+
+
 class WMField(torch.autograd.Function):
     """u = F(b, kappa): the fields of loads b; backward by the adjoint solves."""
 

@@ -71,6 +71,10 @@ _PROTOS = {
                                       C.POINTER(Stats), _vp]),
     "wm_sample_fields_backward": (_i, [_vp, C.POINTER(SampleDesc), _vp, _vp, _vp, C.POINTER(_d), _vp]),
     "wm_beta_plan": (_i, [_d, _i, C.POINTER(_i), C.POINTER(_d), C.POINTER(_i)]),
+    "wm_profile_enable": (_i, [_i]),
+    "wm_profile_read": (_i, [_i, C.POINTER(_d), C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_d), C.POINTER(_d),
+                             C.POINTER(C.c_char_p)]),
+    "wm_profile_categories": (_i, []),
     "wm_error_string": (C.c_char_p, [_i]),
     "wm_last_error": (C.c_char_p, []),
     "wm_destroy_hier": (None, [_vp]),

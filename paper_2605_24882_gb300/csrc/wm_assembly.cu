@@ -219,7 +219,7 @@ static GeoArgs geo_args(const wm_hier* h, const wm_level& L) {
 int wm_k_metric(const wm_hier* h, const wm_level& L, cudaStream_t s) {
   int64_t nQ = (int64_t)L.E * h->nq * h->nq;
   int bs = 256;
-  k_metric<<<(unsigned)((nQ + bs - 1) / bs), bs, 0, s>>>(geo_args(h, L), h->d_gx.p, nQ, L.d_metric.p);
+  WM_LAUNCH(WM_PC_ASSEMBLY, s, k_metric<<<(unsigned)((nQ + bs - 1) / bs), bs, 0, s>>>(geo_args(h, L), h->d_gx.p, nQ, L.d_metric.p));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
@@ -231,6 +231,7 @@ int wm_k_element_matrices(const wm_hier* h, wm_level& L, cudaStream_t s) {
 #define WM_EM(PP)                                                                                    \
   k_element_matrices<PP><<<grid, bs, 0, s>>>(L.E, L.nu, L.nv, L.d_metric.p, h->d_gw.p, L.d_bu.p,      \
                                              L.d_du.p, L.d_bv.p, L.d_dv.p, L.d_Se.p, L.d_Me.p)
+  wm_prof_begin(WM_PC_ASSEMBLY, s);
   switch (h->p) {
     case 1: WM_EM(1); break;
     case 2: WM_EM(2); break;
@@ -239,6 +240,7 @@ int wm_k_element_matrices(const wm_hier* h, wm_level& L, cudaStream_t s) {
     default: wm_set_error("degree %d unsupported", h->p); return WM_ERR_UNSUPPORTED;
   }
 #undef WM_EM
+  wm_prof_end(WM_PC_ASSEMBLY, s);
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
@@ -247,12 +249,12 @@ int wm_k_assemble_rows(const wm_hier* h, wm_level& L, cudaStream_t s) {
   (void)h;
   int64_t n = (int64_t)L.N * L.W;
   int bs = 256;
-  k_assemble_rows<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(
+  WM_LAUNCH(WM_PC_ASSEMBLY, s, k_assemble_rows<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(
       L.N, L.W, L.nk, L.d_col.p, L.d_ng_ptr.p, L.d_ng_idx.p, L.d_conn.p, L.d_Se.p, L.d_Me.p, L.d_S64.p,
-      L.d_M64.p, L.d_S32.p, L.d_M32.p);
+      L.d_M64.p, L.d_S32.p, L.d_M32.p));
   WM_CUDA(cudaGetLastError());
-  k_diagonals<<<(L.N + 255) / 256, 256, 0, s>>>(L.N, L.W, L.d_diag_slot.p, L.d_S64.p, L.d_M64.p, L.d_dS64.p,
-                                                L.d_dM64.p, L.d_dS32.p, L.d_dM32.p);
+  WM_LAUNCH(WM_PC_ASSEMBLY, s, k_diagonals<<<(L.N + 255) / 256, 256, 0, s>>>(L.N, L.W, L.d_diag_slot.p, L.d_S64.p, L.d_M64.p, L.d_dS64.p,
+                                                L.d_dM64.p, L.d_dS32.p, L.d_dM32.p));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
@@ -261,8 +263,8 @@ int wm_k_dense_coarse(const wm_level& L, cudaStream_t s) {
   WM_CUDA(cudaMemsetAsync(L.d_Sdense.p, 0, sizeof(double) * (size_t)L.N * L.N, s));
   WM_CUDA(cudaMemsetAsync(L.d_Mdense.p, 0, sizeof(double) * (size_t)L.N * L.N, s));
   int64_t n = (int64_t)L.N * L.W;
-  k_dense<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L.N, L.W, L.d_col.p, L.d_S64.p, L.d_M64.p, L.d_Sdense.p,
-                                                      L.d_Mdense.p);
+  WM_LAUNCH(WM_PC_ASSEMBLY, s, k_dense<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L.N, L.W, L.d_col.p, L.d_S64.p, L.d_M64.p, L.d_Sdense.p,
+                                                      L.d_Mdense.p));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }

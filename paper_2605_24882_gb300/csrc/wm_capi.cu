@@ -182,6 +182,7 @@ static int assemble(wm_hier* h, int n_levels, cudaStream_t s) {
     wm_level& F = h->lv[l];
     F.nP = F.N;
     F.nR = h->lv[l + 1].N;
+    F.nnzP = (int64_t)Pc.size();
     WM_TRY(F.d_Pptr.upload(Pp, s));
     WM_TRY(F.d_Pcol.upload(Pc, s));
     WM_TRY(F.d_Pval64.upload(Pv, s));

@@ -276,6 +276,8 @@ int wm_host_build_level(const wm_geom_desc& g, int np, int nu, int nv, wm_level&
   int W = 0;
   for (int i = 0; i < L.N; ++i) W = std::max(W, (int)cnt[i]);
   L.W = W;
+  L.nnz = 0;
+  for (int i = 0; i < L.N; ++i) L.nnz += cnt[i];
   L.col.assign((size_t)L.N * W, 0);
   L.diag_slot.assign(L.N, 0);
   for (int i = 0; i < L.N; ++i) {

@@ -76,6 +76,8 @@ struct wm_level {
   int E = 0;             // elements (all patches)
   int nk = 0;            // local functions per element, (p+1)^2
   int W = 0;             // stored entries per operator row (max row length)
+  int64_t nnz = 0;       // non-padding entries of all rows
+  int64_t nnzP = 0;      // entries of the prolongation to this level
   std::vector<int32_t> l2g;   // [np][nlv][nlu]
   std::vector<int32_t> conn;  // [E][nk]
   std::vector<int32_t> col;   // [N][W], padded with the row index
@@ -158,3 +160,36 @@ int wm_k_restrict(const wm_level& fine, int tiles, const T* rf, T* rc, const int
 // layout conversion between [n][N] and [tiles][N][32]
 int wm_k_to_tiled(const double* src, int n, int N, double* dst, int tiles, cudaStream_t s);
 int wm_k_from_tiled(const double* src, int tiles, int N, double* dst, int n, cudaStream_t s);
+
+// ---------------------------------------------------------------- profiling
+// Launch categories for live per-kernel timing (CUDA events around each launch
+// when enabled through wm_profile_enable) and launch counting (always on).
+enum {
+  WM_PC_APPLY64 = 0,   // float64 operator apply of the outer CG (q = A p)
+  WM_PC_SMOOTH0,       // Chebyshev smoothing steps on the finest level
+  WM_PC_SMOOTHC,       // Chebyshev smoothing steps on coarser levels
+  WM_PC_RESID0,        // residual before restriction, finest level
+  WM_PC_RESIDC,        // residual before restriction, coarser levels
+  WM_PC_RESTRICT,      // restriction P^T
+  WM_PC_PROLONG,       // prolongation P (add)
+  WM_PC_COARSE,        // dense coarse solve
+  WM_PC_CGVEC,         // outer CG vector updates and dot products
+  WM_PC_SCALAR,        // per-system scalar kernels
+  WM_PC_NOISE,         // Philox white-noise loads
+  WM_PC_SINC,          // sinc accumulation, mass apply of pass rhs, copies
+  WM_PC_SETUP,         // smoother bounds (power iteration), coarse inverses
+  WM_PC_LAYOUT,        // [n][N] <-> tiled layout conversions
+  WM_PC_ASSEMBLY,      // metric, element matrices, rows
+  WM_PC_APPLY,         // component operator applies
+  WM_PC_COUNT
+};
+void wm_prof_begin(int cat, cudaStream_t s);
+void wm_prof_end(int cat, cudaStream_t s);
+// algorithmic bytes and flops of the launch just made (counted while timing is on)
+void wm_prof_units(int cat, double bytes, double flops);
+#define WM_LAUNCH(cat, s, ...)  \
+  do {                          \
+    wm_prof_begin((cat), (s));  \
+    __VA_ARGS__;                \
+    wm_prof_end((cat), (s));    \
+  } while (0)

@@ -146,15 +146,15 @@ __global__ void k_noise_gather(int N, int ns, int s0, const int32_t* __restrict_
 
 int wm_k_philox(const uint32_t* ctr, uint64_t key, uint32_t* out, int64_t n, cudaStream_t s) {
   if (n <= 0) return WM_OK;
-  k_philox<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctr, (uint32_t)(key & 0xFFFFFFFFull),
-                                                       (uint32_t)(key >> 32), out, n);
+  WM_LAUNCH(WM_PC_NOISE, s, k_philox<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctr, (uint32_t)(key & 0xFFFFFFFFull),
+                                                       (uint32_t)(key >> 32), out, n));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
 
 int wm_k_normals(uint64_t seed, int sample, int stream_id, int64_t q0, int64_t n, double* out, cudaStream_t s) {
   if (n <= 0) return WM_OK;
-  k_normals<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(seed, sample, stream_id, q0, n, out);
+  WM_LAUNCH(WM_PC_NOISE, s, k_normals<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(seed, sample, stream_id, q0, n, out));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
@@ -167,6 +167,7 @@ int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int s0, int ns, double* b_
 #define WM_NL(PP)                                                                                        \
   k_noise_local<PP><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, ns, s0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, \
                                        L.d_bv.p, bl)
+  wm_prof_begin(WM_PC_NOISE, s);
   switch (h->p) {
     case 1: WM_NL(1); break;
     case 2: WM_NL(2); break;
@@ -175,10 +176,11 @@ int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int s0, int ns, double* b_
     default: return WM_ERR_UNSUPPORTED;
   }
 #undef WM_NL
+  wm_prof_end(WM_PC_NOISE, s);
   WM_CUDA(cudaGetLastError());
   int64_t n2 = (int64_t)L.N * ns;
-  k_noise_gather<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(L.N, ns, s0, L.d_ng_ptr.p, L.d_ng_idx.p, bl,
-                                                              b_tiled);
+  WM_LAUNCH(WM_PC_NOISE, s, k_noise_gather<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(L.N, ns, s0, L.d_ng_ptr.p, L.d_ng_idx.p, bl,
+                                                              b_tiled));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }

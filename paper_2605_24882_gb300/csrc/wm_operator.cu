@@ -151,8 +151,8 @@ template <typename T>
 int wm_k_apply(const wm_level& L, int tiles, const double* sigma, const T* x, T* y, const int* tile_active,
                cudaStream_t s) {
   if (tiles <= 0) return WM_OK;
-  k_apply<T><<<row_grid(L.N, tiles), kBlock, 0, s>>>(L.N, L.W, L.d_col.p, rowsS<T>(L), rowsM<T>(L), sigma, x, y,
-                                                     tile_active);
+  WM_LAUNCH(WM_PC_APPLY, s, k_apply<T><<<row_grid(L.N, tiles), kBlock, 0, s>>>(L.N, L.W, L.d_col.p, rowsS<T>(L), rowsM<T>(L), sigma, x, y,
+                                                     tile_active));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
@@ -164,7 +164,7 @@ template int wm_k_apply<float>(const wm_level&, int, const double*, const float*
 int wm_k_apply_mass64(const wm_level& L, int tiles, const double* x, double* y, const int* tile_active,
                       cudaStream_t s) {
   if (tiles <= 0) return WM_OK;
-  k_apply_mass<<<row_grid(L.N, tiles), kBlock, 0, s>>>(L.N, L.W, L.d_col.p, L.d_M64.p, x, y, tile_active);
+  WM_LAUNCH(WM_PC_SINC, s, k_apply_mass<<<row_grid(L.N, tiles), kBlock, 0, s>>>(L.N, L.W, L.d_col.p, L.d_M64.p, x, y, tile_active));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
@@ -173,8 +173,8 @@ int wm_k_apply_mass64(const wm_level& L, int tiles, const double* x, double* y, 
 template <typename T>
 int wm_k_prolong_add(const wm_level& fine, int tiles, const T* xc, T* xf, const int* tile_active, cudaStream_t s) {
   if (tiles <= 0) return WM_OK;
-  k_prolong_add<T><<<row_grid(fine.nP, tiles), kBlock, 0, s>>>(fine.nP, fine.nR, fine.d_Pptr.p, fine.d_Pcol.p,
-                                                               pval<T>(fine), xc, xf, tile_active);
+  WM_LAUNCH(WM_PC_PROLONG, s, k_prolong_add<T><<<row_grid(fine.nP, tiles), kBlock, 0, s>>>(fine.nP, fine.nR, fine.d_Pptr.p, fine.d_Pcol.p,
+                                                               pval<T>(fine), xc, xf, tile_active));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
@@ -184,8 +184,8 @@ template int wm_k_prolong_add<float>(const wm_level&, int, const float*, float*,
 template <typename T>
 int wm_k_restrict(const wm_level& fine, int tiles, const T* rf, T* rc, const int* tile_active, cudaStream_t s) {
   if (tiles <= 0) return WM_OK;
-  k_restrict<T><<<row_grid(fine.nR, tiles), kBlock, 0, s>>>(fine.nR, fine.nP, fine.d_Rptr.p, fine.d_Rcol.p,
-                                                            rval<T>(fine), rf, rc, tile_active);
+  WM_LAUNCH(WM_PC_RESTRICT, s, k_restrict<T><<<row_grid(fine.nR, tiles), kBlock, 0, s>>>(fine.nR, fine.nP, fine.d_Rptr.p, fine.d_Rcol.p,
+                                                            rval<T>(fine), rf, rc, tile_active));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
@@ -194,14 +194,14 @@ template int wm_k_restrict<float>(const wm_level&, int, const float*, float*, co
 
 int wm_k_to_tiled(const double* src, int n, int N, double* dst, int tiles, cudaStream_t s) {
   if (tiles <= 0 || N <= 0) return WM_OK;
-  k_to_tiled<<<dim3((N + 31) / 32, tiles), dim3(32, 8), 0, s>>>(src, n, N, dst);
+  WM_LAUNCH(WM_PC_LAYOUT, s, k_to_tiled<<<dim3((N + 31) / 32, tiles), dim3(32, 8), 0, s>>>(src, n, N, dst));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
 
 int wm_k_from_tiled(const double* src, int tiles, int N, double* dst, int n, cudaStream_t s) {
   if (tiles <= 0 || N <= 0) return WM_OK;
-  k_from_tiled<<<dim3((N + 31) / 32, tiles), dim3(32, 8), 0, s>>>(src, N, dst, n);
+  WM_LAUNCH(WM_PC_LAYOUT, s, k_from_tiled<<<dim3((N + 31) / 32, tiles), dim3(32, 8), 0, s>>>(src, N, dst, n));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }

@@ -210,7 +210,7 @@ __global__ void k_scal_conv(int nsys_pad, int chunks, const double* part_rr, con
   }
   if (active[g]) {
     atomicAdd(&counters[0], 1);
-    tile_active[g / WM_LANES] = 1;
+    if (atomicExch(&tile_active[g / WM_LANES], 1) == 0) atomicAdd(&counters[2], 1);
   }
 }
 
@@ -515,6 +515,12 @@ inline unsigned nblk(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 }  // namespace
 
 // ====================================================================== host
+// algorithmic bytes/flops of a launch over the active tiles: `b` bytes and `f`
+// flops per system of one tile
+static inline void units(int cat, const Batch& bt, double b, double f) {
+  double sys = (double)bt.active_tiles * WM_LANES;
+  wm_prof_units(cat, b * sys, f * sys);
+}
 int Batch::chunks_for(int N) const {
   // enough blocks to cover the GPU several times, at least 64 rows per chunk
   int target = std::max(1, (152 * 8 + tiles - 1) / std::max(1, tiles));
@@ -614,17 +620,17 @@ static int estimate_lmax(const wm_hier* h, WorkSpace& ws, const std::vector<doub
   for (int l = 0; l < L - 1; ++l) {
     const wm_level& Lv = h->lv[l];
     int ch = bt.chunks_for(Lv.N);
-    k_power_init<<<dim3(64, tiles), kBlk, 0, s>>>(Lv.N, ws.pw_v.p);
+    WM_LAUNCH(WM_PC_SETUP, s, k_power_init<<<dim3(64, tiles), kBlk, 0, s>>>(Lv.N, ws.pw_v.p));
     double* v = ws.pw_v.p;
     double* w = ws.pw_w.p;
     for (int it = 0; it < 15; ++it) {
-      k_power_step<<<dim3(ch, tiles), kBlk, 0, s>>>(Lv.N, Lv.W, ch, Lv.d_col.p, Lv.d_S64.p, Lv.d_M64.p,
+      WM_LAUNCH(WM_PC_SETUP, s, k_power_step<<<dim3(ch, tiles), kBlk, 0, s>>>(Lv.N, Lv.W, ch, Lv.d_col.p, Lv.d_S64.p, Lv.d_M64.p,
                                                     Lv.d_dS64.p, Lv.d_dM64.p, ws.pw_sigma.p, v, w, ws.part[0].p,
-                                                    ws.part[1].p);
-      if (it < 14) k_power_scale<<<dim3(ch, tiles), kBlk, 0, s>>>(Lv.N, ch, ws.part[0].p, w);
+                                                    ws.part[1].p));
+      if (it < 14) WM_LAUNCH(WM_PC_SETUP, s, k_power_scale<<<dim3(ch, tiles), kBlk, 0, s>>>(Lv.N, ch, ws.part[0].p, w));
       std::swap(v, w);
     }
-    k_power_final<<<nblk(nsh, 128), 128, 0, s>>>(nsh, ch, ws.part[0].p, ws.part[1].p, ws.lmax.p + (size_t)l * nsh);
+    WM_LAUNCH(WM_PC_SETUP, s, k_power_final<<<nblk(nsh, 128), 128, 0, s>>>(nsh, ch, ws.part[0].p, ws.part[1].p, ws.lmax.p + (size_t)l * nsh));
     WM_CUDA(cudaGetLastError());
   }
   return WM_OK;
@@ -641,7 +647,7 @@ int wm_prepare_shifts(const wm_hier* h, WorkSpace& ws, const std::vector<double>
     return WM_ERR_UNSUPPORTED;
   }
   WM_CUDA(cudaFuncSetAttribute(k_coarse_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_coarse_inverse<<<nsh, 256, smem, s>>>(C.N, C.d_Sdense.p, C.d_Mdense.p, ws.shifts.p, ws.ainv.p);
+  WM_LAUNCH(WM_PC_SETUP, s, k_coarse_inverse<<<nsh, 256, smem, s>>>(C.N, C.d_Sdense.p, C.d_Mdense.p, ws.shifts.p, ws.ainv.p));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
@@ -665,12 +671,19 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   const T* dM = std::is_same<T, double>::value ? (const T*)Lv.d_dM64.p : (const T*)Lv.d_dM32.p;
   T* za = lvbuf<T>(B.za);
   T* zb = lvbuf<T>(B.zb);
+  const double Rb = rin_double ? 8.0 : (double)sizeof(T), Tb = (double)sizeof(T);
+  const int csm = l == 0 ? WM_PC_SMOOTH0 : WM_PC_SMOOTHC;
+  const int cre = l == 0 ? WM_PC_RESID0 : WM_PC_RESIDC;
   if (l == L - 1) {
     int gx = std::max(1, std::min(64, (Lv.N + kWarps - 1) / kWarps));
-    if (rin_double)
-      k_coarse_solve<T, double><<<dim3(gx, tiles), kBlk, 0, s>>>(Lv.N, ws.ainv.p, ws.sid.p, (const double*)rin, za, ta);
-    else
-      k_coarse_solve<T, T><<<dim3(gx, tiles), kBlk, 0, s>>>(Lv.N, ws.ainv.p, ws.sid.p, (const T*)rin, za, ta);
+    if (rin_double) {
+      WM_LAUNCH(WM_PC_COARSE, s, k_coarse_solve<T, double><<<dim3(gx, tiles), kBlk, 0, s>>>(
+                                     Lv.N, ws.ainv.p, ws.sid.p, (const double*)rin, za, ta));
+    } else {
+      WM_LAUNCH(WM_PC_COARSE, s, k_coarse_solve<T, T><<<dim3(gx, tiles), kBlk, 0, s>>>(
+                                     Lv.N, ws.ainv.p, ws.sid.p, (const T*)rin, za, ta));
+    }
+    units(WM_PC_COARSE, bt, (Rb + Tb) * Lv.N, 2.0 * Lv.N * Lv.N);
     WM_CUDA(cudaGetLastError());
     *zout = za;
     return WM_OK;
@@ -679,48 +692,55 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   T* res = lvbuf<T>(B.res);
   int nu = bt.degree;
   double ratio = bt.cheb_ratio;
-#define WM_R_ARGS(RT) (const RT*)rin
+  auto cheb_step = [&](int k, const T* zin, T* zo) {
+    if (rin_double) {
+      WM_LAUNCH(csm, s, k_cheb_step<T, double><<<grid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, k, Lv.d_col.p, S, M, dS, dM,
+                                                                     ws.sigma.p, lmax, ws.sid.p, ratio,
+                                                                     (const double*)rin, zin, d, zo, ta));
+    } else {
+      WM_LAUNCH(csm, s, k_cheb_step<T, T><<<grid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, k, Lv.d_col.p, S, M, dS, dM,
+                                                                ws.sigma.p, lmax, ws.sid.p, ratio, (const T*)rin,
+                                                                zin, d, zo, ta));
+    }
+    units(csm, bt, (Rb + 4.0 * Tb) * Lv.N, 4.0 * Lv.nnz + 8.0 * Lv.N);
+  };
   // pre-smoothing from z = 0
-  if (rin_double)
-    k_cheb_first<T, double><<<grid, kBlk, 0, s>>>(Lv.N, ch, WM_R_ARGS(double), dS, dM, ws.sigma.p, lmax, ws.sid.p,
-                                                  ratio, d, za, ta);
-  else
-    k_cheb_first<T, T><<<grid, kBlk, 0, s>>>(Lv.N, ch, WM_R_ARGS(T), dS, dM, ws.sigma.p, lmax, ws.sid.p, ratio, d,
-                                             za, ta);
+  if (rin_double) {
+    WM_LAUNCH(csm, s, k_cheb_first<T, double><<<grid, kBlk, 0, s>>>(Lv.N, ch, (const double*)rin, dS, dM, ws.sigma.p,
+                                                                    lmax, ws.sid.p, ratio, d, za, ta));
+  } else {
+    WM_LAUNCH(csm, s, k_cheb_first<T, T><<<grid, kBlk, 0, s>>>(Lv.N, ch, (const T*)rin, dS, dM, ws.sigma.p, lmax,
+                                                               ws.sid.p, ratio, d, za, ta));
+  }
+  units(csm, bt, (Rb + 2.0 * Tb) * Lv.N, 4.0 * Lv.N);
   T* cur = za;
   T* oth = zb;
   for (int k = 1; k < nu; ++k) {
-    if (rin_double)
-      k_cheb_step<T, double><<<grid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, k, Lv.d_col.p, S, M, dS, dM, ws.sigma.p, lmax,
-                                                   ws.sid.p, ratio, WM_R_ARGS(double), cur, d, oth, ta);
-    else
-      k_cheb_step<T, T><<<grid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, k, Lv.d_col.p, S, M, dS, dM, ws.sigma.p, lmax,
-                                              ws.sid.p, ratio, WM_R_ARGS(T), cur, d, oth, ta);
+    cheb_step(k, cur, oth);
     std::swap(cur, oth);
   }
   // residual, restriction, coarse correction
-  if (rin_double)
-    k_residual<T, double><<<grid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, Lv.d_col.p, S, M, ws.sigma.p, WM_R_ARGS(double), cur,
-                                                res, ta);
-  else
-    k_residual<T, T><<<grid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, Lv.d_col.p, S, M, ws.sigma.p, WM_R_ARGS(T), cur, res, ta);
+  if (rin_double) {
+    WM_LAUNCH(cre, s, k_residual<T, double><<<grid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, Lv.d_col.p, S, M, ws.sigma.p,
+                                                                  (const double*)rin, cur, res, ta));
+  } else {
+    WM_LAUNCH(cre, s, k_residual<T, T><<<grid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, Lv.d_col.p, S, M, ws.sigma.p,
+                                                             (const T*)rin, cur, res, ta));
+  }
+  units(cre, bt, (Rb + 2.0 * Tb) * Lv.N, 4.0 * Lv.nnz + 3.0 * Lv.N);
   WM_CUDA(cudaGetLastError());
   T* rc = lvbuf<T>(ws.lvl[l + 1].r);
   WM_TRY(wm_k_restrict<T>(Lv, tiles, res, rc, ta, s));
+  units(WM_PC_RESTRICT, bt, Tb * (Lv.N + h->lv[l + 1].N), 2.0 * Lv.nnzP);
   T* zc = nullptr;
   WM_TRY(vcycle<T>(h, ws, bt, l + 1, rc, false, &zc, s));
   WM_TRY(wm_k_prolong_add<T>(Lv, tiles, zc, cur, ta, s));
+  units(WM_PC_PROLONG, bt, Tb * (2.0 * Lv.N + h->lv[l + 1].N), 2.0 * Lv.nnzP);
   // post-smoothing
   for (int k = 0; k < nu; ++k) {
-    if (rin_double)
-      k_cheb_step<T, double><<<grid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, k, Lv.d_col.p, S, M, dS, dM, ws.sigma.p, lmax,
-                                                   ws.sid.p, ratio, WM_R_ARGS(double), cur, d, oth, ta);
-    else
-      k_cheb_step<T, T><<<grid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, k, Lv.d_col.p, S, M, dS, dM, ws.sigma.p, lmax,
-                                              ws.sid.p, ratio, WM_R_ARGS(T), cur, d, oth, ta);
+    cheb_step(k, cur, oth);
     std::swap(cur, oth);
   }
-#undef WM_R_ARGS
   WM_CUDA(cudaGetLastError());
   *zout = cur;
   return WM_OK;
@@ -742,8 +762,10 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
   int nsys_pad = tiles * WM_LANES;
   unsigned sb = nblk(nsys_pad, 128);
   WM_CUDA(cudaMemsetAsync(ws.flags.p, 0, 4 * sizeof(int), s));
-  k_gather_rhs<<<grid, kBlk, 0, s>>>(N, ch, rhs_tiled, ws.src_of.p, ws.r.p, ws.x.p, ws.part[0].p);
+  WM_LAUNCH(WM_PC_CGVEC, s, k_gather_rhs<<<grid, kBlk, 0, s>>>(N, ch, rhs_tiled, ws.src_of.p, ws.r.p, ws.x.p, ws.part[0].p));
   WM_CUDA(cudaGetLastError());
+  bt.active_tiles = tiles;
+  units(WM_PC_CGVEC, bt, 24.0 * N, 2.0 * N);
   // all tiles active for the first preconditioner application
   {
     std::vector<int> ones(tiles, 1);
@@ -751,42 +773,47 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
   }
   T* z = nullptr;
   WM_TRY(precondition<T>(h, ws, bt, &z, s));
-  k_dots_rz_zq<T><<<grid, kBlk, 0, s>>>(N, ch, ws.r.p, z, nullptr, ws.tile_active.p, ws.part[1].p, ws.part[2].p);
-  k_scal_init<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[0].p, ws.part[1].p, ws.src_of.p, ws.bb.p, ws.rho.p, ws.rr.p,
-                                 ws.active.p, ws.flags.p);
-  k_fill_tile_active<<<nblk(tiles, 128), 128, 0, s>>>(tiles, ws.tile_active.p, ws.active.p);
+  WM_LAUNCH(WM_PC_CGVEC, s, k_dots_rz_zq<T><<<grid, kBlk, 0, s>>>(N, ch, ws.r.p, z, nullptr, ws.tile_active.p, ws.part[1].p, ws.part[2].p));
+  WM_LAUNCH(WM_PC_SCALAR, s, k_scal_init<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[0].p, ws.part[1].p, ws.src_of.p, ws.bb.p, ws.rho.p, ws.rr.p,
+                                 ws.active.p, ws.flags.p));
+  WM_LAUNCH(WM_PC_SCALAR, s, k_fill_tile_active<<<nblk(tiles, 128), 128, 0, s>>>(tiles, ws.tile_active.p, ws.active.p));
   WM_CUDA(cudaGetLastError());
   // p = z
   WM_CUDA(cudaMemsetAsync(ws.beta.p, 0, nsys_pad * sizeof(double), s));
-  k_update_p<T><<<grid, kBlk, 0, s>>>(N, ch, ws.beta.p, z, ws.p.p, ws.tile_active.p);
+  WM_LAUNCH(WM_PC_CGVEC, s, k_update_p<T><<<grid, kBlk, 0, s>>>(N, ch, ws.beta.p, z, ws.p.p, ws.tile_active.p));
   double rtol2 = bt.rtol * bt.rtol;
   int it = 0;
   int n_active = nsys_pad;
   for (it = 1; it <= bt.max_iter; ++it) {
-    k_apply_pq<<<grid, kBlk, 0, s>>>(N, L0.W, ch, L0.d_col.p, L0.d_S64.p, L0.d_M64.p, ws.sigma.p, ws.p.p, ws.q.p,
-                                     ws.tile_active.p, ws.part[0].p);
-    k_scal_alpha<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[0].p, ws.rho.p, ws.active.p, ws.alpha.p, ws.flags.p);
-    k_update_xr<<<grid, kBlk, 0, s>>>(N, ch, ws.alpha.p, ws.p.p, ws.q.p, ws.x.p, ws.r.p, ws.tile_active.p,
-                                      ws.part[0].p);
-    WM_CUDA(cudaMemsetAsync(ws.counters.p, 0, sizeof(int), s));
+    WM_LAUNCH(WM_PC_APPLY64, s, k_apply_pq<<<grid, kBlk, 0, s>>>(N, L0.W, ch, L0.d_col.p, L0.d_S64.p, L0.d_M64.p, ws.sigma.p, ws.p.p, ws.q.p,
+                                     ws.tile_active.p, ws.part[0].p));
+    units(WM_PC_APPLY64, bt, 16.0 * N, 4.0 * L0.nnz + 4.0 * N);
+    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_alpha<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[0].p, ws.rho.p, ws.active.p, ws.alpha.p, ws.flags.p));
+    WM_LAUNCH(WM_PC_CGVEC, s, k_update_xr<<<grid, kBlk, 0, s>>>(N, ch, ws.alpha.p, ws.p.p, ws.q.p, ws.x.p, ws.r.p, ws.tile_active.p,
+                                      ws.part[0].p));
+    units(WM_PC_CGVEC, bt, 48.0 * N, 6.0 * N);
+    WM_CUDA(cudaMemsetAsync(ws.counters.p, 0, 3 * sizeof(int), s));
     // tiles stay flagged until all their lanes have converged
     WM_CUDA(cudaMemsetAsync(ws.tile_active.p, 0, tiles * sizeof(int), s));
-    k_scal_conv<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[0].p, ws.bb.p, rtol2, ws.rr.p, ws.active.p,
-                                   ws.tile_active.p, ws.counters.p, ws.flags.p);
+    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_conv<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[0].p, ws.bb.p, rtol2, ws.rr.p, ws.active.p,
+                                   ws.tile_active.p, ws.counters.p, ws.flags.p));
     WM_CUDA(cudaGetLastError());
-    WM_CUDA(cudaMemcpyAsync(ws.host_small, ws.counters.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    WM_CUDA(cudaMemcpyAsync(ws.host_small, ws.counters.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
     WM_CUDA(cudaStreamSynchronize(s));
     n_active = ws.host_small[0];
+    bt.active_tiles = ws.host_small[2];
     if (n_active == 0) break;
     WM_TRY(precondition<T>(h, ws, bt, &z, s));
-    k_dots_rz_zq<T><<<grid, kBlk, 0, s>>>(N, ch, ws.r.p, z, ws.q.p, ws.tile_active.p, ws.part[1].p, ws.part[2].p);
-    k_scal_beta<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[1].p, ws.part[2].p, ws.alpha.p, ws.active.p, ws.rho.p,
-                                   ws.beta.p, 0);
-    k_update_p<T><<<grid, kBlk, 0, s>>>(N, ch, ws.beta.p, z, ws.p.p, ws.tile_active.p);
+    WM_LAUNCH(WM_PC_CGVEC, s, k_dots_rz_zq<T><<<grid, kBlk, 0, s>>>(N, ch, ws.r.p, z, ws.q.p, ws.tile_active.p, ws.part[1].p, ws.part[2].p));
+    units(WM_PC_CGVEC, bt, (16.0 + sizeof(T)) * N, 4.0 * N);
+    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_beta<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[1].p, ws.part[2].p, ws.alpha.p, ws.active.p, ws.rho.p,
+                                   ws.beta.p, 0));
+    WM_LAUNCH(WM_PC_CGVEC, s, k_update_p<T><<<grid, kBlk, 0, s>>>(N, ch, ws.beta.p, z, ws.p.p, ws.tile_active.p));
+    units(WM_PC_CGVEC, bt, (16.0 + sizeof(T)) * N, 2.0 * N);
     WM_CUDA(cudaGetLastError());
   }
   res->iterations = std::min(it, bt.max_iter);
-  k_reduce_stats<<<1, 256, 0, s>>>(bt.nsys, ws.rr.p, ws.bb.p, ws.active.p, ws.statd.p, ws.counters.p + 1);
+  WM_LAUNCH(WM_PC_SCALAR, s, k_reduce_stats<<<1, 256, 0, s>>>(bt.nsys, ws.rr.p, ws.bb.p, ws.active.p, ws.statd.p, ws.counters.p + 1));
   WM_CUDA(cudaMemcpyAsync(ws.host_small + 2, ws.counters.p + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   WM_CUDA(cudaMemcpyAsync(ws.host_small + 4, ws.flags.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   double maxrel = 0.0;
@@ -814,11 +841,11 @@ int wm_vcycle_apply(const wm_hier* h, WorkSpace& ws, const Batch& bt, cudaStream
   if (bt.precision == WM_FP64) {
     double* z = nullptr;
     WM_TRY(precondition<double>(h, ws, bt, &z, s));
-    k_copy_tiles<<<nblk(n, 256), 256, 0, s>>>(n, z, ws.q.p);
+    WM_LAUNCH(WM_PC_SINC, s, k_copy_tiles<<<nblk(n, 256), 256, 0, s>>>(n, z, ws.q.p));
   } else {
     float* z = nullptr;
     WM_TRY(precondition<float>(h, ws, bt, &z, s));
-    k_widen<float><<<nblk(n, 256), 256, 0, s>>>(n, z, ws.q.p);
+    WM_LAUNCH(WM_PC_SINC, s, k_widen<float><<<nblk(n, 256), 256, 0, s>>>(n, z, ws.q.p));
   }
   WM_CUDA(cudaGetLastError());
   return WM_OK;
@@ -829,28 +856,28 @@ int wm_sinc_accumulate(const wm_hier* h, int ns, int g0, int g1, const double* c
   const wm_level& L0 = h->lv[0];
   int stiles = (ns + WM_LANES - 1) / WM_LANES;
   int gx = std::max(1, std::min(256, (L0.N + kWarps - 1) / kWarps));
-  k_sinc_accumulate<<<dim3(gx, stiles), kBlk, 0, s>>>(L0.N, ns, g0, g1, c_dev, x, v_tiled);
+  WM_LAUNCH(WM_PC_SINC, s, k_sinc_accumulate<<<dim3(gx, stiles), kBlk, 0, s>>>(L0.N, ns, g0, g1, c_dev, x, v_tiled));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
 
 int wm_copy(const double* a, double* b, size_t n, cudaStream_t s) {
   if (n == 0) return WM_OK;
-  k_copy_tiles<<<nblk(n, 256), 256, 0, s>>>(n, a, b);
+  WM_LAUNCH(WM_PC_SINC, s, k_copy_tiles<<<nblk(n, 256), 256, 0, s>>>(n, a, b));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
 
 int wm_convert_f32(const double* a, float* b, size_t n, cudaStream_t s) {
   if (n == 0) return WM_OK;
-  k_convert<float><<<nblk(n, 256), 256, 0, s>>>(n, a, b);
+  WM_LAUNCH(WM_PC_SINC, s, k_convert<float><<<nblk(n, 256), 256, 0, s>>>(n, a, b));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
 
 int wm_widen_f32(const float* a, double* b, size_t n, cudaStream_t s) {
   if (n == 0) return WM_OK;
-  k_widen<float><<<nblk(n, 256), 256, 0, s>>>(n, a, b);
+  WM_LAUNCH(WM_PC_SINC, s, k_widen<float><<<nblk(n, 256), 256, 0, s>>>(n, a, b));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }

@@ -28,6 +28,7 @@ struct Batch {
   int max_iter = 200;
   int degree = 2;     // Chebyshev degree of each smoothing sweep
   double cheb_ratio = 8.0;
+  mutable int active_tiles = 0;  // host copy of the active tile count (for work accounting)
   int chunks_for(int N) const;
 };
 
