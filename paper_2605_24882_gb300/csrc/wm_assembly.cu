@@ -202,6 +202,24 @@ __global__ void k_dense(int N, int W, const int32_t* __restrict__ col, const dou
   Md[(size_t)i * N + j] = M[tid];
 }
 
+__global__ void k_pack_rows(int64_t n, const int32_t* __restrict__ col, const double* __restrict__ S,
+                            const double* __restrict__ M, PkRow32* __restrict__ p32, PkRow64* __restrict__ p64) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  PkRow32 a;
+  a.col = col[t];
+  a.s = (float)S[t];
+  a.m = (float)M[t];
+  a.pad = 0;
+  p32[t] = a;
+  PkRow64 b;
+  b.s = S[t];
+  b.m = M[t];
+  b.col = col[t];
+  b.pad = 0;
+  p64[t] = b;
+}
+
 }  // namespace
 
 static GeoArgs geo_args(const wm_hier* h, const wm_level& L) {
@@ -265,6 +283,17 @@ int wm_k_dense_coarse(const wm_level& L, cudaStream_t s) {
   int64_t n = (int64_t)L.N * L.W;
   WM_LAUNCH(WM_PC_ASSEMBLY, s, k_dense<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L.N, L.W, L.d_col.p, L.d_S64.p, L.d_M64.p, L.d_Sdense.p,
                                                       L.d_Mdense.p));
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
+int wm_k_pack_rows(wm_level& L, cudaStream_t s) {
+  int64_t n = (int64_t)L.N * L.W;
+  WM_TRY(L.d_pk32.alloc(n));
+  WM_TRY(L.d_pk64.alloc(n));
+  WM_LAUNCH(WM_PC_ASSEMBLY, s, k_pack_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, L.d_col.p, L.d_S64.p,
+                                                                                      L.d_M64.p, L.d_pk32.p,
+                                                                                      L.d_pk64.p));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }

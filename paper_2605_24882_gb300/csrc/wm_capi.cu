@@ -33,10 +33,11 @@ WorkSpace& workspace(wm_hier_t h) {
   return *h->ws;
 }
 
-// per-system bytes of a batched solve (float64 outer vectors + V-cycle levels)
+// per-system bytes of a batched solve (float64 solution, recursion vectors and
+// V-cycle levels in the solve's precision)
 size_t bytes_per_system(const wm_hier* h, bool dbl) {
-  size_t b = (size_t)h->lv[0].N * 4 * sizeof(double);
   size_t e = dbl ? sizeof(double) : sizeof(float);
+  size_t b = (size_t)h->lv[0].N * (sizeof(double) + 3 * e);
   for (size_t l = 0; l < h->lv.size(); ++l) b += (size_t)h->lv[l].N * e * (l + 1 < h->lv.size() ? 5 : 3);
   return b;
 }
@@ -118,6 +119,8 @@ static void release_level(wm_level& L) {
   L.d_Pptr.release(); L.d_Pcol.release(); L.d_Rptr.release(); L.d_Rcol.release();
   L.d_Pval64.release(); L.d_Rval64.release(); L.d_Pval32.release(); L.d_Rval32.release();
   L.d_ng_ptr.release(); L.d_ng_idx.release(); L.d_Sdense.release(); L.d_Mdense.release();
+  L.d_pk32.release(); L.d_pk64.release(); L.d_P32.release(); L.d_R32.release(); L.d_P64.release();
+  L.d_R64.release();
 }
 
 extern "C" void wm_destroy_hier(wm_hier_t h) {
@@ -166,6 +169,7 @@ static int assemble(wm_hier* h, int n_levels, cudaStream_t s) {
     WM_TRY(wm_k_metric(h, L, s));
     WM_TRY(wm_k_element_matrices(h, L, s));
     WM_TRY(wm_k_assemble_rows(h, L, s));
+    WM_TRY(wm_k_pack_rows(L, s));
     // element matrices are not needed after assembly
     WM_CUDA(cudaStreamSynchronize(s));
     L.d_Se.release();
@@ -192,6 +196,23 @@ static int assemble(wm_hier* h, int n_levels, cudaStream_t s) {
     std::vector<float> Pf(Pv.begin(), Pv.end()), Rf(Rv.begin(), Rv.end());
     WM_TRY(F.d_Pval32.upload(Pf, s));
     WM_TRY(F.d_Rval32.upload(Rf, s));
+    {
+      std::vector<PkTr32> p32(Pc.size()), r32(Rc.size());
+      std::vector<PkTr64> p64(Pc.size()), r64(Rc.size());
+      for (size_t t = 0; t < Pc.size(); ++t) {
+        p32[t] = {Pc[t], (float)Pv[t]};
+        p64[t] = {Pv[t], Pc[t], 0};
+      }
+      for (size_t t = 0; t < Rc.size(); ++t) {
+        r32[t] = {Rc[t], (float)Rv[t]};
+        r64[t] = {Rv[t], Rc[t], 0};
+      }
+      WM_TRY(F.d_P32.upload(p32, s));
+      WM_TRY(F.d_R32.upload(r32, s));
+      WM_TRY(F.d_P64.upload(p64, s));
+      WM_TRY(F.d_R64.upload(r64, s));
+      WM_CUDA(cudaStreamSynchronize(s));
+    }
     WM_CUDA(cudaStreamSynchronize(s));
   }
   wm_level& C = h->lv[n_levels - 1];
@@ -394,9 +415,9 @@ extern "C" int wm_vcycle(wm_hier_t h, int n_vec, const double* sigma, const doub
   bt.precision = precision;
   bt.degree = smoother_degree;
   bt.cheb_ratio = cheb_ratio;
-  WM_TRY(wm_k_to_tiled(r, n_vec, h->lv[0].N, ws.r.p, tiles, s));
-  WM_TRY(wm_vcycle_apply(h, ws, bt, s));
-  WM_TRY(wm_k_from_tiled(ws.q.p, tiles, h->lv[0].N, z, n_vec, s));
+  WM_TRY(wm_k_to_tiled(r, n_vec, h->lv[0].N, ws.x.p, tiles, s));
+  WM_TRY(wm_vcycle_apply(h, ws, bt, ws.x.p, ws.x.p, s));
+  WM_TRY(wm_k_from_tiled(ws.x.p, tiles, h->lv[0].N, z, n_vec, s));
   WM_CUDA(cudaStreamSynchronize(s));
   return WM_OK;
 }
@@ -533,6 +554,7 @@ int run_pass(wm_hier_t h, WorkSpace& ws, const wm_sample_desc* d, const Pass& ps
     bt.max_iter = d->max_iter;
     bt.degree = d->smoother_degree;
     bt.cheb_ratio = d->cheb_ratio;
+    bt.replace_drop = dbl ? 0.0 : 1e-3;
     BatchResult br;
     WM_TRY(wm_solve_batch(h, ws, bt, rhs_t, &br, s));
     if (br.flags & 1) *worst = std::min(*worst, WM_ERR_NONFINITE);

@@ -62,6 +62,27 @@ struct DevBuf {
   }
 };
 
+// Packed operator rows and transfer entries: one aligned load per stored
+// nonzero (column index with both matrix values), so a warp reads a row entry
+// with one broadcast load instead of three.
+struct __align__(16) PkRow32 {
+  int col;
+  float s, m;
+  int pad;
+};
+struct __align__(8) PkRow64 {
+  double s, m;
+  int col, pad;
+};
+struct __align__(8) PkTr32 {
+  int col;
+  float v;
+};
+struct __align__(16) PkTr64 {
+  double v;
+  int col, pad;
+};
+
 // ---------------------------------------------------------------- host setup
 struct wm_geom {
   wm_geom_desc d;
@@ -100,6 +121,12 @@ struct wm_level {
   DevBuf<double> d_Pval64, d_Rval64;
   DevBuf<float> d_Pval32, d_Rval32;
   int nP = 0, nR = 0;  // rows of P (fine N) and R (coarse N)
+  // packed copies of the rows, the prolongation (fine rows) and restriction
+  // (coarse rows)
+  DevBuf<PkRow32> d_pk32;
+  DevBuf<PkRow64> d_pk64;
+  DevBuf<PkTr32> d_P32, d_R32;
+  DevBuf<PkTr64> d_P64, d_R64;
   // noise gather on this level: DOF i <- sum over (e, k) entries
   DevBuf<int32_t> d_ng_ptr, d_ng_idx;
   // coarse dense operators (coarsest level only): [N][N] row-major
@@ -134,6 +161,7 @@ int wm_k_metric(const wm_hier* h, const wm_level& L, cudaStream_t s);
 int wm_k_element_matrices(const wm_hier* h, wm_level& L, cudaStream_t s);
 int wm_k_assemble_rows(const wm_hier* h, wm_level& L, cudaStream_t s);
 int wm_k_dense_coarse(const wm_level& L, cudaStream_t s);
+int wm_k_pack_rows(wm_level& L, cudaStream_t s);
 
 // noise (wm_noise.cu)
 int wm_k_philox(const uint32_t* ctr, uint64_t key, uint32_t* out, int64_t n, cudaStream_t s);
@@ -165,7 +193,7 @@ int wm_k_from_tiled(const double* src, int tiles, int N, double* dst, int n, cud
 // Launch categories for live per-kernel timing (CUDA events around each launch
 // when enabled through wm_profile_enable) and launch counting (always on).
 enum {
-  WM_PC_APPLY64 = 0,   // float64 operator apply of the outer CG (q = A p)
+  WM_PC_APPLY64 = 0,   // operator apply of the outer CG (q = A p)
   WM_PC_SMOOTH0,       // Chebyshev smoothing steps on the finest level
   WM_PC_SMOOTHC,       // Chebyshev smoothing steps on coarser levels
   WM_PC_RESID0,        // residual before restriction, finest level
@@ -181,6 +209,7 @@ enum {
   WM_PC_LAYOUT,        // [n][N] <-> tiled layout conversions
   WM_PC_ASSEMBLY,      // metric, element matrices, rows
   WM_PC_APPLY,         // component operator applies
+  WM_PC_TRUERES,       // float64 true residual b - A x (residual replacement)
   WM_PC_COUNT
 };
 void wm_prof_begin(int cat, cudaStream_t s);

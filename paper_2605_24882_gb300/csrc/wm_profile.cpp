@@ -12,9 +12,9 @@
 namespace {
 
 const char* kNames[WM_PC_COUNT] = {
-    "apply_f64_outer", "smooth_level0", "smooth_coarse", "residual_level0", "residual_coarse", "restrict",
+    "apply_outer", "smooth_level0", "smooth_coarse", "residual_level0", "residual_coarse", "restrict",
     "prolong", "coarse_solve", "cg_vectors", "cg_scalars", "noise", "sinc_mass_copy", "setup_bounds_inverse",
-    "layout", "assembly", "apply_component"};
+    "layout", "assembly", "apply_component", "true_residual_f64"};
 
 constexpr int kPool = 1 << 16;
 

@@ -5,41 +5,82 @@
 // Chebyshev–Jacobi smoothing, restriction P^T and knot-insertion prolongation P,
 // and a dense float64 solve on the coarsest level.
 //
-// Precision: the outer iteration (x, r, p, q, dot products, step lengths) is
-// float64; the V-cycle runs in float64 (WM_FP64) or float32 (WM_MIXED).
+// Precision (WM_MIXED): the recursion (r, p, q, z) and the V-cycle are float32;
+// the solution x, the right-hand sides and the true residuals b - A x are
+// float64.  A system's recursive residual is replaced by its float64 true
+// residual whenever it has fallen by `replace_drop` since the last replacement,
+// and a system is declared converged only on its true residual, so float32
+// rounding in the recursion cannot stall or fake convergence.  WM_FP64 runs
+// the same algorithm with every vector in float64.
 //
-// Layout: systems are packed 32 per tile, vectors are [tiles][N][32]; grids are
-// (row chunks, tiles) with one warp per row and lane = system, so per-system
-// dot products are per-lane sums over rows followed by a fixed-order
-// reduction over warps and chunks (deterministic, no atomics).
+// Layout: systems are packed 32 per tile, vectors are [tiles][N][32]; lane =
+// system.  Operator kernels give each warp one row of kTPW tiles: a row's
+// packed entries (column, S, M) are loaded once per warp and reused for 4 x 32
+// systems.  Per-system dot products are per-lane sums over rows followed by a
+// fixed-order reduction over warps and chunks (deterministic, no atomics).
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "wm_solver.h"
 
 namespace {
 
 constexpr int kWarps = 8;
+constexpr int kTPW = 4;  // tiles per warp in operator kernels
 const dim3 kBlk(WM_LANES, kWarps);
 
-// ------------------------------------------------------------ dot partials
-// Block (chunk c, tile t) reduces rows [c*rows, (c+1)*rows) and writes
-// partial[(t * chunks + c) * 32 + lane].
-template <int ND>
-__device__ __forceinline__ void block_reduce_store(double (&acc)[ND], double* const* partial, int chunks) {
-  __shared__ double sm[ND][kWarps][WM_LANES];
-#pragma unroll
-  for (int d = 0; d < ND; ++d) sm[d][threadIdx.y][threadIdx.x] = acc[d];
-  __syncthreads();
-  if (threadIdx.y == 0) {
-#pragma unroll
-    for (int d = 0; d < ND; ++d) {
-      double s = 0.0;
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) s += sm[d][w][threadIdx.x];
-      partial[d][((size_t)blockIdx.y * chunks + blockIdx.x) * WM_LANES + threadIdx.x] = s;
-    }
-  }
+template <typename T>
+struct RowT;
+template <>
+struct RowT<float> {
+  using type = PkRow32;
+};
+template <>
+struct RowT<double> {
+  using type = PkRow64;
+};
+template <typename T>
+struct TrT;
+template <>
+struct TrT<float> {
+  using type = PkTr32;
+};
+template <>
+struct TrT<double> {
+  using type = PkTr64;
+};
+
+__device__ __forceinline__ PkRow32 ld_row(const PkRow32* p) {
+  int4 v = __ldg(reinterpret_cast<const int4*>(p));
+  PkRow32 r;
+  r.col = v.x;
+  r.s = __int_as_float(v.y);
+  r.m = __int_as_float(v.z);
+  r.pad = 0;
+  return r;
+}
+__device__ __forceinline__ PkRow64 ld_row(const PkRow64* p) {
+  PkRow64 r;
+  r.s = __ldg(&p->s);
+  r.m = __ldg(&p->m);
+  r.col = __ldg(&p->col);
+  r.pad = 0;
+  return r;
+}
+__device__ __forceinline__ PkTr32 ld_tr(const PkTr32* p) {
+  int2 v = __ldg(reinterpret_cast<const int2*>(p));
+  PkTr32 r;
+  r.col = v.x;
+  r.v = __int_as_float(v.y);
+  return r;
+}
+__device__ __forceinline__ PkTr64 ld_tr(const PkTr64* p) {
+  PkTr64 r;
+  r.v = __ldg(&p->v);
+  r.col = __ldg(&p->col);
+  r.pad = 0;
+  return r;
 }
 
 struct RowRange {
@@ -54,104 +95,238 @@ __device__ __forceinline__ RowRange chunk_rows(int N, int chunks) {
 
 __device__ __forceinline__ size_t vidx(int t, int N, int i) { return ((size_t)t * N + i) * WM_LANES + threadIdx.x; }
 
-// r = rhs(source sample), x = 0; partials (r, r)
-__global__ void k_gather_rhs(int N, int chunks, const double* __restrict__ src, const int* __restrict__ src_of,
-                             double* __restrict__ r, double* __restrict__ x, double* part_rr) {
+// Reduce acc[d][k] over the warps of the block and store the partial of tile
+// t = tile0 + k, chunk blockIdx.x, at part[d][(t * chunks + chunk) * 32 + lane].
+template <int ND, int NT>
+__device__ __forceinline__ void block_reduce_store(double (&acc)[ND][NT], double* const* part, int chunks, int tile0,
+                                                   int tiles) {
+  __shared__ double sm[ND][NT][kWarps][WM_LANES];
+#pragma unroll
+  for (int d = 0; d < ND; ++d)
+#pragma unroll
+    for (int k = 0; k < NT; ++k) sm[d][k][threadIdx.y][threadIdx.x] = acc[d][k];
+  __syncthreads();
+  if (threadIdx.y == 0) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d)
+#pragma unroll
+      for (int k = 0; k < NT; ++k) {
+        int t = tile0 + k;
+        if (t >= tiles) continue;
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) s += sm[d][k][w][threadIdx.x];
+        part[d][((size_t)t * chunks + blockIdx.x) * WM_LANES + threadIdx.x] = s;
+      }
+  }
+}
+
+// per-thread dot accumulator: products summed in T, flushed into double
+// every 16 rows (bounded float rounding, little float64 work)
+template <typename T>
+struct Acc {
+  double d = 0.0;
+  T f = 0;
+  int n = 0;
+  __device__ __forceinline__ void add(T v) {
+    f += v;
+    if (++n == 16) {
+      d += (double)f;
+      f = 0;
+      n = 0;
+    }
+  }
+  __device__ __forceinline__ double get() const { return d + (double)f; }
+};
+
+// ------------------------------------------------------------ outer CG kernels
+// r = rhs (of the system's sample), x = 0; partial ||rhs||^2 in float64
+template <typename T>
+__global__ void k_gather_rhs(int N, int chunks, int tiles, const double* __restrict__ src,
+                             const int* __restrict__ src_of, T* __restrict__ r, double* __restrict__ x,
+                             double* part_rr) {
   int t = blockIdx.y;
   int g = t * WM_LANES + threadIdx.x;
   int s = src_of[g];
   RowRange rr = chunk_rows(N, chunks);
-  double acc[1] = {0.0};
+  double acc[1][1] = {{0.0}};
   for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
     double v = s >= 0 ? src[((size_t)(s / WM_LANES) * N + i) * WM_LANES + (s % WM_LANES)] : 0.0;
-    r[vidx(t, N, i)] = v;
+    r[vidx(t, N, i)] = (T)v;
     x[vidx(t, N, i)] = 0.0;
-    acc[0] += v * v;
+    acc[0][0] += v * v;
   }
   double* parts[1] = {part_rr};
-  block_reduce_store<1>(acc, parts, chunks);
+  block_reduce_store<1, 1>(acc, parts, chunks, t, tiles);
 }
 
-// q = A p in float64 with partials (p, q)
-__global__ void __launch_bounds__(256) k_apply_pq(int N, int W, int chunks, const int32_t* __restrict__ col,
-                                                  const double* __restrict__ S, const double* __restrict__ M,
-                                                  const double* __restrict__ sigma, const double* __restrict__ p,
-                                                  double* __restrict__ q, const int* __restrict__ tile_active,
+// q = A p with partial (p, q), tiles kTPW per warp
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply_pq(int N, int W, int chunks, int tiles,
+                                                  const typename RowT<T>::type* __restrict__ pk,
+                                                  const double* __restrict__ sigma, const T* __restrict__ p,
+                                                  T* __restrict__ q, const int* __restrict__ tile_active,
                                                   double* part_pq) {
-  int t = blockIdx.y;
-  if (!tile_active[t]) return;
-  double sg = sigma[t * WM_LANES + threadIdx.x];
-  const double* pt = p + (size_t)t * N * WM_LANES;
-  RowRange rr = chunk_rows(N, chunks);
-  double acc[1] = {0.0};
-  for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
-    const int32_t* c = col + (size_t)i * W;
-    const double* s = S + (size_t)i * W;
-    const double* m = M + (size_t)i * W;
-    double aS = 0.0, aM = 0.0;
-    for (int w = 0; w < W; ++w) {
-      double v = pt[(size_t)c[w] * WM_LANES + threadIdx.x];
-      aS += s[w] * v;
-      aM += m[w] * v;
-    }
-    double qv = aS + sg * aM;
-    q[vidx(t, N, i)] = qv;
-    acc[0] += pt[(size_t)i * WM_LANES + threadIdx.x] * qv;
+  const int t0 = blockIdx.y * kTPW;
+  const int lane = threadIdx.x;
+  bool act[kTPW];
+  T sg[kTPW];
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < kTPW; ++k) {
+    int t = t0 + k;
+    act[k] = t < tiles && tile_active[t];
+    any |= act[k];
+    sg[k] = act[k] ? (T)sigma[t * WM_LANES + lane] : (T)0;
   }
+  if (!any) return;
+  RowRange rr = chunk_rows(N, chunks);
+  Acc<T> acc[kTPW];
+  for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
+    T aS[kTPW], aM[kTPW];
+#pragma unroll
+    for (int k = 0; k < kTPW; ++k) aS[k] = aM[k] = 0;
+    const auto* e = pk + (size_t)i * W;
+    for (int w = 0; w < W; ++w) {
+      auto en = ld_row(e + w);
+#pragma unroll
+      for (int k = 0; k < kTPW; ++k)
+        if (act[k]) {
+          T v = p[((size_t)(t0 + k) * N + en.col) * WM_LANES + lane];
+          aS[k] += en.s * v;
+          aM[k] += en.m * v;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kTPW; ++k)
+      if (act[k]) {
+        size_t o = vidx(t0 + k, N, i);
+        T qv = aS[k] + sg[k] * aM[k];
+        q[o] = qv;
+        acc[k].add(p[o] * qv);
+      }
+  }
+  double a[1][kTPW];
+#pragma unroll
+  for (int k = 0; k < kTPW; ++k) a[0][k] = acc[k].get();
   double* parts[1] = {part_pq};
-  block_reduce_store<1>(acc, parts, chunks);
+  block_reduce_store<1, kTPW>(a, parts, chunks, t0, tiles);
 }
 
-// x += alpha p, r -= alpha q; partials (r, r)
-__global__ void k_update_xr(int N, int chunks, const double* __restrict__ alpha, const double* __restrict__ p,
-                            const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r,
+// float64 true residual b - A x of the systems flagged for replacement; their
+// recursive residual is overwritten, partial ||b - A x||^2 in float64
+template <typename T>
+__global__ void __launch_bounds__(256) k_true_residual(int N, int W, int chunks, int tiles,
+                                                       const PkRow64* __restrict__ pk, const double* __restrict__ sigma,
+                                                       const double* __restrict__ x, const double* __restrict__ rhs,
+                                                       const int* __restrict__ src_of, const int* __restrict__ rep,
+                                                       const int* __restrict__ tile_rep, T* __restrict__ r,
+                                                       double* part_rr) {
+  const int t0 = blockIdx.y * kTPW;
+  const int lane = threadIdx.x;
+  bool act[kTPW];
+  double sg[kTPW];
+  int src[kTPW];
+  bool mine[kTPW];
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < kTPW; ++k) {
+    int t = t0 + k;
+    act[k] = t < tiles && tile_rep[t];
+    any |= act[k];
+    int g = t * WM_LANES + lane;
+    sg[k] = act[k] ? sigma[g] : 0.0;
+    src[k] = act[k] ? src_of[g] : -1;
+    mine[k] = act[k] && rep[g];
+  }
+  if (!any) return;
+  RowRange rr = chunk_rows(N, chunks);
+  double acc[1][kTPW];
+#pragma unroll
+  for (int k = 0; k < kTPW; ++k) acc[0][k] = 0.0;
+  for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
+    double aS[kTPW], aM[kTPW];
+#pragma unroll
+    for (int k = 0; k < kTPW; ++k) aS[k] = aM[k] = 0.0;
+    const PkRow64* e = pk + (size_t)i * W;
+    for (int w = 0; w < W; ++w) {
+      PkRow64 en = ld_row(e + w);
+#pragma unroll
+      for (int k = 0; k < kTPW; ++k)
+        if (act[k]) {
+          double v = x[((size_t)(t0 + k) * N + en.col) * WM_LANES + lane];
+          aS[k] += en.s * v;
+          aM[k] += en.m * v;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kTPW; ++k)
+      if (mine[k]) {
+        int s = src[k];
+        double b = s >= 0 ? rhs[((size_t)(s / WM_LANES) * N + i) * WM_LANES + (s % WM_LANES)] : 0.0;
+        double rt = b - (aS[k] + sg[k] * aM[k]);
+        r[vidx(t0 + k, N, i)] = (T)rt;
+        acc[0][k] += rt * rt;
+      }
+  }
+  double* parts[1] = {part_rr};
+  block_reduce_store<1, kTPW>(acc, parts, chunks, t0, tiles);
+}
+
+// x += alpha p (float64), r -= alpha q; partial (r, r)
+template <typename T>
+__global__ void k_update_xr(int N, int chunks, int tiles, const double* __restrict__ alpha, const T* __restrict__ p,
+                            const T* __restrict__ q, double* __restrict__ x, T* __restrict__ r,
                             const int* __restrict__ tile_active, double* part_rr) {
   int t = blockIdx.y;
   if (!tile_active[t]) return;
   double a = alpha[t * WM_LANES + threadIdx.x];
+  T af = (T)a;
   RowRange rr = chunk_rows(N, chunks);
-  double acc[1] = {0.0};
+  Acc<T> acc;
   for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
     size_t k = vidx(t, N, i);
-    x[k] += a * p[k];
-    double rv = r[k] - a * q[k];
+    x[k] += a * (double)p[k];
+    T rv = r[k] - af * q[k];
     r[k] = rv;
-    acc[0] += rv * rv;
+    acc.add(rv * rv);
   }
+  double v[1][1] = {{acc.get()}};
   double* parts[1] = {part_rr};
-  block_reduce_store<1>(acc, parts, chunks);
+  block_reduce_store<1, 1>(v, parts, chunks, t, tiles);
 }
 
 // partials (r, z) and (z, q)
-template <typename Tz>
-__global__ void k_dots_rz_zq(int N, int chunks, const double* __restrict__ r, const Tz* __restrict__ z,
-                             const double* __restrict__ q, const int* __restrict__ tile_active, double* part_rz,
+template <typename T>
+__global__ void k_dots_rz_zq(int N, int chunks, int tiles, const T* __restrict__ r, const T* __restrict__ z,
+                             const T* __restrict__ q, const int* __restrict__ tile_active, double* part_rz,
                              double* part_zq) {
   int t = blockIdx.y;
   if (!tile_active[t]) return;
   RowRange rr = chunk_rows(N, chunks);
-  double acc[2] = {0.0, 0.0};
+  Acc<T> a0, a1;
   for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
     size_t k = vidx(t, N, i);
-    double zv = (double)z[k];
-    acc[0] += r[k] * zv;
-    if (q) acc[1] += zv * q[k];
+    T zv = z[k];
+    a0.add(r[k] * zv);
+    if (q) a1.add(zv * q[k]);
   }
+  double v[2][1] = {{a0.get()}, {a1.get()}};
   double* parts[2] = {part_rz, part_zq};
-  block_reduce_store<2>(acc, parts, chunks);
+  block_reduce_store<2, 1>(v, parts, chunks, t, tiles);
 }
 
 // p = z + beta p
-template <typename Tz>
-__global__ void k_update_p(int N, int chunks, const double* __restrict__ beta, const Tz* __restrict__ z,
-                           double* __restrict__ p, const int* __restrict__ tile_active) {
+template <typename T>
+__global__ void k_update_p(int N, int chunks, const double* __restrict__ beta, const T* __restrict__ z,
+                           T* __restrict__ p, const int* __restrict__ tile_active) {
   int t = blockIdx.y;
   if (!tile_active[t]) return;
-  double b = beta[t * WM_LANES + threadIdx.x];
+  T b = (T)beta[t * WM_LANES + threadIdx.x];
   RowRange rr = chunk_rows(N, chunks);
   for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
     size_t k = vidx(t, N, i);
-    p[k] = (double)z[k] + b * p[k];
+    p[k] = z[k] + b * p[k];
   }
 }
 
@@ -164,14 +339,17 @@ __device__ __forceinline__ double sum_parts(const double* part, int chunks, int 
 }
 
 __global__ void k_scal_init(int nsys_pad, int chunks, const double* part_rr, const double* part_rz,
-                            const int* src_of, double* bb, double* rho, double* rr, int* active, int* flags) {
+                            const int* src_of, double* bb, double* rho, double* rr, double* rr_ref, int* active,
+                            int* restart, int* flags) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= nsys_pad) return;
   double b2 = sum_parts(part_rr, chunks, g);
   double rz = sum_parts(part_rz, chunks, g);
   bb[g] = b2;
   rr[g] = b2;
+  rr_ref[g] = b2;
   rho[g] = rz;
+  restart[g] = 0;
   int a = (src_of[g] >= 0 && b2 > 0.0) ? 1 : 0;
   if (a && !(isfinite(b2) && isfinite(rz))) {
     atomicOr(&flags[0], 1);
@@ -180,27 +358,65 @@ __global__ void k_scal_init(int nsys_pad, int chunks, const double* part_rr, con
   active[g] = a;
 }
 
-__global__ void k_scal_alpha(int nsys_pad, int chunks, const double* part_pq, const double* rho,
-                             const int* active, double* alpha, int* flags) {
+__global__ void k_scal_alpha(int nsys_pad, int chunks, const double* part_pq, const double* rho, int* active,
+                             double* alpha, int* flags) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= nsys_pad) return;
   double a = 0.0;
   if (active[g]) {
     double pq = sum_parts(part_pq, chunks, g);
-    if (pq > 0.0 && isfinite(pq)) a = rho[g] / pq;
-    else atomicOr(&flags[0], 2);
+    if (pq > 0.0 && isfinite(pq)) {
+      a = rho[g] / pq;
+    } else {
+      atomicOr(&flags[0], 2);
+      active[g] = 0;
+    }
   }
   alpha[g] = a;
 }
 
-// convergence test; counts active systems and flags active tiles
-__global__ void k_scal_conv(int nsys_pad, int chunks, const double* part_rr, const double* bb, double rtol2,
-                            double* rr, int* active, int* tile_active, int* counters, int* flags) {
+// recursive-residual test: flags systems for a float64 residual replacement;
+// counters: [0] active systems, [1] flagged systems, [2] active tiles, [3] flagged tiles
+__global__ void k_scal_conv(int nsys_pad, int chunks, const double* part_rr, const double* bb, const double* rr_ref,
+                            double rtol2, double drop2, double* rr, int* active, int* rep, int* tile_active,
+                            int* tile_rep, int* counters, int* flags) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= nsys_pad) return;
+  int need = 0;
   if (active[g]) {
     double r2 = sum_parts(part_rr, chunks, g);
     rr[g] = r2;
+    if (!isfinite(r2)) {
+      atomicOr(&flags[0], 1);
+      active[g] = 0;
+    } else {
+      need = (r2 <= drop2 * rr_ref[g] || r2 <= rtol2 * bb[g]) ? 1 : 0;
+    }
+  }
+  rep[g] = need;
+  int t = g / WM_LANES;
+  if (active[g]) {
+    atomicAdd(&counters[0], 1);
+    if (atomicExch(&tile_active[t], 1) == 0) atomicAdd(&counters[2], 1);
+  }
+  if (need) {
+    atomicAdd(&counters[1], 1);
+    if (atomicExch(&tile_rep[t], 1) == 0) atomicAdd(&counters[3], 1);
+  }
+}
+
+// after a replacement: new reference norm, restart flag, convergence on the
+// true residual; recounts active systems and tiles
+__global__ void k_scal_replace(int nsys_pad, int chunks, const double* part_rr, const double* bb, double rtol2,
+                               const int* rep, double* rr, double* rr_ref, int* active, int* restart, int* tile_active,
+                               int* counters, int* flags) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nsys_pad) return;
+  if (rep[g] && active[g]) {
+    double r2 = sum_parts(part_rr, chunks, g);
+    rr[g] = r2;
+    rr_ref[g] = r2;
+    restart[g] = 1;
     if (!isfinite(r2)) {
       atomicOr(&flags[0], 1);
       active[g] = 0;
@@ -215,16 +431,18 @@ __global__ void k_scal_conv(int nsys_pad, int chunks, const double* part_rr, con
 }
 
 __global__ void k_scal_beta(int nsys_pad, int chunks, const double* part_rz, const double* part_zq,
-                            const double* alpha, const int* active, double* rho, double* beta, int first) {
+                            const double* alpha, const int* active, int* restart, double* rho, double* beta) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= nsys_pad) return;
   double rz = sum_parts(part_rz, chunks, g);
   double b = 0.0;
-  if (active[g] && !first) {
+  if (active[g] && !restart[g]) {
     double zq = sum_parts(part_zq, chunks, g);
     double r0 = rho[g];
-    if (r0 != 0.0) b = -alpha[g] * zq / r0;  // Polak–Ribiere: (z, r_new - r_old) / (z_old, r_old)
+    // Polak–Ribiere: (z_new, r_new - r_old) / (z_old, r_old) with r_new - r_old = -alpha q
+    if (r0 != 0.0) b = -alpha[g] * zq / r0;
   }
+  restart[g] = 0;
   beta[g] = b;
   rho[g] = rz;
 }
@@ -238,7 +456,7 @@ __global__ void k_fill_tile_active(int tiles, int* tile_active, const int* activ
 }
 
 // ------------------------------------------------------------ V-cycle kernels
-// Chebyshev coefficients for step k on [lmax/ratio, hi*lmax]:
+// Chebyshev coefficients for step k on [lmax/ratio, 1.1 lmax]:
 // k = 0: d = D^{-1} res / theta; k >= 1: d = rho_k rho_{k-1} d + (2 rho_k/delta) D^{-1} res.
 struct ChebCoef {
   double c1, c2;
@@ -257,94 +475,182 @@ __device__ __forceinline__ ChebCoef cheb_coef(double lmax, double ratio, int k) 
   return {rk * rp, 2.0 * rk / delta};
 }
 
+struct TileSet {
+  bool act[kTPW];
+  bool any;
+};
+__device__ __forceinline__ TileSet tile_set(int t0, int tiles, const int* tile_active) {
+  TileSet ts;
+  ts.any = false;
+#pragma unroll
+  for (int k = 0; k < kTPW; ++k) {
+    int t = t0 + k;
+    ts.act[k] = t < tiles && tile_active[t];
+    ts.any |= ts.act[k];
+  }
+  return ts;
+}
+
 // first pre-smoothing step from z = 0: d = D^{-1} r / theta, z = d
-template <typename T, typename Tr>
-__global__ void k_cheb_first(int N, int chunks, const Tr* __restrict__ r, const T* __restrict__ dS,
+template <typename T>
+__global__ void k_cheb_first(int N, int chunks, int tiles, const T* __restrict__ r, const T* __restrict__ dS,
                              const T* __restrict__ dM, const double* __restrict__ sigma,
                              const double* __restrict__ lmax, const int* __restrict__ sid, double ratio,
                              T* __restrict__ d, T* __restrict__ z, const int* __restrict__ tile_active) {
-  int t = blockIdx.y;
-  if (!tile_active[t]) return;
-  int g = t * WM_LANES + threadIdx.x;
-  T sg = (T)sigma[g];
-  T c2 = (T)cheb_coef(lmax[sid[g]], ratio, 0).c2;
+  const int t0 = blockIdx.y * kTPW;
+  TileSet ts = tile_set(t0, tiles, tile_active);
+  if (!ts.any) return;
+  T sg[kTPW], c2[kTPW];
+#pragma unroll
+  for (int k = 0; k < kTPW; ++k) {
+    int g = (t0 + k) * WM_LANES + threadIdx.x;
+    sg[k] = ts.act[k] ? (T)sigma[g] : (T)0;
+    c2[k] = ts.act[k] ? (T)cheb_coef(lmax[sid[g]], ratio, 0).c2 : (T)0;
+  }
   RowRange rr = chunk_rows(N, chunks);
   for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
-    size_t k = vidx(t, N, i);
-    T dv = c2 * (T)r[k] / (dS[i] + sg * dM[i]);
-    d[k] = dv;
-    z[k] = dv;
+    T ds = dS[i], dm = dM[i];
+#pragma unroll
+    for (int k = 0; k < kTPW; ++k)
+      if (ts.act[k]) {
+        size_t o = vidx(t0 + k, N, i);
+        T dv = c2[k] * r[o] / (ds + sg[k] * dm);
+        d[o] = dv;
+        z[o] = dv;
+      }
   }
 }
 
 // Chebyshev step k with the residual r - A z_in:
 // d = c1 d + c2 D^{-1} (r - A z_in), z_out = z_in + d
-template <typename T, typename Tr>
-__global__ void __launch_bounds__(256) k_cheb_step(int N, int W, int chunks, int kstep, const int32_t* __restrict__ col,
-                                                   const T* __restrict__ S, const T* __restrict__ M,
+template <typename T>
+__global__ void __launch_bounds__(256) k_cheb_step(int N, int W, int chunks, int tiles, int kstep,
+                                                   const typename RowT<T>::type* __restrict__ pk,
                                                    const T* __restrict__ dS, const T* __restrict__ dM,
                                                    const double* __restrict__ sigma, const double* __restrict__ lmax,
-                                                   const int* __restrict__ sid, double ratio, const Tr* __restrict__ r,
+                                                   const int* __restrict__ sid, double ratio, const T* __restrict__ r,
                                                    const T* __restrict__ zin, T* __restrict__ d, T* __restrict__ zout,
                                                    const int* __restrict__ tile_active) {
-  int t = blockIdx.y;
-  if (!tile_active[t]) return;
-  int g = t * WM_LANES + threadIdx.x;
-  T sg = (T)sigma[g];
-  ChebCoef cf = cheb_coef(lmax[sid[g]], ratio, kstep);
-  T c1 = (T)cf.c1, c2 = (T)cf.c2;
-  const T* zt = zin + (size_t)t * N * WM_LANES;
+  const int t0 = blockIdx.y * kTPW;
+  const int lane = threadIdx.x;
+  TileSet ts = tile_set(t0, tiles, tile_active);
+  if (!ts.any) return;
+  T sg[kTPW], c1[kTPW], c2[kTPW];
+#pragma unroll
+  for (int k = 0; k < kTPW; ++k) {
+    int g = (t0 + k) * WM_LANES + lane;
+    ChebCoef cf = ts.act[k] ? cheb_coef(lmax[sid[g]], ratio, kstep) : ChebCoef{0.0, 0.0};
+    sg[k] = ts.act[k] ? (T)sigma[g] : (T)0;
+    c1[k] = (T)cf.c1;
+    c2[k] = (T)cf.c2;
+  }
   RowRange rr = chunk_rows(N, chunks);
   for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
-    const int32_t* c = col + (size_t)i * W;
-    const T* s = S + (size_t)i * W;
-    const T* m = M + (size_t)i * W;
-    T aS = 0, aM = 0;
+    T aS[kTPW], aM[kTPW];
+#pragma unroll
+    for (int k = 0; k < kTPW; ++k) aS[k] = aM[k] = 0;
+    const auto* e = pk + (size_t)i * W;
     for (int w = 0; w < W; ++w) {
-      T v = zt[(size_t)c[w] * WM_LANES + threadIdx.x];
-      aS += s[w] * v;
-      aM += m[w] * v;
+      auto en = ld_row(e + w);
+#pragma unroll
+      for (int k = 0; k < kTPW; ++k)
+        if (ts.act[k]) {
+          T v = zin[((size_t)(t0 + k) * N + en.col) * WM_LANES + lane];
+          aS[k] += en.s * v;
+          aM[k] += en.m * v;
+        }
     }
-    size_t k = vidx(t, N, i);
-    T res = (T)r[k] - (aS + sg * aM);
-    T dv = (kstep == 0 ? (T)0 : c1 * d[k]) + c2 * res / (dS[i] + sg * dM[i]);
-    d[k] = dv;
-    zout[k] = zt[(size_t)i * WM_LANES + threadIdx.x] + dv;
+    T ds = dS[i], dm = dM[i];
+#pragma unroll
+    for (int k = 0; k < kTPW; ++k)
+      if (ts.act[k]) {
+        size_t o = vidx(t0 + k, N, i);
+        T res = r[o] - (aS[k] + sg[k] * aM[k]);
+        T dv = (kstep == 0 ? (T)0 : c1[k] * d[o]) + c2[k] * res / (ds + sg[k] * dm);
+        d[o] = dv;
+        zout[o] = zin[o] + dv;
+      }
   }
 }
 
 // res = r - A z
-template <typename T, typename Tr>
-__global__ void __launch_bounds__(256) k_residual(int N, int W, int chunks, const int32_t* __restrict__ col,
-                                                  const T* __restrict__ S, const T* __restrict__ M,
-                                                  const double* __restrict__ sigma, const Tr* __restrict__ r,
+template <typename T>
+__global__ void __launch_bounds__(256) k_residual(int N, int W, int chunks, int tiles,
+                                                  const typename RowT<T>::type* __restrict__ pk,
+                                                  const double* __restrict__ sigma, const T* __restrict__ r,
                                                   const T* __restrict__ z, T* __restrict__ res,
                                                   const int* __restrict__ tile_active) {
-  int t = blockIdx.y;
-  if (!tile_active[t]) return;
-  T sg = (T)sigma[t * WM_LANES + threadIdx.x];
-  const T* zt = z + (size_t)t * N * WM_LANES;
+  const int t0 = blockIdx.y * kTPW;
+  const int lane = threadIdx.x;
+  TileSet ts = tile_set(t0, tiles, tile_active);
+  if (!ts.any) return;
+  T sg[kTPW];
+#pragma unroll
+  for (int k = 0; k < kTPW; ++k) sg[k] = ts.act[k] ? (T)sigma[(t0 + k) * WM_LANES + lane] : (T)0;
   RowRange rr = chunk_rows(N, chunks);
   for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
-    const int32_t* c = col + (size_t)i * W;
-    const T* s = S + (size_t)i * W;
-    const T* m = M + (size_t)i * W;
-    T aS = 0, aM = 0;
+    T aS[kTPW], aM[kTPW];
+#pragma unroll
+    for (int k = 0; k < kTPW; ++k) aS[k] = aM[k] = 0;
+    const auto* e = pk + (size_t)i * W;
     for (int w = 0; w < W; ++w) {
-      T v = zt[(size_t)c[w] * WM_LANES + threadIdx.x];
-      aS += s[w] * v;
-      aM += m[w] * v;
+      auto en = ld_row(e + w);
+#pragma unroll
+      for (int k = 0; k < kTPW; ++k)
+        if (ts.act[k]) {
+          T v = z[((size_t)(t0 + k) * N + en.col) * WM_LANES + lane];
+          aS[k] += en.s * v;
+          aM[k] += en.m * v;
+        }
     }
-    size_t k = vidx(t, N, i);
-    res[k] = (T)r[k] - (aS + sg * aM);
+#pragma unroll
+    for (int k = 0; k < kTPW; ++k)
+      if (ts.act[k]) {
+        size_t o = vidx(t0 + k, N, i);
+        res[o] = r[o] - (aS[k] + sg[k] * aM[k]);
+      }
+  }
+}
+
+// out (+)= T in over CSR rows with packed entries (restriction: =, prolongation: +=)
+template <typename T, bool ADD>
+__global__ void __launch_bounds__(256) k_transfer(int Nout, int Nin, int chunks, int tiles,
+                                                  const int32_t* __restrict__ ptr,
+                                                  const typename TrT<T>::type* __restrict__ ent,
+                                                  const T* __restrict__ in, T* __restrict__ out,
+                                                  const int* __restrict__ tile_active) {
+  const int t0 = blockIdx.y * kTPW;
+  const int lane = threadIdx.x;
+  TileSet ts = tile_set(t0, tiles, tile_active);
+  if (!ts.any) return;
+  RowRange rr = chunk_rows(Nout, chunks);
+  for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
+    T acc[kTPW];
+#pragma unroll
+    for (int k = 0; k < kTPW; ++k) acc[k] = 0;
+    for (int j = ptr[i]; j < ptr[i + 1]; ++j) {
+      auto en = ld_tr(ent + j);
+#pragma unroll
+      for (int k = 0; k < kTPW; ++k)
+        if (ts.act[k]) acc[k] += en.v * in[((size_t)(t0 + k) * Nin + en.col) * WM_LANES + lane];
+    }
+#pragma unroll
+    for (int k = 0; k < kTPW; ++k)
+      if (ts.act[k]) {
+        size_t o = ((size_t)(t0 + k) * Nout + i) * WM_LANES + lane;
+        if (ADD)
+          out[o] += acc[k];
+        else
+          out[o] = acc[k];
+      }
   }
 }
 
 // z = A_c^{-1} r on the coarsest level, in float64, with the inverse of the
 // system's shift
-template <typename T, typename Tr>
+template <typename T>
 __global__ void k_coarse_solve(int N, const double* __restrict__ Ainv, const int* __restrict__ sid,
-                               const Tr* __restrict__ r, T* __restrict__ z, const int* __restrict__ tile_active) {
+                               const T* __restrict__ r, T* __restrict__ z, const int* __restrict__ tile_active) {
   int t = blockIdx.y;
   if (!tile_active[t]) return;
   int g = t * WM_LANES + threadIdx.x;
@@ -387,7 +693,7 @@ __global__ void k_coarse_inverse(int N, const double* __restrict__ Sd, const dou
   for (int e = tid; e < N * N; e += nt) Ainv[(size_t)sidx * N * N + e] = A[e];
 }
 
-// power iteration helpers for lambda_max(D^{-1}(S + sigma M))
+// power iteration helpers for lambda_max(D^{-1}(S + sigma M)), float64
 __global__ void k_power_init(int N, double* v) {
   int t = blockIdx.y;
   for (int i = blockIdx.x * kWarps + threadIdx.y; i < N; i += gridDim.x * kWarps) {
@@ -400,32 +706,32 @@ __global__ void k_power_init(int N, double* v) {
 }
 
 // w = D^{-1} A v; partials (w, w), (v, v)
-__global__ void __launch_bounds__(256) k_power_step(int N, int W, int chunks, const int32_t* __restrict__ col,
-                                                    const double* __restrict__ S, const double* __restrict__ M,
-                                                    const double* __restrict__ dS, const double* __restrict__ dM,
-                                                    const double* __restrict__ sigma, const double* __restrict__ v,
-                                                    double* __restrict__ w, double* part_ww, double* part_vv) {
+__global__ void __launch_bounds__(256) k_power_step(int N, int W, int chunks, int tiles,
+                                                    const PkRow64* __restrict__ pk, const double* __restrict__ dS,
+                                                    const double* __restrict__ dM, const double* __restrict__ sigma,
+                                                    const double* __restrict__ v, double* __restrict__ w,
+                                                    double* part_ww, double* part_vv) {
   int t = blockIdx.y;
   double sg = sigma[t * WM_LANES + threadIdx.x];
   const double* vt = v + (size_t)t * N * WM_LANES;
   RowRange rr = chunk_rows(N, chunks);
-  double acc[2] = {0.0, 0.0};
+  double acc[2][1] = {{0.0}, {0.0}};
   for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
-    const int32_t* c = col + (size_t)i * W;
     double aS = 0.0, aM = 0.0;
     for (int k = 0; k < W; ++k) {
-      double x = vt[(size_t)c[k] * WM_LANES + threadIdx.x];
-      aS += S[(size_t)i * W + k] * x;
-      aM += M[(size_t)i * W + k] * x;
+      PkRow64 en = ld_row(pk + (size_t)i * W + k);
+      double x = vt[(size_t)en.col * WM_LANES + threadIdx.x];
+      aS += en.s * x;
+      aM += en.m * x;
     }
     double wv = (aS + sg * aM) / (dS[i] + sg * dM[i]);
     w[vidx(t, N, i)] = wv;
     double vv = vt[(size_t)i * WM_LANES + threadIdx.x];
-    acc[0] += wv * wv;
-    acc[1] += vv * vv;
+    acc[0][0] += wv * wv;
+    acc[1][0] += vv * vv;
   }
   double* parts[2] = {part_ww, part_vv};
-  block_reduce_store<2>(acc, parts, chunks);
+  block_reduce_store<2, 1>(acc, parts, chunks, t, tiles);
 }
 
 __global__ void k_power_scale(int N, int chunks, const double* part_ww, double* w) {
@@ -437,8 +743,7 @@ __global__ void k_power_scale(int N, int chunks, const double* part_ww, double* 
   for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) w[vidx(t, N, i)] *= inv;
 }
 
-__global__ void k_power_final(int nshift, int chunks, const double* part_ww, const double* part_vv,
-                              double* lmax) {
+__global__ void k_power_final(int nshift, int chunks, const double* part_ww, const double* part_vv, double* lmax) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= nshift) return;
   double ww = sum_parts(part_ww, chunks, g), vv = sum_parts(part_vv, chunks, g);
@@ -453,10 +758,9 @@ __global__ void k_sinc_accumulate(int N, int ns, int g0, int g1, const double* _
   int st = blockIdx.y;
   int s = st * WM_LANES + threadIdx.x;
   if (s >= ns) return;
-  int jlo = (g0 - s + ns - 1) / ns;
-  if (g0 - s <= 0) jlo = 0;
-  int jhi = (g1 - 1 - s) / ns;
   if (g1 - 1 - s < 0) return;
+  int jlo = g0 - s <= 0 ? 0 : (g0 - s + ns - 1) / ns;
+  int jhi = (g1 - 1 - s) / ns;
   for (int i = blockIdx.x * kWarps + threadIdx.y; i < N; i += gridDim.x * kWarps) {
     double acc = 0.0;
     for (int j = jlo; j <= jhi; ++j) {
@@ -467,7 +771,6 @@ __global__ void k_sinc_accumulate(int N, int ns, int g0, int g1, const double* _
   }
 }
 
-// copy x of systems g = s (one node) into a sample-tiled buffer
 __global__ void k_copy_tiles(size_t n, const double* __restrict__ a, double* __restrict__ b) {
   size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (k < n) b[k] = a[k];
@@ -511,6 +814,7 @@ __global__ void k_reduce_stats(int nsys, const double* rr, const double* bb, con
 }
 
 inline unsigned nblk(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+inline int groups(int tiles) { return (tiles + kTPW - 1) / kTPW; }
 
 }  // namespace
 
@@ -521,19 +825,19 @@ static inline void units(int cat, const Batch& bt, double b, double f) {
   double sys = (double)bt.active_tiles * WM_LANES;
   wm_prof_units(cat, b * sys, f * sys);
 }
+
 int Batch::chunks_for(int N) const {
-  // enough blocks to cover the GPU several times, at least 64 rows per chunk
-  int target = std::max(1, (152 * 8 + tiles - 1) / std::max(1, tiles));
-  int maxc = std::max(1, (N + 63) / 64);
-  return std::min(std::min(target, maxc), 64);
+  // row chunks per tile: at least 128 rows each, at most 64 (the partial-sum
+  // buffers); with tile groups this keeps thousands of blocks in flight
+  return std::max(1, std::min(64, (N + 127) / 128));
 }
 
 template <typename T>
-static T* lvbuf(VBuf& b);
+static T* vb(VBuf& b);
 template <>
-double* lvbuf<double>(VBuf& b) { return b.d.p; }
+double* vb<double>(VBuf& b) { return b.d.p; }
 template <>
-float* lvbuf<float>(VBuf& b) { return b.f.p; }
+float* vb<float>(VBuf& b) { return b.f.p; }
 
 int VBuf::alloc(size_t n, bool dbl) {
   if (dbl) return d.alloc(n);
@@ -544,9 +848,9 @@ int WorkSpace::reserve(const wm_hier* h, int tiles, int nshift, bool dbl) {
   const int L = (int)h->lv.size();
   size_t n0 = (size_t)tiles * h->lv[0].N * WM_LANES;
   WM_TRY(x.alloc(n0));
-  WM_TRY(r.alloc(n0));
-  WM_TRY(p.alloc(n0));
-  WM_TRY(q.alloc(n0));
+  WM_TRY(r.alloc(n0, dbl));
+  WM_TRY(p.alloc(n0, dbl));
+  WM_TRY(q.alloc(n0, dbl));
   lvl.resize(L);
   for (int l = 0; l < L; ++l) {
     size_t n = (size_t)tiles * h->lv[l].N * WM_LANES;
@@ -563,42 +867,50 @@ int WorkSpace::reserve(const wm_hier* h, int tiles, int nshift, bool dbl) {
   WM_TRY(sid.alloc(ns));
   WM_TRY(src_of.alloc(ns));
   WM_TRY(active.alloc(ns));
+  WM_TRY(rep.alloc(ns));
+  WM_TRY(restart.alloc(ns));
   WM_TRY(tile_active.alloc(tiles));
+  WM_TRY(tile_rep.alloc(tiles));
   WM_TRY(rho.alloc(ns));
   WM_TRY(alpha.alloc(ns));
   WM_TRY(beta.alloc(ns));
   WM_TRY(bb.alloc(ns));
   WM_TRY(rr.alloc(ns));
+  WM_TRY(rr_ref.alloc(ns));
   size_t np = (size_t)std::max(tiles, (nshift + WM_LANES - 1) / WM_LANES) * 64 * WM_LANES;
   for (int k = 0; k < 3; ++k) WM_TRY(part[k].alloc(np));
   WM_TRY(flags.alloc(4));
-  WM_TRY(counters.alloc(4));
+  WM_TRY(counters.alloc(8));
   WM_TRY(lmax.alloc((size_t)L * std::max(1, nshift)));
   const wm_level& C = h->lv[L - 1];
   WM_TRY(ainv.alloc((size_t)std::max(1, nshift) * C.N * C.N));
   WM_TRY(shifts.alloc(std::max(1, nshift)));
   WM_TRY(statd.alloc(2));
-  if (!host_small) {
-    WM_CUDA(cudaMallocHost((void**)&host_small, 64));
-  }
+  if (!host_small) WM_CUDA(cudaMallocHost((void**)&host_small, 64));
   return WM_OK;
 }
 
 void WorkSpace::release() {
-  x.release(); r.release(); p.release(); q.release();
+  x.release();
+  r.release();
+  p.release();
+  q.release();
   for (auto& l : lvl) {
-    l.za.d.release(); l.za.f.release(); l.zb.d.release(); l.zb.f.release();
-    l.d.d.release(); l.d.f.release(); l.res.d.release(); l.res.f.release();
-    l.r.d.release(); l.r.f.release();
+    l.za.release();
+    l.zb.release();
+    l.d.release();
+    l.res.release();
+    l.r.release();
   }
   lvl.clear();
-  sigma.release(); sid.release(); src_of.release(); active.release(); tile_active.release();
-  rho.release(); alpha.release(); beta.release(); bb.release(); rr.release();
+  sigma.release(); sid.release(); src_of.release(); active.release(); rep.release(); restart.release();
+  tile_active.release(); tile_rep.release();
+  rho.release(); alpha.release(); beta.release(); bb.release(); rr.release(); rr_ref.release();
   for (auto& pp : part) pp.release();
   flags.release(); counters.release(); lmax.release(); ainv.release(); shifts.release(); statd.release();
   for (auto& b : samp) b.release();
   noise_scratch.release();
-  pw_v.release(); pw_w.release(); pw_sigma.release();
+  pw_v.release(); pw_w.release(); pw_sigma.release(); coef.release();
   if (host_small) cudaFreeHost(host_small);
   host_small = nullptr;
 }
@@ -624,13 +936,14 @@ static int estimate_lmax(const wm_hier* h, WorkSpace& ws, const std::vector<doub
     double* v = ws.pw_v.p;
     double* w = ws.pw_w.p;
     for (int it = 0; it < 15; ++it) {
-      WM_LAUNCH(WM_PC_SETUP, s, k_power_step<<<dim3(ch, tiles), kBlk, 0, s>>>(Lv.N, Lv.W, ch, Lv.d_col.p, Lv.d_S64.p, Lv.d_M64.p,
-                                                    Lv.d_dS64.p, Lv.d_dM64.p, ws.pw_sigma.p, v, w, ws.part[0].p,
-                                                    ws.part[1].p));
+      WM_LAUNCH(WM_PC_SETUP, s, k_power_step<<<dim3(ch, tiles), kBlk, 0, s>>>(
+                                    Lv.N, Lv.W, ch, tiles, Lv.d_pk64.p, Lv.d_dS64.p, Lv.d_dM64.p, ws.pw_sigma.p, v, w,
+                                    ws.part[0].p, ws.part[1].p));
       if (it < 14) WM_LAUNCH(WM_PC_SETUP, s, k_power_scale<<<dim3(ch, tiles), kBlk, 0, s>>>(Lv.N, ch, ws.part[0].p, w));
       std::swap(v, w);
     }
-    WM_LAUNCH(WM_PC_SETUP, s, k_power_final<<<nblk(nsh, 128), 128, 0, s>>>(nsh, ch, ws.part[0].p, ws.part[1].p, ws.lmax.p + (size_t)l * nsh));
+    WM_LAUNCH(WM_PC_SETUP, s, k_power_final<<<nblk(nsh, 128), 128, 0, s>>>(nsh, ch, ws.part[0].p, ws.part[1].p,
+                                                                           ws.lmax.p + (size_t)l * nsh));
     WM_CUDA(cudaGetLastError());
   }
   return WM_OK;
@@ -647,72 +960,80 @@ int wm_prepare_shifts(const wm_hier* h, WorkSpace& ws, const std::vector<double>
     return WM_ERR_UNSUPPORTED;
   }
   WM_CUDA(cudaFuncSetAttribute(k_coarse_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  WM_LAUNCH(WM_PC_SETUP, s, k_coarse_inverse<<<nsh, 256, smem, s>>>(C.N, C.d_Sdense.p, C.d_Mdense.p, ws.shifts.p, ws.ainv.p));
+  WM_LAUNCH(WM_PC_SETUP, s, k_coarse_inverse<<<nsh, 256, smem, s>>>(C.N, C.d_Sdense.p, C.d_Mdense.p, ws.shifts.p,
+                                                                    ws.ainv.p));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
 
-// one V-cycle from level l: input residual rin (level 0: float64 outer residual
-// or the level's own buffer), returns the buffer holding z
 template <typename T>
-static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const void* rin, bool rin_double,
-                  T** zout, cudaStream_t s) {
+static const typename RowT<T>::type* rows_of(const wm_level& L);
+template <>
+const PkRow32* rows_of<float>(const wm_level& L) { return L.d_pk32.p; }
+template <>
+const PkRow64* rows_of<double>(const wm_level& L) { return L.d_pk64.p; }
+template <typename T>
+static const typename TrT<T>::type* P_of(const wm_level& L);
+template <>
+const PkTr32* P_of<float>(const wm_level& L) { return L.d_P32.p; }
+template <>
+const PkTr64* P_of<double>(const wm_level& L) { return L.d_P64.p; }
+template <typename T>
+static const typename TrT<T>::type* R_of(const wm_level& L);
+template <>
+const PkTr32* R_of<float>(const wm_level& L) { return L.d_R32.p; }
+template <>
+const PkTr64* R_of<double>(const wm_level& L) { return L.d_R64.p; }
+template <typename T>
+static const T* dS_of(const wm_level& L) {
+  return std::is_same<T, double>::value ? (const T*)L.d_dS64.p : (const T*)L.d_dS32.p;
+}
+template <typename T>
+static const T* dM_of(const wm_level& L) {
+  return std::is_same<T, double>::value ? (const T*)L.d_dM64.p : (const T*)L.d_dM32.p;
+}
+
+// one V-cycle from level l on residual rin, returns the buffer holding z
+template <typename T>
+static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const T* rin, T** zout, cudaStream_t s) {
   const int L = (int)h->lv.size();
   const wm_level& Lv = h->lv[l];
   LevelBufs& B = ws.lvl[l];
   const int* ta = ws.tile_active.p;
-  int tiles = bt.tiles;
-  int ch = bt.chunks_for(Lv.N);
-  dim3 grid(ch, tiles);
+  const int tiles = bt.tiles;
+  const int ch = bt.chunks_for(Lv.N);
+  const dim3 ggrid(ch, groups(tiles));
   const double* lmax = ws.lmax.p + (size_t)l * bt.nshift;
-  const T* S = std::is_same<T, double>::value ? (const T*)Lv.d_S64.p : (const T*)Lv.d_S32.p;
-  const T* M = std::is_same<T, double>::value ? (const T*)Lv.d_M64.p : (const T*)Lv.d_M32.p;
-  const T* dS = std::is_same<T, double>::value ? (const T*)Lv.d_dS64.p : (const T*)Lv.d_dS32.p;
-  const T* dM = std::is_same<T, double>::value ? (const T*)Lv.d_dM64.p : (const T*)Lv.d_dM32.p;
-  T* za = lvbuf<T>(B.za);
-  T* zb = lvbuf<T>(B.zb);
-  const double Rb = rin_double ? 8.0 : (double)sizeof(T), Tb = (double)sizeof(T);
+  const auto* pk = rows_of<T>(Lv);
+  const T* dS = dS_of<T>(Lv);
+  const T* dM = dM_of<T>(Lv);
+  T* za = vb<T>(B.za);
+  T* zb = vb<T>(B.zb);
+  const double Tb = (double)sizeof(T);
   const int csm = l == 0 ? WM_PC_SMOOTH0 : WM_PC_SMOOTHC;
   const int cre = l == 0 ? WM_PC_RESID0 : WM_PC_RESIDC;
   if (l == L - 1) {
     int gx = std::max(1, std::min(64, (Lv.N + kWarps - 1) / kWarps));
-    if (rin_double) {
-      WM_LAUNCH(WM_PC_COARSE, s, k_coarse_solve<T, double><<<dim3(gx, tiles), kBlk, 0, s>>>(
-                                     Lv.N, ws.ainv.p, ws.sid.p, (const double*)rin, za, ta));
-    } else {
-      WM_LAUNCH(WM_PC_COARSE, s, k_coarse_solve<T, T><<<dim3(gx, tiles), kBlk, 0, s>>>(
-                                     Lv.N, ws.ainv.p, ws.sid.p, (const T*)rin, za, ta));
-    }
-    units(WM_PC_COARSE, bt, (Rb + Tb) * Lv.N, 2.0 * Lv.N * Lv.N);
+    WM_LAUNCH(WM_PC_COARSE, s, k_coarse_solve<T><<<dim3(gx, tiles), kBlk, 0, s>>>(Lv.N, ws.ainv.p, ws.sid.p, rin, za,
+                                                                                   ta));
+    units(WM_PC_COARSE, bt, 2.0 * Tb * Lv.N, 2.0 * Lv.N * Lv.N);
     WM_CUDA(cudaGetLastError());
     *zout = za;
     return WM_OK;
   }
-  T* d = lvbuf<T>(B.d);
-  T* res = lvbuf<T>(B.res);
-  int nu = bt.degree;
-  double ratio = bt.cheb_ratio;
+  T* d = vb<T>(B.d);
+  T* res = vb<T>(B.res);
+  const int nu = bt.degree;
+  const double ratio = bt.cheb_ratio;
   auto cheb_step = [&](int k, const T* zin, T* zo) {
-    if (rin_double) {
-      WM_LAUNCH(csm, s, k_cheb_step<T, double><<<grid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, k, Lv.d_col.p, S, M, dS, dM,
-                                                                     ws.sigma.p, lmax, ws.sid.p, ratio,
-                                                                     (const double*)rin, zin, d, zo, ta));
-    } else {
-      WM_LAUNCH(csm, s, k_cheb_step<T, T><<<grid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, k, Lv.d_col.p, S, M, dS, dM,
-                                                                ws.sigma.p, lmax, ws.sid.p, ratio, (const T*)rin,
-                                                                zin, d, zo, ta));
-    }
-    units(csm, bt, (Rb + 4.0 * Tb) * Lv.N, 4.0 * Lv.nnz + 8.0 * Lv.N);
+    WM_LAUNCH(csm, s, k_cheb_step<T><<<ggrid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, tiles, k, pk, dS, dM, ws.sigma.p, lmax,
+                                                            ws.sid.p, ratio, rin, zin, d, zo, ta));
+    units(csm, bt, 5.0 * Tb * Lv.N, 4.0 * Lv.nnz + 8.0 * Lv.N);
   };
   // pre-smoothing from z = 0
-  if (rin_double) {
-    WM_LAUNCH(csm, s, k_cheb_first<T, double><<<grid, kBlk, 0, s>>>(Lv.N, ch, (const double*)rin, dS, dM, ws.sigma.p,
-                                                                    lmax, ws.sid.p, ratio, d, za, ta));
-  } else {
-    WM_LAUNCH(csm, s, k_cheb_first<T, T><<<grid, kBlk, 0, s>>>(Lv.N, ch, (const T*)rin, dS, dM, ws.sigma.p, lmax,
-                                                               ws.sid.p, ratio, d, za, ta));
-  }
-  units(csm, bt, (Rb + 2.0 * Tb) * Lv.N, 4.0 * Lv.N);
+  WM_LAUNCH(csm, s, k_cheb_first<T><<<ggrid, kBlk, 0, s>>>(Lv.N, ch, tiles, rin, dS, dM, ws.sigma.p, lmax, ws.sid.p,
+                                                           ratio, d, za, ta));
+  units(csm, bt, 3.0 * Tb * Lv.N, 4.0 * Lv.N);
   T* cur = za;
   T* oth = zb;
   for (int k = 1; k < nu; ++k) {
@@ -720,22 +1041,19 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
     std::swap(cur, oth);
   }
   // residual, restriction, coarse correction
-  if (rin_double) {
-    WM_LAUNCH(cre, s, k_residual<T, double><<<grid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, Lv.d_col.p, S, M, ws.sigma.p,
-                                                                  (const double*)rin, cur, res, ta));
-  } else {
-    WM_LAUNCH(cre, s, k_residual<T, T><<<grid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, Lv.d_col.p, S, M, ws.sigma.p,
-                                                             (const T*)rin, cur, res, ta));
-  }
-  units(cre, bt, (Rb + 2.0 * Tb) * Lv.N, 4.0 * Lv.nnz + 3.0 * Lv.N);
-  WM_CUDA(cudaGetLastError());
-  T* rc = lvbuf<T>(ws.lvl[l + 1].r);
-  WM_TRY(wm_k_restrict<T>(Lv, tiles, res, rc, ta, s));
-  units(WM_PC_RESTRICT, bt, Tb * (Lv.N + h->lv[l + 1].N), 2.0 * Lv.nnzP);
+  WM_LAUNCH(cre, s, k_residual<T><<<ggrid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, tiles, pk, ws.sigma.p, rin, cur, res, ta));
+  units(cre, bt, 3.0 * Tb * Lv.N, 4.0 * Lv.nnz + 3.0 * Lv.N);
+  const wm_level& Cv = h->lv[l + 1];
+  T* rc = vb<T>(ws.lvl[l + 1].r);
+  const int chc = bt.chunks_for(Cv.N);
+  WM_LAUNCH(WM_PC_RESTRICT, s, k_transfer<T, false><<<dim3(chc, groups(tiles)), kBlk, 0, s>>>(
+                                   Cv.N, Lv.N, chc, tiles, Lv.d_Rptr.p, R_of<T>(Lv), res, rc, ta));
+  units(WM_PC_RESTRICT, bt, Tb * (Lv.N + Cv.N), 2.0 * Lv.nnzP);
   T* zc = nullptr;
-  WM_TRY(vcycle<T>(h, ws, bt, l + 1, rc, false, &zc, s));
-  WM_TRY(wm_k_prolong_add<T>(Lv, tiles, zc, cur, ta, s));
-  units(WM_PC_PROLONG, bt, Tb * (2.0 * Lv.N + h->lv[l + 1].N), 2.0 * Lv.nnzP);
+  WM_TRY(vcycle<T>(h, ws, bt, l + 1, rc, &zc, s));
+  WM_LAUNCH(WM_PC_PROLONG, s, k_transfer<T, true><<<ggrid, kBlk, 0, s>>>(Lv.N, Cv.N, ch, tiles, Lv.d_Pptr.p,
+                                                                         P_of<T>(Lv), zc, cur, ta));
+  units(WM_PC_PROLONG, bt, Tb * (2.0 * Lv.N + Cv.N), 2.0 * Lv.nnzP);
   // post-smoothing
   for (int k = 0; k < nu; ++k) {
     cheb_step(k, cur, oth);
@@ -746,83 +1064,119 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   return WM_OK;
 }
 
-template <typename T>
-static int precondition(const wm_hier* h, WorkSpace& ws, const Batch& bt, T** z, cudaStream_t s) {
-  return vcycle<T>(h, ws, bt, 0, ws.r.p, true, z, s);
+static int set_all_tiles_active(WorkSpace& ws, int tiles, cudaStream_t s) {
+  std::vector<int> ones(tiles, 1);
+  WM_CUDA(cudaMemcpyAsync(ws.tile_active.p, ones.data(), tiles * sizeof(int), cudaMemcpyHostToDevice, s));
+  WM_CUDA(cudaStreamSynchronize(s));
+  return WM_OK;
 }
 
-// Batched flexible CG on the systems of `bt` (metadata already uploaded).
+// Batched flexible CG with float64 residual replacement on the systems of
+// `bt` (metadata already uploaded).
 template <typename T>
 static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* rhs_tiled, BatchResult* res,
                cudaStream_t s) {
   const wm_level& L0 = h->lv[0];
-  int N = L0.N, tiles = bt.tiles;
-  int ch = bt.chunks_for(N);
-  dim3 grid(ch, tiles);
-  int nsys_pad = tiles * WM_LANES;
-  unsigned sb = nblk(nsys_pad, 128);
+  const int N = L0.N, tiles = bt.tiles;
+  const int ch = bt.chunks_for(N);
+  const dim3 grid(ch, tiles), ggrid(ch, groups(tiles));
+  const int nsys_pad = tiles * WM_LANES;
+  const unsigned sb = nblk(nsys_pad, 128);
+  const double Tb = (double)sizeof(T);
+  T* r = vb<T>(ws.r);
+  T* p = vb<T>(ws.p);
+  T* q = vb<T>(ws.q);
+  int* cnt = ws.counters.p;
   WM_CUDA(cudaMemsetAsync(ws.flags.p, 0, 4 * sizeof(int), s));
-  WM_LAUNCH(WM_PC_CGVEC, s, k_gather_rhs<<<grid, kBlk, 0, s>>>(N, ch, rhs_tiled, ws.src_of.p, ws.r.p, ws.x.p, ws.part[0].p));
+  WM_LAUNCH(WM_PC_CGVEC, s, k_gather_rhs<T><<<grid, kBlk, 0, s>>>(N, ch, tiles, rhs_tiled, ws.src_of.p, r, ws.x.p,
+                                                                  ws.part[0].p));
   WM_CUDA(cudaGetLastError());
   bt.active_tiles = tiles;
-  units(WM_PC_CGVEC, bt, 24.0 * N, 2.0 * N);
-  // all tiles active for the first preconditioner application
-  {
-    std::vector<int> ones(tiles, 1);
-    WM_CUDA(cudaMemcpyAsync(ws.tile_active.p, ones.data(), tiles * sizeof(int), cudaMemcpyHostToDevice, s));
-  }
+  units(WM_PC_CGVEC, bt, (8.0 + 8.0 + Tb) * N, 2.0 * N);
+  WM_TRY(set_all_tiles_active(ws, tiles, s));
   T* z = nullptr;
-  WM_TRY(precondition<T>(h, ws, bt, &z, s));
-  WM_LAUNCH(WM_PC_CGVEC, s, k_dots_rz_zq<T><<<grid, kBlk, 0, s>>>(N, ch, ws.r.p, z, nullptr, ws.tile_active.p, ws.part[1].p, ws.part[2].p));
-  WM_LAUNCH(WM_PC_SCALAR, s, k_scal_init<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[0].p, ws.part[1].p, ws.src_of.p, ws.bb.p, ws.rho.p, ws.rr.p,
-                                 ws.active.p, ws.flags.p));
-  WM_LAUNCH(WM_PC_SCALAR, s, k_fill_tile_active<<<nblk(tiles, 128), 128, 0, s>>>(tiles, ws.tile_active.p, ws.active.p));
+  WM_TRY(vcycle<T>(h, ws, bt, 0, r, &z, s));
+  WM_LAUNCH(WM_PC_CGVEC, s, k_dots_rz_zq<T><<<grid, kBlk, 0, s>>>(N, ch, tiles, r, z, (const T*)nullptr,
+                                                                  ws.tile_active.p, ws.part[1].p, ws.part[2].p));
+  WM_LAUNCH(WM_PC_SCALAR, s, k_scal_init<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[0].p, ws.part[1].p, ws.src_of.p,
+                                                            ws.bb.p, ws.rho.p, ws.rr.p, ws.rr_ref.p, ws.active.p,
+                                                            ws.restart.p, ws.flags.p));
+  WM_LAUNCH(WM_PC_SCALAR, s, k_fill_tile_active<<<nblk(tiles, 128), 128, 0, s>>>(tiles, ws.tile_active.p,
+                                                                                  ws.active.p));
   WM_CUDA(cudaGetLastError());
   // p = z
   WM_CUDA(cudaMemsetAsync(ws.beta.p, 0, nsys_pad * sizeof(double), s));
-  WM_LAUNCH(WM_PC_CGVEC, s, k_update_p<T><<<grid, kBlk, 0, s>>>(N, ch, ws.beta.p, z, ws.p.p, ws.tile_active.p));
-  double rtol2 = bt.rtol * bt.rtol;
-  int it = 0;
-  int n_active = nsys_pad;
+  WM_LAUNCH(WM_PC_CGVEC, s, k_update_p<T><<<grid, kBlk, 0, s>>>(N, ch, ws.beta.p, z, p, ws.tile_active.p));
+  const double rtol2 = bt.rtol * bt.rtol;
+  const double drop2 = bt.replace_drop * bt.replace_drop;
+  int it = 0, n_rep_total = 0;
   for (it = 1; it <= bt.max_iter; ++it) {
-    WM_LAUNCH(WM_PC_APPLY64, s, k_apply_pq<<<grid, kBlk, 0, s>>>(N, L0.W, ch, L0.d_col.p, L0.d_S64.p, L0.d_M64.p, ws.sigma.p, ws.p.p, ws.q.p,
-                                     ws.tile_active.p, ws.part[0].p));
-    units(WM_PC_APPLY64, bt, 16.0 * N, 4.0 * L0.nnz + 4.0 * N);
-    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_alpha<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[0].p, ws.rho.p, ws.active.p, ws.alpha.p, ws.flags.p));
-    WM_LAUNCH(WM_PC_CGVEC, s, k_update_xr<<<grid, kBlk, 0, s>>>(N, ch, ws.alpha.p, ws.p.p, ws.q.p, ws.x.p, ws.r.p, ws.tile_active.p,
-                                      ws.part[0].p));
-    units(WM_PC_CGVEC, bt, 48.0 * N, 6.0 * N);
-    WM_CUDA(cudaMemsetAsync(ws.counters.p, 0, 3 * sizeof(int), s));
-    // tiles stay flagged until all their lanes have converged
+    WM_LAUNCH(WM_PC_APPLY64, s, k_apply_pq<T><<<ggrid, kBlk, 0, s>>>(N, L0.W, ch, tiles, rows_of<T>(L0), ws.sigma.p,
+                                                                     p, q, ws.tile_active.p, ws.part[0].p));
+    units(WM_PC_APPLY64, bt, 2.0 * Tb * N, 4.0 * L0.nnz + 4.0 * N);
+    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_alpha<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[0].p, ws.rho.p, ws.active.p,
+                                                               ws.alpha.p, ws.flags.p));
+    WM_LAUNCH(WM_PC_CGVEC, s, k_update_xr<T><<<grid, kBlk, 0, s>>>(N, ch, tiles, ws.alpha.p, p, q, ws.x.p, r,
+                                                                   ws.tile_active.p, ws.part[0].p));
+    units(WM_PC_CGVEC, bt, (16.0 + 4.0 * Tb) * N, 6.0 * N);
+    WM_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(int), s));
     WM_CUDA(cudaMemsetAsync(ws.tile_active.p, 0, tiles * sizeof(int), s));
-    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_conv<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[0].p, ws.bb.p, rtol2, ws.rr.p, ws.active.p,
-                                   ws.tile_active.p, ws.counters.p, ws.flags.p));
+    WM_CUDA(cudaMemsetAsync(ws.tile_rep.p, 0, tiles * sizeof(int), s));
+    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_conv<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[0].p, ws.bb.p, ws.rr_ref.p, rtol2,
+                                                              drop2, ws.rr.p, ws.active.p, ws.rep.p, ws.tile_active.p,
+                                                              ws.tile_rep.p, cnt, ws.flags.p));
     WM_CUDA(cudaGetLastError());
-    WM_CUDA(cudaMemcpyAsync(ws.host_small, ws.counters.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    WM_CUDA(cudaMemcpyAsync(ws.host_small, cnt, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
     WM_CUDA(cudaStreamSynchronize(s));
-    n_active = ws.host_small[0];
+    int n_active = ws.host_small[0];
+    int n_rep = ws.host_small[1];
+    int rep_tiles = ws.host_small[3];
     bt.active_tiles = ws.host_small[2];
+    if (n_rep > 0) {
+      // float64 true residual of the flagged systems
+      n_rep_total += n_rep;
+      WM_LAUNCH(WM_PC_TRUERES, s, k_true_residual<T><<<ggrid, kBlk, 0, s>>>(
+                                    N, L0.W, ch, tiles, L0.d_pk64.p, ws.sigma.p, ws.x.p, rhs_tiled, ws.src_of.p,
+                                    ws.rep.p, ws.tile_rep.p, r, ws.part[1].p));
+      {
+        int keep = bt.active_tiles;
+        bt.active_tiles = rep_tiles;
+        units(WM_PC_TRUERES, bt, (8.0 + 8.0 + Tb) * N, 4.0 * L0.nnz + 4.0 * N);
+        bt.active_tiles = keep;
+      }
+      WM_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(int), s));
+      WM_CUDA(cudaMemsetAsync(ws.tile_active.p, 0, tiles * sizeof(int), s));
+      WM_LAUNCH(WM_PC_SCALAR, s, k_scal_replace<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[1].p, ws.bb.p, rtol2,
+                                                                   ws.rep.p, ws.rr.p, ws.rr_ref.p, ws.active.p,
+                                                                   ws.restart.p, ws.tile_active.p, cnt, ws.flags.p));
+      WM_CUDA(cudaGetLastError());
+      WM_CUDA(cudaMemcpyAsync(ws.host_small, cnt, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      WM_CUDA(cudaStreamSynchronize(s));
+      n_active = ws.host_small[0];
+      bt.active_tiles = ws.host_small[2];
+    }
     if (n_active == 0) break;
-    WM_TRY(precondition<T>(h, ws, bt, &z, s));
-    WM_LAUNCH(WM_PC_CGVEC, s, k_dots_rz_zq<T><<<grid, kBlk, 0, s>>>(N, ch, ws.r.p, z, ws.q.p, ws.tile_active.p, ws.part[1].p, ws.part[2].p));
-    units(WM_PC_CGVEC, bt, (16.0 + sizeof(T)) * N, 4.0 * N);
-    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_beta<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[1].p, ws.part[2].p, ws.alpha.p, ws.active.p, ws.rho.p,
-                                   ws.beta.p, 0));
-    WM_LAUNCH(WM_PC_CGVEC, s, k_update_p<T><<<grid, kBlk, 0, s>>>(N, ch, ws.beta.p, z, ws.p.p, ws.tile_active.p));
-    units(WM_PC_CGVEC, bt, (16.0 + sizeof(T)) * N, 2.0 * N);
+    WM_TRY(vcycle<T>(h, ws, bt, 0, r, &z, s));
+    WM_LAUNCH(WM_PC_CGVEC, s, k_dots_rz_zq<T><<<grid, kBlk, 0, s>>>(N, ch, tiles, r, z, q, ws.tile_active.p,
+                                                                    ws.part[1].p, ws.part[2].p));
+    units(WM_PC_CGVEC, bt, 3.0 * Tb * N, 4.0 * N);
+    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_beta<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[1].p, ws.part[2].p, ws.alpha.p,
+                                                              ws.active.p, ws.restart.p, ws.rho.p, ws.beta.p));
+    WM_LAUNCH(WM_PC_CGVEC, s, k_update_p<T><<<grid, kBlk, 0, s>>>(N, ch, ws.beta.p, z, p, ws.tile_active.p));
+    units(WM_PC_CGVEC, bt, 3.0 * Tb * N, 2.0 * N);
     WM_CUDA(cudaGetLastError());
   }
   res->iterations = std::min(it, bt.max_iter);
-  WM_LAUNCH(WM_PC_SCALAR, s, k_reduce_stats<<<1, 256, 0, s>>>(bt.nsys, ws.rr.p, ws.bb.p, ws.active.p, ws.statd.p, ws.counters.p + 1));
-  WM_CUDA(cudaMemcpyAsync(ws.host_small + 2, ws.counters.p + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-  WM_CUDA(cudaMemcpyAsync(ws.host_small + 4, ws.flags.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-  double maxrel = 0.0;
+  res->replacements = n_rep_total;
+  WM_LAUNCH(WM_PC_SCALAR, s, k_reduce_stats<<<1, 256, 0, s>>>(bt.nsys, ws.rr.p, ws.bb.p, ws.active.p, ws.statd.p,
+                                                              cnt + 4));
+  WM_CUDA(cudaMemcpyAsync(ws.host_small + 4, cnt + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
+  WM_CUDA(cudaMemcpyAsync(ws.host_small + 6, ws.flags.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   WM_CUDA(cudaMemcpyAsync(&ws.host_d, ws.statd.p, sizeof(double), cudaMemcpyDeviceToHost, s));
   WM_CUDA(cudaStreamSynchronize(s));
-  maxrel = ws.host_d;
-  res->n_not_converged = ws.host_small[2];
-  res->max_rel_residual = maxrel;
-  res->flags = ws.host_small[4];
+  res->n_not_converged = ws.host_small[4];
+  res->max_rel_residual = ws.host_d;
+  res->flags = ws.host_small[6];
   return WM_OK;
 }
 
@@ -832,22 +1186,22 @@ int wm_solve_batch(const wm_hier* h, WorkSpace& ws, const Batch& bt, const doubl
   return fcg<float>(h, ws, bt, rhs_tiled, res, s);
 }
 
-int wm_vcycle_apply(const wm_hier* h, WorkSpace& ws, const Batch& bt, cudaStream_t s) {
-  // z of one V-cycle on ws.r into ws.q (float64)
+int wm_vcycle_apply(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r64, double* z64,
+                    cudaStream_t s) {
   size_t n = (size_t)bt.tiles * h->lv[0].N * WM_LANES;
-  std::vector<int> ones(bt.tiles, 1);
-  WM_CUDA(cudaMemcpyAsync(ws.tile_active.p, ones.data(), bt.tiles * sizeof(int), cudaMemcpyHostToDevice, s));
-  WM_CUDA(cudaStreamSynchronize(s));
+  bt.active_tiles = bt.tiles;
+  WM_TRY(set_all_tiles_active(ws, bt.tiles, s));
   if (bt.precision == WM_FP64) {
+    WM_TRY(wm_copy(r64, ws.r.d.p, n, s));
     double* z = nullptr;
-    WM_TRY(precondition<double>(h, ws, bt, &z, s));
-    WM_LAUNCH(WM_PC_SINC, s, k_copy_tiles<<<nblk(n, 256), 256, 0, s>>>(n, z, ws.q.p));
+    WM_TRY(vcycle<double>(h, ws, bt, 0, ws.r.d.p, &z, s));
+    WM_TRY(wm_copy(z, z64, n, s));
   } else {
+    WM_TRY(wm_convert_f32(r64, ws.r.f.p, n, s));
     float* z = nullptr;
-    WM_TRY(precondition<float>(h, ws, bt, &z, s));
-    WM_LAUNCH(WM_PC_SINC, s, k_widen<float><<<nblk(n, 256), 256, 0, s>>>(n, z, ws.q.p));
+    WM_TRY(vcycle<float>(h, ws, bt, 0, ws.r.f.p, &z, s));
+    WM_TRY(wm_widen_f32(z, z64, n, s));
   }
-  WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
 

@@ -3,12 +3,15 @@
 
 #include "wm_internal.h"
 
-// float or double buffer of a V-cycle level (only the one of the V-cycle's
-// precision is allocated)
+// float or double buffer (only the one of the solve's precision is allocated)
 struct VBuf {
   DevBuf<double> d;
   DevBuf<float> f;
   int alloc(size_t n, bool dbl);
+  void release() {
+    d.release();
+    f.release();
+  }
 };
 
 struct LevelBufs {
@@ -28,33 +31,39 @@ struct Batch {
   int max_iter = 200;
   int degree = 2;     // Chebyshev degree of each smoothing sweep
   double cheb_ratio = 8.0;
+  // float64 residual replacement once the recursive residual of a system has
+  // fallen by this factor since its last replacement (and always before a
+  // system is declared converged)
+  double replace_drop = 1e-3;
   mutable int active_tiles = 0;  // host copy of the active tile count (for work accounting)
   int chunks_for(int N) const;
 };
 
 struct BatchResult {
   int iterations = 0;
+  int replacements = 0;
   int n_not_converged = 0;
   double max_rel_residual = 0.0;
   int flags = 0;  // bit 0: non-finite value, bit 1: CG breakdown
 };
 
 struct WorkSpace {
-  DevBuf<double> x, r, p, q;  // outer float64 iterates [tiles][N0][32]
+  DevBuf<double> x;           // float64 solution [tiles][N0][32]
+  VBuf r, p, q;               // recursion in the V-cycle precision
   std::vector<LevelBufs> lvl;
-  DevBuf<double> sigma;   // per system shift
-  DevBuf<int> sid;        // per system shift index
-  DevBuf<int> src_of;     // per system right-hand-side sample (-1: padding)
-  DevBuf<int> active, tile_active;
-  DevBuf<double> rho, alpha, beta, bb, rr;
+  DevBuf<double> sigma;       // per system shift
+  DevBuf<int> sid;            // per system shift index
+  DevBuf<int> src_of;         // per system right-hand-side sample (-1: padding)
+  DevBuf<int> active, rep, restart, tile_active, tile_rep;
+  DevBuf<double> rho, alpha, beta, bb, rr, rr_ref;
   DevBuf<double> part[3];
   DevBuf<int> flags, counters;
   DevBuf<double> lmax, ainv, shifts, statd;
-  // sample-tiled float64 buffers: loads, integer iterate, field, pass rhs, scratch
+  // sample-tiled float64 buffers: loads, integer iterate, field, pass rhs, staging
   DevBuf<double> samp[5];
   DevBuf<double> noise_scratch;
   DevBuf<double> pw_v, pw_w, pw_sigma;
-  DevBuf<double> coef;  // sinc weights of the current pass
+  DevBuf<double> coef;        // sinc weights of the current pass
   int* host_small = nullptr;  // pinned
   double host_d = 0.0;
   int reserve(const wm_hier* h, int tiles, int nshift, bool dbl);
@@ -64,7 +73,10 @@ struct WorkSpace {
 int wm_prepare_shifts(const wm_hier* h, WorkSpace& ws, const std::vector<double>& shifts, cudaStream_t s);
 int wm_solve_batch(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* rhs_tiled, BatchResult* res,
                    cudaStream_t s);
-int wm_vcycle_apply(const wm_hier* h, WorkSpace& ws, const Batch& bt, cudaStream_t s);
+// one V-cycle on the float64 tiled residual `r64` (staged through ws.r) with
+// the result widened to float64 in `z64`
+int wm_vcycle_apply(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r64, double* z64,
+                    cudaStream_t s);
 int wm_sinc_accumulate(const wm_hier* h, int ns, int g0, int g1, const double* c_dev, const double* x,
                        double* v_tiled, cudaStream_t s);
 int wm_copy(const double* a, double* b, size_t n, cudaStream_t s);
