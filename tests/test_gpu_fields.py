@@ -118,3 +118,21 @@ def test_full_size_bench_workload_sampled(wm):
                            c["l_hi"], c["n_samples"], c["seed"], "mixed", c["rtol"], samples=[0, 255])
     assert err.max() < 1e-6, (err, st)
     assert st["n_systems"] == 256 * 72 and st["n_not_converged"] == 0
+
+
+def test_failure_reporting_not_converged_and_nonfinite(wm):
+    """Host-side fault injection: an iteration cap of 1 must report
+    NOT_CONVERGED (fields still written), NaN-poisoned loads NONFINITE."""
+    from paper_2605_24882_gb300 import _capi
+    hier = wm.Hierarchy(wm.Geometry("sphere", 2, 8), 3)
+    kw = dict(kappa=2.0, beta=0.75, sinc_k=0.4, l_lo=-5, l_hi=5, n_samples=3, seed=1, precision="mixed")
+    with pytest.raises(wm.WMError) as e:
+        hier.sample_fields(max_iter=1, **kw)
+    assert e.value.code == _capi.WM_ERR_NOT_CONVERGED
+    u, st = hier.sample_fields(max_iter=1, check_convergence=False, **kw)
+    assert st["n_not_converged"] > 0 and torch.isfinite(u).all()
+    b = hier.noise_loads(1, 3)
+    b[1, 7] = float("nan")
+    with pytest.raises(wm.WMError) as e:
+        hier.sample_fields(b=b, **kw)
+    assert e.value.code == _capi.WM_ERR_NONFINITE
