@@ -174,6 +174,24 @@ int wm_normals(uint64_t seed, int sample, int stream_id, int64_t q0, int64_t n,
  */
 int wm_noise_loads(wm_hier_t h, uint64_t seed, int n_samples, double* b, void* stream);
 
+/*
+ * wm_noise_loads without any device allocation, for callers that cannot
+ * allocate device memory (code inside a CUDA graph being captured, or a host
+ * framework whose allocator owns all device memory).  The paper has no
+ * counterpart: this is a packaging variant of wm_noise_loads with the same
+ * result (b: device [n_samples][N], caller-owned).  Its element-local scratch
+ * is a fixed file-scope device array of 2^22 doubles (32 MiB) that every GPU
+ * which loads the library holds until process exit; a call needs
+ * elements x (p+1)^2 x n_samples <= 2^22 and otherwise returns
+ * WM_ERR_INVALID_ARG without launching anything.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and caches it:
+ * make that first call before any stream capture.  Every call writes all the
+ * scratch it reads, so nothing needs to start at zero; all calls share the
+ * array, so calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race.  Stream-ordered, no synchronisation.
+ */
+int wm_noise_loads_noalloc(wm_hier_t h, uint64_t seed, int n_samples, double* b, void* stream);
+
 /* ---- the sampler ------------------------------------------------------------ */
 typedef struct {
   double kappa;         /* kappa > 0                                                 */

@@ -184,3 +184,79 @@ int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int s0, int ns, double* b_
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
+
+// ---------------------------------------------------------------- no-alloc entry
+// White-noise loads for callers that cannot allocate device memory (for
+// example code running inside a CUDA graph being captured, or a host framework
+// whose allocator owns all device memory).  The element-local contributions go
+// to a fixed file-scope device array instead of workspace memory; the loads are
+// gathered straight into the caller's [n][N] output.
+#include <mutex>
+
+#define WM_NOALLOC_SCRATCH_DOUBLES (1 << 22) /* 32 MiB, resident on every device that loads the library */
+
+static __device__ __align__(256) double g_noalloc_scratch[WM_NOALLOC_SCRATCH_DOUBLES];
+
+namespace {
+
+// b[s][i] = sum over the element functions containing i of their contributions
+__global__ void k_noise_gather_rows(int N, int ns, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                    const double* __restrict__ bl, double* __restrict__ b) {
+  int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)N * ns) return;
+  int s = (int)(tid / N);
+  int i = (int)(tid - (int64_t)s * N);
+  double acc = 0.0;
+  for (int t = ptr[i]; t < ptr[i + 1]; ++t) acc += bl[(size_t)idx[t] * ns + s];
+  b[(size_t)s * N + i] = acc;
+}
+
+// Device address of the scratch array, looked up once per device with that
+// device current (a host-side name of a __device__ array is not its address).
+int noalloc_scratch(double** out) {
+  static std::mutex mu;
+  static double* addr[256] = {};
+  int dev = 0;
+  WM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return WM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    WM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    addr[dev] = static_cast<double*>(p);
+  }
+  *out = addr[dev];
+  return WM_OK;
+}
+
+}  // namespace
+
+extern "C" int wm_noise_loads_noalloc(wm_hier_t h, uint64_t seed, int n_samples, double* b, void* stream) {
+  if (!h || n_samples < 0 || (n_samples > 0 && !b)) return WM_ERR_INVALID_ARG;
+  if (n_samples == 0) return WM_OK;
+  const wm_level& L = h->lv[0];
+  int64_t need = (int64_t)L.E * L.nk * n_samples;
+  if (need > (int64_t)WM_NOALLOC_SCRATCH_DOUBLES) {
+    wm_set_error("wm_noise_loads_noalloc: elements x (p+1)^2 x samples = %lld exceeds the fixed scratch of %d "
+                 "doubles; use fewer samples per call",
+                 (long long)need, WM_NOALLOC_SCRATCH_DOUBLES);
+    return WM_ERR_INVALID_ARG;
+  }
+  double* bl = nullptr;
+  WM_TRY(noalloc_scratch(&bl));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int64_t n1 = (int64_t)L.E * n_samples;
+  unsigned g1 = (unsigned)((n1 + 127) / 128);
+  switch (h->p) {
+    case 1: k_noise_local<1><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, n_samples, 0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, L.d_bv.p, bl); break;
+    case 2: k_noise_local<2><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, n_samples, 0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, L.d_bv.p, bl); break;
+    case 3: k_noise_local<3><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, n_samples, 0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, L.d_bv.p, bl); break;
+    case 4: k_noise_local<4><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, n_samples, 0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, L.d_bv.p, bl); break;
+    default: return WM_ERR_UNSUPPORTED;
+  }
+  WM_CUDA(cudaGetLastError());
+  int64_t n2 = (int64_t)L.N * n_samples;
+  k_noise_gather_rows<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(L.N, n_samples, L.d_ng_ptr.p, L.d_ng_idx.p, bl, b);
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
