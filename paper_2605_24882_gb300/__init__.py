@@ -233,18 +233,26 @@ def profile_read():
 
 
 class WMField(torch.autograd.Function):
-    """u = F(b, kappa): the fields of loads b; backward by the adjoint solves."""
+    """u = F(b, kappa): the fields of loads b [n_samples, N]; the backward pass
+    runs the adjoint solves (wm_sample_fields_backward) for dL/db and dL/dkappa.
+
+    ``kw`` holds the remaining sampler parameters (beta, sinc_k, l_lo, l_hi,
+    n_samples, precision, rtol, ...), without kappa and b.
+    """
 
     @staticmethod
     def forward(ctx, b, kappa, hier, kw):
         kappa_f = float(kappa)
-        u, _ = hier.sample_fields(b=b.contiguous(), kappa=kappa_f, **kw)
+        u, _ = hier.sample_fields(b=b.detach().contiguous(), kappa=kappa_f, **kw)
         ctx.save_for_backward(b)
         ctx.hier, ctx.kw, ctx.kappa = hier, kw, kappa_f
+        ctx.kappa_is_tensor = isinstance(kappa, torch.Tensor)
         return u
 
     @staticmethod
     def backward(ctx, grad_u):
         (b,) = ctx.saved_tensors
-        gb, gk = ctx.hier.sample_fields_backward(b.contiguous(), grad_u.contiguous(), kappa=ctx.kappa, **ctx.kw)
-        return gb, torch.tensor(gk, dtype=torch.float64), None, None
+        gb, gk = ctx.hier.sample_fields_backward(b.detach().contiguous(), grad_u.contiguous(), kappa=ctx.kappa,
+                                                 **ctx.kw)
+        gk_t = torch.tensor(gk, dtype=torch.float64) if ctx.kappa_is_tensor else None
+        return gb, gk_t, None, None

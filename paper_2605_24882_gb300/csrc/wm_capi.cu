@@ -512,61 +512,82 @@ struct Pass {
   int ns = 0;
 };
 
+// systems per batched solve: the caller's cap, else what fits 80% of free
+// memory (plus what the workspace already holds); extra_bytes per DOF-system
+// for callers that keep more per-system vectors (the adjoint)
+int64_t batch_size(wm_hier_t h, WorkSpace& ws, const wm_sample_desc* d, int64_t nsys, size_t extra_bytes) {
+  bool dbl = d->precision == WM_FP64;
+  size_t per = bytes_per_system(h, dbl) + extra_bytes * (size_t)h->lv[0].N;
+  int64_t maxsys = d->max_systems > 0 ? d->max_systems : 0;
+  if (maxsys == 0) {
+    size_t freeb = 0, totb = 0;
+    if (cudaMemGetInfo(&freeb, &totb) != cudaSuccess) {
+      cudaGetLastError();
+      freeb = 0;
+    }
+    size_t have = ws.x.n / std::max(1, h->lv[0].N);  // systems the workspace already holds
+    size_t budget = (size_t)(freeb * 0.8) + have * per;
+    maxsys = std::max<int64_t>(WM_LANES, (int64_t)(budget / per) / WM_LANES * WM_LANES);
+  }
+  int64_t per_batch = std::min<int64_t>(nsys, maxsys);
+  if (per_batch > WM_LANES) per_batch = per_batch / WM_LANES * WM_LANES;
+  return std::max<int64_t>(1, per_batch);
+}
+
+// one batched solve of the systems [g0, g1) of a pass (g = j * ns + s); the
+// solutions are left in ws.x
+int solve_range(wm_hier_t h, WorkSpace& ws, const wm_sample_desc* d, const Pass& ps, int64_t g0, int64_t g1,
+                const double* rhs_t, wm_stats* st, int* worst, cudaStream_t s) {
+  bool dbl = d->precision == WM_FP64;
+  int nj = (int)ps.sigma.size();
+  int nb = (int)(g1 - g0);
+  int tiles = (nb + WM_LANES - 1) / WM_LANES;
+  std::vector<double> sg(nb);
+  std::vector<int> sid(nb), src(nb);
+  for (int k = 0; k < nb; ++k) {
+    int64_t g = g0 + k;
+    int j = (int)(g / ps.ns);
+    sg[k] = ps.sigma[j];
+    sid[k] = j;
+    src[k] = (int)(g % ps.ns);
+  }
+  WM_TRY(set_batch_meta(ws, tiles, sg, sid, src, s));
+  Batch bt;
+  bt.tiles = tiles;
+  bt.nsys = nb;
+  bt.nshift = nj;
+  bt.precision = d->precision;
+  bt.rtol = d->rtol;
+  bt.max_iter = d->max_iter;
+  bt.degree = d->smoother_degree;
+  bt.cheb_ratio = d->cheb_ratio;
+  bt.replace_drop = dbl ? 0.0 : 1e-3;
+  BatchResult br;
+  WM_TRY(wm_solve_batch(h, ws, bt, rhs_t, &br, s));
+  if (br.flags & 1) *worst = std::min(*worst, WM_ERR_NONFINITE);
+  if ((br.n_not_converged > 0 || (br.flags & 2)) && *worst == WM_OK) *worst = WM_ERR_NOT_CONVERGED;
+  if (st) {
+    st->n_systems += nb;
+    st->n_batches += 1;
+    st->max_iterations = std::max(st->max_iterations, br.iterations);
+    st->total_iterations += br.iterations;
+    st->n_not_converged += br.n_not_converged;
+    st->max_rel_residual = std::max(st->max_rel_residual, br.max_rel_residual);
+  }
+  return WM_OK;
+}
+
 template <typename Sink>
 int run_pass(wm_hier_t h, WorkSpace& ws, const wm_sample_desc* d, const Pass& ps, const double* rhs_t,
              wm_stats* st, int* worst, Sink sink, cudaStream_t s) {
   int nj = (int)ps.sigma.size();
   int64_t nsys = (int64_t)nj * ps.ns;
-  bool dbl = d->precision == WM_FP64;
-  int64_t maxsys = d->max_systems > 0 ? d->max_systems : 0;
-  if (maxsys == 0) {
-    size_t freeb = 0, totb = 0;
-    WM_CUDA(cudaMemGetInfo(&freeb, &totb));
-    size_t have = ws.x.n / std::max(1, h->lv[0].N);  // systems the workspace already holds
-    size_t budget = (size_t)(freeb * 0.8) + have * bytes_per_system(h, dbl);
-    maxsys = std::max<int64_t>(WM_LANES, (int64_t)(budget / bytes_per_system(h, dbl)) / WM_LANES * WM_LANES);
-  }
-  int64_t per_batch = std::min<int64_t>(nsys, maxsys);
-  if (per_batch > WM_LANES) per_batch = per_batch / WM_LANES * WM_LANES;
-  int tiles_max = (int)((per_batch + WM_LANES - 1) / WM_LANES);
-  WM_TRY(ws.reserve(h, tiles_max, nj, dbl));
+  int64_t per_batch = batch_size(h, ws, d, nsys, 0);
+  WM_TRY(ws.reserve(h, (int)((per_batch + WM_LANES - 1) / WM_LANES), nj, d->precision == WM_FP64));
   WM_TRY(wm_prepare_shifts(h, ws, ps.sigma, s));
   for (int64_t g0 = 0; g0 < nsys; g0 += per_batch) {
     int64_t g1 = std::min(nsys, g0 + per_batch);
-    int nb = (int)(g1 - g0);
-    int tiles = (nb + WM_LANES - 1) / WM_LANES;
-    std::vector<double> sg(nb);
-    std::vector<int> sid(nb), src(nb);
-    for (int k = 0; k < nb; ++k) {
-      int64_t g = g0 + k;
-      int j = (int)(g / ps.ns);
-      sg[k] = ps.sigma[j];
-      sid[k] = j;
-      src[k] = (int)(g % ps.ns);
-    }
-    WM_TRY(set_batch_meta(ws, tiles, sg, sid, src, s));
-    Batch bt;
-    bt.tiles = tiles;
-    bt.nsys = nb;
-    bt.nshift = nj;
-    bt.precision = d->precision;
-    bt.rtol = d->rtol;
-    bt.max_iter = d->max_iter;
-    bt.degree = d->smoother_degree;
-    bt.cheb_ratio = d->cheb_ratio;
-    bt.replace_drop = dbl ? 0.0 : 1e-3;
-    BatchResult br;
-    WM_TRY(wm_solve_batch(h, ws, bt, rhs_t, &br, s));
-    if (br.flags & 1) *worst = std::min(*worst, WM_ERR_NONFINITE);
-    if (br.n_not_converged > 0 || (br.flags & 2)) *worst = std::min(*worst, (*worst == WM_OK ? WM_ERR_NOT_CONVERGED : *worst));
-    if (st) {
-      st->n_systems += nb;
-      st->n_batches += 1;
-      st->max_iterations = std::max(st->max_iterations, br.iterations);
-      st->total_iterations += br.iterations;
-      st->n_not_converged += br.n_not_converged;
-      st->max_rel_residual = std::max(st->max_rel_residual, br.max_rel_residual);
-    }
+    WM_TRY(solve_range(h, ws, d, ps, g0, g1, rhs_t, st, worst, s));
     WM_TRY(sink((int)g0, (int)g1, s));
   }
   return WM_OK;
@@ -695,9 +716,133 @@ extern "C" int wm_sample_fields_batched(int n_inst, const wm_hier_t* h, const wm
   return worst;
 }
 
+// Adjoint of the sampler for a scalar loss L(u): with A_l = S + sigma_l M
+// symmetric, dL/dr_s = sum_l c_l A_l^{-1} dL/du_s and
+// dL/dkappa = -2 kappa sum_{l,s} c_l z_{l,s}^T M x_{l,s} (x: forward solutions,
+// z: adjoint solutions; sigma_l = e^{y_l} + kappa^2).  Through the integer part
+// r = M w_n, w_i = A0^{-1} M w_{i-1}, w_1 = A0^{-1} b: lambda_n = A0^{-1} M dL/dr,
+// lambda_{i-1} = A0^{-1} M lambda_i, dL/db = lambda_1, and each solve adds
+// -2 kappa lambda_i^T M w_i.  Each batch of shifted systems is solved forward
+// (its solutions kept as the batch checkpoint) and then adjoint.
 extern "C" int wm_sample_fields_backward(wm_hier_t h, const wm_sample_desc* d, const double* b, const double* grad_u,
                                          double* grad_b, double* grad_kappa, void* stream) {
-  (void)h; (void)d; (void)b; (void)grad_u; (void)grad_b; (void)grad_kappa; (void)stream;
-  wm_set_error("backward not built yet");
-  return WM_ERR_UNSUPPORTED;
+  WM_TRY(validate_desc(h, d));
+  if (!b || !grad_u) return WM_ERR_INVALID_ARG;
+  Plan P;
+  WM_TRY(make_plan(d, P));
+  if (P.passes > 1) {
+    wm_set_error("backward supports one fractional pass (standard split)");
+    return WM_ERR_UNSUPPORTED;
+  }
+  int ns = d->n_samples;
+  if (ns == 0) {
+    if (grad_kappa) *grad_kappa = 0.0;
+    return WM_OK;
+  }
+  if (!is_device_ptr(b) || !is_device_ptr(grad_u) || (grad_b && !is_device_ptr(grad_b))) {
+    wm_set_error("backward takes device buffers");
+    return WM_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = as_stream(stream);
+  const wm_level& L0 = h->lv[0];
+  const int N = L0.N;
+  const int stiles = (ns + WM_LANES - 1) / WM_LANES;
+  const size_t sn = (size_t)stiles * N * WM_LANES;
+  const double kappa = d->kappa;
+  WorkSpace& ws = workspace(h);
+  for (int k = 0; k < 4; ++k) WM_TRY(ws.samp[k].alloc(sn));
+  double* b_t = ws.samp[0].p;   // loads
+  double* g_t = ws.samp[1].p;   // dL/du
+  double* dr = ws.samp[2].p;    // dL/dr accumulator, then lambda
+  double* tmp = ws.samp[3].p;   // M-products
+  WM_TRY(wm_k_to_tiled(b, ns, N, b_t, stiles, s));
+  WM_TRY(wm_k_to_tiled(grad_u, ns, N, g_t, stiles, s));
+  int worst = WM_OK;
+  double dk = 0.0;
+  std::vector<double> dots;
+  // forward integer chain, keeping every iterate
+  ws.chain.resize(P.n_int);
+  Pass ip;
+  ip.sigma = {kappa * kappa};
+  ip.ns = ns;
+  for (int i = 0; i < P.n_int; ++i) {
+    WM_TRY(ws.chain[i].alloc(sn));
+    const double* r = b_t;
+    if (i > 0) {
+      WM_TRY(wm_k_apply_mass64(L0, stiles, ws.chain[i - 1].p, tmp, nullptr, s));
+      r = tmp;
+    }
+    double* wi = ws.chain[i].p;
+    auto sink = [&](int g0, int g1, cudaStream_t ss) -> int {
+      size_t off = (size_t)(g0 / WM_LANES) * N * WM_LANES;
+      size_t n = (size_t)((g1 - g0 + WM_LANES - 1) / WM_LANES) * N * WM_LANES;
+      return wm_copy(ws.x.p, wi + off, n, ss);
+    };
+    WM_TRY(run_pass(h, ws, d, ip, r, nullptr, &worst, sink, s));
+  }
+  // fractional pass: forward then adjoint per batch
+  WM_CUDA(cudaMemsetAsync(dr, 0, sizeof(double) * sn, s));
+  if (P.passes == 1) {
+    // r = M w_n (or b); kept in tmp for the whole pass
+    const double* r = b_t;
+    if (P.n_int > 0) {
+      WM_TRY(wm_k_apply_mass64(L0, stiles, ws.chain[P.n_int - 1].p, tmp, nullptr, s));
+      r = tmp;
+    }
+    WM_TRY(ws.coef.upload(P.c, s));
+    Pass fp;
+    fp.sigma = P.sigma;
+    fp.ns = ns;
+    int nj = (int)P.sigma.size();
+    int64_t nsys = (int64_t)nj * ns;
+    int64_t per_batch = batch_size(h, ws, d, nsys, 2 * sizeof(double));
+    int tiles_max = (int)((per_batch + WM_LANES - 1) / WM_LANES);
+    WM_TRY(ws.reserve(h, tiles_max, nj, d->precision == WM_FP64));
+    WM_TRY(ws.ckpt.alloc((size_t)tiles_max * N * WM_LANES));
+    WM_TRY(ws.mx.alloc((size_t)tiles_max * N * WM_LANES));
+    WM_TRY(wm_prepare_shifts(h, ws, fp.sigma, s));
+    for (int64_t g0 = 0; g0 < nsys; g0 += per_batch) {
+      int64_t g1 = std::min(nsys, g0 + per_batch);
+      int tiles = (int)((g1 - g0 + WM_LANES - 1) / WM_LANES);
+      size_t n = (size_t)tiles * N * WM_LANES;
+      WM_TRY(solve_range(h, ws, d, fp, g0, g1, r, nullptr, &worst, s));
+      WM_TRY(wm_k_apply_mass64(L0, tiles, ws.x.p, ws.mx.p, nullptr, s));  // M x (checkpoint as M x)
+      WM_TRY(solve_range(h, ws, d, fp, g0, g1, g_t, nullptr, &worst, s));
+      WM_TRY(wm_sinc_accumulate(h, ns, (int)g0, (int)g1, ws.coef.p, ws.x.p, dr, s));
+      if (grad_kappa) {
+        WM_TRY(wm_system_dots(ws, tiles, N, ws.x.p, ws.mx.p, dots, s));
+        for (int64_t g = g0; g < g1; ++g) dk += -2.0 * kappa * P.c[(size_t)(g / ns)] * dots[(size_t)(g - g0)];
+      }
+      (void)n;
+    }
+  } else {
+    // integer beta: dL/dw_n = dL/du
+    WM_TRY(wm_copy(g_t, dr, sn, s));
+  }
+  // integer chain adjoint
+  if (P.n_int > 0) {
+    for (int i = P.n_int - 1; i >= 0; --i) {
+      // lambda_{i+1} = A0^{-1} (M * incoming), incoming = dL/dr for the last solve
+      const double* incoming = dr;
+      if (P.passes == 1 || i < P.n_int - 1) {
+        WM_TRY(wm_k_apply_mass64(L0, stiles, dr, tmp, nullptr, s));
+        incoming = tmp;
+      }
+      auto sink = [&](int g0, int g1, cudaStream_t ss) -> int {
+        size_t off = (size_t)(g0 / WM_LANES) * N * WM_LANES;
+        size_t nn = (size_t)((g1 - g0 + WM_LANES - 1) / WM_LANES) * N * WM_LANES;
+        return wm_copy(ws.x.p, dr + off, nn, ss);
+      };
+      WM_TRY(run_pass(h, ws, d, ip, incoming, nullptr, &worst, sink, s));
+      if (grad_kappa) {
+        WM_TRY(wm_k_apply_mass64(L0, stiles, ws.chain[i].p, tmp, nullptr, s));
+        WM_TRY(wm_system_dots(ws, stiles, N, dr, tmp, dots, s));
+        for (int g = 0; g < ns; ++g) dk += -2.0 * kappa * dots[g];
+      }
+    }
+  }
+  if (grad_b) WM_TRY(wm_k_from_tiled(dr, stiles, N, grad_b, ns, s));
+  WM_CUDA(cudaStreamSynchronize(s));
+  if (grad_kappa) *grad_kappa = dk;
+  return worst;
 }

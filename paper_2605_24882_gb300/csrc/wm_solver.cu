@@ -350,10 +350,13 @@ __global__ void k_scal_init(int nsys_pad, int chunks, const double* part_rr, con
   rr_ref[g] = b2;
   rho[g] = rz;
   restart[g] = 0;
-  int a = (src_of[g] >= 0 && b2 > 0.0) ? 1 : 0;
-  if (a && !(isfinite(b2) && isfinite(rz))) {
-    atomicOr(&flags[0], 1);
-    a = 0;
+  int a = 0;
+  if (src_of[g] >= 0) {
+    if (!(isfinite(b2) && isfinite(rz))) {
+      atomicOr(&flags[0], 1);  // a non-finite right-hand side or preconditioned residual
+    } else if (b2 > 0.0) {
+      a = 1;
+    }
   }
   active[g] = a;
 }
@@ -445,6 +448,12 @@ __global__ void k_scal_beta(int nsys_pad, int chunks, const double* part_rz, con
   restart[g] = 0;
   beta[g] = b;
   rho[g] = rz;
+}
+
+__global__ void k_sum_parts(int nsys_pad, int chunks, const double* part, double* out) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nsys_pad) return;
+  out[g] = sum_parts(part, chunks, g);
 }
 
 __global__ void k_fill_tile_active(int tiles, int* tile_active, const int* active) {
@@ -911,6 +920,9 @@ void WorkSpace::release() {
   for (auto& b : samp) b.release();
   noise_scratch.release();
   pw_v.release(); pw_w.release(); pw_sigma.release(); coef.release();
+  ckpt.release(); mx.release(); dots.release();
+  for (auto& c : chain) c.release();
+  chain.clear();
   if (host_small) cudaFreeHost(host_small);
   host_small = nullptr;
 }
@@ -1233,5 +1245,28 @@ int wm_widen_f32(const float* a, double* b, size_t n, cudaStream_t s) {
   if (n == 0) return WM_OK;
   WM_LAUNCH(WM_PC_SINC, s, k_widen<float><<<nblk(n, 256), 256, 0, s>>>(n, a, b));
   WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
+int wm_system_dots(WorkSpace& ws, int tiles, int N, const double* a, const double* b, std::vector<double>& out,
+                   cudaStream_t s) {
+  Batch bt;
+  bt.tiles = tiles;
+  const int ch = bt.chunks_for(N);
+  const int nsys_pad = tiles * WM_LANES;
+  WM_TRY(ws.dots.alloc(nsys_pad));
+  if (ws.part[1].n < (size_t)tiles * ch * WM_LANES || ws.tile_active.n < (size_t)tiles) {
+    wm_set_error("workspace too small for the system dots");
+    return WM_ERR_INVALID_ARG;
+  }
+  WM_TRY(set_all_tiles_active(ws, tiles, s));
+  WM_LAUNCH(WM_PC_SINC, s, k_dots_rz_zq<double><<<dim3(ch, tiles), kBlk, 0, s>>>(
+                               N, ch, tiles, a, b, (const double*)nullptr, ws.tile_active.p, ws.part[1].p,
+                               ws.part[2].p));
+  WM_LAUNCH(WM_PC_SINC, s, k_sum_parts<<<nblk(nsys_pad, 128), 128, 0, s>>>(nsys_pad, ch, ws.part[1].p, ws.dots.p));
+  WM_CUDA(cudaGetLastError());
+  out.resize(nsys_pad);
+  WM_CUDA(cudaMemcpyAsync(out.data(), ws.dots.p, nsys_pad * sizeof(double), cudaMemcpyDeviceToHost, s));
+  WM_CUDA(cudaStreamSynchronize(s));
   return WM_OK;
 }

@@ -64,6 +64,8 @@ struct WorkSpace {
   DevBuf<double> noise_scratch;
   DevBuf<double> pw_v, pw_w, pw_sigma;
   DevBuf<double> coef;        // sinc weights of the current pass
+  DevBuf<double> ckpt, mx, dots;  // adjoint: forward solutions of a batch, M x, per-system dots
+  std::vector<DevBuf<double>> chain;  // adjoint: integer-part iterates w_1..w_n (sample-tiled)
   int* host_small = nullptr;  // pinned
   double host_d = 0.0;
   int reserve(const wm_hier* h, int tiles, int nshift, bool dbl);
@@ -80,5 +82,8 @@ int wm_vcycle_apply(const wm_hier* h, WorkSpace& ws, const Batch& bt, const doub
 int wm_sinc_accumulate(const wm_hier* h, int ns, int g0, int g1, const double* c_dev, const double* x,
                        double* v_tiled, cudaStream_t s);
 int wm_copy(const double* a, double* b, size_t n, cudaStream_t s);
+// out[g] = (a_g, b_g) for the 32*tiles systems of two tiled float64 vectors
+int wm_system_dots(WorkSpace& ws, int tiles, int N, const double* a, const double* b, std::vector<double>& out,
+                   cudaStream_t s);
 int wm_convert_f32(const double* a, float* b, size_t n, cudaStream_t s);
 int wm_widen_f32(const float* a, double* b, size_t n, cudaStream_t s);
