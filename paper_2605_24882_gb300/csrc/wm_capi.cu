@@ -5,6 +5,7 @@
 #include <new>
 
 #include "wm_solver.h"
+#include "wm_stencil.h"
 
 namespace {
 
@@ -121,6 +122,7 @@ static void release_level(wm_level& L) {
   L.d_ng_ptr.release(); L.d_ng_idx.release(); L.d_Sdense.release(); L.d_Mdense.release();
   L.d_pk32.release(); L.d_pk64.release(); L.d_P32.release(); L.d_R32.release(); L.d_P64.release();
   L.d_R64.release();
+  L.d_ext.release(); L.d_own.release(); L.d_csm32.release(); L.d_csm64.release();
 }
 
 extern "C" void wm_destroy_hier(wm_hier_t h) {
@@ -170,6 +172,7 @@ static int assemble(wm_hier* h, int n_levels, cudaStream_t s) {
     WM_TRY(wm_k_element_matrices(h, L, s));
     WM_TRY(wm_k_assemble_rows(h, L, s));
     WM_TRY(wm_k_pack_rows(L, s));
+    WM_TRY(wm_sten_build(g, h->np, L, s));
     // element matrices are not needed after assembly
     WM_CUDA(cudaStreamSynchronize(s));
     L.d_Se.release();
@@ -510,7 +513,18 @@ int validate_desc(wm_hier_t h, const wm_sample_desc* d) {
 struct Pass {
   std::vector<double> sigma;  // per node j
   int ns = 0;
+  int sid_base = 0;           // index of node 0's shift in the call's shift list
+  int nshift_total = 0;       // length of the call's shift list
 };
+
+// The call's shift list: the fractional shifts sigma_l (index j), then
+// kappa^2 of the integer part (index n_nodes) when there is one.  Smoother
+// bounds and coarse inverses are prepared once for the whole list.
+std::vector<double> call_shifts(const Plan& P, double kappa) {
+  std::vector<double> all = P.sigma;
+  if (P.n_int > 0) all.push_back(kappa * kappa);
+  return all;
+}
 
 // systems per batched solve: the caller's cap, else what fits 80% of free
 // memory (plus what the workspace already holds); extra_bytes per DOF-system
@@ -548,20 +562,20 @@ int solve_range(wm_hier_t h, WorkSpace& ws, const wm_sample_desc* d, const Pass&
     int64_t g = g0 + k;
     int j = (int)(g / ps.ns);
     sg[k] = ps.sigma[j];
-    sid[k] = j;
+    sid[k] = ps.sid_base + j;
     src[k] = (int)(g % ps.ns);
   }
   WM_TRY(set_batch_meta(ws, tiles, sg, sid, src, s));
   Batch bt;
   bt.tiles = tiles;
   bt.nsys = nb;
-  bt.nshift = nj;
+  bt.nshift = ps.nshift_total;
   bt.precision = d->precision;
   bt.rtol = d->rtol;
   bt.max_iter = d->max_iter;
   bt.degree = d->smoother_degree;
   bt.cheb_ratio = d->cheb_ratio;
-  bt.replace_drop = dbl ? 0.0 : 1e-3;
+  bt.replace_drop = dbl ? 0.0 : 1e-4;
   BatchResult br;
   WM_TRY(wm_solve_batch(h, ws, bt, rhs_t, &br, s));
   if (br.flags & 1) *worst = std::min(*worst, WM_ERR_NONFINITE);
@@ -582,9 +596,9 @@ int run_pass(wm_hier_t h, WorkSpace& ws, const wm_sample_desc* d, const Pass& ps
              wm_stats* st, int* worst, Sink sink, cudaStream_t s) {
   int nj = (int)ps.sigma.size();
   int64_t nsys = (int64_t)nj * ps.ns;
+  (void)nj;
   int64_t per_batch = batch_size(h, ws, d, nsys, 0);
-  WM_TRY(ws.reserve(h, (int)((per_batch + WM_LANES - 1) / WM_LANES), nj, d->precision == WM_FP64));
-  WM_TRY(wm_prepare_shifts(h, ws, ps.sigma, s));
+  WM_TRY(ws.reserve(h, (int)((per_batch + WM_LANES - 1) / WM_LANES), ps.nshift_total, d->precision == WM_FP64));
   for (int64_t g0 = 0; g0 < nsys; g0 += per_batch) {
     int64_t g1 = std::min(nsys, g0 + per_batch);
     WM_TRY(solve_range(h, ws, d, ps, g0, g1, rhs_t, st, worst, s));
@@ -645,10 +659,20 @@ static int sample_fields_impl(wm_hier_t h, const wm_sample_desc* d, double* u, d
     WM_TRY(wm_k_to_tiled(src, ns, N, b_t, stiles, s));
   }
   int worst = WM_OK;
+  const std::vector<double> shifts = call_shifts(P, d->kappa);
+  {
+    int64_t most = (int64_t)std::max<size_t>(1, P.sigma.size()) * ns;
+    int64_t per_batch = batch_size(h, ws, d, most, 0);
+    WM_TRY(ws.reserve(h, (int)((per_batch + WM_LANES - 1) / WM_LANES), (int)shifts.size(),
+                      d->precision == WM_FP64));
+    WM_TRY(wm_prepare_shifts(h, ws, shifts, s));
+  }
   // integer part: (S + kappa^2 M) w_1 = b, (S + kappa^2 M) w_i = M w_{i-1}
   Pass ip;
   ip.sigma = {d->kappa * d->kappa};
   ip.ns = ns;
+  ip.sid_base = (int)P.sigma.size();
+  ip.nshift_total = (int)shifts.size();
   for (int i = 0; i < P.n_int; ++i) {
     const double* r = b_t;
     if (i > 0) {
@@ -669,6 +693,8 @@ static int sample_fields_impl(wm_hier_t h, const wm_sample_desc* d, double* u, d
     Pass fp;
     fp.sigma = P.sigma;
     fp.ns = ns;
+    fp.sid_base = 0;
+    fp.nshift_total = (int)shifts.size();
     for (int pass = 0; pass < P.passes; ++pass) {
       const double* r = b_t;
       if (P.n_int > 0 || pass > 0) {
@@ -760,11 +786,18 @@ extern "C" int wm_sample_fields_backward(wm_hier_t h, const wm_sample_desc* d, c
   int worst = WM_OK;
   double dk = 0.0;
   std::vector<double> dots;
+  const std::vector<double> shifts = call_shifts(P, kappa);
+  int64_t per_batch_f = batch_size(h, ws, d, (int64_t)std::max<size_t>(1, P.sigma.size()) * ns, 2 * sizeof(double));
+  int tiles_max_f = (int)((per_batch_f + WM_LANES - 1) / WM_LANES);
+  WM_TRY(ws.reserve(h, tiles_max_f, (int)shifts.size(), d->precision == WM_FP64));
+  WM_TRY(wm_prepare_shifts(h, ws, shifts, s));
   // forward integer chain, keeping every iterate
   ws.chain.resize(P.n_int);
   Pass ip;
   ip.sigma = {kappa * kappa};
   ip.ns = ns;
+  ip.sid_base = (int)P.sigma.size();
+  ip.nshift_total = (int)shifts.size();
   for (int i = 0; i < P.n_int; ++i) {
     WM_TRY(ws.chain[i].alloc(sn));
     const double* r = b_t;
@@ -793,14 +826,13 @@ extern "C" int wm_sample_fields_backward(wm_hier_t h, const wm_sample_desc* d, c
     Pass fp;
     fp.sigma = P.sigma;
     fp.ns = ns;
+    fp.sid_base = 0;
+    fp.nshift_total = (int)shifts.size();
     int nj = (int)P.sigma.size();
     int64_t nsys = (int64_t)nj * ns;
-    int64_t per_batch = batch_size(h, ws, d, nsys, 2 * sizeof(double));
-    int tiles_max = (int)((per_batch + WM_LANES - 1) / WM_LANES);
-    WM_TRY(ws.reserve(h, tiles_max, nj, d->precision == WM_FP64));
-    WM_TRY(ws.ckpt.alloc((size_t)tiles_max * N * WM_LANES));
+    int64_t per_batch = per_batch_f;
+    int tiles_max = tiles_max_f;
     WM_TRY(ws.mx.alloc((size_t)tiles_max * N * WM_LANES));
-    WM_TRY(wm_prepare_shifts(h, ws, fp.sigma, s));
     for (int64_t g0 = 0; g0 < nsys; g0 += per_batch) {
       int64_t g1 = std::min(nsys, g0 + per_batch);
       int tiles = (int)((g1 - g0 + WM_LANES - 1) / WM_LANES);

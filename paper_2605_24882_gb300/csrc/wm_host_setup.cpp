@@ -450,3 +450,111 @@ extern "C" int wm_beta_plan(double beta, int split, int* n_int, double* beta_fra
   if (!n_int || !beta_frac || !n_passes) return WM_ERR_INVALID_ARG;
   return wm_split_beta(beta, split, n_int, beta_frac, n_passes);
 }
+
+// ------------------------------------------------------------ stencil form
+// Extended patch grids for the shared-memory stencil kernels.  Each patch's
+// local DOF grid is extended by a halo of width p: halo cells across a cube
+// edge are the adjacent face's DOFs at the same distance from the edge (the
+// integer cube lattice folded over the edge), halo cells of the periodic torus
+// wrap around, and cells beyond a cube corner are empty (-1).  Every operator
+// row is then a (2p+1)^2 stencil in the frame of the patch that owns the row
+// (the first patch in which the DOF occurs); slot[i][w] gives the stencil slot
+// of the stored entry w of row i (-1 for padding).  Returns WM_ERR_UNSUPPORTED
+// if some entry falls outside its owner's stencil window.
+int wm_host_stencil(const wm_geom_desc& g, int np, const wm_level& L, std::vector<int32_t>& ext,
+                    std::vector<int32_t>& own, std::vector<int16_t>& slot) {
+  const int p = g.degree;
+  const int nlu = L.nlu, nlv = L.nlv;
+  const int ELU = nlu + 2 * p, ELV = nlv + 2 * p;
+  const int SW = 2 * p + 1;
+  ext.assign((size_t)np * ELV * ELU, -1);
+  own.assign((size_t)np * nlv * nlu, -1);
+  if (g.kind == WM_TORUS) {
+    for (int ev = 0; ev < ELV; ++ev)
+      for (int eu = 0; eu < ELU; ++eu) {
+        int iu = ((eu - p) % nlu + nlu) % nlu, iv = ((ev - p) % nlv + nlv) % nlv;
+        ext[(size_t)ev * ELU + eu] = L.l2g[(size_t)iv * nlu + iu];
+      }
+    for (int t = 0; t < nlu * nlv; ++t) own[t] = L.l2g[t];
+  } else {
+    const int nl = nlu;
+    const int64_t span = 2 * nl + 1;
+    auto key = [&](const int c[3]) { return ((int64_t)(c[0] + nl) * span + (c[1] + nl)) * span + (c[2] + nl); };
+    std::unordered_map<int64_t, int32_t> lat;
+    lat.reserve((size_t)L.N * 2);
+    std::vector<char> seen(L.N, 0);
+    for (int m = 0; m < np; ++m)
+      for (int iv = 0; iv < nl; ++iv)
+        for (int iu = 0; iu < nl; ++iu) {
+          int c[3];
+          c[kFace[m][0]] = 2 * iu - (nl - 1);
+          c[kFace[m][1]] = 2 * iv - (nl - 1);
+          c[kFace[m][2]] = kFace[m][3] * (nl - 1);
+          int32_t gi = L.l2g[((size_t)m * nl + iv) * nl + iu];
+          lat[key(c)] = gi;
+          if (!seen[gi]) {
+            seen[gi] = 1;
+            own[((size_t)m * nl + iv) * nl + iu] = gi;
+          }
+        }
+    for (int m = 0; m < np; ++m)
+      for (int ev = 0; ev < ELV; ++ev)
+        for (int eu = 0; eu < ELU; ++eu) {
+          int iu = eu - p, iv = ev - p;
+          bool ou = iu < 0 || iu >= nl, ov = iv < 0 || iv >= nl;
+          if (ou && ov) continue;  // beyond a cube corner
+          int c[3];
+          c[kFace[m][0]] = 2 * iu - (nl - 1);
+          c[kFace[m][1]] = 2 * iv - (nl - 1);
+          c[kFace[m][2]] = kFace[m][3] * (nl - 1);
+          if (ou) {  // fold over the edge iu = 0 or iu = nl-1 onto the adjacent face
+            int k = iu < 0 ? -iu : iu - (nl - 1);
+            c[kFace[m][0]] = iu < 0 ? -(nl - 1) : (nl - 1);
+            c[kFace[m][2]] = kFace[m][3] * (nl - 1 - 2 * k);
+          }
+          if (ov) {
+            int k = iv < 0 ? -iv : iv - (nl - 1);
+            c[kFace[m][1]] = iv < 0 ? -(nl - 1) : (nl - 1);
+            c[kFace[m][2]] = kFace[m][3] * (nl - 1 - 2 * k);
+          }
+          auto it = lat.find(key(c));
+          if (it != lat.end()) ext[((size_t)m * ELV + ev) * ELU + eu] = it->second;
+        }
+  }
+  // owner frame of every row and the slot of each stored entry
+  std::vector<int32_t> om(L.N, -1), ou(L.N, -1), ov(L.N, -1);
+  for (int m = 0; m < np; ++m)
+    for (int iv = 0; iv < nlv; ++iv)
+      for (int iu = 0; iu < nlu; ++iu) {
+        int32_t gi = own[((size_t)m * nlv + iv) * nlu + iu];
+        if (gi >= 0) {
+          om[gi] = m;
+          ou[gi] = iu;
+          ov[gi] = iv;
+        }
+      }
+  slot.assign((size_t)L.N * L.W, -1);
+  std::vector<char> used(SW * SW);
+  for (int i = 0; i < L.N; ++i) {
+    if (om[i] < 0) return WM_ERR_UNSUPPORTED;
+    std::fill(used.begin(), used.end(), 0);
+    const int32_t* E = &ext[(size_t)om[i] * ELV * ELU];
+    for (int w = 0; w < L.W; ++w) {
+      int32_t j = L.col[(size_t)i * L.W + w];
+      bool dup = false;
+      for (int w2 = 0; w2 < w; ++w2)
+        if (L.col[(size_t)i * L.W + w2] == j) dup = true;
+      if (dup) continue;  // padding
+      int found = -1;
+      for (int s = 0; s < SW * SW && found < 0; ++s) {
+        int dv = s / SW - p, du = s % SW - p;
+        int eu = ou[i] + p + du, ev = ov[i] + p + dv;
+        if (!used[s] && E[(size_t)ev * ELU + eu] == j) found = s;
+      }
+      if (found < 0) return WM_ERR_UNSUPPORTED;
+      used[found] = 1;
+      slot[(size_t)i * L.W + w] = (int16_t)found;
+    }
+  }
+  return WM_OK;
+}

@@ -26,10 +26,10 @@ void wm_set_error(const char* fmt, ...);
     }                                                                             \
   } while (0)
 
-#define WM_TRY(expr)          \
-  do {                        \
-    int rc_ = (expr);         \
-    if (rc_ != WM_OK) return rc_; \
+#define WM_TRY(expr)                          \
+  do {                                        \
+    int wm_try_rc_ = (expr);                  \
+    if (wm_try_rc_ != WM_OK) return wm_try_rc_; \
   } while (0)
 
 template <typename T>
@@ -127,6 +127,14 @@ struct wm_level {
   DevBuf<PkRow64> d_pk64;
   DevBuf<PkTr32> d_P32, d_R32;
   DevBuf<PkTr64> d_P64, d_R64;
+  // stencil form (shared-memory kernels): extended patch grids with halo p,
+  // owner map, per-row (2p+1)^2 coefficient pairs (S, M); sten = false when the
+  // level uses the row (ELL) kernels only
+  bool sten = false;
+  int ELU = 0, ELV = 0, nbu = 0, nbv = 0;
+  DevBuf<int32_t> d_ext, d_own;
+  DevBuf<float2> d_csm32;
+  DevBuf<double2> d_csm64;
   // noise gather on this level: DOF i <- sum over (e, k) entries
   DevBuf<int32_t> d_ng_ptr, d_ng_idx;
   // coarse dense operators (coarsest level only): [N][N] row-major
@@ -153,6 +161,8 @@ int wm_host_prolongation(const wm_geom_desc& g, int np, const wm_level& fine, co
 void wm_host_tables(const wm_geom_desc& g, const std::vector<double>& gx, wm_level& L);
 void wm_host_assembly_map(const wm_level& L, std::vector<int32_t>& ptr, std::vector<int32_t>& idx);
 void wm_host_noise_map(const wm_level& L, std::vector<int32_t>& ptr, std::vector<int32_t>& idx);
+int wm_host_stencil(const wm_geom_desc& g, int np, const wm_level& L, std::vector<int32_t>& ext,
+                    std::vector<int32_t>& own, std::vector<int16_t>& slot);
 int wm_split_beta(double beta, int split, int* n, double* bp, int* passes);
 
 // ---------------------------------------------------------------- kernels

@@ -23,6 +23,7 @@
 #include <type_traits>
 
 #include "wm_solver.h"
+#include "wm_stencil.h"
 
 namespace {
 
@@ -484,6 +485,30 @@ __device__ __forceinline__ ChebCoef cheb_coef(double lmax, double ratio, int k) 
   return {rk * rp, 2.0 * rk / delta};
 }
 
+// (c1, c2) of every smoothing step for every level and shift, computed once
+// per batch in float64 (the smoothing kernels only load them)
+__global__ void k_cheb_table(int nlev, int nshift, int degree, double ratio, const double* __restrict__ lmax,
+                             float2* __restrict__ t32, double2* __restrict__ t64) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nlev * nshift * WM_MAX_CHEB) return;
+  int k = t % WM_MAX_CHEB;
+  int ls = t / WM_MAX_CHEB;
+  ChebCoef c = k < degree ? cheb_coef(lmax[ls], ratio, k) : ChebCoef{0.0, 0.0};
+  t32[t] = make_float2((float)c.c1, (float)c.c2);
+  t64[t] = make_double2(c.c1, c.c2);
+}
+
+template <typename T>
+struct C2T;
+template <>
+struct C2T<float> {
+  using type = float2;
+};
+template <>
+struct C2T<double> {
+  using type = double2;
+};
+
 struct TileSet {
   bool act[kTPW];
   bool any;
@@ -504,7 +529,7 @@ __device__ __forceinline__ TileSet tile_set(int t0, int tiles, const int* tile_a
 template <typename T>
 __global__ void k_cheb_first(int N, int chunks, int tiles, const T* __restrict__ r, const T* __restrict__ dS,
                              const T* __restrict__ dM, const double* __restrict__ sigma,
-                             const double* __restrict__ lmax, const int* __restrict__ sid, double ratio,
+                             const typename C2T<T>::type* __restrict__ ctab, const int* __restrict__ sid,
                              T* __restrict__ d, T* __restrict__ z, const int* __restrict__ tile_active) {
   const int t0 = blockIdx.y * kTPW;
   TileSet ts = tile_set(t0, tiles, tile_active);
@@ -514,7 +539,7 @@ __global__ void k_cheb_first(int N, int chunks, int tiles, const T* __restrict__
   for (int k = 0; k < kTPW; ++k) {
     int g = (t0 + k) * WM_LANES + threadIdx.x;
     sg[k] = ts.act[k] ? (T)sigma[g] : (T)0;
-    c2[k] = ts.act[k] ? (T)cheb_coef(lmax[sid[g]], ratio, 0).c2 : (T)0;
+    c2[k] = ts.act[k] ? ctab[sid[g] * WM_MAX_CHEB].y : (T)0;
   }
   RowRange rr = chunk_rows(N, chunks);
   for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
@@ -536,8 +561,9 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_cheb_step(int N, int W, int chunks, int tiles, int kstep,
                                                    const typename RowT<T>::type* __restrict__ pk,
                                                    const T* __restrict__ dS, const T* __restrict__ dM,
-                                                   const double* __restrict__ sigma, const double* __restrict__ lmax,
-                                                   const int* __restrict__ sid, double ratio, const T* __restrict__ r,
+                                                   const double* __restrict__ sigma,
+                                                   const typename C2T<T>::type* __restrict__ ctab,
+                                                   const int* __restrict__ sid, const T* __restrict__ r,
                                                    const T* __restrict__ zin, T* __restrict__ d, T* __restrict__ zout,
                                                    const int* __restrict__ tile_active) {
   const int t0 = blockIdx.y * kTPW;
@@ -548,10 +574,10 @@ __global__ void __launch_bounds__(256) k_cheb_step(int N, int W, int chunks, int
 #pragma unroll
   for (int k = 0; k < kTPW; ++k) {
     int g = (t0 + k) * WM_LANES + lane;
-    ChebCoef cf = ts.act[k] ? cheb_coef(lmax[sid[g]], ratio, kstep) : ChebCoef{0.0, 0.0};
+    typename C2T<T>::type cf = ctab[sid[g] * WM_MAX_CHEB + kstep];
     sg[k] = ts.act[k] ? (T)sigma[g] : (T)0;
-    c1[k] = (T)cf.c1;
-    c2[k] = (T)cf.c2;
+    c1[k] = ts.act[k] ? cf.x : (T)0;
+    c2[k] = ts.act[k] ? cf.y : (T)0;
   }
   RowRange rr = chunk_rows(N, chunks);
   for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
@@ -886,7 +912,8 @@ int WorkSpace::reserve(const wm_hier* h, int tiles, int nshift, bool dbl) {
   WM_TRY(bb.alloc(ns));
   WM_TRY(rr.alloc(ns));
   WM_TRY(rr_ref.alloc(ns));
-  size_t np = (size_t)std::max(tiles, (nshift + WM_LANES - 1) / WM_LANES) * 64 * WM_LANES;
+  size_t nch = (size_t)std::max(64, wm_sten_chunks(h->lv[0], h->np));
+  size_t np = (size_t)std::max(tiles, (nshift + WM_LANES - 1) / WM_LANES) * nch * WM_LANES;
   for (int k = 0; k < 3; ++k) WM_TRY(part[k].alloc(np));
   WM_TRY(flags.alloc(4));
   WM_TRY(counters.alloc(8));
@@ -920,6 +947,7 @@ void WorkSpace::release() {
   for (auto& b : samp) b.release();
   noise_scratch.release();
   pw_v.release(); pw_w.release(); pw_sigma.release(); coef.release();
+  cheb32.release(); cheb64.release();
   ckpt.release(); mx.release(); dots.release();
   for (auto& c : chain) c.release();
   chain.clear();
@@ -963,6 +991,10 @@ static int estimate_lmax(const wm_hier* h, WorkSpace& ws, const std::vector<doub
 
 int wm_prepare_shifts(const wm_hier* h, WorkSpace& ws, const std::vector<double>& shifts, cudaStream_t s) {
   int nsh = (int)shifts.size();
+  // bounds and inverses depend only on the hierarchy and the shifts: reuse them
+  // when a call repeats the previous shifts and the buffers were not reallocated
+  if (shifts == ws.prep_shifts && ws.lmax.p == ws.prep_lmax && ws.ainv.p == ws.prep_ainv && nsh > 0) return WM_OK;
+  ws.prep_shifts.clear();
   WM_TRY(ws.shifts.upload(shifts, s));
   WM_TRY(estimate_lmax(h, ws, shifts, s));
   const wm_level& C = h->lv.back();
@@ -975,6 +1007,9 @@ int wm_prepare_shifts(const wm_hier* h, WorkSpace& ws, const std::vector<double>
   WM_LAUNCH(WM_PC_SETUP, s, k_coarse_inverse<<<nsh, 256, smem, s>>>(C.N, C.d_Sdense.p, C.d_Mdense.p, ws.shifts.p,
                                                                     ws.ainv.p));
   WM_CUDA(cudaGetLastError());
+  ws.prep_shifts = shifts;
+  ws.prep_lmax = ws.lmax.p;
+  ws.prep_ainv = ws.ainv.p;
   return WM_OK;
 }
 
@@ -1005,6 +1040,25 @@ static const T* dM_of(const wm_level& L) {
   return std::is_same<T, double>::value ? (const T*)L.d_dM64.p : (const T*)L.d_dM32.p;
 }
 
+template <typename T>
+static const typename C2T<T>::type* cheb_tab(WorkSpace& ws);
+template <>
+const float2* cheb_tab<float>(WorkSpace& ws) { return ws.cheb32.p; }
+template <>
+const double2* cheb_tab<double>(WorkSpace& ws) { return ws.cheb64.p; }
+
+// Chebyshev coefficients of the batch's smoother for every level and shift
+static int build_cheb_table(const wm_hier* h, WorkSpace& ws, const Batch& bt, cudaStream_t s) {
+  int n = (int)h->lv.size() * bt.nshift * WM_MAX_CHEB;
+  WM_TRY(ws.cheb32.alloc(n));
+  WM_TRY(ws.cheb64.alloc(n));
+  WM_LAUNCH(WM_PC_SETUP, s, k_cheb_table<<<nblk(n, 128), 128, 0, s>>>((int)h->lv.size(), bt.nshift, bt.degree,
+                                                                      bt.cheb_ratio, ws.lmax.p, ws.cheb32.p,
+                                                                      ws.cheb64.p));
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
 // one V-cycle from level l on residual rin, returns the buffer holding z
 template <typename T>
 static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const T* rin, T** zout, cudaStream_t s) {
@@ -1016,6 +1070,8 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   const int ch = bt.chunks_for(Lv.N);
   const dim3 ggrid(ch, groups(tiles));
   const double* lmax = ws.lmax.p + (size_t)l * bt.nshift;
+  (void)lmax;
+  const typename C2T<T>::type* ctab = cheb_tab<T>(ws) + (size_t)l * bt.nshift * WM_MAX_CHEB;
   const auto* pk = rows_of<T>(Lv);
   const T* dS = dS_of<T>(Lv);
   const T* dM = dM_of<T>(Lv);
@@ -1036,15 +1092,21 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   T* d = vb<T>(B.d);
   T* res = vb<T>(B.res);
   const int nu = bt.degree;
-  const double ratio = bt.cheb_ratio;
+  int step_rc = WM_OK;
   auto cheb_step = [&](int k, const T* zin, T* zo) {
-    WM_LAUNCH(csm, s, k_cheb_step<T><<<ggrid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, tiles, k, pk, dS, dM, ws.sigma.p, lmax,
-                                                            ws.sid.p, ratio, rin, zin, d, zo, ta));
+    if (Lv.sten) {
+      int e = wm_sten_cheb_step<T>(Lv, h->np, h->p, tiles, k, ws.sigma.p, ctab, ws.sid.p, rin, zin, d, zo, ta,
+                                   csm, s);
+      if (e != WM_OK) step_rc = e;
+    } else {
+      WM_LAUNCH(csm, s, k_cheb_step<T><<<ggrid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, tiles, k, pk, dS, dM, ws.sigma.p,
+                                                              ctab, ws.sid.p, rin, zin, d, zo, ta));
+    }
     units(csm, bt, 5.0 * Tb * Lv.N, 4.0 * Lv.nnz + 8.0 * Lv.N);
   };
   // pre-smoothing from z = 0
-  WM_LAUNCH(csm, s, k_cheb_first<T><<<ggrid, kBlk, 0, s>>>(Lv.N, ch, tiles, rin, dS, dM, ws.sigma.p, lmax, ws.sid.p,
-                                                           ratio, d, za, ta));
+  WM_LAUNCH(csm, s, k_cheb_first<T><<<ggrid, kBlk, 0, s>>>(Lv.N, ch, tiles, rin, dS, dM, ws.sigma.p, ctab,
+                                                           ws.sid.p, d, za, ta));
   units(csm, bt, 3.0 * Tb * Lv.N, 4.0 * Lv.N);
   T* cur = za;
   T* oth = zb;
@@ -1053,8 +1115,14 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
     std::swap(cur, oth);
   }
   // residual, restriction, coarse correction
-  WM_LAUNCH(cre, s, k_residual<T><<<ggrid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, tiles, pk, ws.sigma.p, rin, cur, res, ta));
+  if (Lv.sten) {
+    WM_TRY(wm_sten_residual<T>(Lv, h->np, h->p, tiles, ws.sigma.p, rin, cur, res, ta, cre, s));
+  } else {
+    WM_LAUNCH(cre, s, k_residual<T><<<ggrid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, tiles, pk, ws.sigma.p, rin, cur, res,
+                                                           ta));
+  }
   units(cre, bt, 3.0 * Tb * Lv.N, 4.0 * Lv.nnz + 3.0 * Lv.N);
+  WM_TRY(step_rc);
   const wm_level& Cv = h->lv[l + 1];
   T* rc = vb<T>(ws.lvl[l + 1].r);
   const int chc = bt.chunks_for(Cv.N);
@@ -1071,6 +1139,7 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
     cheb_step(k, cur, oth);
     std::swap(cur, oth);
   }
+  WM_TRY(step_rc);
   WM_CUDA(cudaGetLastError());
   *zout = cur;
   return WM_OK;
@@ -1095,10 +1164,13 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
   const int nsys_pad = tiles * WM_LANES;
   const unsigned sb = nblk(nsys_pad, 128);
   const double Tb = (double)sizeof(T);
+  // partial-sum chunks of the operator kernels (stencil: one per spatial block)
+  const int ch_op = L0.sten ? wm_sten_chunks(L0, h->np) : ch;
   T* r = vb<T>(ws.r);
   T* p = vb<T>(ws.p);
   T* q = vb<T>(ws.q);
   int* cnt = ws.counters.p;
+  WM_TRY(build_cheb_table(h, ws, bt, s));
   WM_CUDA(cudaMemsetAsync(ws.flags.p, 0, 4 * sizeof(int), s));
   WM_LAUNCH(WM_PC_CGVEC, s, k_gather_rhs<T><<<grid, kBlk, 0, s>>>(N, ch, tiles, rhs_tiled, ws.src_of.p, r, ws.x.p,
                                                                   ws.part[0].p));
@@ -1123,10 +1195,15 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
   const double drop2 = bt.replace_drop * bt.replace_drop;
   int it = 0, n_rep_total = 0;
   for (it = 1; it <= bt.max_iter; ++it) {
-    WM_LAUNCH(WM_PC_APPLY64, s, k_apply_pq<T><<<ggrid, kBlk, 0, s>>>(N, L0.W, ch, tiles, rows_of<T>(L0), ws.sigma.p,
-                                                                     p, q, ws.tile_active.p, ws.part[0].p));
+    if (L0.sten) {
+      WM_TRY(wm_sten_apply_pq<T>(L0, h->np, h->p, tiles, ws.sigma.p, p, q, ws.tile_active.p, ws.part[0].p, s));
+    } else {
+      WM_LAUNCH(WM_PC_APPLY64, s, k_apply_pq<T><<<ggrid, kBlk, 0, s>>>(N, L0.W, ch, tiles, rows_of<T>(L0),
+                                                                       ws.sigma.p, p, q, ws.tile_active.p,
+                                                                       ws.part[0].p));
+    }
     units(WM_PC_APPLY64, bt, 2.0 * Tb * N, 4.0 * L0.nnz + 4.0 * N);
-    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_alpha<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[0].p, ws.rho.p, ws.active.p,
+    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_alpha<<<sb, 128, 0, s>>>(nsys_pad, ch_op, ws.part[0].p, ws.rho.p, ws.active.p,
                                                                ws.alpha.p, ws.flags.p));
     WM_LAUNCH(WM_PC_CGVEC, s, k_update_xr<T><<<grid, kBlk, 0, s>>>(N, ch, tiles, ws.alpha.p, p, q, ws.x.p, r,
                                                                    ws.tile_active.p, ws.part[0].p));
@@ -1147,9 +1224,14 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
     if (n_rep > 0) {
       // float64 true residual of the flagged systems
       n_rep_total += n_rep;
-      WM_LAUNCH(WM_PC_TRUERES, s, k_true_residual<T><<<ggrid, kBlk, 0, s>>>(
-                                    N, L0.W, ch, tiles, L0.d_pk64.p, ws.sigma.p, ws.x.p, rhs_tiled, ws.src_of.p,
-                                    ws.rep.p, ws.tile_rep.p, r, ws.part[1].p));
+      if (L0.sten) {
+        WM_TRY(wm_sten_true_residual<T>(L0, h->np, h->p, tiles, ws.sigma.p, ws.x.p, rhs_tiled, ws.src_of.p, ws.rep.p,
+                                        ws.tile_rep.p, r, ws.part[1].p, s));
+      } else {
+        WM_LAUNCH(WM_PC_TRUERES, s, k_true_residual<T><<<ggrid, kBlk, 0, s>>>(
+                                      N, L0.W, ch, tiles, L0.d_pk64.p, ws.sigma.p, ws.x.p, rhs_tiled, ws.src_of.p,
+                                      ws.rep.p, ws.tile_rep.p, r, ws.part[1].p));
+      }
       {
         int keep = bt.active_tiles;
         bt.active_tiles = rep_tiles;
@@ -1158,7 +1240,7 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
       }
       WM_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(int), s));
       WM_CUDA(cudaMemsetAsync(ws.tile_active.p, 0, tiles * sizeof(int), s));
-      WM_LAUNCH(WM_PC_SCALAR, s, k_scal_replace<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[1].p, ws.bb.p, rtol2,
+      WM_LAUNCH(WM_PC_SCALAR, s, k_scal_replace<<<sb, 128, 0, s>>>(nsys_pad, ch_op, ws.part[1].p, ws.bb.p, rtol2,
                                                                    ws.rep.p, ws.rr.p, ws.rr_ref.p, ws.active.p,
                                                                    ws.restart.p, ws.tile_active.p, cnt, ws.flags.p));
       WM_CUDA(cudaGetLastError());
@@ -1202,6 +1284,7 @@ int wm_vcycle_apply(const wm_hier* h, WorkSpace& ws, const Batch& bt, const doub
                     cudaStream_t s) {
   size_t n = (size_t)bt.tiles * h->lv[0].N * WM_LANES;
   bt.active_tiles = bt.tiles;
+  WM_TRY(build_cheb_table(h, ws, bt, s));
   WM_TRY(set_all_tiles_active(ws, bt.tiles, s));
   if (bt.precision == WM_FP64) {
     WM_TRY(wm_copy(r64, ws.r.d.p, n, s));

@@ -1,6 +1,11 @@
 // Batched solver state shared by the sampler entry points.
 #pragma once
 
+// largest Chebyshev degree of a smoothing sweep
+#ifndef WM_MAX_CHEB
+#define WM_MAX_CHEB 8
+#endif
+
 #include "wm_internal.h"
 
 // float or double buffer (only the one of the solve's precision is allocated)
@@ -59,6 +64,9 @@ struct WorkSpace {
   DevBuf<double> part[3];
   DevBuf<int> flags, counters;
   DevBuf<double> lmax, ainv, shifts, statd;
+  // Chebyshev step coefficients (c1, c2) per [level][shift][step], both precisions
+  DevBuf<float2> cheb32;
+  DevBuf<double2> cheb64;
   // sample-tiled float64 buffers: loads, integer iterate, field, pass rhs, staging
   DevBuf<double> samp[5];
   DevBuf<double> noise_scratch;
@@ -66,6 +74,10 @@ struct WorkSpace {
   DevBuf<double> coef;        // sinc weights of the current pass
   DevBuf<double> ckpt, mx, dots;  // adjoint: forward solutions of a batch, M x, per-system dots
   std::vector<DevBuf<double>> chain;  // adjoint: integer-part iterates w_1..w_n (sample-tiled)
+  // shifts whose smoother bounds and coarse inverses are in lmax / ainv
+  std::vector<double> prep_shifts;
+  const double* prep_lmax = nullptr;
+  const double* prep_ainv = nullptr;
   int* host_small = nullptr;  // pinned
   double host_d = 0.0;
   int reserve(const wm_hier* h, int tiles, int nshift, bool dbl);

@@ -1,0 +1,584 @@
+// Shared-memory stencil kernels for the operator-type steps of the solver.
+//
+// A block owns a BU x BV tile of one patch's local DOF grid for TPB system
+// tiles.  It stages the (BU + 2p) x (BV + 2p) window of the input vector
+// (through the extended grid map: halo cells come from the neighbouring
+// patch, or wrap on the torus) into shared memory, once per block, and every
+// warp then sweeps one column of BV outputs with a (2p+1)-row register window,
+// so each staged value is read from shared memory 2p+1 times instead of each
+// neighbour being fetched from L1/L2 (2p+1)^2 times.  Lane = system, so every
+// staged row is one coalesced 128/256-byte transaction and the row's stencil
+// coefficients (S, M) are warp-uniform loads shared by TPB x 32 systems.
+// Only the owner patch of a shared DOF computes its row.
+#include <algorithm>
+
+#include "wm_solver.h"
+#include "wm_stencil.h"
+
+namespace {
+
+constexpr int BU = 8;   // outputs per block along u (one warp each)
+constexpr int BV = 8;   // outputs per warp along v
+
+template <typename T>
+struct V2;
+template <>
+struct V2<float> {
+  using type = float2;
+};
+template <>
+struct V2<double> {
+  using type = double2;
+};
+
+struct StenGeo {
+  int nlu, nlv, ELU, ELV, nbu, nbv, N;
+  const int32_t* ext;
+  const int32_t* own;
+};
+
+// per-thread dot accumulator (products in T, flushed into double every 16)
+template <typename T>
+struct DAcc {
+  double d = 0.0;
+  T f = 0;
+  int n = 0;
+  __device__ __forceinline__ void add(T v) {
+    f += v;
+    if (++n == 16) {
+      d += (double)f;
+      f = 0;
+      n = 0;
+    }
+  }
+  __device__ __forceinline__ double get() const { return d + (double)f; }
+};
+
+template <int TPB>
+__device__ __forceinline__ void block_reduce(double (&acc)[TPB], double* part, int t0, int tiles) {
+  __shared__ double red[TPB][BU][32];
+#pragma unroll
+  for (int k = 0; k < TPB; ++k) red[k][threadIdx.y][threadIdx.x] = acc[k];
+  __syncthreads();
+  if (threadIdx.y == 0) {
+#pragma unroll
+    for (int k = 0; k < TPB; ++k) {
+      if (t0 + k >= tiles) continue;
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < BU; ++w) s += red[k][w][threadIdx.x];
+      part[((size_t)(t0 + k) * gridDim.x + blockIdx.x) * 32 + threadIdx.x] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- epilogues
+// Chebyshev step: d = c1 d + c2 D^{-1} (r - A z_in), z_out = z_in + d
+template <typename T, int TPB>
+struct ChebEpi {
+  static constexpr int NIN = 2;  // r and d of the output rows are staged
+  const T* in[2];
+  int N, kstep;
+  const T *r, *dS, *dM;
+  T *d, *zout;
+  const double* sigma;
+  const typename V2<T>::type* ctab;  // (c1, c2) per [shift][step] of this level
+  const int* sid;
+  T sg[TPB], c1[TPB], c2[TPB];
+  __device__ __forceinline__ void init(int t0, const bool* act) {
+#pragma unroll
+    for (int k = 0; k < TPB; ++k) {
+      int g = (t0 + k) * 32 + threadIdx.x;
+      sg[k] = c1[k] = c2[k] = 0;
+      if (!act[k]) continue;
+      typename V2<T>::type c = ctab[sid[g] * WM_MAX_CHEB + kstep];
+      c1[k] = c.x;
+      c2[k] = c.y;
+      sg[k] = (T)sigma[g];
+    }
+  }
+  // staged[a][k]: input a of tile k at this output row and lane
+  __device__ __forceinline__ void row(int t0, const bool* act, int i, const T* aS, const T* aM, const T* zc,
+                                      const T (*staged)[TPB]) {
+    T ds = dS[i], dm = dM[i];
+#pragma unroll
+    for (int k = 0; k < TPB; ++k)
+      if (act[k]) {
+        size_t o = ((size_t)(t0 + k) * N + i) * 32 + threadIdx.x;
+        T res = staged[0][k] - (aS[k] + sg[k] * aM[k]);
+        T dv = (kstep == 0 ? (T)0 : c1[k] * staged[1][k]) + c2[k] * res / (ds + sg[k] * dm);
+        d[o] = dv;
+        zout[o] = zc[k] + dv;
+      }
+  }
+  __device__ __forceinline__ void finish(int, int) {}
+};
+
+// residual: res = r - A z
+template <typename T, int TPB>
+struct ResidEpi {
+  static constexpr int NIN = 1;  // r staged
+  const T* in[1];
+  int N;
+  const T* r;
+  T* res;
+  const double* sigma;
+  T sg[TPB];
+  __device__ __forceinline__ void init(int t0, const bool* act) {
+#pragma unroll
+    for (int k = 0; k < TPB; ++k) sg[k] = act[k] ? (T)sigma[(t0 + k) * 32 + threadIdx.x] : (T)0;
+  }
+  __device__ __forceinline__ void row(int t0, const bool* act, int i, const T* aS, const T* aM, const T*,
+                                      const T (*staged)[TPB]) {
+#pragma unroll
+    for (int k = 0; k < TPB; ++k)
+      if (act[k]) {
+        size_t o = ((size_t)(t0 + k) * N + i) * 32 + threadIdx.x;
+        res[o] = staged[0][k] - (aS[k] + sg[k] * aM[k]);
+      }
+  }
+  __device__ __forceinline__ void finish(int, int) {}
+};
+
+// outer apply: q = A p, partial (p, q)
+template <typename T, int TPB>
+struct ApplyEpi {
+  static constexpr int NIN = 0;
+  const T* in[1];
+  int N;
+  T* q;
+  const double* sigma;
+  double* part;
+  T sg[TPB];
+  DAcc<T> acc[TPB];
+  __device__ __forceinline__ void init(int t0, const bool* act) {
+#pragma unroll
+    for (int k = 0; k < TPB; ++k) sg[k] = act[k] ? (T)sigma[(t0 + k) * 32 + threadIdx.x] : (T)0;
+  }
+  __device__ __forceinline__ void row(int t0, const bool* act, int i, const T* aS, const T* aM, const T* zc,
+                                      const T (*)[TPB]) {
+#pragma unroll
+    for (int k = 0; k < TPB; ++k)
+      if (act[k]) {
+        size_t o = ((size_t)(t0 + k) * N + i) * 32 + threadIdx.x;
+        T qv = aS[k] + sg[k] * aM[k];
+        q[o] = qv;
+        acc[k].add(zc[k] * qv);
+      }
+  }
+  __device__ __forceinline__ void finish(int t0, int tiles) {
+    double a[TPB];
+#pragma unroll
+    for (int k = 0; k < TPB; ++k) a[k] = acc[k].get();
+    block_reduce<TPB>(a, part, t0, tiles);
+  }
+};
+
+// float64 true residual of flagged systems: r = b - A x, partial ||r||^2
+template <typename Tr, int TPB>
+struct TrueResEpi {
+  static constexpr int NIN = 0;
+  const double* in[1];
+  int N;
+  const double* rhs;
+  const int *src_of, *rep;
+  Tr* r;
+  const double* sigma;
+  double* part;
+  double sg[TPB];
+  int src[TPB];
+  bool mine[TPB];
+  double acc[TPB];
+  __device__ __forceinline__ void init(int t0, const bool* act) {
+#pragma unroll
+    for (int k = 0; k < TPB; ++k) {
+      int g = (t0 + k) * 32 + threadIdx.x;
+      sg[k] = act[k] ? sigma[g] : 0.0;
+      src[k] = act[k] ? src_of[g] : -1;
+      mine[k] = act[k] && rep[g];
+      acc[k] = 0.0;
+    }
+  }
+  __device__ __forceinline__ void row(int t0, const bool*, int i, const double* aS, const double* aM, const double*,
+                                      const double (*)[TPB]) {
+#pragma unroll
+    for (int k = 0; k < TPB; ++k)
+      if (mine[k]) {
+        int s = src[k];
+        double b = s >= 0 ? rhs[((size_t)(s / 32) * N + i) * 32 + (s % 32)] : 0.0;
+        double rt = b - (aS[k] + sg[k] * aM[k]);
+        r[((size_t)(t0 + k) * N + i) * 32 + threadIdx.x] = (Tr)rt;
+        acc[k] += rt * rt;
+      }
+  }
+  __device__ __forceinline__ void finish(int t0, int tiles) { block_reduce<TPB>(acc, part, t0, tiles); }
+};
+
+// ---------------------------------------------------------------- the kernel
+// 16-byte asynchronous global->shared copy; src_bytes = 0 writes zeros
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// coefficient row stride in V2 elements, padded to 16-byte multiples
+template <typename T, int P>
+struct CoefStride {
+  static constexpr int S2 = (2 * P + 1) * (2 * P + 1);
+  static constexpr int value = sizeof(typename V2<T>::type) == 8 ? (S2 + 1) / 2 * 2 : S2;
+};
+
+template <typename T, int P, int TPB, int NIN>
+struct SmemLayout {
+  static constexpr int CU = BU + 2 * P, CV = BV + 2 * P, NC = CU * CV;
+  static constexpr int CS = CoefStride<T, P>::value;
+  static constexpr size_t win = (size_t)TPB * NC * 32 * sizeof(T);
+  static constexpr size_t coef = (size_t)BU * BV * CS * sizeof(typename V2<T>::type);
+  static constexpr size_t rows = (size_t)NIN * TPB * BU * BV * 32 * sizeof(T);
+  static constexpr size_t ids = (size_t)(NC + BU * BV) * sizeof(int);
+  static constexpr size_t total = win + coef + rows + ids;
+};
+
+template <typename T, int P, int TPB, typename Epi>
+__global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGeo G, const typename V2<T>::type* __restrict__ csm,
+                                                  const T* __restrict__ src, int tiles,
+                                                  const int* __restrict__ tile_active, const Epi epi_arg) {
+  using C2 = typename V2<T>::type;
+  using LY = SmemLayout<T, P, TPB, Epi::NIN>;
+  constexpr int NIN = Epi::NIN;
+  constexpr int SW = 2 * P + 1;
+  constexpr int CU = LY::CU, NC = LY::NC, CS = LY::CS;
+  constexpr int ROWCH = 32 * sizeof(T) / 16;  // 16-byte chunks per staged row
+  constexpr int COEFCH = CS * sizeof(C2) / 16;  // 16-byte chunks per coefficient row
+  Epi epi = epi_arg;  // per-thread copy (its per-tile fields live in registers)
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  C2* scf = reinterpret_cast<C2*>(smraw + LY::win);
+  T* srw = reinterpret_cast<T*>(smraw + LY::win + LY::coef);      // [NIN][TPB][BU*BV][32] epilogue inputs
+  int* sid = reinterpret_cast<int*>(smraw + LY::win + LY::coef + LY::rows);  // [NC] cells, then [BU*BV] rows
+  int* srow = sid + NC;
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int tid = w * 32 + lane;
+  int b = blockIdx.x;
+  const int bu = b % G.nbu;
+  b /= G.nbu;
+  const int bv = b % G.nbv;
+  const int m = b / G.nbv;
+  const int t0 = blockIdx.y * TPB;
+  bool act[TPB];
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < TPB; ++k) {
+    act[k] = t0 + k < tiles && tile_active[t0 + k];
+    any |= act[k];
+  }
+  if (!any) return;
+  epi.init(t0, act);
+  // phase 0: global DOF of every window cell and every output row of the block
+  const int32_t* E = G.ext + (size_t)m * G.ELV * G.ELU;
+  const int32_t* OWN = G.own + (size_t)m * G.nlv * G.nlu;
+  for (int c = tid; c < NC + BU * BV; c += BU * 32) {
+    int v = -1;
+    if (c < NC) {
+      int eu = bu * BU + c % CU, ev = bv * BV + c / CU;
+      if (eu < G.ELU && ev < G.ELV) v = E[(size_t)ev * G.ELU + eu];
+    } else {
+      int o = c - NC;
+      int iu = bu * BU + o % BU, iv = bv * BV + o / BU;
+      if (iu < G.nlu && iv < G.nlv) v = OWN[(size_t)iv * G.nlu + iu];
+    }
+    sid[c] = v;
+  }
+  __syncthreads();
+  // phase 1: asynchronous copies of the window rows and the coefficient rows
+  for (int c = tid; c < TPB * NC * ROWCH; c += BU * 32) {
+    int part = c % ROWCH, cell = (c / ROWCH) % NC, k = c / (ROWCH * NC);
+    int gi = sid[cell];
+    bool ok = act[k] && gi >= 0;
+    const T* gp = ok ? src + ((size_t)(t0 + k) * G.N + gi) * 32 + part * (16 / sizeof(T)) : src;
+    cp_async16(sm + ((size_t)k * NC + cell) * 32 + part * (16 / sizeof(T)), gp, ok ? 16 : 0);
+  }
+  for (int c = tid; c < BU * BV * COEFCH; c += BU * 32) {
+    int part = c % COEFCH, o = c / COEFCH;
+    int gi = srow[o];
+    const unsigned char* gp = reinterpret_cast<const unsigned char*>(csm) +
+                              (gi >= 0 ? ((size_t)gi * CS * sizeof(C2) + part * 16) : 0);
+    cp_async16(reinterpret_cast<unsigned char*>(scf) + ((size_t)o * CS * sizeof(C2) + part * 16), gp,
+               gi >= 0 ? 16 : 0);
+  }
+  if constexpr (NIN > 0) {
+    for (int c = tid; c < NIN * TPB * BU * BV * ROWCH; c += BU * 32) {
+      int part = c % ROWCH, o = (c / ROWCH) % (BU * BV), k = (c / (ROWCH * BU * BV)) % TPB,
+          a = c / (ROWCH * BU * BV * TPB);
+      int gi = srow[o];
+      bool ok = act[k] && gi >= 0;
+      const T* gp = ok ? epi.in[a] + ((size_t)(t0 + k) * G.N + gi) * 32 + part * (16 / sizeof(T)) : src;
+      cp_async16(srw + (((size_t)a * TPB + k) * BU * BV + o) * 32 + part * (16 / sizeof(T)), gp, ok ? 16 : 0);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // phase 2: each warp sweeps the column iu with a ring of SW staged rows
+  const int iu = bu * BU + w;
+  if (iu < G.nlu) {
+    T win[TPB][SW][SW];
+#pragma unroll
+    for (int r = 0; r < SW - 1; ++r)
+#pragma unroll
+      for (int du = 0; du < SW; ++du)
+#pragma unroll
+        for (int k = 0; k < TPB; ++k) win[k][r][du] = sm[((size_t)k * NC + r * CU + w + du) * 32 + lane];
+#pragma unroll
+    for (int j = 0; j < BV; ++j) {
+      const int rn = j + SW - 1;  // staged row entering the window
+#pragma unroll
+      for (int du = 0; du < SW; ++du)
+#pragma unroll
+        for (int k = 0; k < TPB; ++k) win[k][rn % SW][du] = sm[((size_t)k * NC + rn * CU + w + du) * 32 + lane];
+      const int i = srow[j * BU + w];
+      if (i >= 0) {
+        const C2* cf = scf + (size_t)(j * BU + w) * CS;
+        T aS[TPB], aM[TPB], zc[TPB];
+#pragma unroll
+        for (int k = 0; k < TPB; ++k) aS[k] = aM[k] = 0;
+#pragma unroll
+        for (int dv = 0; dv < SW; ++dv)
+#pragma unroll
+          for (int du = 0; du < SW; ++du) {
+            C2 c = cf[dv * SW + du];
+#pragma unroll
+            for (int k = 0; k < TPB; ++k) {
+              T z = win[k][(j + dv) % SW][du];
+              aS[k] += c.x * z;
+              aM[k] += c.y * z;
+            }
+          }
+#pragma unroll
+        for (int k = 0; k < TPB; ++k) zc[k] = win[k][(j + P) % SW][P];
+        T stg[NIN > 0 ? NIN : 1][TPB];
+#pragma unroll
+        for (int a = 0; a < NIN; ++a)
+#pragma unroll
+          for (int k = 0; k < TPB; ++k) stg[a][k] = srw[(((size_t)a * TPB + k) * BU * BV + j * BU + w) * 32 + lane];
+        epi.row(t0, act, i, aS, aM, zc, stg);
+      }
+    }
+  }
+  epi.finish(t0, tiles);
+}
+
+template <typename T, int P, int TPB, int NIN>
+constexpr size_t smem_bytes() {
+  return SmemLayout<T, P, TPB, NIN>::total;
+}
+
+StenGeo geo_of(const wm_level& L) {
+  StenGeo G;
+  G.nlu = L.nlu;
+  G.nlv = L.nlv;
+  G.ELU = L.ELU;
+  G.ELV = L.ELV;
+  G.nbu = L.nbu;
+  G.nbv = L.nbv;
+  G.N = L.N;
+  G.ext = L.d_ext.p;
+  G.own = L.d_own.p;
+  return G;
+}
+
+template <typename T>
+const typename V2<T>::type* csm_of(const wm_level& L);
+template <>
+const float2* csm_of<float>(const wm_level& L) { return L.d_csm32.p; }
+template <>
+const double2* csm_of<double>(const wm_level& L) { return L.d_csm64.p; }
+
+// tiles per block: two float tiles for p <= 2 (register window 2 x 25), one otherwise
+template <typename T, int P>
+struct Tpb {
+  static constexpr int value = (sizeof(T) == 4 && P <= 2) ? 2 : 1;
+};
+
+template <typename T, int P, typename Epi>
+int launch(const wm_level& L, int np, int tiles, const T* src, const int* tile_active, Epi epi, int cat,
+           cudaStream_t s) {
+  constexpr int TPB = Tpb<T, P>::value;
+  constexpr size_t sm = smem_bytes<T, P, TPB, Epi::NIN>();
+  static bool configured = false;
+  if (!configured) {
+    WM_CUDA(cudaFuncSetAttribute(k_sten<T, P, TPB, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    configured = true;
+  }
+  dim3 grid(np * L.nbu * L.nbv, (tiles + TPB - 1) / TPB);
+  WM_LAUNCH(cat, s, k_sten<T, P, TPB, Epi><<<grid, dim3(32, BU), sm, s>>>(geo_of(L), csm_of<T>(L), src, tiles,
+                                                                           tile_active, epi));
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
+__global__ void k_build_csm(int N, int W, int cs32, int cs64, const int16_t* __restrict__ slot,
+                            const double* __restrict__ S, const double* __restrict__ M, float2* __restrict__ c32,
+                            double2* __restrict__ c64) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)N * W) return;
+  int sl = slot[t];
+  if (sl < 0) return;
+  int i = (int)(t / W);
+  c32[(size_t)i * cs32 + sl] = make_float2((float)S[t], (float)M[t]);
+  c64[(size_t)i * cs64 + sl] = make_double2(S[t], M[t]);
+}
+
+}  // namespace
+
+// ====================================================================== host
+int wm_sten_build(const wm_geom_desc& g, int np, wm_level& L, cudaStream_t s) {
+  L.sten = false;
+  if (g.degree < 2 || g.degree > 3 || L.nlu < 8 || L.nlv < 8) return WM_OK;
+  std::vector<int32_t> ext, own;
+  std::vector<int16_t> slot;
+  if (wm_host_stencil(g, np, L, ext, own, slot) != WM_OK) return WM_OK;  // row kernels only
+  const int p = g.degree, S2 = (2 * p + 1) * (2 * p + 1);
+  const int cs32 = (S2 + 1) / 2 * 2, cs64 = S2;  // coefficient row strides (16-byte multiples)
+  L.ELU = L.nlu + 2 * p;
+  L.ELV = L.nlv + 2 * p;
+  L.nbu = (L.nlu + BU - 1) / BU;
+  L.nbv = (L.nlv + BV - 1) / BV;
+  WM_TRY(L.d_ext.upload(ext, s));
+  WM_TRY(L.d_own.upload(own, s));
+  DevBuf<int16_t> d_slot;
+  WM_TRY(d_slot.upload(slot, s));
+  WM_TRY(L.d_csm32.alloc((size_t)L.N * cs32));
+  WM_TRY(L.d_csm64.alloc((size_t)L.N * cs64));
+  WM_CUDA(cudaMemsetAsync(L.d_csm32.p, 0, sizeof(float2) * (size_t)L.N * cs32, s));
+  WM_CUDA(cudaMemsetAsync(L.d_csm64.p, 0, sizeof(double2) * (size_t)L.N * cs64, s));
+  int64_t n = (int64_t)L.N * L.W;
+  WM_LAUNCH(WM_PC_ASSEMBLY, s, k_build_csm<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+                                   L.N, L.W, cs32, cs64, d_slot.p, L.d_S64.p, L.d_M64.p, L.d_csm32.p, L.d_csm64.p));
+  WM_CUDA(cudaGetLastError());
+  WM_CUDA(cudaStreamSynchronize(s));
+  d_slot.release();
+  L.sten = true;
+  return WM_OK;
+}
+
+int wm_sten_chunks(const wm_level& L, int np) { return L.sten ? np * L.nbu * L.nbv : 0; }
+
+#define WM_DISPATCH_P(P_, ...)                     \
+  switch (P_) {                                    \
+    case 2: {                                      \
+      constexpr int PP = 2;                        \
+      __VA_ARGS__;                                 \
+    } break;                                       \
+    case 3: {                                      \
+      constexpr int PP = 3;                        \
+      __VA_ARGS__;                                 \
+    } break;                                       \
+    default: return WM_ERR_UNSUPPORTED;            \
+  }
+
+template <typename T>
+int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, const double* sigma,
+                      const typename StenC2<T>::type* ctab, const int* sid, const T* r, const T* zin, T* d, T* zout,
+                      const int* tile_active, int cat, cudaStream_t s) {
+  ChebEpi<T, 2> e2;
+  ChebEpi<T, 1> e1;
+  auto fill = [&](auto& e) {
+    e.N = L.N;
+    e.kstep = kstep;
+    e.r = r;
+    e.dS = std::is_same<T, double>::value ? (const T*)L.d_dS64.p : (const T*)L.d_dS32.p;
+    e.dM = std::is_same<T, double>::value ? (const T*)L.d_dM64.p : (const T*)L.d_dM32.p;
+    e.d = d;
+    e.zout = zout;
+    e.sigma = sigma;
+    e.ctab = ctab;
+    e.sid = sid;
+    e.in[0] = r;
+    e.in[1] = d;
+  };
+  fill(e2);
+  fill(e1);
+  WM_DISPATCH_P(p, {
+    if constexpr (Tpb<T, PP>::value == 2)
+      return launch<T, PP>(L, np, tiles, zin, tile_active, e2, cat, s);
+    else
+      return launch<T, PP>(L, np, tiles, zin, tile_active, e1, cat, s);
+  });
+  return WM_OK;
+}
+
+template <typename T>
+int wm_sten_residual(const wm_level& L, int np, int p, int tiles, const double* sigma, const T* r, const T* z,
+                     T* res, const int* tile_active, int cat, cudaStream_t s) {
+  ResidEpi<T, 2> e2;
+  ResidEpi<T, 1> e1;
+  e2.N = e1.N = L.N;
+  e2.r = e1.r = r;
+  e2.res = e1.res = res;
+  e2.sigma = e1.sigma = sigma;
+  e2.in[0] = e1.in[0] = r;
+  WM_DISPATCH_P(p, {
+    if constexpr (Tpb<T, PP>::value == 2)
+      return launch<T, PP>(L, np, tiles, z, tile_active, e2, cat, s);
+    else
+      return launch<T, PP>(L, np, tiles, z, tile_active, e1, cat, s);
+  });
+  return WM_OK;
+}
+
+template <typename T>
+int wm_sten_apply_pq(const wm_level& L, int np, int p, int tiles, const double* sigma, const T* pv, T* q,
+                     const int* tile_active, double* part, cudaStream_t s) {
+  ApplyEpi<T, 2> e2;
+  ApplyEpi<T, 1> e1;
+  e2.N = e1.N = L.N;
+  e2.q = e1.q = q;
+  e2.sigma = e1.sigma = sigma;
+  e2.part = e1.part = part;
+  WM_DISPATCH_P(p, {
+    if constexpr (Tpb<T, PP>::value == 2)
+      return launch<T, PP>(L, np, tiles, pv, tile_active, e2, WM_PC_APPLY64, s);
+    else
+      return launch<T, PP>(L, np, tiles, pv, tile_active, e1, WM_PC_APPLY64, s);
+  });
+  return WM_OK;
+}
+
+template <typename Tr>
+int wm_sten_true_residual(const wm_level& L, int np, int p, int tiles, const double* sigma, const double* x,
+                          const double* rhs, const int* src_of, const int* rep, const int* tile_rep, Tr* r,
+                          double* part, cudaStream_t s) {
+  TrueResEpi<Tr, 1> e;
+  e.N = L.N;
+  e.rhs = rhs;
+  e.src_of = src_of;
+  e.rep = rep;
+  e.r = r;
+  e.sigma = sigma;
+  e.part = part;
+  WM_DISPATCH_P(p, { return launch<double, PP>(L, np, tiles, x, tile_rep, e, WM_PC_TRUERES, s); });
+  return WM_OK;
+}
+
+template int wm_sten_cheb_step<float>(const wm_level&, int, int, int, int, const double*, const float2*,
+                                      const int*, const float*, const float*, float*, float*, const int*, int,
+                                      cudaStream_t);
+template int wm_sten_cheb_step<double>(const wm_level&, int, int, int, int, const double*, const double2*,
+                                       const int*, const double*, const double*, double*, double*, const int*, int,
+                                       cudaStream_t);
+template int wm_sten_residual<float>(const wm_level&, int, int, int, const double*, const float*, const float*, float*,
+                                     const int*, int, cudaStream_t);
+template int wm_sten_residual<double>(const wm_level&, int, int, int, const double*, const double*, const double*,
+                                      double*, const int*, int, cudaStream_t);
+template int wm_sten_apply_pq<float>(const wm_level&, int, int, int, const double*, const float*, float*, const int*,
+                                     double*, cudaStream_t);
+template int wm_sten_apply_pq<double>(const wm_level&, int, int, int, const double*, const double*, double*,
+                                      const int*, double*, cudaStream_t);
+template int wm_sten_true_residual<float>(const wm_level&, int, int, int, const double*, const double*, const double*,
+                                          const int*, const int*, const int*, float*, double*, cudaStream_t);
+template int wm_sten_true_residual<double>(const wm_level&, int, int, int, const double*, const double*,
+                                           const double*, const int*, const int*, const int*, double*, double*,
+                                           cudaStream_t);

@@ -1,0 +1,41 @@
+// Shared-memory stencil kernels (wm_stencil.cu) for levels with a stencil form.
+#pragma once
+
+#include "wm_internal.h"
+
+#ifndef WM_MAX_CHEB
+#define WM_MAX_CHEB 8
+#endif
+
+// Builds the stencil form of a level (extended grids, owner map, coefficient
+// slots) after its rows are assembled; leaves L.sten = false when the level
+// keeps the row kernels (degree outside 2..3, patches narrower than 8).
+int wm_sten_build(const wm_geom_desc& g, int np, wm_level& L, cudaStream_t s);
+// number of spatial blocks of a stencil launch on the level (partial-sum chunks)
+int wm_sten_chunks(const wm_level& L, int np);
+
+template <typename T>
+struct StenC2;
+template <>
+struct StenC2<float> {
+  using type = float2;
+};
+template <>
+struct StenC2<double> {
+  using type = double2;
+};
+// ctab: (c1, c2) per [shift][step] of the level (WM_MAX_CHEB steps per shift)
+template <typename T>
+int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, const double* sigma,
+                      const typename StenC2<T>::type* ctab, const int* sid, const T* r, const T* zin, T* d, T* zout,
+                      const int* tile_active, int cat, cudaStream_t s);
+template <typename T>
+int wm_sten_residual(const wm_level& L, int np, int p, int tiles, const double* sigma, const T* r, const T* z,
+                     T* res, const int* tile_active, int cat, cudaStream_t s);
+template <typename T>
+int wm_sten_apply_pq(const wm_level& L, int np, int p, int tiles, const double* sigma, const T* pv, T* q,
+                     const int* tile_active, double* part, cudaStream_t s);
+template <typename Tr>
+int wm_sten_true_residual(const wm_level& L, int np, int p, int tiles, const double* sigma, const double* x,
+                          const double* rhs, const int* src_of, const int* rep, const int* tile_rep, Tr* r,
+                          double* part, cudaStream_t s);
