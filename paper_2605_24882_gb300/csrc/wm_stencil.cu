@@ -246,6 +246,7 @@ template <typename T, int P, int TPB, typename Epi>
 __global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGeo G, const typename V2<T>::type* __restrict__ csm,
                                                   const T* __restrict__ src, int tiles,
                                                   const int* __restrict__ tile_active, const Epi epi_arg) {
+  static_assert(TPB == 1 || TPB == 2, "tile selection below assumes at most two tiles per block");
   using C2 = typename V2<T>::type;
   using LY = SmemLayout<T, P, TPB, Epi::NIN>;
   constexpr int NIN = Epi::NIN;
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGe
   for (int c = tid; c < TPB * NC * ROWCH; c += BU * 32) {
     int part = c % ROWCH, cell = (c / ROWCH) % NC, k = c / (ROWCH * NC);
     int gi = sid[cell];
-    bool ok = act[k] && gi >= 0;
+    bool ok = gi >= 0 && (TPB == 1 ? act[0] : (k == 0 ? act[0] : act[TPB - 1]));
     const T* gp = ok ? src + ((size_t)(t0 + k) * G.N + gi) * 32 + part * (16 / sizeof(T)) : src;
     cp_async16(sm + ((size_t)k * NC + cell) * 32 + part * (16 / sizeof(T)), gp, ok ? 16 : 0);
   }
@@ -309,13 +310,14 @@ __global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGe
     cp_async16(reinterpret_cast<unsigned char*>(scf) + ((size_t)o * CS * sizeof(C2) + part * 16), gp,
                gi >= 0 ? 16 : 0);
   }
-  if constexpr (NIN > 0) {
-    for (int c = tid; c < NIN * TPB * BU * BV * ROWCH; c += BU * 32) {
-      int part = c % ROWCH, o = (c / ROWCH) % (BU * BV), k = (c / (ROWCH * BU * BV)) % TPB,
-          a = c / (ROWCH * BU * BV * TPB);
+#pragma unroll
+  for (int a = 0; a < NIN; ++a) {  // compile-time input index keeps epi in registers
+    const T* base = epi.in[a];
+    for (int c = tid; c < TPB * BU * BV * ROWCH; c += BU * 32) {
+      int part = c % ROWCH, o = (c / ROWCH) % (BU * BV), k = c / (ROWCH * BU * BV);
       int gi = srow[o];
-      bool ok = act[k] && gi >= 0;
-      const T* gp = ok ? epi.in[a] + ((size_t)(t0 + k) * G.N + gi) * 32 + part * (16 / sizeof(T)) : src;
+      bool ok = gi >= 0 && (TPB == 1 ? act[0] : (k == 0 ? act[0] : act[TPB - 1]));
+      const T* gp = ok ? base + ((size_t)(t0 + k) * G.N + gi) * 32 + part * (16 / sizeof(T)) : src;
       cp_async16(srw + (((size_t)a * TPB + k) * BU * BV + o) * 32 + part * (16 / sizeof(T)), gp, ok ? 16 : 0);
     }
   }
