@@ -300,7 +300,8 @@ def our_arm(args):
                        "l2": "inputs larger than L2: the batch working set is about 25 GB per step"},
             "dof_solves_per_s": dof_solves,
             "solver": {k: stats[k] for k in ("max_iterations", "total_iterations", "n_not_converged",
-                                             "max_rel_residual", "n_systems", "n_batches")},
+                                             "max_rel_residual", "n_systems", "n_batches", "n_replacements",
+                                             "n_df_fallbacks")},
             "e2e": {"value": world * ns / (e2e_ms / 1e3) if args.e2e_steps else None, "unit": "samples/s",
                     "h2d_bytes_per_step": 120, "d2h_bytes_per_step": ns * N * 8},
             "gpu_launches": launches,

@@ -221,6 +221,9 @@ typedef struct {
   int n_int_solves;       /* integer-part solves per sample                          */
   int n_frac_passes;      /* sinc passes (0, 1 or 2)                                 */
   int n_nodes;            /* sinc nodes per pass                                     */
+  int n_replacements;     /* float64 true-residual evaluations (system count)       */
+  int n_df_fallbacks;     /* batches whose double-float residual failed its error
+                             check and switched to float64 (mixed precision)        */
 } wm_stats;
 
 /*

@@ -38,7 +38,8 @@ class SampleDesc(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("n_systems", C.c_int), ("n_batches", C.c_int), ("max_iterations", C.c_int),
                 ("total_iterations", C.c_int), ("n_not_converged", C.c_int), ("max_rel_residual", C.c_double),
-                ("n_int_solves", C.c_int), ("n_frac_passes", C.c_int), ("n_nodes", C.c_int)]
+                ("n_int_solves", C.c_int), ("n_frac_passes", C.c_int), ("n_nodes", C.c_int),
+                ("n_replacements", C.c_int), ("n_df_fallbacks", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -122,7 +122,7 @@ static void release_level(wm_level& L) {
   L.d_ng_ptr.release(); L.d_ng_idx.release(); L.d_Sdense.release(); L.d_Mdense.release();
   L.d_pk32.release(); L.d_pk64.release(); L.d_P32.release(); L.d_R32.release(); L.d_P64.release();
   L.d_R64.release();
-  L.d_ext.release(); L.d_own.release(); L.d_csm32.release(); L.d_csm64.release();
+  L.d_ext.release(); L.d_own.release(); L.d_csm32.release(); L.d_csm64.release(); L.d_csmdf.release();
 }
 
 extern "C" void wm_destroy_hier(wm_hier_t h) {
@@ -576,6 +576,7 @@ int solve_range(wm_hier_t h, WorkSpace& ws, const wm_sample_desc* d, const Pass&
   bt.degree = d->smoother_degree;
   bt.cheb_ratio = d->cheb_ratio;
   bt.replace_drop = dbl ? 0.0 : 1e-4;
+  bt.df_residual = !dbl;
   BatchResult br;
   WM_TRY(wm_solve_batch(h, ws, bt, rhs_t, &br, s));
   if (br.flags & 1) *worst = std::min(*worst, WM_ERR_NONFINITE);
@@ -587,6 +588,8 @@ int solve_range(wm_hier_t h, WorkSpace& ws, const wm_sample_desc* d, const Pass&
     st->total_iterations += br.iterations;
     st->n_not_converged += br.n_not_converged;
     st->max_rel_residual = std::max(st->max_rel_residual, br.max_rel_residual);
+    st->n_replacements += br.replacements;
+    st->n_df_fallbacks += br.df_fallbacks;
   }
   return WM_OK;
 }

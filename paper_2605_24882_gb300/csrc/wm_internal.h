@@ -135,6 +135,9 @@ struct wm_level {
   DevBuf<int32_t> d_ext, d_own;
   DevBuf<float2> d_csm32;
   DevBuf<double2> d_csm64;
+  // the same coefficients as float pairs (S_hi, S_lo, M_hi, M_lo) for the
+  // double-float residual
+  DevBuf<float4> d_csmdf;
   // noise gather on this level: DOF i <- sum over (e, k) entries
   DevBuf<int32_t> d_ng_ptr, d_ng_idx;
   // coarse dense operators (coarsest level only): [N][N] row-major

@@ -434,6 +434,17 @@ __global__ void k_scal_replace(int nsys_pad, int chunks, const double* part_rr, 
   }
 }
 
+// double-float residual check: counts flagged systems whose rounding-error
+// bound 2^-42 ||B|| exceeds a tenth of the tolerance rtol ||b|| (those
+// residuals are recomputed in float64)
+__global__ void k_df_check(int nsys_pad, int chunks, const double* part_b, const double* bb, double lim2,
+                           const int* rep, int* counter) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nsys_pad || !rep[g]) return;
+  double b2 = sum_parts(part_b, chunks, g);
+  if (!(ldexp(b2, -84) <= lim2 * bb[g])) atomicAdd(counter, 1);
+}
+
 __global__ void k_scal_beta(int nsys_pad, int chunks, const double* part_rz, const double* part_zq,
                             const double* alpha, const int* active, int* restart, double* rho, double* beta) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1194,6 +1205,7 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
   const double rtol2 = bt.rtol * bt.rtol;
   const double drop2 = bt.replace_drop * bt.replace_drop;
   int it = 0, n_rep_total = 0;
+  bool df_res = bt.df_residual;
   for (it = 1; it <= bt.max_iter; ++it) {
     if (L0.sten) {
       WM_TRY(wm_sten_apply_pq<T>(L0, h->np, h->p, tiles, ws.sigma.p, p, q, ws.tile_active.p, ws.part[0].p, s));
@@ -1225,8 +1237,28 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
       // float64 true residual of the flagged systems
       n_rep_total += n_rep;
       if (L0.sten) {
-        WM_TRY(wm_sten_true_residual<T>(L0, h->np, h->p, tiles, ws.sigma.p, ws.x.p, rhs_tiled, ws.src_of.p, ws.rep.p,
-                                        ws.tile_rep.p, r, ws.part[1].p, s));
+        bool done = false;
+        if constexpr (std::is_same<T, float>::value) {
+          if (df_res) {
+            WM_TRY(wm_sten_true_residual_df(L0, h->np, h->p, tiles, ws.sigma.p, ws.x.p, rhs_tiled, ws.src_of.p,
+                                               ws.rep.p, ws.tile_rep.p, r, ws.part[1].p, ws.part[2].p, s));
+            WM_CUDA(cudaMemsetAsync(cnt + 5, 0, sizeof(int), s));
+            WM_LAUNCH(WM_PC_SCALAR, s, k_df_check<<<sb, 128, 0, s>>>(nsys_pad, ch_op, ws.part[2].p, ws.bb.p,
+                                                                     0.01 * rtol2, ws.rep.p, cnt + 5));
+            WM_CUDA(cudaGetLastError());
+            WM_CUDA(cudaMemcpyAsync(ws.host_small + 8, cnt + 5, sizeof(int), cudaMemcpyDeviceToHost, s));
+            WM_CUDA(cudaStreamSynchronize(s));
+            if (ws.host_small[8] == 0) {
+              done = true;
+            } else {
+              df_res = false;  // float64 residuals for the rest of this batch
+              res->df_fallbacks++;
+            }
+          }
+        }
+        if (!done)
+          WM_TRY(wm_sten_true_residual<T>(L0, h->np, h->p, tiles, ws.sigma.p, ws.x.p, rhs_tiled, ws.src_of.p,
+                                          ws.rep.p, ws.tile_rep.p, r, ws.part[1].p, s));
       } else {
         WM_LAUNCH(WM_PC_TRUERES, s, k_true_residual<T><<<ggrid, kBlk, 0, s>>>(
                                       N, L0.W, ch, tiles, L0.d_pk64.p, ws.sigma.p, ws.x.p, rhs_tiled, ws.src_of.p,

@@ -40,6 +40,9 @@ struct Batch {
   // fallen by this factor since its last replacement (and always before a
   // system is declared converged)
   double replace_drop = 1e-3;
+  // float64 true residuals of the float-preconditioned solve evaluated in
+  // double-float arithmetic (stencil levels), checked against the tolerance
+  bool df_residual = false;
   mutable int active_tiles = 0;  // host copy of the active tile count (for work accounting)
   int chunks_for(int N) const;
 };
@@ -50,6 +53,7 @@ struct BatchResult {
   int n_not_converged = 0;
   double max_rel_residual = 0.0;
   int flags = 0;  // bit 0: non-finite value, bit 1: CG breakdown
+  int df_fallbacks = 0;  // double-float residuals rejected by the error check
 };
 
 struct WorkSpace {

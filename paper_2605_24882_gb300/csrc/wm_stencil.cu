@@ -421,9 +421,241 @@ int launch(const wm_level& L, int np, int tiles, const T* src, const int* tile_a
   return WM_OK;
 }
 
+// ------------------------------------------- double-float true residual
+// r = b - (S x + sigma M x) of the systems flagged for residual replacement,
+// with every operation on the FP32 pipes: the FP64 rate of this part is
+// about 1/60 of its FP32 rate (conversions to and from float64 run there
+// too), so the kernel never touches a float64 register in its loops.
+//  * float64 inputs (x, b, sigma) are split into float pairs hi + lo with
+//    integer operations on their bits (relative error at most 2^-47);
+//  * each product a*x is the rounded hi*hi plus its exact rounding error
+//    (FMA) plus the two cross terms; the rounded products are summed with
+//    Knuth's two-sum and all errors gathered in a float tail (about 48
+//    significant bits for the stencil sum);
+//  * where the 32 shifts of a tile are equal (sample-major packing) each
+//    coefficient row is combined once per block into A = S + sigma M in the
+//    same arithmetic and one sum is formed; otherwise S x and M x are summed
+//    separately and combined per output.
+// Each output also accumulates B_i = sum_j |a_ij| |x_j| (float): the entry's
+// rounding error stays below 2^-42 B_i (operand splits 2^-47 and 2^-48,
+// dropped lo*lo and cross-term roundings 2^-47, float tail 25 x 2^-47), and the
+// caller checks 2^-42 ||B|| against the convergence tolerance before it
+// trusts the residuals, recomputing them in float64 otherwise (also when a
+// value of the system is below 2^-102, where float pairs lose precision).
+// The squared norms are accumulated in float over the 8 outputs of a thread
+// (entries of r below about 1e-22 in magnitude lose their contribution).
+
+// v = hi + lo with hi = v rounded to 24 significant bits and lo the rest
+// rounded to float: |v - hi - lo| <= 2^-47 |v| (2^-48 while lo is a normal
+// float), using integer operations on
+// the bits of v and one int->float conversion.  Non-finite v or |v| >= 2^128
+// gives hi = +-inf; 0 < |v| < 2^-102 (lo would be subnormal) sets `tiny` and
+// returns (float(v), 0).
+__device__ __forceinline__ float2 split_bits(double v, bool& tiny) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned long long mag = u & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const int e = (int)(mag >> 52);
+  if (e < 921) {
+    tiny |= mag != 0;
+    return make_float2((float)v, 0.f);
+  }
+  if (e >= 1151) return make_float2(__int_as_float((int)(sign | 0x7F800000u)), 0.f);
+  // round to the nearest multiple of 2^29 units (24 significant bits; a carry
+  // into the exponent is the correct rounding)
+  const unsigned long long H = (mag + (1ull << 28)) & ~((1ull << 29) - 1ull);
+  const int rem = (int)(long long)(mag - H);  // |rem| <= 2^28 units of 2^(e-1075)
+  const int efh = (int)(H >> 52) - 896;
+  if (efh >= 255) return make_float2(__int_as_float((int)(sign | 0x7F800000u)), 0.f);
+  const float h = __int_as_float((int)(sign | ((unsigned)efh << 23) | (unsigned)((H >> 29) & 0x7FFFFFu)));
+  float l = __fmul_rn(__fmul_rn(__int2float_rn(rem), 3.7252902984619141e-09f /* 2^-28 */),
+                      __int_as_float((e - 920) << 23) /* 2^(e-1047) */);
+  return make_float2(h, sign ? -l : l);
+}
+// error-free sum: a + b = s + e exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+// (s, c) += (ah + al) * (xh + xl), dropping al * xl
+__device__ __forceinline__ void df_acc(float& s, float& c, float ah, float al, float xh, float xl) {
+  const float p = __fmul_rn(ah, xh);
+  float e = fmaf(ah, xh, -p);
+  e = fmaf(ah, xl, fmaf(al, xh, e));
+  float t, err;
+  two_sum(s, p, t, err);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+// (ah + al) + (gh + gl) * (mh + ml) as a renormalised pair
+__device__ __forceinline__ float2 df_axpy(float ah, float al, float gh, float gl, float mh, float ml) {
+  const float p = __fmul_rn(gh, mh);
+  float e = fmaf(gh, mh, -p);
+  e = fmaf(gh, ml, fmaf(gl, mh, e));
+  float t, err;
+  two_sum(ah, p, t, err);
+  const float lo = __fadd_rn(al, __fadd_rn(e, err));
+  float h, l;
+  two_sum(t, lo, h, l);
+  return make_float2(h, l);
+}
+
+template <int P>
+struct DfLayout {
+  static constexpr int CU = BU + 2 * P, CV = BV + 2 * P, NC = CU * CV, S2 = (2 * P + 1) * (2 * P + 1);
+  static constexpr size_t win = (size_t)NC * 32 * sizeof(double);
+  static constexpr size_t coef = (size_t)BU * BV * S2 * sizeof(float4);
+  static constexpr size_t ids = (size_t)(NC + BU * BV) * sizeof(int);
+  static constexpr size_t total = win + coef + ids;
+};
+
+template <int P>
+__global__ void __launch_bounds__(BU * 32, 2)
+    k_sten_trueres_df(StenGeo G, const float4* __restrict__ cdf, const double* __restrict__ x, int tiles,
+                      const int* __restrict__ tile_rep, const double* __restrict__ sigma,
+                      const double* __restrict__ rhs, const int* __restrict__ src_of, const int* __restrict__ rep,
+                      float* __restrict__ r, double* __restrict__ part, double* __restrict__ part_bound) {
+  using LY = DfLayout<P>;
+  constexpr int SW = 2 * P + 1, CU = LY::CU, NC = LY::NC, S2 = LY::S2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* smd = reinterpret_cast<double*>(smraw);
+  float2* smf = reinterpret_cast<float2*>(smraw);  // the same cells after the split
+  float4* scf = reinterpret_cast<float4*>(smraw + LY::win);
+  int* sid = reinterpret_cast<int*>(smraw + LY::win + LY::coef);
+  int* srow = sid + NC;
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int tid = w * 32 + lane;
+  int b = blockIdx.x;
+  const int bu = b % G.nbu;
+  b /= G.nbu;
+  const int bv = b % G.nbv;
+  const int m = b / G.nbv;
+  const int t = blockIdx.y;
+  if (t >= tiles || !tile_rep[t]) return;
+  const int g = t * 32 + lane;
+  const double sg = sigma[g];
+  bool tiny = false;  // a value of this system too small for float pairs
+  const float2 sgp = split_bits(sg, tiny);
+  tiny = false;       // (a tiny shift only loses its own negligible part)
+  const bool mine = rep[g] != 0;
+  const int src = src_of[g];
+  // phase 0: global DOF of every window cell and every output row
+  const int32_t* E = G.ext + (size_t)m * G.ELV * G.ELU;
+  const int32_t* OWN = G.own + (size_t)m * G.nlv * G.nlu;
+  for (int c = tid; c < NC + BU * BV; c += BU * 32) {
+    int v = -1;
+    if (c < NC) {
+      int eu = bu * BU + c % CU, ev = bv * BV + c / CU;
+      if (eu < G.ELU && ev < G.ELV) v = E[(size_t)ev * G.ELU + eu];
+    } else {
+      int o = c - NC;
+      int iu = bu * BU + o % BU, iv = bv * BV + o / BU;
+      if (iu < G.nlu && iv < G.nlv) v = OWN[(size_t)iv * G.nlu + iu];
+    }
+    sid[c] = v;
+  }
+  __syncthreads();
+  // phase 1: window rows of x (16 chunks of 16 bytes each) and coefficient rows
+  for (int c = tid; c < NC * 16; c += BU * 32) {
+    int part16 = c % 16, cell = c / 16;
+    int gi = sid[cell];
+    const double* gp = gi >= 0 ? x + ((size_t)t * G.N + gi) * 32 + part16 * 2 : x;
+    cp_async16(smd + (size_t)cell * 32 + part16 * 2, gp, gi >= 0 ? 16 : 0);
+  }
+  for (int c = tid; c < BU * BV * S2; c += BU * 32) {
+    int o = c / S2, k = c % S2;
+    int gi = srow[o];
+    const float4* gp = gi >= 0 ? cdf + (size_t)gi * S2 + k : cdf;
+    cp_async16(scf + c, gp, gi >= 0 ? 16 : 0);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // split x in place; combine the rows when the tile's shifts are equal
+  __shared__ int s_tiny[BU][32];
+  for (int c = tid; c < NC * 32; c += BU * 32) smf[c] = split_bits(smd[c], tiny);  // lane c % 32 == lane
+  s_tiny[w][lane] = tiny;
+  const double sg0 = __shfl_sync(0xffffffffu, sg, 0);
+  const bool uni = __all_sync(0xffffffffu, sg == sg0);  // the same in every warp of the block
+  if (uni) {
+    for (int c = tid; c < BU * BV * S2; c += BU * 32) {
+      float4 q = scf[c];
+      float2 a = df_axpy(q.x, q.y, sgp.x, sgp.y, q.z, q.w);
+      scf[c] = make_float4(a.x, a.y, 0.f, 0.f);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < BU; ++k) tiny |= s_tiny[k][lane] != 0;
+  float acc = 0.f, accb = 0.f;
+  const int iu = bu * BU + w;
+  auto emit = [&](int i, float s, float c, float bnd) {
+    if (!mine) return;
+    const float2 bp = split_bits(src >= 0 ? rhs[((size_t)(src / 32) * G.N + i) * 32 + (src % 32)] : 0.0, tiny);
+    float d, de;
+    two_sum(bp.x, -s, d, de);
+    const float rt = __fadd_rn(d, __fadd_rn(de, __fsub_rn(bp.y, c)));
+    r[((size_t)t * G.N + i) * 32 + lane] = rt;
+    acc = fmaf(rt, rt, acc);
+    accb = fmaf(bnd, bnd, accb);
+  };
+  if (iu < G.nlu && uni) {
+#pragma unroll 1
+    for (int j = 0; j < BV; j += 2) {
+      const int i0 = srow[j * BU + w], i1 = srow[(j + 1) * BU + w];
+      const float4* cf0 = scf + (size_t)(j * BU + w) * S2;
+      const float4* cf1 = cf0 + (size_t)BU * S2;
+      const float2* zw = smf + ((size_t)j * CU + w) * 32 + lane;
+      float s0 = 0.f, c0 = 0.f, b0 = 0.f, s1 = 0.f, c1 = 0.f, b1 = 0.f;
+#pragma unroll
+      for (int dv = 0; dv < SW; ++dv)
+#pragma unroll
+        for (int du = 0; du < SW; ++du) {
+          float4 q0 = cf0[dv * SW + du], q1 = cf1[dv * SW + du];
+          float2 z0 = zw[(dv * CU + du) * 32], z1 = zw[((dv + 1) * CU + du) * 32];
+          df_acc(s0, c0, q0.x, q0.y, z0.x, z0.y);
+          df_acc(s1, c1, q1.x, q1.y, z1.x, z1.y);
+          b0 = fmaf(fabsf(q0.x), fabsf(z0.x), b0);
+          b1 = fmaf(fabsf(q1.x), fabsf(z1.x), b1);
+        }
+      if (i0 >= 0) emit(i0, s0, c0, b0);
+      if (i1 >= 0) emit(i1, s1, c1, b1);
+    }
+  } else if (iu < G.nlu) {
+#pragma unroll 1
+    for (int j = 0; j < BV; ++j) {
+      const int i = srow[j * BU + w];
+      const float4* cf = scf + (size_t)(j * BU + w) * S2;
+      const float2* zw = smf + ((size_t)j * CU + w) * 32 + lane;
+      float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f, b1 = 0.f, b2 = 0.f;
+#pragma unroll 1  // a full unroll makes the scheduler hoist every operand load (spills)
+      for (int dv = 0; dv < SW; ++dv)
+#pragma unroll
+        for (int du = 0; du < SW; ++du) {
+          float4 q = cf[dv * SW + du];
+          float2 z = zw[(dv * CU + du) * 32];
+          df_acc(s1, c1, q.x, q.y, z.x, z.y);
+          df_acc(s2, c2, q.z, q.w, z.x, z.y);
+          b1 = fmaf(fabsf(q.x), fabsf(z.x), b1);
+          b2 = fmaf(fabsf(q.z), fabsf(z.x), b2);
+        }
+      if (i >= 0) {
+        // (s1, c1) + sigma (s2, c2)
+        float2 a = df_axpy(s1, c1, sgp.x, sgp.y, s2, c2);
+        emit(i, a.x, a.y, fmaf(sgp.x, b2, b1));
+      }
+    }
+  }
+  double a2[1] = {(double)acc};
+  block_reduce<1>(a2, part, t, tiles);
+  __syncthreads();
+  a2[0] = tiny && mine ? HUGE_VAL : (double)accb;  // fails the caller's error check
+  block_reduce<1>(a2, part_bound, t, tiles);
+}
+
 __global__ void k_build_csm(int N, int W, int cs32, int cs64, const int16_t* __restrict__ slot,
                             const double* __restrict__ S, const double* __restrict__ M, float2* __restrict__ c32,
-                            double2* __restrict__ c64) {
+                            double2* __restrict__ c64, float4* __restrict__ cdf) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)N * W) return;
   int sl = slot[t];
@@ -431,6 +663,8 @@ __global__ void k_build_csm(int N, int W, int cs32, int cs64, const int16_t* __r
   int i = (int)(t / W);
   c32[(size_t)i * cs32 + sl] = make_float2((float)S[t], (float)M[t]);
   c64[(size_t)i * cs64 + sl] = make_double2(S[t], M[t]);
+  float sh = (float)S[t], mh = (float)M[t];
+  cdf[(size_t)i * cs64 + sl] = make_float4(sh, (float)(S[t] - (double)sh), mh, (float)(M[t] - (double)mh));
 }
 
 }  // namespace
@@ -454,11 +688,14 @@ int wm_sten_build(const wm_geom_desc& g, int np, wm_level& L, cudaStream_t s) {
   WM_TRY(d_slot.upload(slot, s));
   WM_TRY(L.d_csm32.alloc((size_t)L.N * cs32));
   WM_TRY(L.d_csm64.alloc((size_t)L.N * cs64));
+  WM_TRY(L.d_csmdf.alloc((size_t)L.N * cs64));
   WM_CUDA(cudaMemsetAsync(L.d_csm32.p, 0, sizeof(float2) * (size_t)L.N * cs32, s));
   WM_CUDA(cudaMemsetAsync(L.d_csm64.p, 0, sizeof(double2) * (size_t)L.N * cs64, s));
+  WM_CUDA(cudaMemsetAsync(L.d_csmdf.p, 0, sizeof(float4) * (size_t)L.N * cs64, s));
   int64_t n = (int64_t)L.N * L.W;
   WM_LAUNCH(WM_PC_ASSEMBLY, s, k_build_csm<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-                                   L.N, L.W, cs32, cs64, d_slot.p, L.d_S64.p, L.d_M64.p, L.d_csm32.p, L.d_csm64.p));
+                                   L.N, L.W, cs32, cs64, d_slot.p, L.d_S64.p, L.d_M64.p, L.d_csm32.p, L.d_csm64.p,
+                                   L.d_csmdf.p));
   WM_CUDA(cudaGetLastError());
   WM_CUDA(cudaStreamSynchronize(s));
   d_slot.release();
@@ -562,6 +799,33 @@ int wm_sten_true_residual(const wm_level& L, int np, int p, int tiles, const dou
   e.sigma = sigma;
   e.part = part;
   WM_DISPATCH_P(p, { return launch<double, PP>(L, np, tiles, x, tile_rep, e, WM_PC_TRUERES, s); });
+  return WM_OK;
+}
+
+template <int P>
+static int launch_df(const wm_level& L, int np, int tiles, const double* sigma, const double* x, const double* rhs,
+                     const int* src_of, const int* rep, const int* tile_rep, float* r, double* part,
+                     double* part_bound, cudaStream_t s) {
+  constexpr size_t sm = DfLayout<P>::total;
+  static bool configured = false;
+  if (!configured) {
+    WM_CUDA(cudaFuncSetAttribute(k_sten_trueres_df<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    configured = true;
+  }
+  dim3 grid(np * L.nbu * L.nbv, tiles);
+  WM_LAUNCH(WM_PC_TRUERES, s, k_sten_trueres_df<P><<<grid, dim3(32, BU), sm, s>>>(
+                                  geo_of(L), L.d_csmdf.p, x, tiles, tile_rep, sigma, rhs, src_of, rep, r, part,
+                                  part_bound));
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
+int wm_sten_true_residual_df(const wm_level& L, int np, int p, int tiles, const double* sigma, const double* x,
+                             const double* rhs, const int* src_of, const int* rep, const int* tile_rep, float* r,
+                             double* part, double* part_bound, cudaStream_t s) {
+  WM_DISPATCH_P(p, {
+    return launch_df<PP>(L, np, tiles, sigma, x, rhs, src_of, rep, tile_rep, r, part, part_bound, s);
+  });
   return WM_OK;
 }
 

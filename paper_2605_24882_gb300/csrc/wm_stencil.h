@@ -39,3 +39,10 @@ template <typename Tr>
 int wm_sten_true_residual(const wm_level& L, int np, int p, int tiles, const double* sigma, const double* x,
                           const double* rhs, const int* src_of, const int* rep, const int* tile_rep, Tr* r,
                           double* part, cudaStream_t s);
+// the same residual (float output) with the stencil sums in double-float
+// arithmetic on the FP32 pipes; part_bound receives the per-block partial
+// sums of ||B||^2 with B_i = sum_j |a_ij| |x_j| (the rounding error of entry i
+// is below 2^-42 B_i), or +inf for a system with a value below 2^-102
+int wm_sten_true_residual_df(const wm_level& L, int np, int p, int tiles, const double* sigma, const double* x,
+                             const double* rhs, const int* src_of, const int* rep, const int* tile_rep, float* r,
+                             double* part, double* part_bound, cudaStream_t s);

@@ -72,6 +72,25 @@ def test_torus_p3(wm, precision, tol):
     assert err.max() < tol, (err, st)
 
 
+def test_double_float_residual_and_its_fallback(wm):
+    """Mixed precision evaluates the replacement residuals b - A x in
+    double-float arithmetic; at rtol 1e-8 its error bound passes, at 1e-12
+    it cannot, and the solve switches to float64 residuals and still
+    converges to the float64 answer."""
+    kw = dict(kappa=5.0, beta=0.7, sinc_k=0.3, l_lo=-35, l_hi=35, n_samples=40, seed=5)
+    hier = wm.Hierarchy(wm.Geometry("sphere", 2, 16), 4)
+    u8, st8 = hier.sample_fields(precision="mixed", rtol=1e-8, **kw)
+    assert st8["n_replacements"] > 0 and st8["n_df_fallbacks"] == 0, st8
+    u12, st12 = hier.sample_fields(precision="mixed", rtol=1e-12, **kw)
+    assert st12["n_df_fallbacks"] >= 1 and st12["n_not_converged"] == 0, st12
+    assert st12["max_rel_residual"] <= 1e-12
+    ref, _ = hier.sample_fields(precision="fp64", rtol=1e-12, **kw)
+    ref = ref.cpu().numpy()
+    scale = np.abs(ref).max()
+    assert np.abs(u12.cpu().numpy() - ref).max() < 1e-9 * scale
+    assert np.abs(u8.cpu().numpy() - ref).max() < 1e-5 * scale
+
+
 def test_improved_split_two_passes(wm):
     err, st, *_ = run_case(wm, "sphere", 2, 8, 8, 3, 3.0, 1.8, 0.4, -20, 20, 5, 4, "mixed", 1e-9, split="improved")
     assert st["n_frac_passes"] == 2 and st["n_int_solves"] == 1
