@@ -328,8 +328,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--samples", type=int, default=0, help="override the samples per GPU (profiling runs)")
-    ap.add_argument("--smoother-degree", type=int, default=2)
-    ap.add_argument("--cheb-ratio", type=float, default=8.0)
+    ap.add_argument("--smoother-degree", type=int, default=4)
+    ap.add_argument("--cheb-ratio", type=float, default=12.0)
     ap.add_argument("--no-profile", dest="profile", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

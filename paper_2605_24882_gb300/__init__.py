@@ -162,7 +162,7 @@ class Hierarchy:
 
     @staticmethod
     def make_desc(kappa, beta, sinc_k=0.3, l_lo=-35, l_hi=35, n_samples=1, seed=0, split="standard",
-                  precision="mixed", rtol=1e-8, max_iter=200, smoother_degree=2, cheb_ratio=8.0,
+                  precision="mixed", rtol=1e-8, max_iter=200, smoother_degree=4, cheb_ratio=12.0,
                   max_systems=0, noise_given=False):
         return _capi.SampleDesc(kappa=kappa, beta=beta, split=_SPLIT[split], sinc_k=sinc_k, l_lo=l_lo, l_hi=l_hi,
                                 seed=seed, n_samples=n_samples,

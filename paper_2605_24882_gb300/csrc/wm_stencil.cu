@@ -436,7 +436,8 @@ int launch(const wm_level& L, int np, int tiles, const T* src, const int* tile_a
 //    coefficient row is combined once per block into A = S + sigma M in the
 //    same arithmetic and one sum is formed; otherwise S x and M x are summed
 //    separately and combined per output.
-// Each output also accumulates B_i = sum_j |a_ij| |x_j| (float): the entry's
+// Each output also accumulates B_i = sum_j |a_ij x_j| (float, from the rounded
+// hi products, within a factor 1 + 2^-22 of the exact sum): the entry's
 // rounding error stays below 2^-42 B_i (operand splits 2^-47 and 2^-48,
 // dropped lo*lo and cross-term roundings 2^-47, float tail 25 x 2^-47), and the
 // caller checks 2^-42 ||B|| against the convergence tolerance before it
@@ -450,26 +451,28 @@ int launch(const wm_level& L, int np, int tiles, const T* src, const int* tile_a
 // float), using integer operations on
 // the bits of v and one int->float conversion.  Non-finite v or |v| >= 2^128
 // gives hi = +-inf; 0 < |v| < 2^-102 (lo would be subnormal) sets `tiny` and
-// returns (float(v), 0).
+// returns (+-0, 0).
 __device__ __forceinline__ float2 split_bits(double v, bool& tiny) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-  const unsigned long long mag = u & 0x7FFFFFFFFFFFFFFFull;
-  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
-  const int e = (int)(mag >> 52);
+  // 32-bit halves only (no 64-bit integer or float64 instructions)
+  const unsigned hi32 = (unsigned)__double2hiint(v), lo32 = (unsigned)__double2loint(v);
+  const unsigned sign = hi32 & 0x80000000u;
+  const int e = (int)((hi32 >> 20) & 0x7FFu);
   if (e < 921) {
-    tiny |= mag != 0;
-    return make_float2((float)v, 0.f);
+    tiny |= ((hi32 & 0x7FFFFFFFu) | lo32) != 0u;
+    return make_float2(__int_as_float((int)sign), 0.f);
   }
   if (e >= 1151) return make_float2(__int_as_float((int)(sign | 0x7F800000u)), 0.f);
-  // round to the nearest multiple of 2^29 units (24 significant bits; a carry
-  // into the exponent is the correct rounding)
-  const unsigned long long H = (mag + (1ull << 28)) & ~((1ull << 29) - 1ull);
-  const int rem = (int)(long long)(mag - H);  // |rem| <= 2^28 units of 2^(e-1075)
-  const int efh = (int)(H >> 52) - 896;
+  // round the magnitude to the nearest multiple of 2^29 units (24 significant
+  // bits; a carry into the exponent is the correct rounding)
+  const unsigned lr = lo32 + 0x10000000u;
+  const unsigned hr = (hi32 & 0x7FFFFFFFu) + (lr < lo32 ? 1u : 0u);
+  const unsigned hl = lr & 0xE0000000u;
+  const int rem = (int)(lo32 - hl);  // |rem| <= 2^28 units of 2^(e-1075)
+  const int efh = (int)(hr >> 20) - 896;
   if (efh >= 255) return make_float2(__int_as_float((int)(sign | 0x7F800000u)), 0.f);
-  const float h = __int_as_float((int)(sign | ((unsigned)efh << 23) | (unsigned)((H >> 29) & 0x7FFFFFu)));
-  float l = __fmul_rn(__fmul_rn(__int2float_rn(rem), 3.7252902984619141e-09f /* 2^-28 */),
-                      __int_as_float((e - 920) << 23) /* 2^(e-1047) */);
+  const float h = __int_as_float((int)(sign | ((unsigned)efh << 23) | ((hr & 0xFFFFFu) << 3) | (hl >> 29)));
+  const float l = __fmul_rn(__fmul_rn(__int2float_rn(rem), 3.7252902984619141e-09f /* 2^-28 */),
+                            __int_as_float((e - 920) << 23) /* 2^(e-1047) */);
   return make_float2(h, sign ? -l : l);
 }
 // error-free sum: a + b = s + e exactly
@@ -478,9 +481,10 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   const float bp = __fsub_rn(s, a);
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
 }
-// (s, c) += (ah + al) * (xh + xl), dropping al * xl
-__device__ __forceinline__ void df_acc(float& s, float& c, float ah, float al, float xh, float xl) {
+// (s, c) += (ah + al) * (xh + xl), dropping al * xl; bnd += |ah xh|
+__device__ __forceinline__ void df_acc(float& s, float& c, float& bnd, float ah, float al, float xh, float xl) {
   const float p = __fmul_rn(ah, xh);
+  bnd = __fadd_rn(bnd, fabsf(p));
   float e = fmaf(ah, xh, -p);
   e = fmaf(ah, xl, fmaf(al, xh, e));
   float t, err;
@@ -575,8 +579,12 @@ __global__ void __launch_bounds__(BU * 32, 2)
   __shared__ int s_tiny[BU][32];
   for (int c = tid; c < NC * 32; c += BU * 32) smf[c] = split_bits(smd[c], tiny);  // lane c % 32 == lane
   s_tiny[w][lane] = tiny;
-  const double sg0 = __shfl_sync(0xffffffffu, sg, 0);
-  const bool uni = __all_sync(0xffffffffu, sg == sg0);  // the same in every warp of the block
+  // equal shifts compared bit for bit (the same answer in every warp of the
+  // block); both shuffles run on all 32 lanes before any comparison
+  const int sgh = __double2hiint(sg), sgl = __double2loint(sg);
+  const int sgh0 = __shfl_sync(0xffffffffu, sgh, 0);
+  const int sgl0 = __shfl_sync(0xffffffffu, sgl, 0);
+  const bool uni = __all_sync(0xffffffffu, (sgh == sgh0) & (sgl == sgl0));
   if (uni) {
     for (int c = tid; c < BU * BV * S2; c += BU * 32) {
       float4 q = scf[c];
@@ -603,6 +611,7 @@ __global__ void __launch_bounds__(BU * 32, 2)
 #pragma unroll 1
     for (int j = 0; j < BV; j += 2) {
       const int i0 = srow[j * BU + w], i1 = srow[(j + 1) * BU + w];
+      if (i0 < 0 && i1 < 0) continue;  // rows past the patch edge or owned by another patch
       const float4* cf0 = scf + (size_t)(j * BU + w) * S2;
       const float4* cf1 = cf0 + (size_t)BU * S2;
       const float2* zw = smf + ((size_t)j * CU + w) * 32 + lane;
@@ -613,10 +622,8 @@ __global__ void __launch_bounds__(BU * 32, 2)
         for (int du = 0; du < SW; ++du) {
           float4 q0 = cf0[dv * SW + du], q1 = cf1[dv * SW + du];
           float2 z0 = zw[(dv * CU + du) * 32], z1 = zw[((dv + 1) * CU + du) * 32];
-          df_acc(s0, c0, q0.x, q0.y, z0.x, z0.y);
-          df_acc(s1, c1, q1.x, q1.y, z1.x, z1.y);
-          b0 = fmaf(fabsf(q0.x), fabsf(z0.x), b0);
-          b1 = fmaf(fabsf(q1.x), fabsf(z1.x), b1);
+          df_acc(s0, c0, b0, q0.x, q0.y, z0.x, z0.y);
+          df_acc(s1, c1, b1, q1.x, q1.y, z1.x, z1.y);
         }
       if (i0 >= 0) emit(i0, s0, c0, b0);
       if (i1 >= 0) emit(i1, s1, c1, b1);
@@ -625,6 +632,7 @@ __global__ void __launch_bounds__(BU * 32, 2)
 #pragma unroll 1
     for (int j = 0; j < BV; ++j) {
       const int i = srow[j * BU + w];
+      if (i < 0) continue;
       const float4* cf = scf + (size_t)(j * BU + w) * S2;
       const float2* zw = smf + ((size_t)j * CU + w) * 32 + lane;
       float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f, b1 = 0.f, b2 = 0.f;
@@ -634,10 +642,8 @@ __global__ void __launch_bounds__(BU * 32, 2)
         for (int du = 0; du < SW; ++du) {
           float4 q = cf[dv * SW + du];
           float2 z = zw[(dv * CU + du) * 32];
-          df_acc(s1, c1, q.x, q.y, z.x, z.y);
-          df_acc(s2, c2, q.z, q.w, z.x, z.y);
-          b1 = fmaf(fabsf(q.x), fabsf(z.x), b1);
-          b2 = fmaf(fabsf(q.z), fabsf(z.x), b2);
+          df_acc(s1, c1, b1, q.x, q.y, z.x, z.y);
+          df_acc(s2, c2, b2, q.z, q.w, z.x, z.y);
         }
       if (i >= 0) {
         // (s1, c1) + sigma (s2, c2)
