@@ -380,14 +380,32 @@ static int set_batch_meta(WorkSpace& ws, int tiles, const std::vector<double>& s
   size_t n = (size_t)tiles * WM_LANES;
   std::vector<double> sg(n, sigma.empty() ? 1.0 : sigma[0]);
   std::vector<int> si(n, 0), sr(n, -1);
-  for (size_t g = 0; g < sigma.size() && g < n; ++g) {
-    sg[g] = sigma[g];
-    si[g] = sid[g];
-    sr[g] = src[g];
+  for (size_t g = 0; g < n; ++g) {
+    if (g < sigma.size()) {
+      sg[g] = sigma[g];
+      si[g] = sid[g];
+      sr[g] = src[g];
+    } else if (g > 0) {  // padding systems (zero right-hand side) copy the last real shift
+      sg[g] = sg[g - 1];
+      si[g] = si[g - 1];
+    }
   }
+  // tiles whose 32 shifts are equal (bit for bit) take the combined-coefficient kernels
+  std::vector<int> uni(tiles, 1);
+  int n_uni = 0;
+  for (int t = 0; t < tiles; ++t) {
+    for (int l = 1; l < WM_LANES; ++l)
+      if (std::memcmp(&sg[(size_t)t * WM_LANES + l], &sg[(size_t)t * WM_LANES], sizeof(double)) != 0) {
+        uni[t] = 0;
+        break;
+      }
+    n_uni += uni[t];
+  }
+  ws.n_uni_tiles = n_uni;
   WM_CUDA(cudaMemcpyAsync(ws.sigma.p, sg.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
   WM_CUDA(cudaMemcpyAsync(ws.sid.p, si.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
   WM_CUDA(cudaMemcpyAsync(ws.src_of.p, sr.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+  WM_CUDA(cudaMemcpyAsync(ws.tile_uni.p, uni.data(), tiles * sizeof(int), cudaMemcpyHostToDevice, s));
   WM_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
   return WM_OK;
 }

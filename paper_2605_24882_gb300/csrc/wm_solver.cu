@@ -536,12 +536,12 @@ __device__ __forceinline__ TileSet tile_set(int t0, int tiles, const int* tile_a
   return ts;
 }
 
-// first pre-smoothing step from z = 0: d = D^{-1} r / theta, z = d
+// first pre-smoothing step from z = 0: z = c2 D^{-1} r
 template <typename T>
 __global__ void k_cheb_first(int N, int chunks, int tiles, const T* __restrict__ r, const T* __restrict__ dS,
                              const T* __restrict__ dM, const double* __restrict__ sigma,
                              const typename C2T<T>::type* __restrict__ ctab, const int* __restrict__ sid,
-                             T* __restrict__ d, T* __restrict__ z, const int* __restrict__ tile_active) {
+                             T* __restrict__ z, const int* __restrict__ tile_active) {
   const int t0 = blockIdx.y * kTPW;
   TileSet ts = tile_set(t0, tiles, tile_active);
   if (!ts.any) return;
@@ -559,15 +559,13 @@ __global__ void k_cheb_first(int N, int chunks, int tiles, const T* __restrict__
     for (int k = 0; k < kTPW; ++k)
       if (ts.act[k]) {
         size_t o = vidx(t0 + k, N, i);
-        T dv = c2[k] * r[o] / (ds + sg[k] * dm);
-        d[o] = dv;
-        z[o] = dv;
+        z[o] = c2[k] * r[o] / (ds + sg[k] * dm);
       }
   }
 }
 
-// Chebyshev step k with the residual r - A z_in:
-// d = c1 d + c2 D^{-1} (r - A z_in), z_out = z_in + d
+// Chebyshev step k in three-term form: out = z + c1 (z - prev) + c2 D^{-1} (r - A z)
+// (c1 = 0 at step 0; prev = nullptr for z_prev = 0; out may alias prev)
 template <typename T>
 __global__ void __launch_bounds__(256) k_cheb_step(int N, int W, int chunks, int tiles, int kstep,
                                                    const typename RowT<T>::type* __restrict__ pk,
@@ -575,7 +573,7 @@ __global__ void __launch_bounds__(256) k_cheb_step(int N, int W, int chunks, int
                                                    const double* __restrict__ sigma,
                                                    const typename C2T<T>::type* __restrict__ ctab,
                                                    const int* __restrict__ sid, const T* __restrict__ r,
-                                                   const T* __restrict__ zin, T* __restrict__ d, T* __restrict__ zout,
+                                                   const T* __restrict__ zin, const T* prev, T* out,
                                                    const int* __restrict__ tile_active) {
   const int t0 = blockIdx.y * kTPW;
   const int lane = threadIdx.x;
@@ -584,11 +582,13 @@ __global__ void __launch_bounds__(256) k_cheb_step(int N, int W, int chunks, int
   T sg[kTPW], c1[kTPW], c2[kTPW];
 #pragma unroll
   for (int k = 0; k < kTPW; ++k) {
+    sg[k] = c1[k] = c2[k] = 0;
+    if (!ts.act[k]) continue;  // (t0 + k may lie past the last tile)
     int g = (t0 + k) * WM_LANES + lane;
     typename C2T<T>::type cf = ctab[sid[g] * WM_MAX_CHEB + kstep];
-    sg[k] = ts.act[k] ? (T)sigma[g] : (T)0;
-    c1[k] = ts.act[k] ? cf.x : (T)0;
-    c2[k] = ts.act[k] ? cf.y : (T)0;
+    sg[k] = (T)sigma[g];
+    c1[k] = kstep > 0 ? cf.x : (T)0;
+    c2[k] = cf.y;
   }
   RowRange rr = chunk_rows(N, chunks);
   for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
@@ -612,9 +612,9 @@ __global__ void __launch_bounds__(256) k_cheb_step(int N, int W, int chunks, int
       if (ts.act[k]) {
         size_t o = vidx(t0 + k, N, i);
         T res = r[o] - (aS[k] + sg[k] * aM[k]);
-        T dv = (kstep == 0 ? (T)0 : c1[k] * d[o]) + c2[k] * res / (ds + sg[k] * dm);
-        d[o] = dv;
-        zout[o] = zin[o] + dv;
+        T zc = zin[o];
+        T zp = prev ? prev[o] : (T)0;
+        out[o] = zc + c1[k] * (zc - zp) + c2[k] * res / (ds + sg[k] * dm);
       }
   }
 }
@@ -902,10 +902,7 @@ int WorkSpace::reserve(const wm_hier* h, int tiles, int nshift, bool dbl) {
     size_t n = (size_t)tiles * h->lv[l].N * WM_LANES;
     WM_TRY(lvl[l].za.alloc(n, dbl));
     WM_TRY(lvl[l].zb.alloc(n, dbl));
-    if (l < L - 1) {
-      WM_TRY(lvl[l].d.alloc(n, dbl));
-      WM_TRY(lvl[l].res.alloc(n, dbl));
-    }
+    if (l < L - 1) WM_TRY(lvl[l].res.alloc(n, dbl));
     if (l > 0) WM_TRY(lvl[l].r.alloc(n, dbl));
   }
   size_t ns = (size_t)tiles * WM_LANES;
@@ -917,6 +914,7 @@ int WorkSpace::reserve(const wm_hier* h, int tiles, int nshift, bool dbl) {
   WM_TRY(restart.alloc(ns));
   WM_TRY(tile_active.alloc(tiles));
   WM_TRY(tile_rep.alloc(tiles));
+  WM_TRY(tile_uni.alloc(tiles));
   WM_TRY(rho.alloc(ns));
   WM_TRY(alpha.alloc(ns));
   WM_TRY(beta.alloc(ns));
@@ -945,13 +943,12 @@ void WorkSpace::release() {
   for (auto& l : lvl) {
     l.za.release();
     l.zb.release();
-    l.d.release();
     l.res.release();
     l.r.release();
   }
   lvl.clear();
   sigma.release(); sid.release(); src_of.release(); active.release(); rep.release(); restart.release();
-  tile_active.release(); tile_rep.release();
+  tile_active.release(); tile_rep.release(); tile_uni.release();
   rho.release(); alpha.release(); beta.release(); bb.release(); rr.release(); rr_ref.release();
   for (auto& pp : part) pp.release();
   flags.release(); counters.release(); lmax.release(); ainv.release(); shifts.release(); statd.release();
@@ -1100,29 +1097,31 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
     *zout = za;
     return WM_OK;
   }
-  T* d = vb<T>(B.d);
   T* res = vb<T>(B.res);
   const int nu = bt.degree;
   int step_rc = WM_OK;
-  auto cheb_step = [&](int k, const T* zin, T* zo) {
+  // three-term step k from z = cur: the result overwrites z_prev in `oth`
+  // (has_prev false: z_prev = 0, or unused at k = 0)
+  auto cheb_step = [&](int k, const T* zin, T* zo, bool has_prev) {
+    const T* prev = has_prev ? zo : nullptr;
     if (Lv.sten) {
-      int e = wm_sten_cheb_step<T>(Lv, h->np, h->p, tiles, k, ws.sigma.p, ctab, ws.sid.p, rin, zin, d, zo, ta,
-                                   csm, s);
+      int e = wm_sten_cheb_step<T>(Lv, h->np, h->p, tiles, k, ws.sigma.p, ctab, ws.sid.p, rin, zin, prev, zo, ta,
+                                   ws.tile_uni.p, ws.n_uni_tiles, csm, s);
       if (e != WM_OK) step_rc = e;
     } else {
       WM_LAUNCH(csm, s, k_cheb_step<T><<<ggrid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, tiles, k, pk, dS, dM, ws.sigma.p,
-                                                              ctab, ws.sid.p, rin, zin, d, zo, ta));
+                                                              ctab, ws.sid.p, rin, zin, prev, zo, ta));
     }
-    units(csm, bt, 5.0 * Tb * Lv.N, 4.0 * Lv.nnz + 8.0 * Lv.N);
+    units(csm, bt, (has_prev ? 4.0 : 3.0) * Tb * Lv.N, 2.0 * Lv.nnz + 8.0 * Lv.N);
   };
   // pre-smoothing from z = 0
   WM_LAUNCH(csm, s, k_cheb_first<T><<<ggrid, kBlk, 0, s>>>(Lv.N, ch, tiles, rin, dS, dM, ws.sigma.p, ctab,
-                                                           ws.sid.p, d, za, ta));
-  units(csm, bt, 3.0 * Tb * Lv.N, 4.0 * Lv.N);
+                                                           ws.sid.p, za, ta));
+  units(csm, bt, 2.0 * Tb * Lv.N, 3.0 * Lv.N);
   T* cur = za;
   T* oth = zb;
   for (int k = 1; k < nu; ++k) {
-    cheb_step(k, cur, oth);
+    cheb_step(k, cur, oth, k >= 2);  // z_0 = 0
     std::swap(cur, oth);
   }
   // residual, restriction, coarse correction
@@ -1145,9 +1144,9 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   WM_LAUNCH(WM_PC_PROLONG, s, k_transfer<T, true><<<ggrid, kBlk, 0, s>>>(Lv.N, Cv.N, ch, tiles, Lv.d_Pptr.p,
                                                                          P_of<T>(Lv), zc, cur, ta));
   units(WM_PC_PROLONG, bt, Tb * (2.0 * Lv.N + Cv.N), 2.0 * Lv.nnzP);
-  // post-smoothing
+  // post-smoothing from the corrected z (no z_prev at step 0)
   for (int k = 0; k < nu; ++k) {
-    cheb_step(k, cur, oth);
+    cheb_step(k, cur, oth, k >= 1);
     std::swap(cur, oth);
   }
   WM_TRY(step_rc);

@@ -20,8 +20,7 @@ struct VBuf {
 };
 
 struct LevelBufs {
-  VBuf za, zb;  // smoother iterates (ping-pong)
-  VBuf d;       // Chebyshev direction
+  VBuf za, zb;  // smoother iterates (three-term recurrence: the new iterate overwrites z_prev)
   VBuf res;     // residual before restriction
   VBuf r;       // restricted residual (levels >= 1)
 };
@@ -64,6 +63,8 @@ struct WorkSpace {
   DevBuf<int> sid;            // per system shift index
   DevBuf<int> src_of;         // per system right-hand-side sample (-1: padding)
   DevBuf<int> active, rep, restart, tile_active, tile_rep;
+  DevBuf<int> tile_uni;       // 1 where the 32 shifts of a tile are equal
+  int n_uni_tiles = 0;        // host count of such tiles in the current batch
   DevBuf<double> rho, alpha, beta, bb, rr, rr_ref;
   DevBuf<double> part[3];
   DevBuf<int> flags, counters;

@@ -73,14 +73,16 @@ __device__ __forceinline__ void block_reduce(double (&acc)[TPB], double* part, i
 }
 
 // ---------------------------------------------------------------- epilogues
-// Chebyshev step: d = c1 d + c2 D^{-1} (r - A z_in), z_out = z_in + d
+// Chebyshev step in three-term form (tiles with per-lane shifts):
+// z_next = z + c1 (z - z_prev) + c2 D^{-1} (r - A z), with c1 = 0 at step 0
+// and z_prev = 0 where has_prev is false; out may alias z_prev
 template <typename T, int TPB>
 struct ChebEpi {
-  static constexpr int NIN = 2;  // r and d of the output rows are staged
-  const T* in[2];
+  static constexpr int NIN = 2;  // r and z_prev of the output rows are staged
+  const T* in[2];                // in[1] = nullptr: z_prev = 0
   int N, kstep;
-  const T *r, *dS, *dM;
-  T *d, *zout;
+  const T *dS, *dM;
+  T* out;
   const double* sigma;
   const typename V2<T>::type* ctab;  // (c1, c2) per [shift][step] of this level
   const int* sid;
@@ -92,7 +94,7 @@ struct ChebEpi {
       sg[k] = c1[k] = c2[k] = 0;
       if (!act[k]) continue;
       typename V2<T>::type c = ctab[sid[g] * WM_MAX_CHEB + kstep];
-      c1[k] = c.x;
+      c1[k] = kstep == 0 ? (T)0 : c.x;
       c2[k] = c.y;
       sg[k] = (T)sigma[g];
     }
@@ -106,9 +108,8 @@ struct ChebEpi {
       if (act[k]) {
         size_t o = ((size_t)(t0 + k) * N + i) * 32 + threadIdx.x;
         T res = staged[0][k] - (aS[k] + sg[k] * aM[k]);
-        T dv = (kstep == 0 ? (T)0 : c1[k] * staged[1][k]) + c2[k] * res / (ds + sg[k] * dm);
-        d[o] = dv;
-        zout[o] = zc[k] + dv;
+        T zp = in[1] ? staged[1][k] : (T)0;
+        out[o] = zc[k] + c1[k] * (zc[k] - zp) + c2[k] * res / (ds + sg[k] * dm);
       }
   }
   __device__ __forceinline__ void finish(int, int) {}
@@ -245,7 +246,8 @@ struct SmemLayout {
 template <typename T, int P, int TPB, typename Epi>
 __global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGeo G, const typename V2<T>::type* __restrict__ csm,
                                                   const T* __restrict__ src, int tiles,
-                                                  const int* __restrict__ tile_active, const Epi epi_arg) {
+                                                  const int* __restrict__ tile_active, const Epi epi_arg,
+                                                  const int* __restrict__ skip_uni) {
   static_assert(TPB == 1 || TPB == 2, "tile selection below assumes at most two tiles per block");
   using C2 = typename V2<T>::type;
   using LY = SmemLayout<T, P, TPB, Epi::NIN>;
@@ -273,7 +275,8 @@ __global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGe
   bool any = false;
 #pragma unroll
   for (int k = 0; k < TPB; ++k) {
-    act[k] = t0 + k < tiles && tile_active[t0 + k];
+    // skip_uni: tiles with a single shift are done by k_cheb_uni
+    act[k] = t0 + k < tiles && tile_active[t0 + k] && !(skip_uni && skip_uni[t0 + k]);
     any |= act[k];
   }
   if (!any) return;
@@ -313,6 +316,7 @@ __global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGe
 #pragma unroll
   for (int a = 0; a < NIN; ++a) {  // compile-time input index keeps epi in registers
     const T* base = epi.in[a];
+    if (!base) continue;
     for (int c = tid; c < TPB * BU * BV * ROWCH; c += BU * 32) {
       int part = c % ROWCH, o = (c / ROWCH) % (BU * BV), k = c / (ROWCH * BU * BV);
       int gi = srow[o];
@@ -372,6 +376,194 @@ __global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGe
   epi.finish(t0, tiles);
 }
 
+// ------------------------------------------- Chebyshev step, one shift per tile
+// The same three-term step for blocks of one tile whose 32 systems share a
+// shift sigma (sample-major packing puts the 32 samples of one sinc node in
+// a tile).  After the DOF ids of the window are known, every global input of
+// the block (window of z, rows of r and z_prev, coefficient rows (S, M), the
+// diagonals) is requested in one batch of asynchronous copies; the block
+// then combines its rows once into A = S + sigma M and the weights
+// w = c2 / (dS + sigma dM), so an output costs one FMA per stencil entry and
+// no division, each combined row being read back with 16-byte shared loads.
+// One tile per block keeps the register window at (2p+1)^2 values; for
+// p = 2 in float the block holds 57 KB of shared memory and four blocks
+// share an SM.
+template <typename T, int P>
+struct UniLayout {
+  static constexpr int CU = BU + 2 * P, CV = BV + 2 * P, NC = CU * CV, S2 = (2 * P + 1) * (2 * P + 1);
+  static constexpr int VEC = 16 / sizeof(T);                  // values per 16-byte load
+  static constexpr int S2P = (S2 + VEC - 1) / VEC * VEC;      // padded combined row length
+  static constexpr int CS = CoefStride<T, P>::value;          // (S, M) row stride of the level tables
+  static constexpr size_t win = (size_t)NC * 32 * sizeof(T);
+  static constexpr size_t rows = (size_t)2 * BU * BV * 32 * sizeof(T);          // r, z_prev
+  static constexpr size_t raw = (size_t)BU * BV * CS * sizeof(typename V2<T>::type);  // (S, M) rows
+  static constexpr size_t coef = (size_t)BU * BV * S2P * sizeof(T);
+  static constexpr size_t diag = (size_t)2 * BU * BV * sizeof(T);               // dS, dM
+  static constexpr size_t wts = (size_t)BU * BV * sizeof(T);
+  static constexpr size_t ids = (size_t)(NC + BU * BV) * sizeof(int);
+  static constexpr size_t total = win + rows + raw + coef + diag + wts + ids;
+};
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static __device__ __forceinline__ float at(const float4& v, int k) {
+    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+  }
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static __device__ __forceinline__ double at(const double2& v, int k) { return k == 0 ? v.x : v.y; }
+};
+// blocks per SM the register budget is sized for
+template <typename T, int P>
+struct UniMinBlocks {
+  static constexpr int value = sizeof(T) == 4 ? (P == 2 ? 4 : 2) : (P == 2 ? 2 : 1);
+};
+// 4- or 8-byte asynchronous copy through L1 (diagonal entries)
+template <int BYTES>
+__device__ __forceinline__ void cp_async_ca(void* smem, const void* gmem, int src_bytes) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sa), "l"(gmem), "n"(BYTES), "r"(src_bytes)
+               : "memory");
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P>::value)
+    k_cheb_uni(StenGeo G, const typename V2<T>::type* __restrict__ csm, const T* __restrict__ dS,
+               const T* __restrict__ dM, const double* __restrict__ sigma, const typename V2<T>::type* __restrict__ ctab,
+               const int* __restrict__ sid, int kstep, const T* __restrict__ z, const T* __restrict__ r, const T* prev,
+               T* out, int tiles, const int* __restrict__ tile_active, const int* __restrict__ tile_uni) {
+  using C2 = typename V2<T>::type;
+  using LY = UniLayout<T, P>;
+  using VT = typename Vec16<T>::type;
+  constexpr int SW = 2 * P + 1, CU = LY::CU, NC = LY::NC, S2 = LY::S2, S2P = LY::S2P, VEC = LY::VEC, CS = LY::CS;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  T* srw = reinterpret_cast<T*>(smraw + LY::win);                                   // [2][64][32]
+  C2* sraw = reinterpret_cast<C2*>(smraw + LY::win + LY::rows);                     // [64][CS]
+  T* scf = reinterpret_cast<T*>(smraw + LY::win + LY::rows + LY::raw);              // [64][S2P]
+  T* sdg = reinterpret_cast<T*>(smraw + LY::win + LY::rows + LY::raw + LY::coef);   // [2][64]
+  T* swt = sdg + 2 * BU * BV;                                                       // [64]
+  int* sid_ = reinterpret_cast<int*>(smraw + LY::win + LY::rows + LY::raw + LY::coef + LY::diag + LY::wts);
+  int* srow = sid_ + NC;
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int tid = w * 32 + lane;
+  int b = blockIdx.x;
+  const int bu = b % G.nbu;
+  b /= G.nbu;
+  const int bv = b % G.nbv;
+  const int m = b / G.nbv;
+  const int t = blockIdx.y;
+  if (t >= tiles || !tile_active[t] || !tile_uni[t]) return;  // mixed-shift tiles are done by k_sten
+  T sg, c1, c2;
+  {
+    const int g = t * 32;  // every lane of the tile has this shift
+    const C2 c = ctab[sid[g] * WM_MAX_CHEB + kstep];
+    c1 = kstep == 0 ? (T)0 : c.x;
+    c2 = c.y;
+    sg = (T)sigma[g];
+  }
+  // phase 0: global DOF of every window cell and every output row
+  const int32_t* E = G.ext + (size_t)m * G.ELV * G.ELU;
+  const int32_t* OWN = G.own + (size_t)m * G.nlv * G.nlu;
+  for (int c = tid; c < NC + BU * BV; c += BU * 32) {
+    int v = -1;
+    if (c < NC) {
+      int eu = bu * BU + c % CU, ev = bv * BV + c / CU;
+      if (eu < G.ELU && ev < G.ELV) v = E[ev * G.ELU + eu];
+    } else {
+      int o = c - NC;
+      int iu = bu * BU + o % BU, iv = bv * BV + o / BU;
+      if (iu < G.nlu && iv < G.nlv) v = OWN[iv * G.nlu + iu];
+    }
+    sid_[c] = v;
+  }
+  __syncthreads();
+  // phase 1: every global input in one batch of asynchronous copies
+  constexpr int ROWCH = 32 * sizeof(T) / 16;        // 16-byte chunks per staged row
+  constexpr int RAWCH = CS * (int)sizeof(C2) / 16;  // 16-byte chunks per (S, M) row
+  constexpr int EPT = 16 / sizeof(T);               // values per chunk
+  const T* zt = z + (size_t)t * G.N * 32;
+  for (int c = tid; c < NC * ROWCH; c += BU * 32) {
+    const int part = c % ROWCH, cell = c / ROWCH;
+    const int gi = sid_[cell];
+    cp_async16(sm + cell * 32 + part * EPT, gi >= 0 ? zt + (size_t)gi * 32 + part * EPT : z, gi >= 0 ? 16 : 0);
+  }
+  const T* rt = r + (size_t)t * G.N * 32;
+  const T* pt = prev ? prev + (size_t)t * G.N * 32 : nullptr;
+  for (int c = tid; c < 2 * BU * BV * ROWCH; c += BU * 32) {
+    const int part = c % ROWCH, o = (c / ROWCH) % (BU * BV), a = c / (ROWCH * BU * BV);
+    const int gi = srow[o];
+    const T* base = a == 0 ? rt : pt;
+    const bool ok = gi >= 0 && base != nullptr;
+    cp_async16(srw + (a * BU * BV + o) * 32 + part * EPT, ok ? base + (size_t)gi * 32 + part * EPT : z, ok ? 16 : 0);
+  }
+  for (int c = tid; c < BU * BV * RAWCH; c += BU * 32) {
+    const int part = c % RAWCH, o = c / RAWCH;
+    const int gi = srow[o];
+    cp_async16(reinterpret_cast<unsigned char*>(sraw) + o * (CS * sizeof(C2)) + part * 16,
+               gi >= 0 ? reinterpret_cast<const unsigned char*>(csm + (size_t)gi * CS) + part * 16
+                       : reinterpret_cast<const unsigned char*>(csm),
+               gi >= 0 ? 16 : 0);
+  }
+  for (int c = tid; c < 2 * BU * BV; c += BU * 32) {
+    const int o = c % (BU * BV);
+    const int gi = srow[o];
+    const T* base = c < BU * BV ? dS : dM;
+    cp_async_ca<sizeof(T)>(sdg + c, gi >= 0 ? base + gi : dS, gi >= 0 ? (int)sizeof(T) : 0);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // combined rows and diagonal weights
+  for (int c = tid; c < BU * BV * S2P; c += BU * 32) {
+    const int o = c / S2P, sl = c - o * S2P;
+    T a = 0;
+    if (sl < S2) {
+      const C2 q = sraw[o * CS + sl];
+      a = q.x + sg * q.y;
+    }
+    scf[c] = a;
+  }
+  for (int c = tid; c < BU * BV; c += BU * 32) swt[c] = srow[c] >= 0 ? c2 / (sdg[c] + sg * sdg[BU * BV + c]) : (T)0;
+  __syncthreads();
+  // phase 2: each warp sweeps the column iu with a ring of SW staged rows
+  const int iu = bu * BU + w;
+  if (iu >= G.nlu) return;
+  T win[SW][SW];
+#pragma unroll
+  for (int rr = 0; rr < SW - 1; ++rr)
+#pragma unroll
+    for (int du = 0; du < SW; ++du) win[rr][du] = sm[(rr * CU + w + du) * 32 + lane];
+#pragma unroll
+  for (int j = 0; j < BV; ++j) {
+    const int rnx = j + SW - 1;  // staged row entering the window
+#pragma unroll
+    for (int du = 0; du < SW; ++du) win[rnx % SW][du] = sm[(rnx * CU + w + du) * 32 + lane];
+    const int o = j * BU + w;
+    const int i = srow[o];
+    if (i >= 0) {
+      const VT* cf = reinterpret_cast<const VT*>(scf + o * S2P);
+      T acc = 0;
+#pragma unroll
+      for (int q = 0; q < S2P / VEC; ++q) {
+        const VT a = cf[q];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+          const int sl = q * VEC + e;
+          if (sl < S2) acc = fma(Vec16<T>::at(a, e), win[(j + sl / SW) % SW][sl % SW], acc);
+        }
+      }
+      const T zc = win[(j + P) % SW][P];
+      const T rv = srw[o * 32 + lane];
+      const T zp = prev ? srw[(BU * BV + o) * 32 + lane] : (T)0;
+      out[((size_t)t * G.N + i) * 32 + lane] = zc + c1 * (zc - zp) + swt[o] * (rv - acc);
+    }
+  }
+}
+
 template <typename T, int P, int TPB, int NIN>
 constexpr size_t smem_bytes() {
   return SmemLayout<T, P, TPB, NIN>::total;
@@ -406,7 +598,7 @@ struct Tpb {
 
 template <typename T, int P, typename Epi>
 int launch(const wm_level& L, int np, int tiles, const T* src, const int* tile_active, Epi epi, int cat,
-           cudaStream_t s) {
+           cudaStream_t s, const int* skip_uni = nullptr) {
   constexpr int TPB = Tpb<T, P>::value;
   constexpr size_t sm = smem_bytes<T, P, TPB, Epi::NIN>();
   static bool configured = false;
@@ -416,7 +608,7 @@ int launch(const wm_level& L, int np, int tiles, const T* src, const int* tile_a
   }
   dim3 grid(np * L.nbu * L.nbv, (tiles + TPB - 1) / TPB);
   WM_LAUNCH(cat, s, k_sten<T, P, TPB, Epi><<<grid, dim3(32, BU), sm, s>>>(geo_of(L), csm_of<T>(L), src, tiles,
-                                                                           tile_active, epi));
+                                                                           tile_active, epi, skip_uni));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
@@ -724,33 +916,57 @@ int wm_sten_chunks(const wm_level& L, int np) { return L.sten ? np * L.nbu * L.n
     default: return WM_ERR_UNSUPPORTED;            \
   }
 
+template <typename T, int P>
+static int launch_uni(const wm_level& L, int np, int tiles, int kstep, const double* sigma,
+                      const typename V2<T>::type* ctab, const int* sid, const T* r, const T* z, const T* prev,
+                      T* out, const int* tile_active, const int* tile_uni, int cat, cudaStream_t s) {
+  constexpr size_t sm = UniLayout<T, P>::total;
+  static bool configured = false;
+  if (!configured) {
+    WM_CUDA(cudaFuncSetAttribute(k_cheb_uni<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    configured = true;
+  }
+  const T* dS = std::is_same<T, double>::value ? (const T*)L.d_dS64.p : (const T*)L.d_dS32.p;
+  const T* dM = std::is_same<T, double>::value ? (const T*)L.d_dM64.p : (const T*)L.d_dM32.p;
+  dim3 grid(np * L.nbu * L.nbv, tiles);
+  WM_LAUNCH(cat, s, k_cheb_uni<T, P><<<grid, dim3(32, BU), sm, s>>>(geo_of(L), csm_of<T>(L), dS, dM, sigma, ctab, sid,
+                                                                   kstep, z, r, prev, out, tiles, tile_active,
+                                                                   tile_uni));
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
 template <typename T>
 int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, const double* sigma,
-                      const typename StenC2<T>::type* ctab, const int* sid, const T* r, const T* zin, T* d, T* zout,
-                      const int* tile_active, int cat, cudaStream_t s) {
+                      const typename StenC2<T>::type* ctab, const int* sid, const T* r, const T* z, const T* prev,
+                      T* out, const int* tile_active, const int* tile_uni, int n_uni, int cat, cudaStream_t s) {
+  if (n_uni > 0) {
+    WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP>(L, np, tiles, kstep, sigma, ctab, sid, r, z, prev, out,
+                                                 tile_active, tile_uni, cat, s))); });
+    if (n_uni >= tiles) return WM_OK;
+  }
   ChebEpi<T, 2> e2;
   ChebEpi<T, 1> e1;
   auto fill = [&](auto& e) {
     e.N = L.N;
     e.kstep = kstep;
-    e.r = r;
     e.dS = std::is_same<T, double>::value ? (const T*)L.d_dS64.p : (const T*)L.d_dS32.p;
     e.dM = std::is_same<T, double>::value ? (const T*)L.d_dM64.p : (const T*)L.d_dM32.p;
-    e.d = d;
-    e.zout = zout;
+    e.out = out;
     e.sigma = sigma;
     e.ctab = ctab;
     e.sid = sid;
     e.in[0] = r;
-    e.in[1] = d;
+    e.in[1] = prev;
   };
   fill(e2);
   fill(e1);
+  const int* skip = n_uni > 0 ? tile_uni : nullptr;
   WM_DISPATCH_P(p, {
     if constexpr (Tpb<T, PP>::value == 2)
-      return launch<T, PP>(L, np, tiles, zin, tile_active, e2, cat, s);
+      return launch<T, PP>(L, np, tiles, z, tile_active, e2, cat, s, skip);
     else
-      return launch<T, PP>(L, np, tiles, zin, tile_active, e1, cat, s);
+      return launch<T, PP>(L, np, tiles, z, tile_active, e1, cat, s, skip);
   });
   return WM_OK;
 }
@@ -836,11 +1052,11 @@ int wm_sten_true_residual_df(const wm_level& L, int np, int p, int tiles, const 
 }
 
 template int wm_sten_cheb_step<float>(const wm_level&, int, int, int, int, const double*, const float2*,
-                                      const int*, const float*, const float*, float*, float*, const int*, int,
-                                      cudaStream_t);
+                                      const int*, const float*, const float*, const float*, float*, const int*,
+                                      const int*, int, int, cudaStream_t);
 template int wm_sten_cheb_step<double>(const wm_level&, int, int, int, int, const double*, const double2*,
-                                       const int*, const double*, const double*, double*, double*, const int*, int,
-                                       cudaStream_t);
+                                       const int*, const double*, const double*, const double*, double*, const int*,
+                                       const int*, int, int, cudaStream_t);
 template int wm_sten_residual<float>(const wm_level&, int, int, int, const double*, const float*, const float*, float*,
                                      const int*, int, cudaStream_t);
 template int wm_sten_residual<double>(const wm_level&, int, int, int, const double*, const double*, const double*,

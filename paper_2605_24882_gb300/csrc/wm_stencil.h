@@ -24,11 +24,16 @@ template <>
 struct StenC2<double> {
   using type = double2;
 };
-// ctab: (c1, c2) per [shift][step] of the level (WM_MAX_CHEB steps per shift)
+// Three-term Chebyshev step out = z + c1 (z - prev) + c2 D^{-1} (r - A z)
+// (c1 = 0 at kstep 0, prev = nullptr for z_prev = 0; out may alias prev).
+// ctab: (c1, c2) per [shift][step] of the level (WM_MAX_CHEB steps per shift).
+// tile_uni[t] = 1 when the 32 shifts of tile t are equal; those tiles
+// (n_uni of them) go to the combined-coefficient kernel (one tile per
+// block), the others to the generic one.
 template <typename T>
 int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, const double* sigma,
-                      const typename StenC2<T>::type* ctab, const int* sid, const T* r, const T* zin, T* d, T* zout,
-                      const int* tile_active, int cat, cudaStream_t s);
+                      const typename StenC2<T>::type* ctab, const int* sid, const T* r, const T* z, const T* prev,
+                      T* out, const int* tile_active, const int* tile_uni, int n_uni, int cat, cudaStream_t s);
 template <typename T>
 int wm_sten_residual(const wm_level& L, int np, int p, int tiles, const double* sigma, const T* r, const T* z,
                      T* res, const int* tile_active, int cat, cudaStream_t s);
