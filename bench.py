@@ -216,13 +216,15 @@ def roofline(prof, pk, pk_kind):
                            "FP32 CUDA cores 152 SMs x 128 lanes x 2 x 2.07 GHz")}
     r.update({"kernel": name, "launches": d["timed"], "avg_launch_ms": d["ms"] / d["timed"],
               "alg_bytes_per_launch": per_launch, "alg_flops_per_launch": d["flops"] / d["timed"],
-              "traffic": traffic_for(name)})
+              "traffic": traffic_for(name, per_launch)})
     return r, name
 
 
-def traffic_for(name):
-    """DRAM bytes per launch of category `name` from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
+def traffic_for(name, alg_bytes_per_launch):
+    """DRAM bytes per launch of category `name`: the committed ncu capture's
+    DRAM bytes per algorithmic byte (taken on a smaller case of the same
+    kernel) times this run's algorithmic bytes per launch, if the capture was
+    taken on the current kernel source (else None)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
@@ -233,7 +235,51 @@ def traffic_for(name):
     src = os.path.join(ROOT, "paper_2605_24882_gb300", "csrc", e["source"])
     if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != e["source_sha"]:
         return None
-    return e["dram_bytes_per_launch"]
+    return e["dram_per_alg_byte"] * alg_bytes_per_launch
+
+
+def fp64_legs(hier, kw, u_mixed, N, systems_per_sample, args):
+    """The same fields by the plain FP64 path, outside the timed region: (1) the
+    batched solve in FP64 (same kernels, FP64 V-cycle); (2) one system at a
+    time (max_systems = 1, FP64), timed on a bounded number of samples.  Also
+    the relative M-norm distance of the mixed fields from the FP64 ones."""
+    import torch
+
+    out = {}
+    ns = kw["n_samples"]
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kwb = dict(kw, precision="fp64")
+    u64 = torch.empty_like(u_mixed)
+    hier.sample_fields(out=u64, **kwb)  # warm-up (FP64 workspace, shift tables)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    hier.sample_fields(out=u64, **kwb)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    out["batched_fp64"] = {"value": ns / t, "unit": "samples/s", "ms_per_step": 1e3 * t,
+                           "dof_solves_per_s": N * systems_per_sample * ns / t}
+    d = u_mixed - u64
+    md = hier.apply_mass(d)
+    mu = hier.apply_mass(u64)
+    rel = torch.sqrt((d * md).sum(1) / (u64 * mu).sum(1))
+    out["mixed_vs_fp64_rel_mnorm_max"] = float(rel.max())
+    n1 = max(1, args.plain_samples)
+    kwp = dict(kw, n_samples=n1, precision="fp64", max_systems=1)
+    u1 = torch.empty((n1, N), dtype=torch.float64, device="cuda")
+    hier.sample_fields(out=u1, **dict(kwp, n_samples=1))  # warm-up
+    torch.cuda.synchronize()
+    e0.record(stream)
+    hier.sample_fields(out=u1, **kwp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t1 = e0.elapsed_time(e1) / 1e3
+    out["plain_fp64_one_system_at_a_time"] = {
+        "value": n1 / t1, "unit": "samples/s", "dof_solves_per_s": N * systems_per_sample * n1 / t1,
+        "sample": "%d sample(s) = %d systems, each solved alone (one tile, FP64 V-cycle and CG, same rtol)"
+                  % (n1, n1 * systems_per_sample)}
+    return out
 
 
 def our_arm(args):
@@ -308,6 +354,11 @@ def our_arm(args):
             "roofline": rl,
             "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["ms"] > 0},
             "clocks": clocks}
+    if not args.no_fp64_legs:
+        legs = fp64_legs(hier, kw, u, N, n_int + passes * n_nodes, args)
+        legs["speedup_batched_mixed_vs_plain_fp64"] = value / world / legs["plain_fp64_one_system_at_a_time"]["value"]
+        legs["speedup_batched_mixed_vs_batched_fp64"] = value / world / legs["batched_fp64"]["value"]
+        line["fp64_comparison"] = legs
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, total, sample, _ = oracle_estimate(c)
         line["cpu_baseline"] = {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle", "sample": sample,
@@ -328,6 +379,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--samples", type=int, default=0, help="override the samples per GPU (profiling runs)")
+    ap.add_argument("--no-fp64-legs", action="store_true", help="skip the plain FP64 comparison legs")
+    ap.add_argument("--plain-samples", type=int, default=1,
+                    help="samples timed on the one-system-at-a-time FP64 path")
     ap.add_argument("--smoother-degree", type=int, default=4)
     ap.add_argument("--cheb-ratio", type=float, default=12.0)
     ap.add_argument("--no-profile", dest="profile", action="store_false")

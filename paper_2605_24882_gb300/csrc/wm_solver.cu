@@ -1266,7 +1266,7 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
       {
         int keep = bt.active_tiles;
         bt.active_tiles = rep_tiles;
-        units(WM_PC_TRUERES, bt, (8.0 + 8.0 + Tb) * N, 4.0 * L0.nnz + 4.0 * N);
+        units(WM_PC_TRUERES, bt, (8.0 + Tb) * N, 4.0 * L0.nnz + 4.0 * N);  // loads b_s: shared by a sample's nodes
         bt.active_tiles = keep;
       }
       WM_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(int), s));
