@@ -1126,7 +1126,8 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   }
   // residual, restriction, coarse correction
   if (Lv.sten) {
-    WM_TRY(wm_sten_residual<T>(Lv, h->np, h->p, tiles, ws.sigma.p, rin, cur, res, ta, cre, s));
+    WM_TRY(wm_sten_residual<T>(Lv, h->np, h->p, tiles, ws.sigma.p, rin, cur, res, ta, ws.tile_uni.p, ws.n_uni_tiles,
+                               cre, s));
   } else {
     WM_LAUNCH(cre, s, k_residual<T><<<ggrid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, tiles, pk, ws.sigma.p, rin, cur, res,
                                                            ta));
@@ -1207,7 +1208,8 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
   bool df_res = bt.df_residual;
   for (it = 1; it <= bt.max_iter; ++it) {
     if (L0.sten) {
-      WM_TRY(wm_sten_apply_pq<T>(L0, h->np, h->p, tiles, ws.sigma.p, p, q, ws.tile_active.p, ws.part[0].p, s));
+      WM_TRY(wm_sten_apply_pq<T>(L0, h->np, h->p, tiles, ws.sigma.p, p, q, ws.tile_active.p, ws.tile_uni.p,
+                                 ws.n_uni_tiles, ws.part[0].p, s));
     } else {
       WM_LAUNCH(WM_PC_APPLY64, s, k_apply_pq<T><<<ggrid, kBlk, 0, s>>>(N, L0.W, ch, tiles, rows_of<T>(L0),
                                                                        ws.sigma.p, p, q, ws.tile_active.p,

@@ -54,8 +54,10 @@ struct DAcc {
   __device__ __forceinline__ double get() const { return d + (double)f; }
 };
 
+// per-block partial sums of the TPB tiles (tiles not in `act` are left untouched:
+// another kernel owns them)
 template <int TPB>
-__device__ __forceinline__ void block_reduce(double (&acc)[TPB], double* part, int t0, int tiles) {
+__device__ __forceinline__ void block_reduce(double (&acc)[TPB], double* part, int t0, int tiles, const bool* act) {
   __shared__ double red[TPB][BU][32];
 #pragma unroll
   for (int k = 0; k < TPB; ++k) red[k][threadIdx.y][threadIdx.x] = acc[k];
@@ -63,7 +65,7 @@ __device__ __forceinline__ void block_reduce(double (&acc)[TPB], double* part, i
   if (threadIdx.y == 0) {
 #pragma unroll
     for (int k = 0; k < TPB; ++k) {
-      if (t0 + k >= tiles) continue;
+      if (t0 + k >= tiles || !act[k]) continue;
       double s = 0.0;
 #pragma unroll
       for (int w = 0; w < BU; ++w) s += red[k][w][threadIdx.x];
@@ -112,7 +114,7 @@ struct ChebEpi {
         out[o] = zc[k] + c1[k] * (zc[k] - zp) + c2[k] * res / (ds + sg[k] * dm);
       }
   }
-  __device__ __forceinline__ void finish(int, int) {}
+  __device__ __forceinline__ void finish(int, int, const bool*) {}
 };
 
 // residual: res = r - A z
@@ -138,7 +140,7 @@ struct ResidEpi {
         res[o] = staged[0][k] - (aS[k] + sg[k] * aM[k]);
       }
   }
-  __device__ __forceinline__ void finish(int, int) {}
+  __device__ __forceinline__ void finish(int, int, const bool*) {}
 };
 
 // outer apply: q = A p, partial (p, q)
@@ -167,11 +169,11 @@ struct ApplyEpi {
         acc[k].add(zc[k] * qv);
       }
   }
-  __device__ __forceinline__ void finish(int t0, int tiles) {
+  __device__ __forceinline__ void finish(int t0, int tiles, const bool* act) {
     double a[TPB];
 #pragma unroll
     for (int k = 0; k < TPB; ++k) a[k] = acc[k].get();
-    block_reduce<TPB>(a, part, t0, tiles);
+    block_reduce<TPB>(a, part, t0, tiles, act);
   }
 };
 
@@ -212,7 +214,9 @@ struct TrueResEpi {
         acc[k] += rt * rt;
       }
   }
-  __device__ __forceinline__ void finish(int t0, int tiles) { block_reduce<TPB>(acc, part, t0, tiles); }
+  __device__ __forceinline__ void finish(int t0, int tiles, const bool* act) {
+    block_reduce<TPB>(acc, part, t0, tiles, act);
+  }
 };
 
 // ---------------------------------------------------------------- the kernel
@@ -275,7 +279,7 @@ __global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGe
   bool any = false;
 #pragma unroll
   for (int k = 0; k < TPB; ++k) {
-    // skip_uni: tiles with a single shift are done by k_cheb_uni
+    // skip_uni: tiles with a single shift are done by k_sten_uni
     act[k] = t0 + k < tiles && tile_active[t0 + k] && !(skip_uni && skip_uni[t0 + k]);
     any |= act[k];
   }
@@ -373,35 +377,45 @@ __global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGe
       }
     }
   }
-  epi.finish(t0, tiles);
+  epi.finish(t0, tiles, act);
 }
 
-// ------------------------------------------- Chebyshev step, one shift per tile
-// The same three-term step for blocks of one tile whose 32 systems share a
-// shift sigma (sample-major packing puts the 32 samples of one sinc node in
-// a tile).  After the DOF ids of the window are known, every global input of
-// the block (window of z, rows of r and z_prev, coefficient rows (S, M), the
-// diagonals) is requested in one batch of asynchronous copies; the block
-// then combines its rows once into A = S + sigma M and the weights
-// w = c2 / (dS + sigma dM), so an output costs one FMA per stencil entry and
-// no division, each combined row being read back with 16-byte shared loads.
-// One tile per block keeps the register window at (2p+1)^2 values; for
-// p = 2 in float the block holds 57 KB of shared memory and four blocks
-// share an SM.
-template <typename T, int P>
+// ------------------------------------------- operator steps, one shift per tile
+// Operator-type steps for blocks of one tile whose 32 systems share a shift
+// sigma (sample-major packing puts the 32 samples of one sinc node in a
+// tile):
+//   UNI_CHEB   three-term Chebyshev step  out = z + c1 (z - z_prev) + w (r - A z)
+//   UNI_RESID  residual                   out = r - A z
+//   UNI_APPLY  outer apply                out = A z, per-block partial (z, A z)
+// After the DOF ids of the window are known, every global input of the block
+// (window of z, the rows of r and z_prev, coefficient rows (S, M), the
+// diagonals) is requested in one batch of asynchronous copies; the block then
+// combines its rows once into A = S + sigma M (and w = c2 / (dS + sigma dM)),
+// so an output costs one FMA per stencil entry and no division, each combined
+// row being read back with 16-byte shared loads.  One tile per block keeps
+// the register window at (2p+1)^2 values; for p = 2 in float the Chebyshev
+// block holds 57 KB of shared memory and four blocks share an SM.
+enum { UNI_CHEB = 0, UNI_RESID = 1, UNI_APPLY = 2 };
+template <int MODE>
+struct UniRows {  // staged 32-system rows per output row
+  static constexpr int value = MODE == UNI_CHEB ? 2 : (MODE == UNI_RESID ? 1 : 0);
+};
+template <typename T, int P, int MODE>
 struct UniLayout {
   static constexpr int CU = BU + 2 * P, CV = BV + 2 * P, NC = CU * CV, S2 = (2 * P + 1) * (2 * P + 1);
   static constexpr int VEC = 16 / sizeof(T);                  // values per 16-byte load
   static constexpr int S2P = (S2 + VEC - 1) / VEC * VEC;      // padded combined row length
   static constexpr int CS = CoefStride<T, P>::value;          // (S, M) row stride of the level tables
+  static constexpr int NR = UniRows<MODE>::value;
+  static constexpr int ND = MODE == UNI_CHEB ? 2 : 0;         // staged diagonals dS, dM
   static constexpr size_t win = (size_t)NC * 32 * sizeof(T);
-  static constexpr size_t rows = (size_t)2 * BU * BV * 32 * sizeof(T);          // r, z_prev
+  static constexpr size_t rows = (size_t)NR * BU * BV * 32 * sizeof(T);
   static constexpr size_t raw = (size_t)BU * BV * CS * sizeof(typename V2<T>::type);  // (S, M) rows
   static constexpr size_t coef = (size_t)BU * BV * S2P * sizeof(T);
-  static constexpr size_t diag = (size_t)2 * BU * BV * sizeof(T);               // dS, dM
-  static constexpr size_t wts = (size_t)BU * BV * sizeof(T);
+  static constexpr size_t diag = (size_t)(ND + 1) * BU * BV * sizeof(T);         // dS, dM, w
+  static constexpr size_t diag16 = (diag + 15) / 16 * 16;
   static constexpr size_t ids = (size_t)(NC + BU * BV) * sizeof(int);
-  static constexpr size_t total = win + rows + raw + coef + diag + wts + ids;
+  static constexpr size_t total = win + rows + raw + coef + diag16 + ids;
 };
 template <typename T>
 struct Vec16;
@@ -430,24 +444,26 @@ __device__ __forceinline__ void cp_async_ca(void* smem, const void* gmem, int sr
                : "memory");
 }
 
-template <typename T, int P>
+template <typename T, int P, int MODE>
 __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P>::value)
-    k_cheb_uni(StenGeo G, const typename V2<T>::type* __restrict__ csm, const T* __restrict__ dS,
+    k_sten_uni(StenGeo G, const typename V2<T>::type* __restrict__ csm, const T* __restrict__ dS,
                const T* __restrict__ dM, const double* __restrict__ sigma, const typename V2<T>::type* __restrict__ ctab,
                const int* __restrict__ sid, int kstep, const T* __restrict__ z, const T* __restrict__ r, const T* prev,
-               T* out, int tiles, const int* __restrict__ tile_active, const int* __restrict__ tile_uni) {
+               T* out, int tiles, const int* __restrict__ tile_active, const int* __restrict__ tile_uni,
+               double* __restrict__ part) {
   using C2 = typename V2<T>::type;
-  using LY = UniLayout<T, P>;
+  using LY = UniLayout<T, P, MODE>;
   using VT = typename Vec16<T>::type;
   constexpr int SW = 2 * P + 1, CU = LY::CU, NC = LY::NC, S2 = LY::S2, S2P = LY::S2P, VEC = LY::VEC, CS = LY::CS;
+  constexpr int NR = LY::NR;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
-  T* srw = reinterpret_cast<T*>(smraw + LY::win);                                   // [2][64][32]
+  T* srw = reinterpret_cast<T*>(smraw + LY::win);                                   // [NR][64][32]
   C2* sraw = reinterpret_cast<C2*>(smraw + LY::win + LY::rows);                     // [64][CS]
   T* scf = reinterpret_cast<T*>(smraw + LY::win + LY::rows + LY::raw);              // [64][S2P]
-  T* sdg = reinterpret_cast<T*>(smraw + LY::win + LY::rows + LY::raw + LY::coef);   // [2][64]
-  T* swt = sdg + 2 * BU * BV;                                                       // [64]
-  int* sid_ = reinterpret_cast<int*>(smraw + LY::win + LY::rows + LY::raw + LY::coef + LY::diag + LY::wts);
+  T* sdg = reinterpret_cast<T*>(smraw + LY::win + LY::rows + LY::raw + LY::coef);   // [ND][64], then w [64]
+  T* swt = sdg + LY::ND * BU * BV;
+  int* sid_ = reinterpret_cast<int*>(smraw + LY::win + LY::rows + LY::raw + LY::coef + LY::diag16);
   int* srow = sid_ + NC;
   const int lane = threadIdx.x, w = threadIdx.y;
   const int tid = w * 32 + lane;
@@ -458,12 +474,14 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P>::value)
   const int m = b / G.nbv;
   const int t = blockIdx.y;
   if (t >= tiles || !tile_active[t] || !tile_uni[t]) return;  // mixed-shift tiles are done by k_sten
-  T sg, c1, c2;
+  T sg, c1 = 0, c2 = 0;
   {
     const int g = t * 32;  // every lane of the tile has this shift
-    const C2 c = ctab[sid[g] * WM_MAX_CHEB + kstep];
-    c1 = kstep == 0 ? (T)0 : c.x;
-    c2 = c.y;
+    if constexpr (MODE == UNI_CHEB) {
+      const C2 c = ctab[sid[g] * WM_MAX_CHEB + kstep];
+      c1 = kstep == 0 ? (T)0 : c.x;
+      c2 = c.y;
+    }
     sg = (T)sigma[g];
   }
   // phase 0: global DOF of every window cell and every output row
@@ -488,36 +506,41 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P>::value)
   constexpr int EPT = 16 / sizeof(T);               // values per chunk
   const T* zt = z + (size_t)t * G.N * 32;
   for (int c = tid; c < NC * ROWCH; c += BU * 32) {
-    const int part = c % ROWCH, cell = c / ROWCH;
+    const int part16 = c % ROWCH, cell = c / ROWCH;
     const int gi = sid_[cell];
-    cp_async16(sm + cell * 32 + part * EPT, gi >= 0 ? zt + (size_t)gi * 32 + part * EPT : z, gi >= 0 ? 16 : 0);
+    cp_async16(sm + cell * 32 + part16 * EPT, gi >= 0 ? zt + (size_t)gi * 32 + part16 * EPT : z, gi >= 0 ? 16 : 0);
   }
-  const T* rt = r + (size_t)t * G.N * 32;
-  const T* pt = prev ? prev + (size_t)t * G.N * 32 : nullptr;
-  for (int c = tid; c < 2 * BU * BV * ROWCH; c += BU * 32) {
-    const int part = c % ROWCH, o = (c / ROWCH) % (BU * BV), a = c / (ROWCH * BU * BV);
-    const int gi = srow[o];
-    const T* base = a == 0 ? rt : pt;
-    const bool ok = gi >= 0 && base != nullptr;
-    cp_async16(srw + (a * BU * BV + o) * 32 + part * EPT, ok ? base + (size_t)gi * 32 + part * EPT : z, ok ? 16 : 0);
+  if constexpr (NR > 0) {
+    const T* rt = r + (size_t)t * G.N * 32;
+    const T* pt = prev ? prev + (size_t)t * G.N * 32 : nullptr;
+    for (int c = tid; c < NR * BU * BV * ROWCH; c += BU * 32) {
+      const int part16 = c % ROWCH, o = (c / ROWCH) % (BU * BV), a = c / (ROWCH * BU * BV);
+      const int gi = srow[o];
+      const T* base = a == 0 ? rt : pt;
+      const bool ok = gi >= 0 && base != nullptr;
+      cp_async16(srw + (a * BU * BV + o) * 32 + part16 * EPT, ok ? base + (size_t)gi * 32 + part16 * EPT : z,
+                 ok ? 16 : 0);
+    }
   }
   for (int c = tid; c < BU * BV * RAWCH; c += BU * 32) {
-    const int part = c % RAWCH, o = c / RAWCH;
+    const int part16 = c % RAWCH, o = c / RAWCH;
     const int gi = srow[o];
-    cp_async16(reinterpret_cast<unsigned char*>(sraw) + o * (CS * sizeof(C2)) + part * 16,
-               gi >= 0 ? reinterpret_cast<const unsigned char*>(csm + (size_t)gi * CS) + part * 16
+    cp_async16(reinterpret_cast<unsigned char*>(sraw) + o * (CS * sizeof(C2)) + part16 * 16,
+               gi >= 0 ? reinterpret_cast<const unsigned char*>(csm + (size_t)gi * CS) + part16 * 16
                        : reinterpret_cast<const unsigned char*>(csm),
                gi >= 0 ? 16 : 0);
   }
-  for (int c = tid; c < 2 * BU * BV; c += BU * 32) {
-    const int o = c % (BU * BV);
-    const int gi = srow[o];
-    const T* base = c < BU * BV ? dS : dM;
-    cp_async_ca<sizeof(T)>(sdg + c, gi >= 0 ? base + gi : dS, gi >= 0 ? (int)sizeof(T) : 0);
+  if constexpr (MODE == UNI_CHEB) {
+    for (int c = tid; c < 2 * BU * BV; c += BU * 32) {
+      const int o = c % (BU * BV);
+      const int gi = srow[o];
+      const T* base = c < BU * BV ? dS : dM;
+      cp_async_ca<sizeof(T)>(sdg + c, gi >= 0 ? base + gi : dS, gi >= 0 ? (int)sizeof(T) : 0);
+    }
   }
   cp_async_wait_all();
   __syncthreads();
-  // combined rows and diagonal weights
+  // combined rows (and the Chebyshev diagonal weights)
   for (int c = tid; c < BU * BV * S2P; c += BU * 32) {
     const int o = c / S2P, sl = c - o * S2P;
     T a = 0;
@@ -527,40 +550,58 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P>::value)
     }
     scf[c] = a;
   }
-  for (int c = tid; c < BU * BV; c += BU * 32) swt[c] = srow[c] >= 0 ? c2 / (sdg[c] + sg * sdg[BU * BV + c]) : (T)0;
+  if constexpr (MODE == UNI_CHEB)
+    for (int c = tid; c < BU * BV; c += BU * 32)
+      swt[c] = srow[c] >= 0 ? c2 / (sdg[c] + sg * sdg[BU * BV + c]) : (T)0;
   __syncthreads();
   // phase 2: each warp sweeps the column iu with a ring of SW staged rows
   const int iu = bu * BU + w;
-  if (iu >= G.nlu) return;
-  T win[SW][SW];
+  DAcc<T> dot;  // UNI_APPLY: (z, A z) over this thread's outputs
+  if (iu < G.nlu) {
+    T win[SW][SW];
 #pragma unroll
-  for (int rr = 0; rr < SW - 1; ++rr)
+    for (int rr = 0; rr < SW - 1; ++rr)
 #pragma unroll
-    for (int du = 0; du < SW; ++du) win[rr][du] = sm[(rr * CU + w + du) * 32 + lane];
+      for (int du = 0; du < SW; ++du) win[rr][du] = sm[(rr * CU + w + du) * 32 + lane];
 #pragma unroll
-  for (int j = 0; j < BV; ++j) {
-    const int rnx = j + SW - 1;  // staged row entering the window
+    for (int j = 0; j < BV; ++j) {
+      const int rnx = j + SW - 1;  // staged row entering the window
 #pragma unroll
-    for (int du = 0; du < SW; ++du) win[rnx % SW][du] = sm[(rnx * CU + w + du) * 32 + lane];
-    const int o = j * BU + w;
-    const int i = srow[o];
-    if (i >= 0) {
-      const VT* cf = reinterpret_cast<const VT*>(scf + o * S2P);
-      T acc = 0;
+      for (int du = 0; du < SW; ++du) win[rnx % SW][du] = sm[(rnx * CU + w + du) * 32 + lane];
+      const int o = j * BU + w;
+      const int i = srow[o];
+      if (i >= 0) {
+        const VT* cf = reinterpret_cast<const VT*>(scf + o * S2P);
+        T acc = 0;
 #pragma unroll
-      for (int q = 0; q < S2P / VEC; ++q) {
-        const VT a = cf[q];
+        for (int q = 0; q < S2P / VEC; ++q) {
+          const VT a = cf[q];
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-          const int sl = q * VEC + e;
-          if (sl < S2) acc = fma(Vec16<T>::at(a, e), win[(j + sl / SW) % SW][sl % SW], acc);
+          for (int e = 0; e < VEC; ++e) {
+            const int sl = q * VEC + e;
+            if (sl < S2) acc = fma(Vec16<T>::at(a, e), win[(j + sl / SW) % SW][sl % SW], acc);
+          }
         }
+        const T zc = win[(j + P) % SW][P];
+        T res;
+        if constexpr (MODE == UNI_CHEB) {
+          const T rv = srw[o * 32 + lane];
+          const T zp = prev ? srw[(BU * BV + o) * 32 + lane] : (T)0;
+          res = zc + c1 * (zc - zp) + swt[o] * (rv - acc);
+        } else if constexpr (MODE == UNI_RESID) {
+          res = srw[o * 32 + lane] - acc;
+        } else {
+          res = acc;
+          dot.add(zc * acc);
+        }
+        out[((size_t)t * G.N + i) * 32 + lane] = res;
       }
-      const T zc = win[(j + P) % SW][P];
-      const T rv = srw[o * 32 + lane];
-      const T zp = prev ? srw[(BU * BV + o) * 32 + lane] : (T)0;
-      out[((size_t)t * G.N + i) * 32 + lane] = zc + c1 * (zc - zp) + swt[o] * (rv - acc);
     }
+  }
+  if constexpr (MODE == UNI_APPLY) {
+    const bool one[1] = {true};
+    double a1[1] = {dot.get()};
+    block_reduce<1>(a1, part, t, tiles, one);
   }
 }
 
@@ -844,11 +885,12 @@ __global__ void __launch_bounds__(BU * 32, 2)
       }
     }
   }
+  const bool one[1] = {true};
   double a2[1] = {(double)acc};
-  block_reduce<1>(a2, part, t, tiles);
+  block_reduce<1>(a2, part, t, tiles, one);
   __syncthreads();
   a2[0] = tiny && mine ? HUGE_VAL : (double)accb;  // fails the caller's error check
-  block_reduce<1>(a2, part_bound, t, tiles);
+  block_reduce<1>(a2, part_bound, t, tiles, one);
 }
 
 __global__ void k_build_csm(int N, int W, int cs32, int cs64, const int16_t* __restrict__ slot,
@@ -916,22 +958,22 @@ int wm_sten_chunks(const wm_level& L, int np) { return L.sten ? np * L.nbu * L.n
     default: return WM_ERR_UNSUPPORTED;            \
   }
 
-template <typename T, int P>
+template <typename T, int P, int MODE>
 static int launch_uni(const wm_level& L, int np, int tiles, int kstep, const double* sigma,
                       const typename V2<T>::type* ctab, const int* sid, const T* r, const T* z, const T* prev,
-                      T* out, const int* tile_active, const int* tile_uni, int cat, cudaStream_t s) {
-  constexpr size_t sm = UniLayout<T, P>::total;
+                      T* out, const int* tile_active, const int* tile_uni, double* part, int cat, cudaStream_t s) {
+  constexpr size_t sm = UniLayout<T, P, MODE>::total;
   static bool configured = false;
   if (!configured) {
-    WM_CUDA(cudaFuncSetAttribute(k_cheb_uni<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    WM_CUDA(cudaFuncSetAttribute(k_sten_uni<T, P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     configured = true;
   }
   const T* dS = std::is_same<T, double>::value ? (const T*)L.d_dS64.p : (const T*)L.d_dS32.p;
   const T* dM = std::is_same<T, double>::value ? (const T*)L.d_dM64.p : (const T*)L.d_dM32.p;
   dim3 grid(np * L.nbu * L.nbv, tiles);
-  WM_LAUNCH(cat, s, k_cheb_uni<T, P><<<grid, dim3(32, BU), sm, s>>>(geo_of(L), csm_of<T>(L), dS, dM, sigma, ctab, sid,
-                                                                   kstep, z, r, prev, out, tiles, tile_active,
-                                                                   tile_uni));
+  WM_LAUNCH(cat, s, k_sten_uni<T, P, MODE><<<grid, dim3(32, BU), sm, s>>>(geo_of(L), csm_of<T>(L), dS, dM, sigma,
+                                                                         ctab, sid, kstep, z, r, prev, out, tiles,
+                                                                         tile_active, tile_uni, part));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
@@ -941,8 +983,8 @@ int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, co
                       const typename StenC2<T>::type* ctab, const int* sid, const T* r, const T* z, const T* prev,
                       T* out, const int* tile_active, const int* tile_uni, int n_uni, int cat, cudaStream_t s) {
   if (n_uni > 0) {
-    WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP>(L, np, tiles, kstep, sigma, ctab, sid, r, z, prev, out,
-                                                 tile_active, tile_uni, cat, s))); });
+    WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_CHEB>(L, np, tiles, kstep, sigma, ctab, sid, r, z, prev, out,
+                                                           tile_active, tile_uni, nullptr, cat, s))); });
     if (n_uni >= tiles) return WM_OK;
   }
   ChebEpi<T, 2> e2;
@@ -973,7 +1015,12 @@ int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, co
 
 template <typename T>
 int wm_sten_residual(const wm_level& L, int np, int p, int tiles, const double* sigma, const T* r, const T* z,
-                     T* res, const int* tile_active, int cat, cudaStream_t s) {
+                     T* res, const int* tile_active, const int* tile_uni, int n_uni, int cat, cudaStream_t s) {
+  if (n_uni > 0) {
+    WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_RESID>(L, np, tiles, 0, sigma, nullptr, nullptr, r, z, nullptr,
+                                                            res, tile_active, tile_uni, nullptr, cat, s))); });
+    if (n_uni >= tiles) return WM_OK;
+  }
   ResidEpi<T, 2> e2;
   ResidEpi<T, 1> e1;
   e2.N = e1.N = L.N;
@@ -981,29 +1028,37 @@ int wm_sten_residual(const wm_level& L, int np, int p, int tiles, const double* 
   e2.res = e1.res = res;
   e2.sigma = e1.sigma = sigma;
   e2.in[0] = e1.in[0] = r;
+  const int* skip = n_uni > 0 ? tile_uni : nullptr;
   WM_DISPATCH_P(p, {
     if constexpr (Tpb<T, PP>::value == 2)
-      return launch<T, PP>(L, np, tiles, z, tile_active, e2, cat, s);
+      return launch<T, PP>(L, np, tiles, z, tile_active, e2, cat, s, skip);
     else
-      return launch<T, PP>(L, np, tiles, z, tile_active, e1, cat, s);
+      return launch<T, PP>(L, np, tiles, z, tile_active, e1, cat, s, skip);
   });
   return WM_OK;
 }
 
 template <typename T>
 int wm_sten_apply_pq(const wm_level& L, int np, int p, int tiles, const double* sigma, const T* pv, T* q,
-                     const int* tile_active, double* part, cudaStream_t s) {
+                     const int* tile_active, const int* tile_uni, int n_uni, double* part, cudaStream_t s) {
+  if (n_uni > 0) {
+    WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_APPLY>(L, np, tiles, 0, sigma, nullptr, nullptr, nullptr, pv,
+                                                            nullptr, q, tile_active, tile_uni, part, WM_PC_APPLY64,
+                                                            s))); });
+    if (n_uni >= tiles) return WM_OK;
+  }
   ApplyEpi<T, 2> e2;
   ApplyEpi<T, 1> e1;
   e2.N = e1.N = L.N;
   e2.q = e1.q = q;
   e2.sigma = e1.sigma = sigma;
   e2.part = e1.part = part;
+  const int* skip = n_uni > 0 ? tile_uni : nullptr;
   WM_DISPATCH_P(p, {
     if constexpr (Tpb<T, PP>::value == 2)
-      return launch<T, PP>(L, np, tiles, pv, tile_active, e2, WM_PC_APPLY64, s);
+      return launch<T, PP>(L, np, tiles, pv, tile_active, e2, WM_PC_APPLY64, s, skip);
     else
-      return launch<T, PP>(L, np, tiles, pv, tile_active, e1, WM_PC_APPLY64, s);
+      return launch<T, PP>(L, np, tiles, pv, tile_active, e1, WM_PC_APPLY64, s, skip);
   });
   return WM_OK;
 }
@@ -1058,13 +1113,13 @@ template int wm_sten_cheb_step<double>(const wm_level&, int, int, int, int, cons
                                        const int*, const double*, const double*, const double*, double*, const int*,
                                        const int*, int, int, cudaStream_t);
 template int wm_sten_residual<float>(const wm_level&, int, int, int, const double*, const float*, const float*, float*,
-                                     const int*, int, cudaStream_t);
+                                     const int*, const int*, int, int, cudaStream_t);
 template int wm_sten_residual<double>(const wm_level&, int, int, int, const double*, const double*, const double*,
-                                      double*, const int*, int, cudaStream_t);
+                                      double*, const int*, const int*, int, int, cudaStream_t);
 template int wm_sten_apply_pq<float>(const wm_level&, int, int, int, const double*, const float*, float*, const int*,
-                                     double*, cudaStream_t);
+                                     const int*, int, double*, cudaStream_t);
 template int wm_sten_apply_pq<double>(const wm_level&, int, int, int, const double*, const double*, double*,
-                                      const int*, double*, cudaStream_t);
+                                      const int*, const int*, int, double*, cudaStream_t);
 template int wm_sten_true_residual<float>(const wm_level&, int, int, int, const double*, const double*, const double*,
                                           const int*, const int*, const int*, float*, double*, cudaStream_t);
 template int wm_sten_true_residual<double>(const wm_level&, int, int, int, const double*, const double*,

@@ -34,12 +34,15 @@ template <typename T>
 int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, const double* sigma,
                       const typename StenC2<T>::type* ctab, const int* sid, const T* r, const T* z, const T* prev,
                       T* out, const int* tile_active, const int* tile_uni, int n_uni, int cat, cudaStream_t s);
+// residual res = r - A z and outer apply q = A p with per-block partial sums
+// (p, q) in `part` ([tile][chunk][32], chunk = spatial block); one-shift
+// tiles (tile_uni, n_uni of them) take the combined-coefficient kernel
 template <typename T>
 int wm_sten_residual(const wm_level& L, int np, int p, int tiles, const double* sigma, const T* r, const T* z,
-                     T* res, const int* tile_active, int cat, cudaStream_t s);
+                     T* res, const int* tile_active, const int* tile_uni, int n_uni, int cat, cudaStream_t s);
 template <typename T>
 int wm_sten_apply_pq(const wm_level& L, int np, int p, int tiles, const double* sigma, const T* pv, T* q,
-                     const int* tile_active, double* part, cudaStream_t s);
+                     const int* tile_active, const int* tile_uni, int n_uni, double* part, cudaStream_t s);
 template <typename Tr>
 int wm_sten_true_residual(const wm_level& L, int np, int p, int tiles, const double* sigma, const double* x,
                           const double* rhs, const int* src_of, const int* rep, const int* tile_rep, Tr* r,
