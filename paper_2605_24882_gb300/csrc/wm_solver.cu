@@ -878,6 +878,11 @@ int Batch::chunks_for(int N) const {
   return std::max(1, std::min(64, (N + 127) / 128));
 }
 
+// row chunks per tile inside the V-cycle (no partial sums there): at least 16
+// rows each (two per warp), so that the small coarse levels still spread
+// over the SMs instead of running a few long, latency-bound warps
+static int vcycle_chunks(int N) { return std::max(1, std::min(64, (N + 15) / 16)); }
+
 template <typename T>
 static T* vb(VBuf& b);
 template <>
@@ -1075,7 +1080,7 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   LevelBufs& B = ws.lvl[l];
   const int* ta = ws.tile_active.p;
   const int tiles = bt.tiles;
-  const int ch = bt.chunks_for(Lv.N);
+  const int ch = vcycle_chunks(Lv.N);
   const dim3 ggrid(ch, groups(tiles));
   const double* lmax = ws.lmax.p + (size_t)l * bt.nshift;
   (void)lmax;
@@ -1136,7 +1141,7 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   WM_TRY(step_rc);
   const wm_level& Cv = h->lv[l + 1];
   T* rc = vb<T>(ws.lvl[l + 1].r);
-  const int chc = bt.chunks_for(Cv.N);
+  const int chc = vcycle_chunks(Cv.N);
   WM_LAUNCH(WM_PC_RESTRICT, s, k_transfer<T, false><<<dim3(chc, groups(tiles)), kBlk, 0, s>>>(
                                    Cv.N, Lv.N, chc, tiles, Lv.d_Rptr.p, R_of<T>(Lv), res, rc, ta));
   units(WM_PC_RESTRICT, bt, Tb * (Lv.N + Cv.N), 2.0 * Lv.nnzP);
