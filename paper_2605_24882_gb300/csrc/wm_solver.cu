@@ -301,9 +301,9 @@ __global__ void k_update_xr(int N, int chunks, int tiles, const double* __restri
 template <typename T>
 __global__ void k_dots_rz_zq(int N, int chunks, int tiles, const T* __restrict__ r, const T* __restrict__ z,
                              const T* __restrict__ q, const int* __restrict__ tile_active, double* part_rz,
-                             double* part_zq) {
+                             double* part_zq, const int* __restrict__ skip) {
   int t = blockIdx.y;
-  if (!tile_active[t]) return;
+  if (!tile_active[t] || (skip && skip[t])) return;  // skip: tiles whose partials another kernel formed
   RowRange rr = chunk_rows(N, chunks);
   Acc<T> a0, a1;
   for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
@@ -1072,9 +1072,22 @@ static int build_cheb_table(const wm_hier* h, WorkSpace& ws, const Batch& bt, cu
   return WM_OK;
 }
 
-// one V-cycle from level l on residual rin, returns the buffer holding z
+// partial sums the outer CG wants from the V-cycle's last step
 template <typename T>
-static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const T* rin, T** zout, cudaStream_t s) {
+struct VDots {
+  const T* q = nullptr;
+  double* prz = nullptr;
+  double* pzq = nullptr;
+  bool fused = false;
+};
+
+// one V-cycle from level l on residual rin, returns the buffer holding z.
+// With dots given (level 0 of the outer solve), the last post-smoothing step of
+// the one-shift tiles also forms the partials (r, z) and (z, q) of the outer CG
+// in dots->prz / dots->pzq; dots->fused reports whether it did.
+template <typename T>
+static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const T* rin, T** zout, cudaStream_t s,
+                  VDots<T>* dots = nullptr) {
   const int L = (int)h->lv.size();
   const wm_level& Lv = h->lv[l];
   LevelBufs& B = ws.lvl[l];
@@ -1107,11 +1120,14 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   int step_rc = WM_OK;
   // three-term step k from z = cur: the result overwrites z_prev in `oth`
   // (has_prev false: z_prev = 0, or unused at k = 0)
-  auto cheb_step = [&](int k, const T* zin, T* zo, bool has_prev) {
+  auto cheb_step = [&](int k, const T* zin, T* zo, bool has_prev, VDots<T>* dd) {
     const T* prev = has_prev ? zo : nullptr;
     if (Lv.sten) {
+      const bool fuse = dd && ws.n_uni_tiles > 0;
       int e = wm_sten_cheb_step<T>(Lv, h->np, h->p, tiles, k, ws.sigma.p, ctab, ws.sid.p, rin, zin, prev, zo, ta,
-                                   ws.tile_uni.p, ws.n_uni_tiles, csm, s);
+                                   ws.tile_uni.p, ws.n_uni_tiles, csm, s, fuse ? dd->q : nullptr,
+                                   fuse ? dd->prz : nullptr, fuse ? dd->pzq : nullptr);
+      if (fuse) dd->fused = true;
       if (e != WM_OK) step_rc = e;
     } else {
       WM_LAUNCH(csm, s, k_cheb_step<T><<<ggrid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, tiles, k, pk, dS, dM, ws.sigma.p,
@@ -1126,7 +1142,7 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   T* cur = za;
   T* oth = zb;
   for (int k = 1; k < nu; ++k) {
-    cheb_step(k, cur, oth, k >= 2);  // z_0 = 0
+    cheb_step(k, cur, oth, k >= 2, nullptr);  // z_0 = 0
     std::swap(cur, oth);
   }
   // residual, restriction, coarse correction
@@ -1152,7 +1168,7 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   units(WM_PC_PROLONG, bt, Tb * (2.0 * Lv.N + Cv.N), 2.0 * Lv.nnzP);
   // post-smoothing from the corrected z (no z_prev at step 0)
   for (int k = 0; k < nu; ++k) {
-    cheb_step(k, cur, oth, k >= 1);
+    cheb_step(k, cur, oth, k >= 1, k == nu - 1 ? dots : nullptr);
     std::swap(cur, oth);
   }
   WM_TRY(step_rc);
@@ -1197,7 +1213,8 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
   T* z = nullptr;
   WM_TRY(vcycle<T>(h, ws, bt, 0, r, &z, s));
   WM_LAUNCH(WM_PC_CGVEC, s, k_dots_rz_zq<T><<<grid, kBlk, 0, s>>>(N, ch, tiles, r, z, (const T*)nullptr,
-                                                                  ws.tile_active.p, ws.part[1].p, ws.part[2].p));
+                                                                  ws.tile_active.p, ws.part[1].p, ws.part[2].p,
+                                                                  (const int*)nullptr));
   WM_LAUNCH(WM_PC_SCALAR, s, k_scal_init<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[0].p, ws.part[1].p, ws.src_of.p,
                                                             ws.bb.p, ws.rho.p, ws.rr.p, ws.rr_ref.p, ws.active.p,
                                                             ws.restart.p, ws.flags.p));
@@ -1288,12 +1305,24 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
       bt.active_tiles = ws.host_small[2];
     }
     if (n_active == 0) break;
-    WM_TRY(vcycle<T>(h, ws, bt, 0, r, &z, s));
-    WM_LAUNCH(WM_PC_CGVEC, s, k_dots_rz_zq<T><<<grid, kBlk, 0, s>>>(N, ch, tiles, r, z, q, ws.tile_active.p,
-                                                                    ws.part[1].p, ws.part[2].p));
-    units(WM_PC_CGVEC, bt, 3.0 * Tb * N, 4.0 * N);
-    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_beta<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[1].p, ws.part[2].p, ws.alpha.p,
-                                                              ws.active.p, ws.restart.p, ws.rho.p, ws.beta.p));
+    // the V-cycle's last step forms (r, z) and (z, q) for the one-shift tiles
+    // (chunks = its spatial blocks); the dots kernel covers the other tiles
+    VDots<T> vd;
+    vd.q = q;
+    vd.prz = ws.part[1].p;
+    vd.pzq = ws.part[2].p;
+    WM_TRY(vcycle<T>(h, ws, bt, 0, r, &z, s, &vd));
+    const int ch_dots = vd.fused ? ch_op : ch;
+    if (vd.fused) units(WM_PC_SMOOTH0, bt, Tb * N, 4.0 * N);  // q read and the two products
+    if (!vd.fused || ws.n_uni_tiles < tiles) {
+      WM_LAUNCH(WM_PC_CGVEC, s, k_dots_rz_zq<T><<<dim3(ch_dots, tiles), kBlk, 0, s>>>(
+                                    N, ch_dots, tiles, r, z, q, ws.tile_active.p, ws.part[1].p, ws.part[2].p,
+                                    vd.fused ? ws.tile_uni.p : (const int*)nullptr));
+      if (!vd.fused) units(WM_PC_CGVEC, bt, 3.0 * Tb * N, 4.0 * N);
+    }
+    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_beta<<<sb, 128, 0, s>>>(nsys_pad, ch_dots, ws.part[1].p, ws.part[2].p,
+                                                              ws.alpha.p, ws.active.p, ws.restart.p, ws.rho.p,
+                                                              ws.beta.p));
     WM_LAUNCH(WM_PC_CGVEC, s, k_update_p<T><<<grid, kBlk, 0, s>>>(N, ch, ws.beta.p, z, p, ws.tile_active.p));
     units(WM_PC_CGVEC, bt, 3.0 * Tb * N, 2.0 * N);
     WM_CUDA(cudaGetLastError());
@@ -1383,7 +1412,7 @@ int wm_system_dots(WorkSpace& ws, int tiles, int N, const double* a, const doubl
   WM_TRY(set_all_tiles_active(ws, tiles, s));
   WM_LAUNCH(WM_PC_SINC, s, k_dots_rz_zq<double><<<dim3(ch, tiles), kBlk, 0, s>>>(
                                N, ch, tiles, a, b, (const double*)nullptr, ws.tile_active.p, ws.part[1].p,
-                               ws.part[2].p));
+                               ws.part[2].p, (const int*)nullptr));
   WM_LAUNCH(WM_PC_SINC, s, k_sum_parts<<<nblk(nsys_pad, 128), 128, 0, s>>>(nsys_pad, ch, ws.part[1].p, ws.dots.p));
   WM_CUDA(cudaGetLastError());
   out.resize(nsys_pad);

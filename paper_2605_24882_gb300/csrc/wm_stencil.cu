@@ -395,10 +395,17 @@ __global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGe
 // row being read back with 16-byte shared loads.  One tile per block keeps
 // the register window at (2p+1)^2 values; for p = 2 in float the Chebyshev
 // block holds 57 KB of shared memory and four blocks share an SM.
-enum { UNI_CHEB = 0, UNI_RESID = 1, UNI_APPLY = 2 };
+//   UNI_CHEBDOT  the Chebyshev step that ends a V-cycle, also forming the
+//                per-block partials (r, z_new) and (z_new, q) of the outer CG
+//                (q staged as a third row)
+enum { UNI_CHEB = 0, UNI_RESID = 1, UNI_APPLY = 2, UNI_CHEBDOT = 3 };
+template <int MODE>
+struct UniCheb {
+  static constexpr bool value = MODE == UNI_CHEB || MODE == UNI_CHEBDOT;
+};
 template <int MODE>
 struct UniRows {  // staged 32-system rows per output row
-  static constexpr int value = MODE == UNI_CHEB ? 2 : (MODE == UNI_RESID ? 1 : 0);
+  static constexpr int value = MODE == UNI_CHEBDOT ? 3 : (MODE == UNI_CHEB ? 2 : (MODE == UNI_RESID ? 1 : 0));
 };
 template <typename T, int P, int MODE>
 struct UniLayout {
@@ -407,7 +414,7 @@ struct UniLayout {
   static constexpr int S2P = (S2 + VEC - 1) / VEC * VEC;      // padded combined row length
   static constexpr int CS = CoefStride<T, P>::value;          // (S, M) row stride of the level tables
   static constexpr int NR = UniRows<MODE>::value;
-  static constexpr int ND = MODE == UNI_CHEB ? 2 : 0;         // staged diagonals dS, dM
+  static constexpr int ND = UniCheb<MODE>::value ? 2 : 0;     // staged diagonals dS, dM
   static constexpr size_t win = (size_t)NC * 32 * sizeof(T);
   static constexpr size_t rows = (size_t)NR * BU * BV * 32 * sizeof(T);
   static constexpr size_t raw = (size_t)BU * BV * CS * sizeof(typename V2<T>::type);  // (S, M) rows
@@ -450,9 +457,10 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P>::value)
                const T* __restrict__ dM, const double* __restrict__ sigma, const typename V2<T>::type* __restrict__ ctab,
                const int* __restrict__ sid, int kstep, const T* __restrict__ z, const T* __restrict__ r, const T* prev,
                T* out, int tiles, const int* __restrict__ tile_active, const int* __restrict__ tile_uni,
-               double* __restrict__ part) {
+               double* __restrict__ part, const T* __restrict__ qd, double* __restrict__ part2) {
   using C2 = typename V2<T>::type;
   using LY = UniLayout<T, P, MODE>;
+  constexpr bool CHEB = UniCheb<MODE>::value;
   using VT = typename Vec16<T>::type;
   constexpr int SW = 2 * P + 1, CU = LY::CU, NC = LY::NC, S2 = LY::S2, S2P = LY::S2P, VEC = LY::VEC, CS = LY::CS;
   constexpr int NR = LY::NR;
@@ -477,7 +485,7 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P>::value)
   T sg, c1 = 0, c2 = 0;
   {
     const int g = t * 32;  // every lane of the tile has this shift
-    if constexpr (MODE == UNI_CHEB) {
+    if constexpr (CHEB) {
       const C2 c = ctab[sid[g] * WM_MAX_CHEB + kstep];
       c1 = kstep == 0 ? (T)0 : c.x;
       c2 = c.y;
@@ -513,10 +521,11 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P>::value)
   if constexpr (NR > 0) {
     const T* rt = r + (size_t)t * G.N * 32;
     const T* pt = prev ? prev + (size_t)t * G.N * 32 : nullptr;
+    const T* qt = (MODE == UNI_CHEBDOT && qd) ? qd + (size_t)t * G.N * 32 : nullptr;
     for (int c = tid; c < NR * BU * BV * ROWCH; c += BU * 32) {
       const int part16 = c % ROWCH, o = (c / ROWCH) % (BU * BV), a = c / (ROWCH * BU * BV);
       const int gi = srow[o];
-      const T* base = a == 0 ? rt : pt;
+      const T* base = a == 0 ? rt : (a == 1 ? pt : qt);
       const bool ok = gi >= 0 && base != nullptr;
       cp_async16(srw + (a * BU * BV + o) * 32 + part16 * EPT, ok ? base + (size_t)gi * 32 + part16 * EPT : z,
                  ok ? 16 : 0);
@@ -530,7 +539,7 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P>::value)
                        : reinterpret_cast<const unsigned char*>(csm),
                gi >= 0 ? 16 : 0);
   }
-  if constexpr (MODE == UNI_CHEB) {
+  if constexpr (CHEB) {
     for (int c = tid; c < 2 * BU * BV; c += BU * 32) {
       const int o = c % (BU * BV);
       const int gi = srow[o];
@@ -550,13 +559,14 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P>::value)
     }
     scf[c] = a;
   }
-  if constexpr (MODE == UNI_CHEB)
+  if constexpr (CHEB)
     for (int c = tid; c < BU * BV; c += BU * 32)
       swt[c] = srow[c] >= 0 ? c2 / (sdg[c] + sg * sdg[BU * BV + c]) : (T)0;
   __syncthreads();
   // phase 2: each warp sweeps the column iu with a ring of SW staged rows
   const int iu = bu * BU + w;
-  DAcc<T> dot;  // UNI_APPLY: (z, A z) over this thread's outputs
+  DAcc<T> dot;   // UNI_APPLY: (z, A z); UNI_CHEBDOT: (r, z_new) over this thread's outputs
+  DAcc<T> dot2;  // UNI_CHEBDOT: (z_new, q)
   if (iu < G.nlu) {
     T win[SW][SW];
 #pragma unroll
@@ -584,10 +594,14 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P>::value)
         }
         const T zc = win[(j + P) % SW][P];
         T res;
-        if constexpr (MODE == UNI_CHEB) {
+        if constexpr (CHEB) {
           const T rv = srw[o * 32 + lane];
           const T zp = prev ? srw[(BU * BV + o) * 32 + lane] : (T)0;
           res = zc + c1 * (zc - zp) + swt[o] * (rv - acc);
+          if constexpr (MODE == UNI_CHEBDOT) {
+            dot.add(rv * res);
+            if (qd) dot2.add(res * srw[(2 * BU * BV + o) * 32 + lane]);
+          }
         } else if constexpr (MODE == UNI_RESID) {
           res = srw[o * 32 + lane] - acc;
         } else {
@@ -598,10 +612,15 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P>::value)
       }
     }
   }
-  if constexpr (MODE == UNI_APPLY) {
+  if constexpr (MODE == UNI_APPLY || MODE == UNI_CHEBDOT) {
     const bool one[1] = {true};
     double a1[1] = {dot.get()};
     block_reduce<1>(a1, part, t, tiles, one);
+    if (MODE == UNI_CHEBDOT && qd) {
+      __syncthreads();
+      a1[0] = dot2.get();
+      block_reduce<1>(a1, part2, t, tiles, one);
+    }
   }
 }
 
@@ -961,7 +980,8 @@ int wm_sten_chunks(const wm_level& L, int np) { return L.sten ? np * L.nbu * L.n
 template <typename T, int P, int MODE>
 static int launch_uni(const wm_level& L, int np, int tiles, int kstep, const double* sigma,
                       const typename V2<T>::type* ctab, const int* sid, const T* r, const T* z, const T* prev,
-                      T* out, const int* tile_active, const int* tile_uni, double* part, int cat, cudaStream_t s) {
+                      T* out, const int* tile_active, const int* tile_uni, double* part, int cat, cudaStream_t s,
+                      const T* qd = nullptr, double* part2 = nullptr) {
   constexpr size_t sm = UniLayout<T, P, MODE>::total;
   static bool configured = false;
   if (!configured) {
@@ -973,7 +993,7 @@ static int launch_uni(const wm_level& L, int np, int tiles, int kstep, const dou
   dim3 grid(np * L.nbu * L.nbv, tiles);
   WM_LAUNCH(cat, s, k_sten_uni<T, P, MODE><<<grid, dim3(32, BU), sm, s>>>(geo_of(L), csm_of<T>(L), dS, dM, sigma,
                                                                          ctab, sid, kstep, z, r, prev, out, tiles,
-                                                                         tile_active, tile_uni, part));
+                                                                         tile_active, tile_uni, part, qd, part2));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
@@ -981,8 +1001,13 @@ static int launch_uni(const wm_level& L, int np, int tiles, int kstep, const dou
 template <typename T>
 int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, const double* sigma,
                       const typename StenC2<T>::type* ctab, const int* sid, const T* r, const T* z, const T* prev,
-                      T* out, const int* tile_active, const int* tile_uni, int n_uni, int cat, cudaStream_t s) {
-  if (n_uni > 0) {
+                      T* out, const int* tile_active, const int* tile_uni, int n_uni, int cat, cudaStream_t s,
+                      const T* q, double* part_rz, double* part_zq) {
+  if (n_uni > 0 && part_rz) {
+    WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_CHEBDOT>(L, np, tiles, kstep, sigma, ctab, sid, r, z, prev,
+                                                              out, tile_active, tile_uni, part_rz, cat, s, q,
+                                                              part_zq))); });
+  } else if (n_uni > 0) {
     WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_CHEB>(L, np, tiles, kstep, sigma, ctab, sid, r, z, prev, out,
                                                            tile_active, tile_uni, nullptr, cat, s))); });
     if (n_uni >= tiles) return WM_OK;
@@ -1108,10 +1133,10 @@ int wm_sten_true_residual_df(const wm_level& L, int np, int p, int tiles, const 
 
 template int wm_sten_cheb_step<float>(const wm_level&, int, int, int, int, const double*, const float2*,
                                       const int*, const float*, const float*, const float*, float*, const int*,
-                                      const int*, int, int, cudaStream_t);
+                                      const int*, int, int, cudaStream_t, const float*, double*, double*);
 template int wm_sten_cheb_step<double>(const wm_level&, int, int, int, int, const double*, const double2*,
                                        const int*, const double*, const double*, const double*, double*, const int*,
-                                       const int*, int, int, cudaStream_t);
+                                       const int*, int, int, cudaStream_t, const double*, double*, double*);
 template int wm_sten_residual<float>(const wm_level&, int, int, int, const double*, const float*, const float*, float*,
                                      const int*, const int*, int, int, cudaStream_t);
 template int wm_sten_residual<double>(const wm_level&, int, int, int, const double*, const double*, const double*,

@@ -33,7 +33,11 @@ struct StenC2<double> {
 template <typename T>
 int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, const double* sigma,
                       const typename StenC2<T>::type* ctab, const int* sid, const T* r, const T* z, const T* prev,
-                      T* out, const int* tile_active, const int* tile_uni, int n_uni, int cat, cudaStream_t s);
+                      T* out, const int* tile_active, const int* tile_uni, int n_uni, int cat, cudaStream_t s,
+                      const T* q = nullptr, double* part_rz = nullptr, double* part_zq = nullptr);
+// With part_rz set, the one-shift tiles of the step also leave per-block partial
+// sums (r, out) in part_rz and, with q set, (out, q) in part_zq ([tile][chunk][32],
+// chunk = spatial block); the other tiles get none (the caller forms them).
 // residual res = r - A z and outer apply q = A p with per-block partial sums
 // (p, q) in `part` ([tile][chunk][32], chunk = spatial block); one-shift
 // tiles (tile_uni, n_uni of them) take the combined-coefficient kernel
