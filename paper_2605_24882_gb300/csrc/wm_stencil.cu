@@ -686,8 +686,10 @@ int launch(const wm_level& L, int np, int tiles, const T* src, const int* tile_a
 //    significant bits for the stencil sum);
 //  * where the 32 shifts of a tile are equal (sample-major packing) each
 //    coefficient row is combined once per block into A = S + sigma M in the
-//    same arithmetic and one sum is formed; otherwise S x and M x are summed
-//    separately and combined per output.
+//    same arithmetic and one sum is formed, two output rows at a time on the
+//    packed FP32 instructions (FMUL2/FFMA2/FADD2, rounding per component as
+//    the scalar ones); otherwise S x and M x are summed separately and
+//    combined per output.
 // Each output also accumulates B_i = sum_j |a_ij x_j| (float, from the rounded
 // hi products, within a factor 1 + 2^-22 of the exact sum): the entry's
 // rounding error stays below 2^-42 B_i (operand splits 2^-47 and 2^-48,
@@ -755,6 +757,23 @@ __device__ __forceinline__ float2 df_axpy(float ah, float al, float gh, float gl
   float h, l;
   two_sum(t, lo, h, l);
   return make_float2(h, l);
+}
+
+// the same accumulation for two outputs at once on the packed FP32 pipe
+// (FMUL2 / FFMA2 / FADD2: each component rounds exactly as the scalar form)
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ void df_acc2(float2& s, float2& c, float& b0, float& b1, float2 ah, float2 al, float2 xh,
+                                        float2 xl) {
+  const float2 p = __fmul2_rn(ah, xh);
+  b0 = __fadd_rn(b0, fabsf(p.x));
+  b1 = __fadd_rn(b1, fabsf(p.y));
+  float2 e = __ffma2_rn(ah, xh, neg2(p));
+  e = __ffma2_rn(ah, xl, __ffma2_rn(al, xh, e));
+  const float2 t = __fadd2_rn(s, p);
+  const float2 bp = __fadd2_rn(t, neg2(s));
+  const float2 err = __fadd2_rn(__fadd2_rn(s, neg2(__fadd2_rn(t, neg2(bp)))), __fadd2_rn(p, neg2(bp)));
+  s = t;
+  c = __fadd2_rn(c, __fadd2_rn(err, e));
 }
 
 template <int P>
@@ -838,10 +857,29 @@ __global__ void __launch_bounds__(BU * 32, 2)
   const int sgl0 = __shfl_sync(0xffffffffu, sgl, 0);
   const bool uni = __all_sync(0xffffffffu, (sgh == sgh0) & (sgl == sgl0));
   if (uni) {
-    for (int c = tid; c < BU * BV * S2; c += BU * 32) {
-      float4 q = scf[c];
-      float2 a = df_axpy(q.x, q.y, sgp.x, sgp.y, q.z, q.w);
-      scf[c] = make_float4(a.x, a.y, 0.f, 0.f);
+    // combined rows A = S + sigma M, rewritten in place as row pairs: entry
+    // (pair jj*BU + w, slot) = (A_hi of rows 2jj and 2jj+1, A_lo of both), the
+    // operand layout of the packed two-row loop below
+    constexpr int NPS = BU * (BV / 2) * S2;            // pair-slot entries
+    constexpr int KPT = (NPS + BU * 32 - 1) / (BU * 32);  // per thread
+    float4 pv[KPT];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int c = tid + k * BU * 32;
+      if (c < NPS) {
+        const int pi = c / S2, sl = c - pi * S2;
+        const int o0 = (pi / BU) * 2 * BU + pi % BU;  // rows 2jj and 2jj+1 of column w
+        const float4 q0 = scf[o0 * S2 + sl], q1 = scf[(o0 + BU) * S2 + sl];
+        const float2 a0 = df_axpy(q0.x, q0.y, sgp.x, sgp.y, q0.z, q0.w);
+        const float2 a1 = df_axpy(q1.x, q1.y, sgp.x, sgp.y, q1.z, q1.w);
+        pv[k] = make_float4(a0.x, a1.x, a0.y, a1.y);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int c = tid + k * BU * 32;
+      if (c < NPS) scf[c] = pv[k];
     }
   }
   __syncthreads();
@@ -864,21 +902,21 @@ __global__ void __launch_bounds__(BU * 32, 2)
     for (int j = 0; j < BV; j += 2) {
       const int i0 = srow[j * BU + w], i1 = srow[(j + 1) * BU + w];
       if (i0 < 0 && i1 < 0) continue;  // rows past the patch edge or owned by another patch
-      const float4* cf0 = scf + (size_t)(j * BU + w) * S2;
-      const float4* cf1 = cf0 + (size_t)BU * S2;
+      const float4* cf = scf + (size_t)((j / 2) * BU + w) * S2;  // row pair (j, j+1)
       const float2* zw = smf + ((size_t)j * CU + w) * 32 + lane;
-      float s0 = 0.f, c0 = 0.f, b0 = 0.f, s1 = 0.f, c1 = 0.f, b1 = 0.f;
+      float2 sp = make_float2(0.f, 0.f), cp = make_float2(0.f, 0.f);
+      float b0 = 0.f, b1 = 0.f;
 #pragma unroll
       for (int dv = 0; dv < SW; ++dv)
 #pragma unroll
         for (int du = 0; du < SW; ++du) {
-          float4 q0 = cf0[dv * SW + du], q1 = cf1[dv * SW + du];
-          float2 z0 = zw[(dv * CU + du) * 32], z1 = zw[((dv + 1) * CU + du) * 32];
-          df_acc(s0, c0, b0, q0.x, q0.y, z0.x, z0.y);
-          df_acc(s1, c1, b1, q1.x, q1.y, z1.x, z1.y);
+          const float4 q = cf[dv * SW + du];
+          const float2 z0 = zw[(dv * CU + du) * 32], z1 = zw[((dv + 1) * CU + du) * 32];
+          df_acc2(sp, cp, b0, b1, make_float2(q.x, q.y), make_float2(q.z, q.w), make_float2(z0.x, z1.x),
+                  make_float2(z0.y, z1.y));
         }
-      if (i0 >= 0) emit(i0, s0, c0, b0);
-      if (i1 >= 0) emit(i1, s1, c1, b1);
+      if (i0 >= 0) emit(i0, sp.x, cp.x, b0);
+      if (i1 >= 0) emit(i1, sp.y, cp.y, b1);
     }
   } else if (iu < G.nlu) {
 #pragma unroll 1
