@@ -238,6 +238,13 @@ def traffic_for(name, alg_bytes_per_launch):
     return e["dram_per_alg_byte"] * alg_bytes_per_launch
 
 
+def surface_text(c):
+    if c["kind"] == "sphere":
+        return "unit sphere, 6 patches x %d x %d elements, p = %d" % (c["n_u"], c["n_v"], c["p"])
+    return "torus R = %g, r = %g, one periodic patch of %d x %d elements, p = %d" % (
+        c.get("R", 1.0), c.get("r", 0.4), c["n_u"], c["n_v"], c["p"])
+
+
 def fp64_legs(hier, kw, u_mixed, N, systems_per_sample, args):
     """The same fields by the plain FP64 path, outside the timed region: (1) the
     batched solve in FP64 (same kernels, FP64 V-cycle); (2) one system at a
@@ -339,11 +346,12 @@ def our_arm(args):
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": args.workload, "surface": "unit sphere, 6 patches x 64 x 64 elements, p = 2",
+            "config": {"workload": args.workload, "surface": surface_text(c),
                        "dofs": N, "samples_per_gpu": ns, "integer_solves": n_int, "sinc_nodes": n_nodes,
                        "systems_per_step": ns * (n_int + passes * n_nodes), "rtol": c["rtol"],
                        "precision": c["precision"], "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2: the batch working set is about 25 GB per step"},
+                       "l2": "inputs larger than L2: the batch working set is %.0f GB per step"
+                             % (N * ns * (n_int + passes * n_nodes) * 40 / 1e9)},
             "dof_solves_per_s": dof_solves,
             "solver": {k: stats[k] for k in ("max_iterations", "total_iterations", "n_not_converged",
                                              "max_rel_residual", "n_systems", "n_batches", "n_replacements",

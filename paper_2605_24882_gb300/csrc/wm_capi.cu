@@ -558,7 +558,9 @@ int64_t batch_size(wm_hier_t h, WorkSpace& ws, const wm_sample_desc* d, int64_t 
       freeb = 0;
     }
     size_t have = ws.x.n / std::max(1, h->lv[0].N);  // systems the workspace already holds
-    size_t budget = (size_t)(freeb * 0.8) + have * per;
+    // 80% of what this workspace could reach (free memory plus what it holds),
+    // so that repeated calls do not ratchet the workspace up to all of the memory
+    size_t budget = (size_t)((double)(freeb + have * per) * 0.8);
     maxsys = std::max<int64_t>(WM_LANES, (int64_t)(budget / per) / WM_LANES * WM_LANES);
   }
   int64_t per_batch = std::min<int64_t>(nsys, maxsys);

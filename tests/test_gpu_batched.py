@@ -1,0 +1,88 @@
+"""GPU checks of the multi-instance entry point and of the torus at full size.
+
+* wm_sample_fields_batched on a seeded uneven batch (spheres p = 2 and tori
+  p = 3 at refinement levels 3-4, kappa ~ U[1, 20], beta ~ U[0.55, 1.95], the
+  improved split, 1..64 samples): every instance against the CPU oracle.
+* The periodic bicubic torus 512 x 256 (131,072 DOFs) at full size: the
+  problem is invariant under a rotation about the torus axis by one element,
+  so shifting the loads by one DOF column along u must shift the fields the
+  same way (to the solver tolerance); and the mixed fields must agree with the
+  float64 path.  Neither check needs the oracle, which cannot factor 71
+  shifted matrices of this size in test time.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import geometry as geo
+from oracle.assembly import assemble
+from oracle.fractional import sample_fields as oracle_fields
+from oracle.noise import noise_loads
+from oracle.space import GluedSpace
+from wm_workloads import uneven_instances
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wm():
+    from paper_2605_24882_gb300 import build as b
+    b.build()
+    import paper_2605_24882_gb300 as wm
+    return wm
+
+
+def mnorm_rel(u, ref, M):
+    d = u - ref
+    num = np.einsum("si,si->s", d, (M @ d.T).T)
+    den = np.einsum("si,si->s", ref, (M @ ref.T).T)
+    return np.sqrt(num / den)
+
+
+def test_uneven_instances_batched_against_oracle(wm):
+    insts = uneven_instances(seed=11, n_inst=6, j_lo=3, j_hi=4)
+    hiers, descs = [], []
+    for c in insts:
+        g = wm.Geometry(c["kind"], c["p"], c["n_u"], c["n_v"], c.get("R", 1.0), c.get("r", 0.4))
+        hiers.append(wm.Hierarchy(g, c["levels"]))
+        descs.append(wm.Hierarchy.make_desc(c["kappa"], c["beta"], c["k"], c["l_lo"], c["l_hi"], c["n_samples"],
+                                            c["seed"], c["split"], c["precision"], c["rtol"]))
+    outs, stats = wm.sample_fields_batched(hiers, descs)
+    assert len(outs) == len(insts)
+    for c, u, st in zip(insts, outs, stats):
+        s = geo.Surface(c["kind"], c["p"], c["n_u"], c["n_v"], c.get("R", 1.0), c.get("r", 0.4))
+        sp_ = GluedSpace(s)
+        S, M = assemble(sp_)
+        b = noise_loads(sp_, c["seed"], c["n_samples"])
+        ref = oracle_fields(S, M, b, c["kappa"], c["beta"], c["k"], c["l_lo"], c["l_hi"], c["split"])
+        err = mnorm_rel(u.cpu().numpy(), ref, M)
+        assert st["n_not_converged"] == 0, (c, st)
+        assert err.max() < 1e-6, (c["kind"], c["n_u"], c["beta"], err.max())
+    # the same instance alone gives the same fields as inside the batch
+    u1, _ = hiers[0].sample_fields(kappa=insts[0]["kappa"], beta=insts[0]["beta"], sinc_k=insts[0]["k"],
+                                   l_lo=insts[0]["l_lo"], l_hi=insts[0]["l_hi"], n_samples=insts[0]["n_samples"],
+                                   seed=insts[0]["seed"], split=insts[0]["split"], precision="mixed", rtol=1e-8)
+    np.testing.assert_allclose(u1.cpu().numpy(), outs[0].cpu().numpy(), rtol=0, atol=1e-12 * float(u1.abs().max()))
+
+
+def test_torus_full_size_rotation_and_fp64(wm):
+    n_u, n_v, ns = 512, 256, 4
+    hier = wm.Hierarchy(wm.Geometry("torus", 3, n_u, n_v, 1.0, 0.4), 6)
+    N = hier.num_dofs(0)
+    assert N == n_u * n_v
+    kw = dict(kappa=10.0, beta=0.6, sinc_k=0.3, l_lo=-35, l_hi=35, n_samples=ns, seed=0, precision="mixed", rtol=1e-8)
+    u, b, st = hier.sample_fields(return_loads=True, **kw)
+    assert st["n_not_converged"] == 0 and st["n_systems"] == 71 * ns
+    # DOFs are numbered row by row (v outer, u inner): roll every row by one along u
+    b_rot = torch.roll(b.view(ns, n_v, n_u), shifts=1, dims=2).reshape(ns, N).contiguous()
+    u_rot, _ = hier.sample_fields(b=b_rot, **kw)
+    u_exp = torch.roll(u.view(ns, n_v, n_u), shifts=1, dims=2).reshape(ns, N)
+
+    def rel(a, ref):
+        d = a - ref
+        return torch.sqrt((d * hier.apply_mass(d)).sum(1) / (ref * hier.apply_mass(ref)).sum(1))
+
+    assert float(rel(u_rot, u_exp).max()) < 1e-6
+    u64, st64 = hier.sample_fields(b=b, **dict(kw, precision="fp64"))
+    assert st64["n_not_converged"] == 0
+    assert float(rel(u, u64).max()) < 1e-6
