@@ -394,7 +394,8 @@ __global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGe
 // so an output costs one FMA per stencil entry and no division, each combined
 // row being read back with 16-byte shared loads.  One tile per block keeps
 // the register window at (2p+1)^2 values; for p = 2 in float the Chebyshev
-// block holds 57 KB of shared memory and four blocks share an SM.
+// block holds 50 KB of shared memory and four blocks share an SM (p = 3: 68 KB,
+// three blocks).
 //   UNI_CHEBDOT  the Chebyshev step that ends a V-cycle, also forming the
 //                per-block partials (r, z_new) and (z_new, q) of the outer CG
 //                (q staged as a third row)
@@ -418,7 +419,8 @@ struct UniLayout {
   static constexpr size_t win = (size_t)NC * 32 * sizeof(T);
   static constexpr size_t rows = (size_t)NR * BU * BV * 32 * sizeof(T);
   static constexpr size_t raw = (size_t)BU * BV * CS * sizeof(typename V2<T>::type);  // (S, M) rows
-  static constexpr size_t coef = (size_t)BU * BV * S2P * sizeof(T);
+  static constexpr size_t coef = 0;  // the combined rows overwrite the (S, M) rows (fewer bytes)
+  static_assert((size_t)BU * BV * S2P * sizeof(T) <= raw, "combined rows must fit over the (S, M) rows");
   static constexpr size_t diag = (size_t)(ND + 1) * BU * BV * sizeof(T);         // dS, dM, w
   static constexpr size_t diag16 = (diag + 15) / 16 * 16;
   static constexpr size_t ids = (size_t)(NC + BU * BV) * sizeof(int);
@@ -439,9 +441,10 @@ struct Vec16<double> {
   static __device__ __forceinline__ double at(const double2& v, int k) { return k == 0 ? v.x : v.y; }
 };
 // blocks per SM the register budget is sized for
-template <typename T, int P>
+template <typename T, int P, int MODE>
 struct UniMinBlocks {
-  static constexpr int value = sizeof(T) == 4 ? (P == 2 ? 4 : 2) : (P == 2 ? 2 : 1);
+  static constexpr int value =
+      sizeof(T) == 4 ? (P == 2 ? 4 : ((MODE == UNI_CHEB || MODE == UNI_RESID) ? 3 : 2)) : (P == 2 ? 2 : 1);
 };
 // 4- or 8-byte asynchronous copy through L1 (diagonal entries)
 template <int BYTES>
@@ -452,7 +455,7 @@ __device__ __forceinline__ void cp_async_ca(void* smem, const void* gmem, int sr
 }
 
 template <typename T, int P, int MODE>
-__global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P>::value)
+__global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
     k_sten_uni(StenGeo G, const typename V2<T>::type* __restrict__ csm, const T* __restrict__ dS,
                const T* __restrict__ dM, const double* __restrict__ sigma, const typename V2<T>::type* __restrict__ ctab,
                const int* __restrict__ sid, int kstep, const T* __restrict__ z, const T* __restrict__ r, const T* prev,
@@ -468,7 +471,7 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P>::value)
   T* sm = reinterpret_cast<T*>(smraw);
   T* srw = reinterpret_cast<T*>(smraw + LY::win);                                   // [NR][64][32]
   C2* sraw = reinterpret_cast<C2*>(smraw + LY::win + LY::rows);                     // [64][CS]
-  T* scf = reinterpret_cast<T*>(smraw + LY::win + LY::rows + LY::raw);              // [64][S2P]
+  T* scf = reinterpret_cast<T*>(smraw + LY::win + LY::rows);                        // [64][S2P] over sraw
   T* sdg = reinterpret_cast<T*>(smraw + LY::win + LY::rows + LY::raw + LY::coef);   // [ND][64], then w [64]
   T* swt = sdg + LY::ND * BU * BV;
   int* sid_ = reinterpret_cast<int*>(smraw + LY::win + LY::rows + LY::raw + LY::coef + LY::diag16);
@@ -549,15 +552,25 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P>::value)
   }
   cp_async_wait_all();
   __syncthreads();
-  // combined rows (and the Chebyshev diagonal weights)
-  for (int c = tid; c < BU * BV * S2P; c += BU * 32) {
+  // combined rows (and the Chebyshev diagonal weights): every thread reads its
+  // (S, M) entries first, then, after the barrier, writes the combined rows over them
+  constexpr int CPT = (BU * BV * S2P + BU * 32 - 1) / (BU * 32);
+  T av[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int c = tid + k * BU * 32;
     const int o = c / S2P, sl = c - o * S2P;
-    T a = 0;
-    if (sl < S2) {
+    av[k] = 0;
+    if (c < BU * BV * S2P && sl < S2) {
       const C2 q = sraw[o * CS + sl];
-      a = q.x + sg * q.y;
+      av[k] = q.x + sg * q.y;
     }
-    scf[c] = a;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int c = tid + k * BU * 32;
+    if (c < BU * BV * S2P) scf[c] = av[k];
   }
   if constexpr (CHEB)
     for (int c = tid; c < BU * BV; c += BU * 32)
