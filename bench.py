@@ -303,7 +303,8 @@ def our_arm(args):
     ns = args.samples or c["n_samples"]
     kw = dict(kappa=c["kappa"], beta=c["beta"], sinc_k=c["k"], l_lo=c["l_lo"], l_hi=c["l_hi"], n_samples=ns,
               seed=c["seed"] + 1000003 * rank, split=c["split"], precision=c["precision"], rtol=c["rtol"],
-              smoother_degree=args.smoother_degree, cheb_ratio=args.cheb_ratio)
+              smoother_degree=args.smoother_degree or c.get("smoother_degree", 4),
+              cheb_ratio=args.cheb_ratio or c.get("cheb_ratio", 12.0))
     u = torch.empty((ns, N), dtype=torch.float64, device="cuda")
     stats = None
     for _ in range(args.warmup):
@@ -350,6 +351,7 @@ def our_arm(args):
                        "dofs": N, "samples_per_gpu": ns, "integer_solves": n_int, "sinc_nodes": n_nodes,
                        "systems_per_step": ns * (n_int + passes * n_nodes), "rtol": c["rtol"],
                        "precision": c["precision"], "parallelism": "replicas" if world > 1 else "single GPU",
+                       "smoother": {"chebyshev_degree": kw["smoother_degree"], "interval_ratio": kw["cheb_ratio"]},
                        "l2": "inputs larger than L2: the batch working set is %.0f GB per step"
                              % (N * ns * (n_int + passes * n_nodes) * 40 / 1e9)},
             "dof_solves_per_s": dof_solves,
@@ -390,8 +392,8 @@ def main():
     ap.add_argument("--no-fp64-legs", action="store_true", help="skip the plain FP64 comparison legs")
     ap.add_argument("--plain-samples", type=int, default=1,
                     help="samples timed on the one-system-at-a-time FP64 path")
-    ap.add_argument("--smoother-degree", type=int, default=4)
-    ap.add_argument("--cheb-ratio", type=float, default=12.0)
+    ap.add_argument("--smoother-degree", type=int, default=0, help="0: the workload's tuned value")
+    ap.add_argument("--cheb-ratio", type=float, default=0.0, help="0: the workload's tuned value")
     ap.add_argument("--no-profile", dest="profile", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -13,7 +13,9 @@ no public dataset; every input is synthetic.
 import numpy as np
 
 # Each workload: surface (kind, p, elements per patch side), Matérn parameters,
-# sinc node set y_l = l k for l in [l_lo, l_hi], sample count and seeds, solver.
+# sinc node set y_l = l k for l in [l_lo, l_hi], sample count and seeds, solver
+# (smoother degree and interval ratio where paper_2605_24882_gb300.autotune
+# found a better pair than the library default 4 / 12).
 WORKLOADS = {
     # plain method, FP64, one sample; sphere 6 x (8 x 8), p = 2, 488 glued DOFs
     "sphere_p2_j3_fp64": dict(
@@ -25,12 +27,12 @@ WORKLOADS = {
     "sphere_p2_j6_mixed_s256": dict(
         kind="sphere", p=2, n_u=64, n_v=64, kappa=5.0, beta=1.3, split="standard",
         k=0.3, l_lo=-35, l_hi=35, n_samples=256, seed=0, precision="mixed",
-        levels=7, rtol=1e-8),
+        levels=7, rtol=1e-8, smoother_degree=5, cheb_ratio=8.0),
     # second geometry: periodic bicubic torus R = 1, r = 0.4, 512 x 256 elements
     "torus_p3_512x256_s1024": dict(
         kind="torus", p=3, n_u=512, n_v=256, R=1.0, r=0.4, kappa=10.0, beta=0.6,
         split="standard", k=0.3, l_lo=-35, l_hi=35, n_samples=1024, seed=0,
-        precision="mixed", levels=6, rtol=1e-8),
+        precision="mixed", levels=6, rtol=1e-8, smoother_degree=6, cheb_ratio=24.0),
     # differentiation: sphere 6 x (128 x 128), p = 3, 101,402 DOFs; loss target seed 7
     "sphere_p3_j7_adjoint_s64": dict(
         kind="sphere", p=3, n_u=128, n_v=128, kappa=4.0, beta=0.8, split="standard",
