@@ -541,9 +541,17 @@ template <typename T>
 __global__ void k_cheb_first(int N, int chunks, int tiles, const T* __restrict__ r, const T* __restrict__ dS,
                              const T* __restrict__ dM, const double* __restrict__ sigma,
                              const typename C2T<T>::type* __restrict__ ctab, const int* __restrict__ sid,
-                             T* __restrict__ z, const int* __restrict__ tile_active) {
+                             T* __restrict__ z, const int* __restrict__ tile_active, const int* __restrict__ skip) {
   const int t0 = blockIdx.y * kTPW;
   TileSet ts = tile_set(t0, tiles, tile_active);
+  if (skip) {  // tiles done by another kernel
+    ts.any = false;
+#pragma unroll
+    for (int k = 0; k < kTPW; ++k) {
+      ts.act[k] = ts.act[k] && !skip[t0 + k];
+      ts.any |= ts.act[k];
+    }
+  }
   if (!ts.any) return;
   T sg[kTPW], c2[kTPW];
 #pragma unroll
@@ -1135,13 +1143,30 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
     }
     units(csm, bt, (has_prev ? 4.0 : 3.0) * Tb * Lv.N, 2.0 * Lv.nnz + 8.0 * Lv.N);
   };
-  // pre-smoothing from z = 0
-  WM_LAUNCH(csm, s, k_cheb_first<T><<<ggrid, kBlk, 0, s>>>(Lv.N, ch, tiles, rin, dS, dM, ws.sigma.p, ctab,
-                                                           ws.sid.p, za, ta));
-  units(csm, bt, 2.0 * Tb * Lv.N, 3.0 * Lv.N);
+  // pre-smoothing from z = 0; with a stencil form the one-shift tiles do the
+  // first two steps in one pass over r (z1 in za, z2 in zb)
   T* cur = za;
   T* oth = zb;
-  for (int k = 1; k < nu; ++k) {
+  int k1 = 1;
+  if (Lv.sten && ws.n_uni_tiles > 0 && nu >= 2) {
+    WM_TRY(wm_sten_cheb_first2<T>(Lv, h->np, h->p, tiles, ws.sigma.p, ctab, ws.sid.p, rin, za, zb, ta, ws.tile_uni.p,
+                                  csm, s));
+    units(csm, bt, 3.0 * Tb * Lv.N, 2.0 * Lv.nnz + 8.0 * Lv.N);
+    if (ws.n_uni_tiles < tiles) {
+      WM_LAUNCH(csm, s, k_cheb_first<T><<<ggrid, kBlk, 0, s>>>(Lv.N, ch, tiles, rin, dS, dM, ws.sigma.p, ctab,
+                                                               ws.sid.p, za, ta, ws.tile_uni.p));
+      int e = wm_sten_cheb_step<T>(Lv, h->np, h->p, tiles, 1, ws.sigma.p, ctab, ws.sid.p, rin, za, nullptr, zb, ta,
+                                   ws.tile_uni.p, ws.n_uni_tiles, csm, s, nullptr, nullptr, nullptr, true);
+      if (e != WM_OK) return e;
+    }
+    std::swap(cur, oth);  // cur = z2, oth = z1
+    k1 = 2;
+  } else {
+    WM_LAUNCH(csm, s, k_cheb_first<T><<<ggrid, kBlk, 0, s>>>(Lv.N, ch, tiles, rin, dS, dM, ws.sigma.p, ctab,
+                                                             ws.sid.p, za, ta, (const int*)nullptr));
+    units(csm, bt, 2.0 * Tb * Lv.N, 3.0 * Lv.N);
+  }
+  for (int k = k1; k < nu; ++k) {
     cheb_step(k, cur, oth, k >= 2, nullptr);  // z_0 = 0
     std::swap(cur, oth);
   }

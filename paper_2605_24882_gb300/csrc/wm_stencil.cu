@@ -399,7 +399,10 @@ __global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGe
 //   UNI_CHEBDOT  the Chebyshev step that ends a V-cycle, also forming the
 //                per-block partials (r, z_new) and (z_new, q) of the outer CG
 //                (q staged as a third row)
-enum { UNI_CHEB = 0, UNI_RESID = 1, UNI_APPLY = 2, UNI_CHEBDOT = 3 };
+//   UNI_CHEB1    the first two pre-smoothing steps from z = 0 in one pass:
+//                z1 = c2_0 Dinv r (written to out1), out = z1 + c1 z1 + c2 Dinv (r - A z1),
+//                A z1 formed from the window of r with c2_0 Dinv folded into the rows
+enum { UNI_CHEB = 0, UNI_RESID = 1, UNI_APPLY = 2, UNI_CHEBDOT = 3, UNI_CHEB1 = 4 };
 template <int MODE>
 struct UniCheb {
   static constexpr bool value = MODE == UNI_CHEB || MODE == UNI_CHEBDOT;
@@ -421,7 +424,8 @@ struct UniLayout {
   static constexpr size_t raw = (size_t)BU * BV * CS * sizeof(typename V2<T>::type);  // (S, M) rows
   static constexpr size_t coef = 0;  // the combined rows overwrite the (S, M) rows (fewer bytes)
   static_assert((size_t)BU * BV * S2P * sizeof(T) <= raw, "combined rows must fit over the (S, M) rows");
-  static constexpr size_t diag = (size_t)(ND + 1) * BU * BV * sizeof(T);         // dS, dM, w
+  static constexpr size_t diag = MODE == UNI_CHEB1 ? (size_t)3 * NC * sizeof(T)  // dS, dM, Dinv of the cells
+                                                   : (size_t)(ND + 1) * BU * BV * sizeof(T);  // dS, dM, w
   static constexpr size_t diag16 = (diag + 15) / 16 * 16;
   static constexpr size_t ids = (size_t)(NC + BU * BV) * sizeof(int);
   static constexpr size_t total = win + rows + raw + coef + diag16 + ids;
@@ -460,7 +464,8 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
                const T* __restrict__ dM, const double* __restrict__ sigma, const typename V2<T>::type* __restrict__ ctab,
                const int* __restrict__ sid, int kstep, const T* __restrict__ z, const T* __restrict__ r, const T* prev,
                T* out, int tiles, const int* __restrict__ tile_active, const int* __restrict__ tile_uni,
-               double* __restrict__ part, const T* __restrict__ qd, double* __restrict__ part2) {
+               double* __restrict__ part, const T* __restrict__ qd, double* __restrict__ part2,
+               T* __restrict__ out1) {
   using C2 = typename V2<T>::type;
   using LY = UniLayout<T, P, MODE>;
   constexpr bool CHEB = UniCheb<MODE>::value;
@@ -485,12 +490,18 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
   const int m = b / G.nbv;
   const int t = blockIdx.y;
   if (t >= tiles || !tile_active[t] || !tile_uni[t]) return;  // mixed-shift tiles are done by k_sten
-  T sg, c1 = 0, c2 = 0;
+  T sg, c1 = 0, c2 = 0, c20 = 0;
   {
     const int g = t * 32;  // every lane of the tile has this shift
     if constexpr (CHEB) {
       const C2 c = ctab[sid[g] * WM_MAX_CHEB + kstep];
       c1 = kstep == 0 ? (T)0 : c.x;
+      c2 = c.y;
+    }
+    if constexpr (MODE == UNI_CHEB1) {  // steps 0 and 1
+      const C2 c0 = ctab[sid[g] * WM_MAX_CHEB], c = ctab[sid[g] * WM_MAX_CHEB + 1];
+      c20 = c0.y;
+      c1 = c.x;
       c2 = c.y;
     }
     sg = (T)sigma[g];
@@ -542,6 +553,14 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
                        : reinterpret_cast<const unsigned char*>(csm),
                gi >= 0 ? 16 : 0);
   }
+  if constexpr (MODE == UNI_CHEB1) {  // diagonals of every window cell
+    for (int c = tid; c < 2 * NC; c += BU * 32) {
+      const int cell = c % NC;
+      const int gi = sid_[cell];
+      const T* base = c < NC ? dS : dM;
+      cp_async_ca<sizeof(T)>(sdg + c, gi >= 0 ? base + gi : dS, gi >= 0 ? (int)sizeof(T) : 0);
+    }
+  }
   if constexpr (CHEB) {
     for (int c = tid; c < 2 * BU * BV; c += BU * 32) {
       const int o = c % (BU * BV);
@@ -552,6 +571,11 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
   }
   cp_async_wait_all();
   __syncthreads();
+  T* sdc = sdg + 2 * NC;  // UNI_CHEB1: Dinv of every window cell
+  if constexpr (MODE == UNI_CHEB1) {
+    for (int c = tid; c < NC; c += BU * 32) sdc[c] = sid_[c] >= 0 ? (T)1 / (sdg[c] + sg * sdg[NC + c]) : (T)0;
+    __syncthreads();
+  }
   // combined rows (and the Chebyshev diagonal weights): every thread reads its
   // (S, M) entries first, then, after the barrier, writes the combined rows over them
   constexpr int CPT = (BU * BV * S2P + BU * 32 - 1) / (BU * 32);
@@ -564,6 +588,8 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
     if (c < BU * BV * S2P && sl < S2) {
       const C2 q = sraw[o * CS + sl];
       av[k] = q.x + sg * q.y;
+      if constexpr (MODE == UNI_CHEB1)  // times c2_0 Dinv of the neighbour's cell: A z1 from r
+        av[k] *= c20 * sdc[((o / BU) + sl / SW) * CU + (o % BU) + sl % SW];
     }
   }
   __syncthreads();
@@ -615,6 +641,11 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
             dot.add(rv * res);
             if (qd) dot2.add(res * srw[(2 * BU * BV + o) * 32 + lane]);
           }
+        } else if constexpr (MODE == UNI_CHEB1) {
+          const T dc = sdc[(j + P) * CU + w + P];  // Dinv of the output row
+          const T z1 = c20 * dc * zc;              // zc is r here
+          out1[((size_t)t * G.N + i) * 32 + lane] = z1;
+          res = z1 + c1 * z1 + c2 * dc * (zc - acc);
         } else if constexpr (MODE == UNI_RESID) {
           res = srw[o * 32 + lane] - acc;
         } else {
@@ -1032,7 +1063,7 @@ template <typename T, int P, int MODE>
 static int launch_uni(const wm_level& L, int np, int tiles, int kstep, const double* sigma,
                       const typename V2<T>::type* ctab, const int* sid, const T* r, const T* z, const T* prev,
                       T* out, const int* tile_active, const int* tile_uni, double* part, int cat, cudaStream_t s,
-                      const T* qd = nullptr, double* part2 = nullptr) {
+                      const T* qd = nullptr, double* part2 = nullptr, T* out1 = nullptr) {
   constexpr size_t sm = UniLayout<T, P, MODE>::total;
   static bool configured = false;
   if (!configured) {
@@ -1044,7 +1075,8 @@ static int launch_uni(const wm_level& L, int np, int tiles, int kstep, const dou
   dim3 grid(np * L.nbu * L.nbv, tiles);
   WM_LAUNCH(cat, s, k_sten_uni<T, P, MODE><<<grid, dim3(32, BU), sm, s>>>(geo_of(L), csm_of<T>(L), dS, dM, sigma,
                                                                          ctab, sid, kstep, z, r, prev, out, tiles,
-                                                                         tile_active, tile_uni, part, qd, part2));
+                                                                         tile_active, tile_uni, part, qd, part2,
+                                                                         out1));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
@@ -1053,16 +1085,18 @@ template <typename T>
 int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, const double* sigma,
                       const typename StenC2<T>::type* ctab, const int* sid, const T* r, const T* z, const T* prev,
                       T* out, const int* tile_active, const int* tile_uni, int n_uni, int cat, cudaStream_t s,
-                      const T* q, double* part_rz, double* part_zq) {
-  if (n_uni > 0 && part_rz) {
+                      const T* q, double* part_rz, double* part_zq, bool generic_only) {
+  if (generic_only) {
+    // the one-shift tiles were done elsewhere: generic kernel for the others only
+  } else if (n_uni > 0 && part_rz) {
     WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_CHEBDOT>(L, np, tiles, kstep, sigma, ctab, sid, r, z, prev,
                                                               out, tile_active, tile_uni, part_rz, cat, s, q,
                                                               part_zq))); });
   } else if (n_uni > 0) {
     WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_CHEB>(L, np, tiles, kstep, sigma, ctab, sid, r, z, prev, out,
                                                            tile_active, tile_uni, nullptr, cat, s))); });
-    if (n_uni >= tiles) return WM_OK;
   }
+  if (n_uni >= tiles) return WM_OK;
   ChebEpi<T, 2> e2;
   ChebEpi<T, 1> e1;
   auto fill = [&](auto& e) {
@@ -1086,6 +1120,16 @@ int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, co
     else
       return launch<T, PP>(L, np, tiles, z, tile_active, e1, cat, s, skip);
   });
+  return WM_OK;
+}
+
+template <typename T>
+int wm_sten_cheb_first2(const wm_level& L, int np, int p, int tiles, const double* sigma,
+                        const typename StenC2<T>::type* ctab, const int* sid, const T* r, T* z1, T* z2,
+                        const int* tile_active, const int* tile_uni, int cat, cudaStream_t s) {
+  WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_CHEB1>(L, np, tiles, 1, sigma, ctab, sid, nullptr, r, nullptr, z2,
+                                                          tile_active, tile_uni, nullptr, cat, s, nullptr, nullptr,
+                                                          z1))); });
   return WM_OK;
 }
 
@@ -1184,10 +1228,14 @@ int wm_sten_true_residual_df(const wm_level& L, int np, int p, int tiles, const 
 
 template int wm_sten_cheb_step<float>(const wm_level&, int, int, int, int, const double*, const float2*,
                                       const int*, const float*, const float*, const float*, float*, const int*,
-                                      const int*, int, int, cudaStream_t, const float*, double*, double*);
+                                      const int*, int, int, cudaStream_t, const float*, double*, double*, bool);
 template int wm_sten_cheb_step<double>(const wm_level&, int, int, int, int, const double*, const double2*,
                                        const int*, const double*, const double*, const double*, double*, const int*,
-                                       const int*, int, int, cudaStream_t, const double*, double*, double*);
+                                       const int*, int, int, cudaStream_t, const double*, double*, double*, bool);
+template int wm_sten_cheb_first2<float>(const wm_level&, int, int, int, const double*, const float2*, const int*,
+                                        const float*, float*, float*, const int*, const int*, int, cudaStream_t);
+template int wm_sten_cheb_first2<double>(const wm_level&, int, int, int, const double*, const double2*, const int*,
+                                         const double*, double*, double*, const int*, const int*, int, cudaStream_t);
 template int wm_sten_residual<float>(const wm_level&, int, int, int, const double*, const float*, const float*, float*,
                                      const int*, const int*, int, int, cudaStream_t);
 template int wm_sten_residual<double>(const wm_level&, int, int, int, const double*, const double*, const double*,

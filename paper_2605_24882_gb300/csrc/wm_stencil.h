@@ -34,10 +34,20 @@ template <typename T>
 int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, const double* sigma,
                       const typename StenC2<T>::type* ctab, const int* sid, const T* r, const T* z, const T* prev,
                       T* out, const int* tile_active, const int* tile_uni, int n_uni, int cat, cudaStream_t s,
-                      const T* q = nullptr, double* part_rz = nullptr, double* part_zq = nullptr);
+                      const T* q = nullptr, double* part_rz = nullptr, double* part_zq = nullptr,
+                      bool generic_only = false);
 // With part_rz set, the one-shift tiles of the step also leave per-block partial
 // sums (r, out) in part_rz and, with q set, (out, q) in part_zq ([tile][chunk][32],
 // chunk = spatial block); the other tiles get none (the caller forms them).
+// generic_only: the one-shift tiles are left alone (done by another launch).
+// The first two pre-smoothing steps from z = 0 for the one-shift tiles only:
+// z1 = c2_0 D^{-1} r and z2 = z1 + c1_1 z1 + c2_1 D^{-1} (r - A z1) in one pass
+// over the window of r (the other tiles take the row-form first step and
+// wm_sten_cheb_step with generic_only).
+template <typename T>
+int wm_sten_cheb_first2(const wm_level& L, int np, int p, int tiles, const double* sigma,
+                        const typename StenC2<T>::type* ctab, const int* sid, const T* r, T* z1, T* z2,
+                        const int* tile_active, const int* tile_uni, int cat, cudaStream_t s);
 // residual res = r - A z and outer apply q = A p with per-block partial sums
 // (p, q) in `part` ([tile][chunk][32], chunk = spatial block); one-shift
 // tiles (tile_uni, n_uni of them) take the combined-coefficient kernel
