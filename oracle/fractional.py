@@ -53,6 +53,32 @@ def sinc_rule(beta_frac, k, l_lo, l_hi):
     return y, c
 
 
+def auto_nodes(beta_frac, kappa, tol):
+    """Sinc step k and node range [l_lo, l_hi] for an absolute error <= tol per
+    unit load (Eq. eq:K-convergence measures the error against ||f||).
+
+    In y = -2t the rule of Eq. eq:beta-approx is a trapezoidal sum of
+    f(y) = s e^{(1-g) y} / (e^y + mu), s = sin(pi g) / pi, whose integral is
+    mu^{-g} for every eigenvalue mu >= kappa^2 of M^{-1}(S + kappa^2 M).
+    Three parts of the error are set to tol / 3 each:
+      * the step, from the trapezoidal bound for functions analytic in the
+        strip |Im y| < pi/2 (the poles sit at Im y = +-pi): 2 M' e^{-pi^2/k},
+        with M' = 2 s (1/g + 1/((1-g) kappa^2)) bounding the strip integral;
+      * the upper tail, sum over y > y_hi ~ s e^{-g y_hi} / g;
+      * the lower tail, sum over y < y_lo ~ s e^{(1-g) y_lo} / ((1-g) kappa^2).
+    """
+    g = float(beta_frac)
+    if not 0.0 < g < 1.0 or not kappa > 0.0 or not 0.0 < tol < 1.0:
+        raise ValueError("need 0 < beta_frac < 1, kappa > 0, 0 < tol < 1")
+    s = math.sin(math.pi * g) / math.pi
+    mu = kappa * kappa
+    m = 2.0 * s * (1.0 / g + 1.0 / ((1.0 - g) * mu))
+    k = math.pi ** 2 / math.log(3.0 * m / tol)
+    y_hi = math.log(3.0 * s / (g * tol)) / g
+    y_lo = math.log(tol * (1.0 - g) * mu / (3.0 * s)) / (1.0 - g)
+    return k, int(math.floor(y_lo / k)), int(math.ceil(y_hi / k))
+
+
 def scalar_sinc(beta_frac, K, lam):
     """The paper's scalar u_K(lambda) with K (2K+1 nodes, t_k = k/sqrt(K))."""
     y, c = sinc_rule(beta_frac, 2.0 / math.sqrt(K), -K, K)

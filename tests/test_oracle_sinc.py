@@ -109,3 +109,31 @@ def test_sinc_rule_weights():
     # c_l = (sin pi b / pi) k e^{(1-b) y_l}
     assert c[35] == pytest.approx(math.sin(0.3 * math.pi) / math.pi * 0.3)
     assert c[36] / c[35] == pytest.approx(math.exp(0.7 * 0.3))
+
+
+@pytest.mark.parametrize("g", [0.05, 0.3, 0.5, 0.55, 0.7, 0.95])
+@pytest.mark.parametrize("kappa", [0.5, 2.0, 10.0])
+@pytest.mark.parametrize("tol", [1e-4, 1e-8])
+def test_auto_nodes_meet_the_tolerance(g, kappa, tol):
+    """Tolerance-driven node sets: the scalar rule against the closed form
+    mu^{-g} (Balakrishnan's integral) over the whole spectrum mu in
+    [kappa^2, 1e12 kappa^2] stays within tol."""
+    from oracle.fractional import auto_nodes
+    k, lo, hi = auto_nodes(g, kappa, tol)
+    assert lo < 0 < hi and 0 < k < 2
+    y, c = fr.sinc_rule(g, k, lo, hi)
+    mu = kappa * kappa * np.logspace(0.0, 12.0, 300)
+    approx = (c[None, :] / (np.exp(y)[None, :] + mu[:, None])).sum(1)
+    assert np.abs(approx - mu ** (-g)).max() <= tol
+
+
+def test_auto_nodes_grow_like_log_squared():
+    """Finer tolerances need more nodes, about (log 1/tol)^2 as Eq. eq:K-convergence implies."""
+    from oracle.fractional import auto_nodes
+    n = []
+    for tol in (1e-4, 1e-8, 1e-12):
+        k, lo, hi = auto_nodes(0.3, 5.0, tol)
+        n.append(hi - lo + 1)
+    assert n[0] < n[1] < n[2]
+    r1 = n[1] / n[0]
+    assert 2.0 < r1 < 6.0  # (log 1e8 / log 1e4)^2 = 4 up to the constants
