@@ -267,6 +267,19 @@ int wm_sample_fields_backward(wm_hier_t h, const wm_sample_desc* desc, const dou
 /* Integer/fractional split of beta (Sec. 3.4): n_int, beta_frac, n_passes. */
 int wm_beta_plan(double beta, int split, int* n_int, double* beta_frac, int* n_passes);
 
+/*
+ * Tolerance-driven sinc node set for the fractional pass of beta under `split`
+ * (Eq. eq:beta-approx in y = -2t, convergence Eq. eq:K-convergence): step
+ * *sinc_k and range [*l_lo, *l_hi] such that, for every eigenvalue
+ * mu >= kappa^2 of M^{-1}(S + kappa^2 M), the rule's value differs from
+ * mu^{-beta'} by at most tol (absolute, per unit load).  The step comes from
+ * the trapezoidal error bound in the strip |Im y| < pi/2, the range from the
+ * integrand's upper and lower tails, each part at tol / 3.  Host only, no GPU
+ * work.  Errors: WM_ERR_INVALID_ARG (null outputs, kappa <= 0, tol outside
+ * (0, 1), beta <= 0), WM_ERR_UNSUPPORTED (integer beta: no fractional pass).
+ */
+int wm_sinc_nodes(double beta, int split, double kappa, double tol, double* sinc_k, int* l_lo, int* l_hi);
+
 /* ---- live profiling --------------------------------------------------------- */
 /*
  * Launch counting is always on.  wm_profile_enable(1) resets the per-category

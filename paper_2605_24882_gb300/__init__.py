@@ -18,7 +18,7 @@ import torch
 from . import _capi
 from ._capi import WMError, check, lib
 
-__all__ = ["Geometry", "Hierarchy", "philox4x32_10", "normals", "beta_plan", "WMError", "WMField"]
+__all__ = ["Geometry", "Hierarchy", "philox4x32_10", "normals", "beta_plan", "sinc_nodes", "WMError", "WMField"]
 
 _PREC = {"fp64": _capi.WM_FP64, "mixed": _capi.WM_MIXED}
 _SPLIT = {"standard": _capi.WM_SPLIT_STANDARD, "improved": _capi.WM_SPLIT_IMPROVED}
@@ -51,6 +51,15 @@ class Geometry:
         if getattr(self, "_h", None) and _capi._lib is not None:
             _capi._lib.wm_destroy_geom(self._h)
             self._h = None
+
+
+def sinc_nodes(beta, kappa, tol, split="standard"):
+    """Sinc step and node range (k, l_lo, l_hi) for an error <= tol per unit load
+    in the fractional pass of beta (pass them as sinc_k, l_lo, l_hi)."""
+    k, lo, hi = C.c_double(), C.c_int(), C.c_int()
+    check(lib().wm_sinc_nodes(beta, _SPLIT[split], kappa, tol, C.byref(k), C.byref(lo), C.byref(hi)),
+          "wm_sinc_nodes")
+    return k.value, lo.value, hi.value
 
 
 def beta_plan(beta, split="standard"):

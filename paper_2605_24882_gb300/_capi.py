@@ -73,6 +73,7 @@ _PROTOS = {
                                       C.POINTER(Stats), _vp]),
     "wm_sample_fields_backward": (_i, [_vp, C.POINTER(SampleDesc), _vp, _vp, _vp, C.POINTER(_d), _vp]),
     "wm_beta_plan": (_i, [_d, _i, C.POINTER(_i), C.POINTER(_d), C.POINTER(_i)]),
+    "wm_sinc_nodes": (_i, [_d, _i, _d, _d, C.POINTER(_d), C.POINTER(_i), C.POINTER(_i)]),
     "wm_profile_enable": (_i, [_i]),
     "wm_profile_read": (_i, [_i, C.POINTER(_d), C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_d), C.POINTER(_d),
                              C.POINTER(C.c_char_p)]),

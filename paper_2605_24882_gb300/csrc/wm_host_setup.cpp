@@ -451,6 +451,36 @@ extern "C" int wm_beta_plan(double beta, int split, int* n_int, double* beta_fra
   return wm_split_beta(beta, split, n_int, beta_frac, n_passes);
 }
 
+// Node set for an absolute error <= tol: with g the pass exponent, the sinc
+// sum approximates mu^{-g} = s * integral of e^{(1-g)y} / (e^y + mu) dy,
+// s = sin(pi g) / pi, mu >= kappa^2.  Step: the trapezoidal error for a
+// function analytic in |Im y| < pi/2 is about 2 B e^{-pi^2/k}, with
+// B = 2 s (1/g + 1/((1-g) kappa^2)) bounding the integrand's strip integral;
+// tails: s e^{-g y_hi} / g above and s e^{(1-g) y_lo} / ((1-g) kappa^2) below.
+// Each part is set to tol / 3.
+extern "C" int wm_sinc_nodes(double beta, int split, double kappa, double tol, double* sinc_k, int* l_lo,
+                             int* l_hi) {
+  if (!sinc_k || !l_lo || !l_hi || !(kappa > 0.0) || !(tol > 0.0 && tol < 1.0)) return WM_ERR_INVALID_ARG;
+  int n = 0, passes = 0;
+  double g = 0.0;
+  WM_TRY(wm_split_beta(beta, split, &n, &g, &passes));
+  if (passes == 0) {
+    wm_set_error("beta = %g is an integer: there is no fractional pass", beta);
+    return WM_ERR_UNSUPPORTED;
+  }
+  const double pi = 3.14159265358979323846;
+  const double s = std::sin(pi * g) / pi;
+  const double mu = kappa * kappa;
+  const double bound = 2.0 * s * (1.0 / g + 1.0 / ((1.0 - g) * mu));
+  const double k = pi * pi / std::log(3.0 * bound / tol);
+  const double y_hi = std::log(3.0 * s / (g * tol)) / g;
+  const double y_lo = std::log(tol * (1.0 - g) * mu / (3.0 * s)) / (1.0 - g);
+  *sinc_k = k;
+  *l_lo = (int)std::floor(y_lo / k);
+  *l_hi = (int)std::ceil(y_hi / k);
+  return WM_OK;
+}
+
 // ------------------------------------------------------------ stencil form
 // Extended patch grids for the shared-memory stencil kernels.  Each patch's
 // local DOF grid is extended by a halo of width p: halo cells across a cube

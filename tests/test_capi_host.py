@@ -47,6 +47,27 @@ def test_beta_plan_matches_oracle(lib):
         wm.beta_plan(-1.0)
 
 
+def test_sinc_nodes_match_oracle(lib):
+    """The library's tolerance-driven node sets (host-only call) equal the oracle's."""
+    from oracle.fractional import auto_nodes, split_beta
+    import paper_2605_24882_gb300 as wm
+    from paper_2605_24882_gb300 import _capi
+    for beta in [0.3, 0.6, 0.75, 1.3, 1.1, 1.9]:
+        for split in ["standard", "improved"]:
+            for kappa in [0.5, 5.0, 20.0]:
+                for tol in [1e-4, 1e-8]:
+                    k, lo, hi = wm.sinc_nodes(beta, kappa, tol, split)
+                    _, g, _ = split_beta(beta, split)
+                    k2, lo2, hi2 = auto_nodes(g, kappa, tol)
+                    assert (lo, hi) == (lo2, hi2) and k == pytest.approx(k2, rel=1e-14)
+    with pytest.raises(wm.WMError) as e:
+        wm.sinc_nodes(2.0, 5.0, 1e-8)
+    assert e.value.code == _capi.WM_ERR_UNSUPPORTED
+    for args in [(0.5, 0.0, 1e-8), (0.5, 5.0, 0.0), (0.5, 5.0, 2.0), (-1.0, 5.0, 1e-8)]:
+        with pytest.raises(wm.WMError):
+            wm.sinc_nodes(*args)
+
+
 def test_geometry_validation(lib):
     import paper_2605_24882_gb300 as wm
     from paper_2605_24882_gb300 import _capi

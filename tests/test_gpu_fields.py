@@ -91,6 +91,36 @@ def test_double_float_residual_and_its_fallback(wm):
     assert np.abs(u8.cpu().numpy() - ref).max() < 1e-5 * scale
 
 
+@pytest.mark.parametrize("beta,split", [(0.7, "standard"), (1.8, "improved")])
+def test_tolerance_driven_nodes_reach_the_fractional_power(wm, beta, split):
+    """Node sets from wm_sinc_nodes: the float64 fields on a small sphere against
+    the exact discrete fractional power from a dense generalised eigendecomposition
+    (S v = lambda M v, u = V diag((lambda + kappa^2)^-beta) V^T b): the error in
+    the M-norm stays below tol ||b||_{M^-1} (per pass), and the mixed path agrees
+    with the oracle on the same nodes."""
+    import scipy.linalg as sla
+    kappa, tol, ns = 3.0, 1e-8, 3
+    k, lo, hi = wm.sinc_nodes(beta, kappa, tol, split)
+    hier = wm.Hierarchy(wm.Geometry("sphere", 2, 8), 3)
+    u, b, st = hier.sample_fields(return_loads=True, kappa=kappa, beta=beta, sinc_k=k, l_lo=lo, l_hi=hi,
+                                  n_samples=ns, seed=9, split=split, precision="fp64", rtol=1e-12)
+    assert st["n_nodes"] == hi - lo + 1
+    sp_ = GluedSpace(geo.Surface("sphere", 2, 8))
+    S, M = assemble(sp_)
+    lam, V = sla.eigh(S.toarray(), M.toarray())  # V^T M V = I
+    bn = b.cpu().numpy()
+    u_ex = (V @ (((lam + kappa ** 2) ** -beta)[:, None] * (V.T @ bn.T))).T
+    d = u.cpu().numpy() - u_ex
+    err = np.sqrt(np.einsum("si,si->s", d, (M @ d.T).T))
+    bnorm = np.sqrt(np.einsum("si,si->s", bn, sla.solve(M.toarray(), bn.T).T))
+    passes = st["n_frac_passes"]
+    assert (err <= passes * tol * bnorm).all(), (err / bnorm)
+    um, stm = hier.sample_fields(kappa=kappa, beta=beta, sinc_k=k, l_lo=lo, l_hi=hi, n_samples=ns, seed=9,
+                                 split=split, precision="mixed", rtol=1e-8)
+    u_or = oracle_fields(S, M, bn, kappa, beta, k, lo, hi, split)
+    assert mnorm_rel(um.cpu().numpy(), u_or, M).max() < 1e-6
+
+
 def test_improved_split_two_passes(wm):
     err, st, *_ = run_case(wm, "sphere", 2, 8, 8, 3, 3.0, 1.8, 0.4, -20, 20, 5, 4, "mixed", 1e-9, split="improved")
     assert st["n_frac_passes"] == 2 and st["n_int_solves"] == 1
