@@ -304,7 +304,7 @@ def our_arm(args):
     kw = dict(kappa=c["kappa"], beta=c["beta"], sinc_k=c["k"], l_lo=c["l_lo"], l_hi=c["l_hi"], n_samples=ns,
               seed=c["seed"] + 1000003 * rank, split=c["split"], precision=c["precision"], rtol=c["rtol"],
               smoother_degree=args.smoother_degree or c.get("smoother_degree", 4),
-              cheb_ratio=args.cheb_ratio or c.get("cheb_ratio", 12.0))
+              cheb_ratio=args.cheb_ratio or c.get("cheb_ratio", 12.0), preconditioner=args.preconditioner)
     u = torch.empty((ns, N), dtype=torch.float64, device="cuda")
     stats = None
     for _ in range(args.warmup):
@@ -351,6 +351,7 @@ def our_arm(args):
                        "dofs": N, "samples_per_gpu": ns, "integer_solves": n_int, "sinc_nodes": n_nodes,
                        "systems_per_step": ns * (n_int + passes * n_nodes), "rtol": c["rtol"],
                        "precision": c["precision"], "parallelism": "replicas" if world > 1 else "single GPU",
+                       "preconditioner": args.preconditioner,
                        "smoother": {"chebyshev_degree": kw["smoother_degree"], "interval_ratio": kw["cheb_ratio"]},
                        "l2": "inputs larger than L2: the batch working set is %.0f GB per step"
                              % (N * ns * (n_int + passes * n_nodes) * 40 / 1e9)},
@@ -390,6 +391,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--samples", type=int, default=0, help="override the samples per GPU (profiling runs)")
     ap.add_argument("--no-fp64-legs", action="store_true", help="skip the plain FP64 comparison legs")
+    ap.add_argument("--preconditioner", default="vcycle", choices=["vcycle", "bpx"])
     ap.add_argument("--plain-samples", type=int, default=1,
                     help="samples timed on the one-system-at-a-time FP64 path")
     ap.add_argument("--smoother-degree", type=int, default=0, help="0: the workload's tuned value")

@@ -61,6 +61,9 @@ extern "C" {
 #define WM_NOISE_DRAW 0   /* draw b_s from Philox with desc.seed               */
 #define WM_NOISE_GIVEN 1  /* take b_s from the caller's b buffer               */
 
+#define WM_PRECOND_VCYCLE 0  /* multiplicative: one V-cycle per CG iteration       */
+#define WM_PRECOND_BPX 1     /* additive: BPX multilevel diagonal scaling           */
+
 /* ---- geometry ------------------------------------------------------------- */
 typedef struct {
   int kind;      /* WM_SPHERE6 or WM_TORUS                                        */
@@ -209,6 +212,11 @@ typedef struct {
   double cheb_ratio;    /* Chebyshev interval [lmax/cheb_ratio, 1.1 lmax]            */
   int max_systems;      /* systems per batched solve (0 = all at once); 1 = one
                            system at a time                                          */
+  int preconditioner;   /* WM_PRECOND_VCYCLE (0): one V-cycle per CG iteration;
+                           WM_PRECOND_BPX (1): additive multilevel diagonal scaling,
+                           the BPX preconditioner the paper's experiments favour
+                           (Sec. 3.5): sum over levels of P D^{-1} P^T with the
+                           dense coarse solve on the coarsest level              */
 } wm_sample_desc;
 
 typedef struct {

@@ -32,7 +32,8 @@ class SampleDesc(C.Structure):
     _fields_ = [("kappa", C.c_double), ("beta", C.c_double), ("split", C.c_int), ("sinc_k", C.c_double),
                 ("l_lo", C.c_int), ("l_hi", C.c_int), ("seed", C.c_uint64), ("n_samples", C.c_int),
                 ("noise_mode", C.c_int), ("precision", C.c_int), ("rtol", C.c_double), ("max_iter", C.c_int),
-                ("smoother_degree", C.c_int), ("cheb_ratio", C.c_double), ("max_systems", C.c_int)]
+                ("smoother_degree", C.c_int), ("cheb_ratio", C.c_double), ("max_systems", C.c_int),
+                ("preconditioner", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -519,6 +519,10 @@ int validate_desc(wm_hier_t h, const wm_sample_desc* d) {
   }
   if (d->precision != WM_FP64 && d->precision != WM_MIXED) return WM_ERR_INVALID_ARG;
   if (d->noise_mode != WM_NOISE_DRAW && d->noise_mode != WM_NOISE_GIVEN) return WM_ERR_INVALID_ARG;
+  if (d->preconditioner != WM_PRECOND_VCYCLE && d->preconditioner != WM_PRECOND_BPX) {
+    wm_set_error("unknown preconditioner %d", d->preconditioner);
+    return WM_ERR_INVALID_ARG;
+  }
   if (h->lv.back().N > 160) {
     wm_set_error("coarsest level has %d DOFs (> 160): use more levels", h->lv.back().N);
     return WM_ERR_UNSUPPORTED;
@@ -597,6 +601,7 @@ int solve_range(wm_hier_t h, WorkSpace& ws, const wm_sample_desc* d, const Pass&
   bt.cheb_ratio = d->cheb_ratio;
   bt.replace_drop = dbl ? 0.0 : 1e-4;
   bt.df_residual = !dbl;
+  bt.precond = d->preconditioner;
   BatchResult br;
   WM_TRY(wm_solve_batch(h, ws, bt, rhs_t, &br, s));
   if (br.flags & 1) *worst = std::min(*worst, WM_ERR_NONFINITE);

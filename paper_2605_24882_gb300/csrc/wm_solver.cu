@@ -572,6 +572,29 @@ __global__ void k_cheb_first(int N, int chunks, int tiles, const T* __restrict__
   }
 }
 
+// z = D^{-1} r with D = diag(S + sigma M) (the BPX level scaling)
+template <typename T>
+__global__ void k_diag_scale(int N, int chunks, int tiles, const T* __restrict__ r, const T* __restrict__ dS,
+                             const T* __restrict__ dM, const double* __restrict__ sigma, T* __restrict__ z,
+                             const int* __restrict__ tile_active) {
+  const int t0 = blockIdx.y * kTPW;
+  TileSet ts = tile_set(t0, tiles, tile_active);
+  if (!ts.any) return;
+  T sg[kTPW];
+#pragma unroll
+  for (int k = 0; k < kTPW; ++k) sg[k] = ts.act[k] ? (T)sigma[(t0 + k) * WM_LANES + threadIdx.x] : (T)0;
+  RowRange rr = chunk_rows(N, chunks);
+  for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
+    T ds = dS[i], dm = dM[i];
+#pragma unroll
+    for (int k = 0; k < kTPW; ++k)
+      if (ts.act[k]) {
+        size_t o = vidx(t0 + k, N, i);
+        z[o] = r[o] / (ds + sg[k] * dm);
+      }
+  }
+}
+
 // Chebyshev step k in three-term form: out = z + c1 (z - prev) + c2 D^{-1} (r - A z)
 // (c1 = 0 at step 0; prev = nullptr for z_prev = 0; out may alias prev)
 template <typename T>
@@ -1202,6 +1225,55 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   return WM_OK;
 }
 
+// BPX (additive multilevel diagonal scaling, Sec. 3.5):
+// z = sum_l P_{0<-l} D_l^{-1} R_{l<-0} r, with the dense coarse solve in place of
+// D^{-1} on the coarsest level; restrictions down, then scaled levels added up
+// the prolongation chain.  Returns the buffer holding z (level 0's za).
+template <typename T>
+static int bpx(const wm_hier* h, WorkSpace& ws, const Batch& bt, const T* rin, T** zout, cudaStream_t s) {
+  const int L = (int)h->lv.size();
+  const int* ta = ws.tile_active.p;
+  const int tiles = bt.tiles;
+  const double Tb = (double)sizeof(T);
+  for (int l = 0; l + 1 < L; ++l) {
+    const wm_level& Lv = h->lv[l];
+    const wm_level& Cv = h->lv[l + 1];
+    const T* rl = l == 0 ? rin : vb<T>(ws.lvl[l].r);
+    const int chc = vcycle_chunks(Cv.N);
+    WM_LAUNCH(WM_PC_RESTRICT, s, k_transfer<T, false><<<dim3(chc, groups(tiles)), kBlk, 0, s>>>(
+                                     Cv.N, Lv.N, chc, tiles, Lv.d_Rptr.p, R_of<T>(Lv), rl, vb<T>(ws.lvl[l + 1].r),
+                                     ta));
+    units(WM_PC_RESTRICT, bt, Tb * (Lv.N + Cv.N), 2.0 * Lv.nnzP);
+  }
+  {
+    const wm_level& Cv = h->lv[L - 1];
+    const T* rc = L == 1 ? rin : vb<T>(ws.lvl[L - 1].r);
+    int gx = std::max(1, std::min(64, (Cv.N + kWarps - 1) / kWarps));
+    WM_LAUNCH(WM_PC_COARSE, s, k_coarse_solve<T><<<dim3(gx, tiles), kBlk, 0, s>>>(Cv.N, ws.ainv.p, ws.sid.p, rc,
+                                                                                   vb<T>(ws.lvl[L - 1].za), ta));
+    units(WM_PC_COARSE, bt, 2.0 * Tb * Cv.N, 2.0 * Cv.N * Cv.N);
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    const wm_level& Lv = h->lv[l];
+    const wm_level& Cv = h->lv[l + 1];
+    const T* rl = l == 0 ? rin : vb<T>(ws.lvl[l].r);
+    T* zl = vb<T>(ws.lvl[l].za);
+    const int ch = vcycle_chunks(Lv.N);
+    const dim3 ggrid(ch, groups(tiles));
+    const int cat = l == 0 ? WM_PC_SMOOTH0 : WM_PC_SMOOTHC;
+    WM_LAUNCH(cat, s, k_diag_scale<T><<<ggrid, kBlk, 0, s>>>(Lv.N, ch, tiles, rl, dS_of<T>(Lv), dM_of<T>(Lv),
+                                                             ws.sigma.p, zl, ta));
+    units(cat, bt, 2.0 * Tb * Lv.N, 3.0 * Lv.N);
+    WM_LAUNCH(WM_PC_PROLONG, s, k_transfer<T, true><<<ggrid, kBlk, 0, s>>>(Lv.N, Cv.N, ch, tiles, Lv.d_Pptr.p,
+                                                                           P_of<T>(Lv), vb<T>(ws.lvl[l + 1].za), zl,
+                                                                           ta));
+    units(WM_PC_PROLONG, bt, Tb * (2.0 * Lv.N + Cv.N), 2.0 * Lv.nnzP);
+  }
+  WM_CUDA(cudaGetLastError());
+  *zout = vb<T>(ws.lvl[0].za);
+  return WM_OK;
+}
+
 static int set_all_tiles_active(WorkSpace& ws, int tiles, cudaStream_t s) {
   std::vector<int> ones(tiles, 1);
   WM_CUDA(cudaMemcpyAsync(ws.tile_active.p, ones.data(), tiles * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -1236,7 +1308,10 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
   units(WM_PC_CGVEC, bt, (8.0 + 8.0 + Tb) * N, 2.0 * N);
   WM_TRY(set_all_tiles_active(ws, tiles, s));
   T* z = nullptr;
-  WM_TRY(vcycle<T>(h, ws, bt, 0, r, &z, s));
+  if (bt.precond == WM_PRECOND_BPX)
+    WM_TRY(bpx<T>(h, ws, bt, r, &z, s));
+  else
+    WM_TRY(vcycle<T>(h, ws, bt, 0, r, &z, s));
   WM_LAUNCH(WM_PC_CGVEC, s, k_dots_rz_zq<T><<<grid, kBlk, 0, s>>>(N, ch, tiles, r, z, (const T*)nullptr,
                                                                   ws.tile_active.p, ws.part[1].p, ws.part[2].p,
                                                                   (const int*)nullptr));
@@ -1336,7 +1411,10 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
     vd.q = q;
     vd.prz = ws.part[1].p;
     vd.pzq = ws.part[2].p;
-    WM_TRY(vcycle<T>(h, ws, bt, 0, r, &z, s, &vd));
+    if (bt.precond == WM_PRECOND_BPX)
+      WM_TRY(bpx<T>(h, ws, bt, r, &z, s));
+    else
+      WM_TRY(vcycle<T>(h, ws, bt, 0, r, &z, s, &vd));
     const int ch_dots = vd.fused ? ch_op : ch;
     if (vd.fused) units(WM_PC_SMOOTH0, bt, Tb * N, 4.0 * N);  // q read and the two products
     if (!vd.fused || ws.n_uni_tiles < tiles) {

@@ -42,6 +42,7 @@ struct Batch {
   // float64 true residuals of the float-preconditioned solve evaluated in
   // double-float arithmetic (stencil levels), checked against the tolerance
   bool df_residual = false;
+  int precond = WM_PRECOND_VCYCLE;  // or WM_PRECOND_BPX
   mutable int active_tiles = 0;  // host copy of the active tile count (for work accounting)
   int chunks_for(int N) const;
 };

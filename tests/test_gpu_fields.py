@@ -121,6 +121,21 @@ def test_tolerance_driven_nodes_reach_the_fractional_power(wm, beta, split):
     assert mnorm_rel(um.cpu().numpy(), u_or, M).max() < 1e-6
 
 
+@pytest.mark.parametrize("kind,p,nu,nv,levels,precision,tol", [
+    ("sphere", 2, 16, 16, 4, "mixed", 1e-6), ("torus", 3, 32, 16, 2, "fp64", 1e-9)])
+def test_bpx_preconditioner(wm, kind, p, nu, nv, levels, precision, tol):
+    """The additive BPX preconditioner (multilevel diagonal scaling, Sec. 3.5) in
+    place of the V-cycle: same fields as the oracle, more (cheaper) iterations."""
+    rtol = 1e-8 if precision == "mixed" else 1e-11
+    err, st, hier, u = run_case(wm, kind, p, nu, nv, levels, 5.0, 1.3, 0.3, -35, 35, 40, 3, precision, rtol,
+                                preconditioner="bpx", max_iter=2000)
+    assert st["n_not_converged"] == 0
+    assert err.max() < tol, (err, st)
+    _, st_v = hier.sample_fields(kappa=5.0, beta=1.3, sinc_k=0.3, l_lo=-35, l_hi=35, n_samples=40, seed=3,
+                                 precision=precision, rtol=rtol)
+    assert st["max_iterations"] > st_v["max_iterations"]
+
+
 def test_improved_split_two_passes(wm):
     err, st, *_ = run_case(wm, "sphere", 2, 8, 8, 3, 3.0, 1.8, 0.4, -20, 20, 5, 4, "mixed", 1e-9, split="improved")
     assert st["n_frac_passes"] == 2 and st["n_int_solves"] == 1
