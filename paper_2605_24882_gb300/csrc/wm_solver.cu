@@ -2,22 +2,26 @@
 // (Eq. eq:beta-approx nodes x samples, or the integer-part solves of Sec. 3.4)
 // by flexible preconditioned conjugate gradients whose preconditioner is one
 // geometric multigrid V-cycle over the dyadic spline hierarchy (Sec. 3.5):
-// Chebyshev–Jacobi smoothing, restriction P^T and knot-insertion prolongation P,
-// and a dense float64 solve on the coarsest level.
+// three-term Chebyshev–Jacobi smoothing, restriction P^T and knot-insertion
+// prolongation P, and a dense float64 solve on the coarsest level -- or, as an
+// option, the additive BPX preconditioner (multilevel diagonal scaling).
 //
 // Precision (WM_MIXED): the recursion (r, p, q, z) and the V-cycle are float32;
-// the solution x, the right-hand sides and the true residuals b - A x are
-// float64.  A system's recursive residual is replaced by its float64 true
-// residual whenever it has fallen by `replace_drop` since the last replacement,
-// and a system is declared converged only on its true residual, so float32
-// rounding in the recursion cannot stall or fake convergence.  WM_FP64 runs
-// the same algorithm with every vector in float64.
+// the solution x and the right-hand sides are float64, and the true residuals
+// b - A x are formed in double-float arithmetic (float64 when their error
+// bound is too large for the tolerance).  A system's recursive residual is
+// replaced by its true residual whenever it has fallen by `replace_drop` since
+// the last replacement, and a system is declared converged only on its true
+// residual, so float32 rounding in the recursion cannot stall or fake
+// convergence.  WM_FP64 runs the same algorithm with every vector in float64.
 //
 // Layout: systems are packed 32 per tile, vectors are [tiles][N][32]; lane =
-// system.  Operator kernels give each warp one row of kTPW tiles: a row's
-// packed entries (column, S, M) are loaded once per warp and reused for 4 x 32
-// systems.  Per-system dot products are per-lane sums over rows followed by a
-// fixed-order reduction over warps and chunks (deterministic, no atomics).
+// system.  Levels with a stencil form run their operator steps in the
+// shared-memory kernels of wm_stencil.cu; the row kernels here give each warp
+// one row of kTPW tiles, a row's packed entries (column, S, M) loaded once per
+// warp and reused for 4 x 32 systems.  Per-system dot products are per-lane
+// sums over rows followed by a fixed-order reduction over warps and chunks
+// (deterministic, no atomics).
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
@@ -1126,8 +1130,6 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   const int tiles = bt.tiles;
   const int ch = vcycle_chunks(Lv.N);
   const dim3 ggrid(ch, groups(tiles));
-  const double* lmax = ws.lmax.p + (size_t)l * bt.nshift;
-  (void)lmax;
   const typename C2T<T>::type* ctab = cheb_tab<T>(ws) + (size_t)l * bt.nshift * WM_MAX_CHEB;
   const auto* pk = rows_of<T>(Lv);
   const T* dS = dS_of<T>(Lv);
