@@ -92,16 +92,26 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def init_group(world, rank, backend):
+    """One process per GPU (torchrun environment); the N > 1 path has no
+    data-path collective: only the barriers and the max-over-ranks timing."""
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        kw = {}
+        if backend == "nccl":
+            import torch
+            kw["device_id"] = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend, rank=rank, world_size=world, **kw)
+
+
 def dist_setup(n_gpus):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     import torch
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl", rank=rank, world_size=world, device_id=torch.device("cuda", local))
+    init_group(world, rank, "nccl")
     return world, rank, local
 
 
@@ -111,14 +121,25 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def max_over_ranks(x, world, device="cuda"):
+    """The slowest rank's value (each rank times its own replica)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_seed(seed, rank):
+    """Noise seed of a rank's replica: the replicas draw independent samples."""
+    return seed + 1000003 * rank
+
+
+def job_rate(world, samples_per_rank, ms_per_step):
+    """Whole-job samples/s: all ranks' samples over the slowest rank's step time."""
+    return world * samples_per_rank / (ms_per_step / 1e3)
 
 
 # ------------------------------------------------------------------ oracle timing
@@ -302,7 +323,7 @@ def our_arm(args):
     N = hier.num_dofs(0)
     ns = args.samples or c["n_samples"]
     kw = dict(kappa=c["kappa"], beta=c["beta"], sinc_k=c["k"], l_lo=c["l_lo"], l_hi=c["l_hi"], n_samples=ns,
-              seed=c["seed"] + 1000003 * rank, split=c["split"], precision=c["precision"], rtol=c["rtol"],
+              seed=rank_seed(c["seed"], rank), split=c["split"], precision=c["precision"], rtol=c["rtol"],
               smoother_degree=args.smoother_degree or c.get("smoother_degree", 4),
               cheb_ratio=args.cheb_ratio or c.get("cheb_ratio", 12.0), preconditioner=args.preconditioner)
     u = torch.empty((ns, N), dtype=torch.float64, device="cuda")
@@ -329,7 +350,7 @@ def our_arm(args):
     wm.profile_enable(False)
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     launches = sum(prof[k]["launches"] - before[k]["launches"] for k in prof)
-    value = world * ns / (ms / 1e3)
+    value = job_rate(world, ns, ms)
     n_int, bf, passes = wm.beta_plan(c["beta"], c["split"])
     n_nodes = c["l_hi"] - c["l_lo"] + 1
     dof_solves = world * N * (n_int + passes * n_nodes) * ns / (ms / 1e3)
