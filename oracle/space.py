@@ -62,23 +62,6 @@ class GluedSpace:
             self.l2g = l2g
             self.N = nxt
 
-    def element_dofs(self, m, eu, ev):
-        """Global DOFs of the (p+1)^2 functions on element (eu, ev) of patch m.
-
-        Local index k = k_v (p+1) + k_u.
-        """
-        p = self.surf.p
-        out = np.zeros((p + 1) * (p + 1), dtype=np.int64)
-        for kv in range(p + 1):
-            for ku in range(p + 1):
-                if self.surf.periodic:
-                    iu = (eu - p + ku) % self.surf.n_u
-                    iv = (ev - p + kv) % self.surf.n_v
-                else:
-                    iu, iv = eu + ku, ev + kv
-                out[kv * (p + 1) + ku] = self.l2g[m, iv, iu]
-        return out
-
     def connectivity(self):
         """[n_patches, n_v, n_u, (p+1)^2] global DOFs of every element."""
         s = self.surf

@@ -121,3 +121,86 @@ def test_spherical_harmonic_convergence_rate(p):
         errs.append(np.sqrt(e2))
     rates = [errs[i] / errs[i + 1] for i in range(2)]
     assert rates[-1] > 0.75 * 2 ** (p + 1), (errs, rates)
+
+
+def _params_of(s, X):
+    """Patch index and parameters (m, u, v) of points X [n, 3] on surface s: the
+    inverse of the gnomonic cube-sphere patches and of the torus map (Sec. 2.2)."""
+    if s.kind == "torus":
+        u = np.mod(np.arctan2(X[:, 1], X[:, 0]) / (2 * np.pi), 1.0)
+        rho = np.hypot(X[:, 0], X[:, 1])
+        v = np.mod(np.arctan2(X[:, 2], rho - s.R) / (2 * np.pi), 1.0)
+        return np.zeros(len(X), dtype=int), u, v
+    ax = np.argmax(np.abs(X), axis=-1)
+    sg = np.sign(X[np.arange(len(X)), ax])
+    m = np.full(len(X), -1)
+    u = np.zeros(len(X))
+    v = np.zeros(len(X))
+    for k, (a, b, n, sgn) in enumerate(geo.CUBE_FACES):
+        sel = (ax == n) & (sg == sgn)
+        m[sel] = k
+        c = X[sel] / np.abs(X[sel][:, n])[:, None]
+        u[sel] = (c[:, a] + 1) / 2
+        v[sel] = (c[:, b] + 1) / 2
+    assert (m >= 0).all()
+    return m, u, v
+
+
+@pytest.mark.parametrize("kind,p,nu,nv", [("torus", 3, 8, 6), ("torus", 2, 5, 7), ("sphere", 2, 3, None),
+                                           ("sphere", 3, 2, None)])
+def test_spline_reproduction(kind, p, nu, nv):
+    # The Galerkin projection of a function of the space is that function: with
+    # f = sum_j c_j phi_j evaluated pointwise, the load vector by the mass matrix's
+    # own Gauss rule is exactly M c, so M^{-1} F = c up to rounding.  This ties the
+    # element connectivity and the load assembly to the global basis evaluation.
+    s = geo.Surface(kind, p, nu, nv)
+    sp_ = GluedSpace(s)
+    _, M = assemble(sp_)
+    c0 = np.random.default_rng(5).standard_normal(sp_.N)
+
+    def f(X):
+        Xf = X.reshape(-1, 3)
+        m, u, v = _params_of(s, Xf)
+        out = np.zeros(len(Xf))
+        for k in np.unique(m):
+            sel = m == k
+            out[sel] = evaluate(sp_, c0, k, u[sel], v[sel])
+        return out.reshape(X.shape[:-1])
+
+    c = spla.spsolve(M.tocsc(), load_vector(sp_, f))
+    assert np.abs(c - c0).max() < 1e-11 * np.abs(c0).max()
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_torus_energies_closed_form(p):
+    # Torus metric (Sec. 2.2): K = diag((2 pi rho)^2, (2 pi r)^2), a = 4 pi^2 rho r,
+    # rho = R + r cos 2 pi v, so the stiffness weight is G = diag(r / rho, rho / r).
+    # For f = cos(2 pi k u): int f^2 = 2 pi^2 R r and int |grad f|^2 =
+    # (2 pi k)^2 r / (2 sqrt(R^2 - r^2)); for g = cos(2 pi v): int g^2 = 2 pi^2 R r
+    # and int |grad g|^2 = (2 pi)^2 R / (2 r).  The L2 projections' energies
+    # converge to these at the rate h^{2p}.
+    R, r = 1.0, 0.4
+
+    def uv(X):
+        u = np.arctan2(X[..., 1], X[..., 0]) / (2 * np.pi)
+        v = np.arctan2(X[..., 2], np.hypot(X[..., 0], X[..., 1]) - R) / (2 * np.pi)
+        return u, v
+
+    cases = [(lambda X: np.cos(2 * np.pi * uv(X)[0]), (2 * np.pi) ** 2 * r / (2 * np.sqrt(R * R - r * r))),
+             (lambda X: np.cos(4 * np.pi * uv(X)[0]), (4 * np.pi) ** 2 * r / (2 * np.sqrt(R * R - r * r))),
+             (lambda X: np.cos(2 * np.pi * uv(X)[1]), (2 * np.pi) ** 2 * R / (2 * r))]
+    mass = 2 * np.pi ** 2 * R * r
+    errs = []
+    for n in (16, 32):
+        sp_ = GluedSpace(geo.Surface("torus", p, n, n // 2, R, r))
+        S, M = assemble(sp_)
+        lu = spla.splu(M.tocsc())
+        row = []
+        for fn, energy in cases:
+            c = lu.solve(load_vector(sp_, fn))
+            assert c @ (M @ c) == pytest.approx(mass, rel=1e-4)
+            row.append(abs(c @ (S @ c) - energy) / energy)
+        errs.append(row)
+    assert max(errs[1]) < (5e-5 if p == 2 else 5e-7), errs
+    for e0, e1 in zip(*errs):
+        assert e0 / e1 > 0.75 * 2 ** (2 * p), errs
