@@ -87,6 +87,34 @@ typedef struct wm_hier* wm_hier_t;
 int wm_setup_geometry(const wm_geom_desc* desc, wm_geom_t* out);
 
 /*
+ * Host-only queries of the discrete space of a geometry; no CUDA device is
+ * used.  They return what wm_assemble_hierarchy builds on the host for its
+ * level `level` (0 = the description's elements; each level halves the
+ * elements per side) before uploading it.  A level is allowed when a hierarchy
+ * of level+1 levels is (the prolongation needs level+2).
+ *
+ * wm_geom_level_sizes: glued DOFs N of S^0_{j,p} (Eq. def::space2), local
+ *   DOFs per patch side (elems + p open, elems periodic), elements E of all
+ *   patches, and the stored entries of the prolongation from level+1 to
+ *   level (0 at the coarsest allowed level).  NULL outputs are skipped.
+ * wm_geom_dof_map: copies the local-to-global map [np][n_loc_v][n_loc_u]
+ *   (int32, same numbering rule as wm_setup_geometry) to host `l2g`, and, if
+ *   `conn` is not NULL, the element connectivity [E][(p+1)^2] (element
+ *   (m n_v + e_v) n_u + e_u, local function k = k_v (p+1) + k_u; periodic
+ *   elements carry the functions e-p..e mod n).  Capacities are in entries.
+ * wm_geom_prolongation: the prolongation from level+1 to level by dyadic
+ *   knot insertion (Sec. 2.3: the nested spaces Xi_{j,p} of the refinement)
+ *   as host CSR: row_ptr [N_fine + 1], col [nnz] (coarse DOF, ascending in a
+ *   row), val [nnz] float64.  nnz_cap is the capacity of col and val.
+ * Errors: WM_ERR_INVALID_ARG for a NULL handle or buffer, a level out of range
+ * or a capacity too small; nothing is written then.
+ */
+int wm_geom_level_sizes(wm_geom_t g, int level, int* n_dofs, int* n_loc_u, int* n_loc_v, int* n_elems,
+                        int64_t* prolong_nnz);
+int wm_geom_dof_map(wm_geom_t g, int level, int32_t* l2g, int64_t l2g_cap, int32_t* conn, int64_t conn_cap);
+int wm_geom_prolongation(wm_geom_t g, int level, int32_t* row_ptr, int32_t* col, double* val, int64_t nnz_cap);
+
+/*
  * Builds the dyadic hierarchy of n_levels levels (finest = the description's
  * elements, each coarser level halves the elements per side; Sec. 2.3,
  * Xi_{j,p}) on the current CUDA device: the metric terms a_m and a_m K_m^{-1}

@@ -13,6 +13,7 @@ library every call raises.
 """
 import ctypes as C
 
+import numpy as np
 import torch
 
 from . import _capi
@@ -46,6 +47,36 @@ class Geometry:
         check(lib().wm_setup_geometry(C.byref(d), C.byref(h)), "wm_setup_geometry")
         self._h = h
         self.desc = d
+
+    def level_sizes(self, level=0, prolongation=True):
+        """Host-only: (N, n_loc_u, n_loc_v, elements, prolongation entries) of a level;
+        the last is 0 when `prolongation` is False or at the coarsest level."""
+        n, lu, lv, ne, nnz = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int64(0)
+        check(lib().wm_geom_level_sizes(self._h, level, C.byref(n), C.byref(lu), C.byref(lv), C.byref(ne),
+                                        C.byref(nnz) if prolongation else None), "wm_geom_level_sizes")
+        return n.value, lu.value, lv.value, ne.value, nnz.value
+
+    def dof_map(self, level=0):
+        """Host-only: local-to-global map [patches, n_loc_v, n_loc_u] and element
+        connectivity [elements, (p+1)^2] of a level (int32 numpy arrays)."""
+        _, lu, lv, ne, _ = self.level_sizes(level, prolongation=False)
+        n_p = 6 if self.desc.kind == _capi.WM_SPHERE6 else 1
+        l2g = np.empty((n_p, lv, lu), dtype=np.int32)
+        conn = np.empty((ne, (self.desc.degree + 1) ** 2), dtype=np.int32)
+        check(lib().wm_geom_dof_map(self._h, level, l2g.ctypes.data, l2g.size, conn.ctypes.data, conn.size),
+              "wm_geom_dof_map")
+        return l2g, conn
+
+    def prolongation(self, level=0):
+        """Host-only: knot-insertion prolongation from level+1 to level as CSR
+        arrays (row_ptr int32 [N_fine+1], col int32, val float64)."""
+        n, _, _, _, nnz = self.level_sizes(level)
+        row_ptr = np.empty(n + 1, dtype=np.int32)
+        col = np.empty(nnz, dtype=np.int32)
+        val = np.empty(nnz, dtype=np.float64)
+        check(lib().wm_geom_prolongation(self._h, level, row_ptr.ctypes.data, col.ctypes.data, val.ctypes.data,
+                                         nnz), "wm_geom_prolongation")
+        return row_ptr, col, val
 
     def __del__(self):
         if getattr(self, "_h", None) and _capi._lib is not None:

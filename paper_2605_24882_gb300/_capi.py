@@ -59,6 +59,10 @@ _PROTOS = {
     "wm_num_dofs": (_i, [_vp, _i]),
     "wm_num_quad_points": (_i, [_vp, _i]),
     "wm_dof_map": (_i, [_vp, _i, _vp, _i64]),
+    "wm_geom_level_sizes": (_i, [_vp, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i),
+                                 C.POINTER(_i64)]),
+    "wm_geom_dof_map": (_i, [_vp, _i, _vp, _i64, _vp, _i64]),
+    "wm_geom_prolongation": (_i, [_vp, _i, _vp, _vp, _vp, _i64]),
     "wm_metric": (_i, [_vp, _i, _vp, _vp]),
     "wm_apply_shifted": (_i, [_vp, _i, _i, C.POINTER(_d), _vp, _vp, _i, _vp]),
     "wm_apply_mass": (_i, [_vp, _i, _vp, _vp, _i, _vp]),

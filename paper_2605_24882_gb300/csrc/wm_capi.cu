@@ -228,17 +228,21 @@ static int assemble(wm_hier* h, int n_levels, cudaStream_t s) {
   return WM_OK;
 }
 
+// Levels a hierarchy of this surface may have: halving down to one element per
+// patch side (cube sphere) or to 2p+2 elements per side (periodic torus).
+static int max_levels(const wm_geom_desc& g) {
+  int minside = std::min(g.elems_u, g.elems_v);
+  int lowest = g.kind == WM_TORUS ? 2 * g.degree + 2 : 1;
+  int maxlev = 0;
+  while ((minside >> maxlev) >= lowest) ++maxlev;
+  return maxlev;
+}
+
 extern "C" int wm_assemble_hierarchy(wm_geom_t geom, int n_levels, void* stream, wm_hier_t* out) {
   if (!geom || !out) return WM_ERR_INVALID_ARG;
   *out = nullptr;
   const wm_geom_desc& g = geom->d;
-  int minside = std::min(g.elems_u, g.elems_v);
-  int maxlev = 0;
-  while ((minside >> maxlev) >= 1) ++maxlev;
-  if (g.kind == WM_TORUS) {
-    maxlev = 0;
-    while ((minside >> maxlev) >= 2 * g.degree + 2) ++maxlev;
-  }
+  int maxlev = max_levels(g);
   if (n_levels < 1 || n_levels > maxlev) {
     wm_set_error("n_levels %d outside 1..%d for this surface", n_levels, maxlev);
     return WM_ERR_INVALID_ARG;
@@ -280,6 +284,74 @@ extern "C" int wm_dof_map(wm_hier_t h, int level, int32_t* out, int64_t cap) {
   if (!out || cap < (int64_t)L.l2g.size()) return WM_ERR_INVALID_ARG;
   std::memcpy(out, L.l2g.data(), L.l2g.size() * sizeof(int32_t));
   return (int)L.l2g.size();
+}
+
+// ------------------------------------------------------- host-only space queries
+static int geom_level(wm_geom_t g, int level, int need, wm_level& L) {
+  if (!g) return WM_ERR_INVALID_ARG;
+  if (level < 0 || level + need >= max_levels(g->d)) {
+    wm_set_error("level %d outside 0..%d for this surface", level, max_levels(g->d) - 1 - need);
+    return WM_ERR_INVALID_ARG;
+  }
+  return wm_host_build_level(g->d, g->np, g->d.elems_u >> level, g->d.elems_v >> level, L);
+}
+
+static int geom_prolongation(wm_geom_t g, int level, std::vector<int32_t>& Pp, std::vector<int32_t>& Pc,
+                             std::vector<double>& Pv) {
+  wm_level F, C;
+  WM_TRY(geom_level(g, level, 1, F));
+  WM_TRY(geom_level(g, level + 1, 0, C));
+  std::vector<int32_t> Rp, Rc;
+  std::vector<double> Rv;
+  return wm_host_prolongation(g->d, g->np, F, C, Pp, Pc, Pv, Rp, Rc, Rv);
+}
+
+extern "C" int wm_geom_level_sizes(wm_geom_t g, int level, int* n_dofs, int* n_loc_u, int* n_loc_v,
+                                   int* n_elems, int64_t* prolong_nnz) {
+  wm_level L;
+  WM_TRY(geom_level(g, level, 0, L));
+  if (n_dofs) *n_dofs = L.N;
+  if (n_loc_u) *n_loc_u = L.nlu;
+  if (n_loc_v) *n_loc_v = L.nlv;
+  if (n_elems) *n_elems = L.E;
+  if (prolong_nnz) {
+    *prolong_nnz = 0;
+    if (level + 1 < max_levels(g->d)) {
+      std::vector<int32_t> Pp, Pc;
+      std::vector<double> Pv;
+      WM_TRY(geom_prolongation(g, level, Pp, Pc, Pv));
+      *prolong_nnz = (int64_t)Pc.size();
+    }
+  }
+  return WM_OK;
+}
+
+extern "C" int wm_geom_dof_map(wm_geom_t g, int level, int32_t* l2g, int64_t l2g_cap, int32_t* conn,
+                               int64_t conn_cap) {
+  wm_level L;
+  WM_TRY(geom_level(g, level, 0, L));
+  if (!l2g || l2g_cap < (int64_t)L.l2g.size() || (conn && conn_cap < (int64_t)L.conn.size())) {
+    wm_set_error("output buffers too small");
+    return WM_ERR_INVALID_ARG;
+  }
+  std::memcpy(l2g, L.l2g.data(), L.l2g.size() * sizeof(int32_t));
+  if (conn) std::memcpy(conn, L.conn.data(), L.conn.size() * sizeof(int32_t));
+  return WM_OK;
+}
+
+extern "C" int wm_geom_prolongation(wm_geom_t g, int level, int32_t* row_ptr, int32_t* col, double* val,
+                                    int64_t nnz_cap) {
+  std::vector<int32_t> Pp, Pc;
+  std::vector<double> Pv;
+  WM_TRY(geom_prolongation(g, level, Pp, Pc, Pv));
+  if (!row_ptr || !col || !val || nnz_cap < (int64_t)Pc.size()) {
+    wm_set_error("output buffers too small");
+    return WM_ERR_INVALID_ARG;
+  }
+  std::memcpy(row_ptr, Pp.data(), Pp.size() * sizeof(int32_t));
+  std::memcpy(col, Pc.data(), Pc.size() * sizeof(int32_t));
+  std::memcpy(val, Pv.data(), Pv.size() * sizeof(double));
+  return WM_OK;
 }
 
 extern "C" int wm_metric(wm_hier_t h, int level, double* out, void* stream) {

@@ -79,3 +79,91 @@ def test_geometry_validation(lib):
         assert e.value.code == _capi.WM_ERR_INVALID_ARG
     assert lib.wm_error_string(-4).decode() == "not converged"
     assert lib.wm_num_dofs(None, 0) == _capi.WM_ERR_INVALID_ARG
+
+
+def _oracle_space(kind, p, nu, nv, level):
+    from oracle import geometry as geo
+    from oracle.space import GluedSpace
+    return GluedSpace(geo.Surface(kind, p, nu >> level, None if kind == "sphere" else nv >> level))
+
+
+@pytest.mark.parametrize("kind,p,nu,nv", [("sphere", 1, 8, 8), ("sphere", 2, 8, 8), ("sphere", 3, 4, 4),
+                                           ("sphere", 4, 2, 2), ("torus", 3, 32, 16), ("torus", 2, 16, 32)])
+def test_host_dof_maps_match_oracle(lib, kind, p, nu, nv):
+    # The library glues by matching integer lattice points of patch edges; the
+    # oracle by matching the physical anchors of Greville points.  Both number
+    # by the same scan rule, so the maps and connectivities agree bit for bit
+    # at every level of the hierarchy.
+    import numpy as np
+    import paper_2605_24882_gb300 as wm
+    g = wm.Geometry(kind, p, nu, nv)
+    lowest = 1 if kind == "sphere" else 2 * p + 2
+    level = 0
+    while (min(nu, nv) >> level) >= lowest:
+        sp_ = _oracle_space(kind, p, nu, nv, level)
+        n, lu, lv, ne, _ = g.level_sizes(level, prolongation=False)
+        l2g, conn = g.dof_map(level)
+        assert (n, lu, lv) == (sp_.N, sp_.l2g.shape[2], sp_.l2g.shape[1])
+        assert ne == sp_.surf.n_patches * sp_.surf.n_u * sp_.surf.n_v
+        assert np.array_equal(l2g, sp_.l2g)
+        assert np.array_equal(conn, sp_.connectivity().reshape(ne, -1))
+        level += 1
+    assert level >= 2
+    with pytest.raises(wm.WMError):
+        g.dof_map(level)
+
+
+def test_host_dof_map_at_the_largest_sphere(lib):
+    # sphere p = 2 with 512 x 512 elements per patch: 1,579,016 glued DOFs, the
+    # largest surface of the uneven multi-instance workload
+    import numpy as np
+    import paper_2605_24882_gb300 as wm
+    sp_ = _oracle_space("sphere", 2, 512, 512, 0)
+    l2g, _ = wm.Geometry("sphere", 2, 512).dof_map(0)
+    assert sp_.N == 1579016 and l2g.max() + 1 == sp_.N
+    assert np.array_equal(l2g, sp_.l2g)
+
+
+@pytest.mark.parametrize("kind,p,nu,nv", [("sphere", 2, 8, 8), ("sphere", 3, 4, 4), ("sphere", 1, 4, 4),
+                                           ("torus", 3, 32, 16), ("torus", 2, 32, 16)])
+def test_host_prolongation_refines_splines_exactly(lib, kind, p, nu, nv):
+    # Knot insertion (Sec. 2.3): the spaces are nested, so the fine coefficients
+    # P c describe the same function as the coarse coefficients c.  Checked by
+    # the oracle's own basis evaluation at random parameters of every patch.
+    import numpy as np
+    import scipy.sparse as sp
+    import paper_2605_24882_gb300 as wm
+    from oracle.assembly import evaluate
+    g = wm.Geometry(kind, p, nu, nv)
+    fine, coarse = _oracle_space(kind, p, nu, nv, 0), _oracle_space(kind, p, nu, nv, 1)
+    row_ptr, col, val = g.prolongation(0)
+    P = sp.csr_matrix((val, col, row_ptr), shape=(fine.N, coarse.N))
+    assert (val > 0).all()
+    same_row = np.diff(np.repeat(np.arange(fine.N), np.diff(row_ptr))) == 0
+    assert (np.diff(col.astype(np.int64))[same_row] > 0).all()            # columns ascend within a row
+    np.testing.assert_allclose(P @ np.ones(coarse.N), 1.0, rtol=0, atol=1e-14)   # partition of unity
+    rng = np.random.default_rng(2)
+    c = rng.standard_normal(coarse.N)
+    f = P @ c
+    for m in range(fine.surf.n_patches):
+        u, v = rng.random(40), rng.random(40)
+        np.testing.assert_allclose(evaluate(fine, f, m, u, v), evaluate(coarse, c, m, u, v), rtol=0, atol=1e-12)
+
+
+def test_host_queries_reject_bad_arguments(lib):
+    import numpy as np
+    import paper_2605_24882_gb300 as wm
+    from paper_2605_24882_gb300 import _capi
+    g = wm.Geometry("sphere", 2, 4)
+    n, lu, lv, ne, nnz = g.level_sizes(0)
+    assert nnz > 0 and g.level_sizes(2)[4] == 0          # 4 -> 2 -> 1 elements: level 2 is the coarsest
+    for bad in (-1, 3):
+        assert lib.wm_geom_level_sizes(g._h, bad, None, None, None, None, None) == _capi.WM_ERR_INVALID_ARG
+    assert lib.wm_geom_prolongation(g._h, 2, None, None, None, 0) == _capi.WM_ERR_INVALID_ARG
+    small = np.zeros(6 * lu * lv - 1, dtype=np.int32)
+    assert lib.wm_geom_dof_map(g._h, 0, small.ctypes.data, small.size, None, 0) == _capi.WM_ERR_INVALID_ARG
+    assert (small == 0).all()
+    rp, col, val = (np.zeros(n + 1, np.int32), np.zeros(nnz, np.int32), np.zeros(nnz))
+    assert lib.wm_geom_prolongation(g._h, 0, rp.ctypes.data, col.ctypes.data, val.ctypes.data,
+                                    nnz - 1) == _capi.WM_ERR_INVALID_ARG
+    assert lib.wm_geom_level_sizes(None, 0, None, None, None, None, None) == _capi.WM_ERR_INVALID_ARG
