@@ -22,10 +22,14 @@ It computes, in float64 with numpy/scipy, exactly what the sampler defines:
                     (Sec. 3.4), sinc nodes and weights (Eq. eq:beta-approx), and
                     the fields u_s by direct sparse solves and an explicit sum;
                     the field-loss gradient by the adjoint identity.
+* ``sqrt_mass``  -- loads f = sqrt(M) y by the Hale–Higham–Trefethen sum
+                    (Sec. 3.3, Eq. eq:sqrt) and bounds of the mass spectrum.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against values the
 paper prints (Figs. 1, 4, 5), closed forms (areas, spherical harmonics,
 gnomonic area element), invariants (S 1 = 0, symmetry, B B^T = M) and brute
-force (dense generalised eigen-decomposition).  No function here is
+force (dense generalised eigen-decomposition, dense matrix square roots).
+``tests/test_oracle_mutants.py`` plants mistakes in a copy of this package and
+checks that the pins catch each one.  No function here is
 "parity unpinned".
 """

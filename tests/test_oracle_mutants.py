@@ -105,6 +105,20 @@ MUTANTS = [
     ("loss_drop_mass", "fractional.py", "L = float(np.sum(d * (M @ d)))", "L = float(np.sum(d * d))"),
     ("adjoint_rhs_drop_mass", "fractional.py", "gt = 2.0 * (M @ d)", "gt = 2.0 * d"),
     ("adjoint_kappa_sign", "fractional.py", "dk += -2.0 * kappa * cl * float(", "dk += 2.0 * kappa * cl * float("),
+    # sqrt(M) by the Hale–Higham–Trefethen sum (Sec. 3.3)
+    ("hht_midpoint", "sqrt_mass.py", "(np.arange(1, n_nodes + 1) - 0.5)", "(np.arange(1, n_nodes + 1) - 0.25)"),
+    ("hht_prefactor", "sqrt_mass.py", "c = 2.0 * K * math.sqrt(lo)", "c = K * math.sqrt(lo)"),
+    ("hht_jacobian_power", "sqrt_mass.py", "* dn / cn ** 2", "* dn / cn"),
+    ("hht_shift_scale", "sqrt_mass.py", "w2 = lo * (sn / cn) ** 2", "w2 = math.sqrt(lo) * (sn / cn) ** 2"),
+    ("hht_drop_outer_factor", "sqrt_mass.py", "    return A @ acc", "    return acc"),
+    ("hht_parameter", "sqrt_mass.py", "q = 1.0 - lo / hi", "q = lo / hi"),
+    ("hht_no_reflection", "sqrt_mass.py", "far = t > 0.5 * K", "far = t > K"),
+    ("hht_reflection_parameter", "sqrt_mass.py", "w2[far] = lo / kp2 * (cnu / snu) ** 2",
+     "w2[far] = hi * (cnu / snu) ** 2"),
+    ("bounds_diagonal_only", "sqrt_mass.py", "hi = float(np.abs(M).sum(axis=1).max())", "hi = float(M.diagonal().max())"),
+    ("bounds_diagonal_max", "sqrt_mass.py", "return lam * float(M.diagonal().min()), hi",
+     "return lam * float(M.diagonal().max()), hi"),
+    ("bounds_unscaled", "sqrt_mass.py", "A / d[:, :, None] / d[:, None, :]", "A / d[:, :, None]"),
     ("adjoint_drop_integer_term", "fractional.py", "dk += -2.0 * kappa * float(np.sum(lam * (M @ ws[i])))",
      "pass"),
 ]
