@@ -115,6 +115,31 @@ int wm_geom_dof_map(wm_geom_t g, int level, int32_t* l2g, int64_t l2g_cap, int32
 int wm_geom_prolongation(wm_geom_t g, int level, int32_t* row_ptr, int32_t* col, double* val, int64_t nnz_cap);
 
 /*
+ * Host-only bounds lo <= lambda_min(M) and lambda_max(M) <= hi of the
+ * assembled mass matrix of a level (the spectrum bounds m, M of Sec. 3.3 that
+ * the sqrt(M) rule needs).  On each patch the quadrature mass form lies
+ * between the smallest and the largest area element times the flat
+ * tensor-product form M_u (x) M_v; lo and hi combine the closed-form extremes of
+ * the area element (cube sphere: 4 (1+a^2+b^2)^{-3/2} on [-1,1]^2; torus:
+ * 4 pi^2 r (R +- r)) with the extreme eigenvalues of the 1D mass matrices and,
+ * for hi, the three patches that share a cube corner.  Level as for
+ * wm_geom_level_sizes.  Errors: WM_ERR_INVALID_ARG.
+ */
+int wm_geom_mass_bounds(wm_geom_t g, int level, double* lo, double* hi);
+
+/*
+ * Host-only: shifts w2[k] = w_k^2 and weights c[k] (host arrays [n_nodes]) of
+ * the n_nodes-point rule sqrt(A) y ~= A sum_k c_k (A + w_k^2 I)^{-1} y for a
+ * symmetric positive definite A with spectrum in [lo, hi] (Sec. 3.3,
+ * Eq. eq:sqrt, after Hale, Higham and Trefethen): w_k = sqrt(lo) sn(t_k|q) /
+ * cn(t_k|q), c_k = 2 K sqrt(lo) dn(t_k|q) / (pi n_nodes cn(t_k|q)^2),
+ * t_k = (k + 1/2) K / n_nodes, q = 1 - lo/hi, K = K(q) the complete elliptic
+ * integral of the first kind.  Errors: WM_ERR_INVALID_ARG unless 0 < lo < hi,
+ * n_nodes >= 1 and both arrays are given.
+ */
+int wm_hht_rule(double lo, double hi, int n_nodes, double* w2, double* c);
+
+/*
  * Builds the dyadic hierarchy of n_levels levels (finest = the description's
  * elements, each coarser level halves the elements per side; Sec. 2.3,
  * Xi_{j,p}) on the current CUDA device: the metric terms a_m and a_m K_m^{-1}

@@ -19,7 +19,8 @@ import torch
 from . import _capi
 from ._capi import WMError, check, lib
 
-__all__ = ["Geometry", "Hierarchy", "philox4x32_10", "normals", "beta_plan", "sinc_nodes", "WMError", "WMField"]
+__all__ = ["Geometry", "Hierarchy", "philox4x32_10", "normals", "beta_plan", "sinc_nodes", "hht_rule", "WMError",
+           "WMField"]
 
 _PREC = {"fp64": _capi.WM_FP64, "mixed": _capi.WM_MIXED}
 _SPLIT = {"standard": _capi.WM_SPLIT_STANDARD, "improved": _capi.WM_SPLIT_IMPROVED}
@@ -78,6 +79,12 @@ class Geometry:
                                          nnz), "wm_geom_prolongation")
         return row_ptr, col, val
 
+    def mass_bounds(self, level=0):
+        """Host-only: (lo, hi) bracketing the spectrum of the level's mass matrix."""
+        lo, hi = C.c_double(), C.c_double()
+        check(lib().wm_geom_mass_bounds(self._h, level, C.byref(lo), C.byref(hi)), "wm_geom_mass_bounds")
+        return lo.value, hi.value
+
     def __del__(self):
         if getattr(self, "_h", None) and _capi._lib is not None:
             _capi._lib.wm_destroy_geom(self._h)
@@ -91,6 +98,16 @@ def sinc_nodes(beta, kappa, tol, split="standard"):
     check(lib().wm_sinc_nodes(beta, _SPLIT[split], kappa, tol, C.byref(k), C.byref(lo), C.byref(hi)),
           "wm_sinc_nodes")
     return k.value, lo.value, hi.value
+
+
+def hht_rule(lo, hi, n_nodes):
+    """Shifts w_k^2 and weights c_k (float64 numpy arrays) of the n_nodes-point
+    rule sqrt(A) y ~= A sum_k c_k (A + w_k^2 I)^{-1} y for spectra in [lo, hi]."""
+    w2 = np.empty(n_nodes, dtype=np.float64)
+    c = np.empty(n_nodes, dtype=np.float64)
+    check(lib().wm_hht_rule(lo, hi, n_nodes, w2.ctypes.data if n_nodes > 0 else None,
+                            c.ctypes.data if n_nodes > 0 else None), "wm_hht_rule")
+    return w2, c
 
 
 def beta_plan(beta, split="standard"):

@@ -287,12 +287,17 @@ extern "C" int wm_dof_map(wm_hier_t h, int level, int32_t* out, int64_t cap) {
 }
 
 // ------------------------------------------------------- host-only space queries
-static int geom_level(wm_geom_t g, int level, int need, wm_level& L) {
+static int check_geom_level(wm_geom_t g, int level, int need) {
   if (!g) return WM_ERR_INVALID_ARG;
   if (level < 0 || level + need >= max_levels(g->d)) {
     wm_set_error("level %d outside 0..%d for this surface", level, max_levels(g->d) - 1 - need);
     return WM_ERR_INVALID_ARG;
   }
+  return WM_OK;
+}
+
+static int geom_level(wm_geom_t g, int level, int need, wm_level& L) {
+  WM_TRY(check_geom_level(g, level, need));
   return wm_host_build_level(g->d, g->np, g->d.elems_u >> level, g->d.elems_v >> level, L);
 }
 
@@ -337,6 +342,12 @@ extern "C" int wm_geom_dof_map(wm_geom_t g, int level, int32_t* l2g, int64_t l2g
   std::memcpy(l2g, L.l2g.data(), L.l2g.size() * sizeof(int32_t));
   if (conn) std::memcpy(conn, L.conn.data(), L.conn.size() * sizeof(int32_t));
   return WM_OK;
+}
+
+extern "C" int wm_geom_mass_bounds(wm_geom_t g, int level, double* lo, double* hi) {
+  WM_TRY(check_geom_level(g, level, 0));
+  if (!lo || !hi) return WM_ERR_INVALID_ARG;
+  return wm_host_mass_bounds(g->d, g->d.elems_u >> level, g->d.elems_v >> level, lo, hi);
 }
 
 extern "C" int wm_geom_prolongation(wm_geom_t g, int level, int32_t* row_ptr, int32_t* col, double* val,

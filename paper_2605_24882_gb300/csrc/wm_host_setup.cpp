@@ -427,6 +427,194 @@ int wm_host_prolongation(const wm_geom_desc& g, int np, const wm_level& F, const
   return WM_OK;
 }
 
+// ------------------------------------------------------------ sqrt(M) rule
+// Jacobian elliptic functions sn, cn, dn of argument u and parameter q, and the
+// complete elliptic integral of the first kind K(q), by the scale of the
+// arithmetic-geometric mean (Abramowitz & Stegun 16.4 and 17.6):
+// a_0 = 1, b_0 = sqrt(1-q), c_0 = sqrt(q); a_n, b_n the means, c_n = (a_{n-1} - b_{n-1})/2;
+// phi_N = 2^N a_N u and phi_{n-1} = (phi_n + asin(c_n sin(phi_n) / a_n)) / 2;
+// sn = sin phi_0, cn = cos phi_0, dn = cos phi_0 / cos(phi_1 - phi_0); K = pi / (2 a_N).
+namespace {
+struct Agm {
+  double a[40], c[40];
+  int n = 0;
+};
+
+Agm agm_scale(double q) {
+  Agm s;
+  double a = 1.0, b = std::sqrt(1.0 - q);
+  s.a[0] = a;
+  s.c[0] = std::sqrt(q);
+  while (s.n < 38 && std::fabs(a - b) > 3e-16 * a) {
+    double an = 0.5 * (a + b), bn = std::sqrt(a * b);
+    ++s.n;
+    s.c[s.n] = 0.5 * (a - b);
+    s.a[s.n] = an;
+    a = an;
+    b = bn;
+  }
+  return s;
+}
+
+void jacobi_sncndn(const Agm& s, double u, double* sn, double* cn, double* dn) {
+  if (s.n == 0) {
+    *sn = std::sin(u);
+    *cn = std::cos(u);
+    *dn = 1.0;
+    return;
+  }
+  double phi = std::ldexp(s.a[s.n] * u, s.n), prev = phi;
+  for (int k = s.n; k >= 1; --k) {
+    prev = phi;
+    phi = 0.5 * (phi + std::asin(s.c[k] * std::sin(phi) / s.a[k]));
+  }
+  *sn = std::sin(phi);
+  *cn = std::cos(phi);
+  *dn = *cn / std::cos(prev - phi);
+}
+}  // namespace
+
+// Shifts and weights of the K^-node rule A^{1/2} y ~= A sum_k c_k (A + w_k^2 I)^{-1} y
+// (Sec. 3.3, Eq. eq:sqrt): w = sqrt(lo) sn(t|q)/cn(t|q), q = 1 - lo/hi, and the
+// midpoint rule t_k = (k - 1/2) K(q) / K^ on A^{-1/2} = (2/pi) int_0^inf (A + w^2 I)^{-1} dw.
+// Nodes past K/2 are evaluated at the reflected argument u = K - t
+// (sn(t) = cn(u)/dn(u), cn(t) = k' sn(u)/dn(u), dn(t) = k'/dn(u), k'^2 = 1 - q),
+// where cn(t) would otherwise be known only to absolute accuracy.
+extern "C" int wm_hht_rule(double lo, double hi, int n_nodes, double* w2, double* c) {
+  if (!(lo > 0.0 && hi > lo) || n_nodes < 1 || !w2 || !c) {
+    wm_set_error("hht rule needs 0 < lo < hi, n_nodes >= 1 and output arrays");
+    return WM_ERR_INVALID_ARG;
+  }
+  double q = 1.0 - lo / hi, kp2 = 1.0 - q;
+  Agm s = agm_scale(q);
+  double K = 0.5 * M_PI / s.a[s.n];
+  double pre = 2.0 * K / (M_PI * n_nodes);
+  for (int k = 0; k < n_nodes; ++k) {
+    double t = (k + 0.5) * K / n_nodes;
+    double sn, cn, dn;
+    if (t <= 0.5 * K) {
+      jacobi_sncndn(s, t, &sn, &cn, &dn);
+      w2[k] = lo * (sn / cn) * (sn / cn);
+      c[k] = pre * std::sqrt(lo) * dn / (cn * cn);
+    } else {
+      jacobi_sncndn(s, K - t, &sn, &cn, &dn);
+      w2[k] = lo / kp2 * (cn / sn) * (cn / sn);
+      c[k] = pre * std::sqrt(lo / kp2) * dn / (sn * sn);
+    }
+  }
+  return WM_OK;
+}
+
+// Extremes of the spectrum of the 1D mass matrix int_0^1 B_i B_j of the spline
+// space with n elements (exact with the p+1 point Gauss rule).  Open knots: the
+// matrix is banded (bandwidth p) and positive definite, and lambda_min (lambda_max)
+// is located by bisection on sigma with a banded Cholesky factorisation of
+// A - sigma I (sigma I - A), which exists exactly when sigma is below (above)
+// the spectrum.  Periodic: the matrix is circulant, lambda_k = c_0 + 2 sum_j c_j cos(2 pi j k / n).
+static void mass_1d_extremes(const wm_geom_desc& g, int n, const std::vector<double>& gx,
+                             const std::vector<double>& gw, double* lmin, double* lmax) {
+  int p = g.degree, nq = (int)gx.size();
+  bool periodic = g.kind == WM_TORUS;
+  int nd = periodic ? n : n + p;
+  // band storage: B[i][d] = A[i][i+d], d = 0..p (periodic: offsets mod n, c_d)
+  std::vector<double> B((size_t)nd * (p + 1), 0.0);
+  for (int e = 0; e < n; ++e)
+    for (int qi = 0; qi < nq; ++qi) {
+      double val[8], der[8];
+      if (periodic) {
+        for (int a = 0; a <= p; ++a) cardinal_eval(p, gx[qi] + p - a, &val[a], &der[a]);
+      } else {
+        open_local_basis(n, p, e, (e + gx[qi]) / n, val, der);
+      }
+      for (int a = 0; a <= p; ++a)
+        for (int b = a; b <= p; ++b) {
+          int i = periodic ? ((e - p + a) % n + n) % n : e + a;
+          B[(size_t)i * (p + 1) + (b - a)] += gw[qi] / n * val[a] * val[b];
+        }
+    }
+  if (periodic) {
+    // every row of the circulant carries the same c_d; take row 0
+    *lmin = 1e300;
+    *lmax = -1e300;
+    for (int k = 0; k < n; ++k) {
+      double lam = B[0];
+      for (int d = 1; d <= p; ++d) lam += 2.0 * B[d] * std::cos(2.0 * M_PI * d * k / n);
+      *lmin = std::min(*lmin, lam);
+      *lmax = std::max(*lmax, lam);
+    }
+    return;
+  }
+  auto chol_ok = [&](double sigma, double sign) {
+    // factor sign*(A - sigma I) in band form, L[i][d] = L(i, i-d)
+    std::vector<double> L((size_t)nd * (p + 1), 0.0);
+    for (int i = 0; i < nd; ++i)
+      for (int j = std::max(0, i - p); j <= i; ++j) {
+        double v = sign * (B[(size_t)j * (p + 1) + (i - j)] - (i == j ? sigma : 0.0));
+        for (int k = std::max(0, i - p); k < j; ++k) v -= L[(size_t)i * (p + 1) + (i - k)] * L[(size_t)j * (p + 1) + (j - k)];
+        if (i == j) {
+          if (!(v > 0.0)) return false;
+          L[(size_t)i * (p + 1)] = std::sqrt(v);
+        } else {
+          L[(size_t)i * (p + 1) + (i - j)] = v / L[(size_t)j * (p + 1)];
+        }
+      }
+    return true;
+  };
+  double rowmax = 0.0;
+  for (int i = 0; i < nd; ++i) {
+    double r = 0.0;
+    for (int j = std::max(0, i - p); j <= std::min(nd - 1, i + p); ++j)
+      r += std::fabs(i <= j ? B[(size_t)i * (p + 1) + (j - i)] : B[(size_t)j * (p + 1) + (i - j)]);
+    rowmax = std::max(rowmax, r);
+  }
+  double a = 0.0, b = rowmax;  // chol(A - a I) succeeds, chol(A - b I) fails
+  for (int it = 0; it < 200 && b - a > 1e-15 * rowmax; ++it) {
+    double m = 0.5 * (a + b);
+    (chol_ok(m, 1.0) ? a : b) = m;
+  }
+  *lmin = a;
+  a = 0.0;
+  b = rowmax * (1.0 + 1e-12);  // chol(b I - A) succeeds, chol(a I - A) fails
+  for (int it = 0; it < 200 && b - a > 1e-15 * rowmax; ++it) {
+    double m = 0.5 * (a + b);
+    (chol_ok(m, -1.0) ? b : a) = m;
+  }
+  *lmax = b;
+}
+
+// Bounds lo <= lambda_min(M) <= lambda_max(M) <= hi of the assembled mass matrix
+// of one level.  On a patch the quadrature mass form is sum_q w_q a_q (sum_i x_i phi_i)^2,
+// between a_min and a_max times the flat form x^T (M_u (x) M_v) x, which the
+// p+1 point rule integrates exactly; the patches' DOF vectors x_m satisfy
+// |x|^2 <= sum_m |x_m|^2 <= mult |x|^2 (mult = 3 on the cube sphere, whose corner
+// DOFs lie on three patches).  Area elements: gnomonic 4 (1 + a^2 + b^2)^{-3/2},
+// a, b in [-1, 1], so a in [4 / 3^{3/2}, 4]; torus 4 pi^2 r (R + r cos 2 pi v).
+int wm_host_mass_bounds(const wm_geom_desc& g, int nu, int nv, double* lo, double* hi) {
+  std::vector<double> gx, gw;
+  wm_gauss_legendre01(g.degree + 1, gx, gw);
+  double umin, umax, vmin, vmax;
+  mass_1d_extremes(g, nu, gx, gw, &umin, &umax);
+  mass_1d_extremes(g, nv, gx, gw, &vmin, &vmax);
+  double amin, amax, mult;
+  if (g.kind == WM_TORUS) {
+    amin = 4.0 * M_PI * M_PI * g.r * (g.R - g.r);
+    amax = 4.0 * M_PI * M_PI * g.r * (g.R + g.r);
+    mult = 1.0;
+  } else {
+    amin = 4.0 / (3.0 * std::sqrt(3.0));
+    amax = 4.0;
+    mult = 3.0;
+  }
+  if (!(umin > 0.0 && vmin > 0.0)) {
+    wm_set_error("1D mass matrix not positive definite");
+    return WM_ERR_INVALID_ARG;
+  }
+  // relative margins cover the rounding of the bisection and of the area elements
+  *lo = amin * umin * vmin * (1.0 - 1e-9);
+  *hi = mult * amax * umax * vmax * (1.0 + 1e-9);
+  return WM_OK;
+}
+
 // ------------------------------------------------------------ beta split
 int wm_split_beta(double beta, int split, int* n, double* bp, int* passes) {
   if (!(beta > 0.0) || !std::isfinite(beta)) return WM_ERR_INVALID_ARG;

@@ -167,6 +167,7 @@ void wm_host_noise_map(const wm_level& L, std::vector<int32_t>& ptr, std::vector
 int wm_host_stencil(const wm_geom_desc& g, int np, const wm_level& L, std::vector<int32_t>& ext,
                     std::vector<int32_t>& own, std::vector<int16_t>& slot);
 int wm_split_beta(double beta, int split, int* n, double* bp, int* passes);
+int wm_host_mass_bounds(const wm_geom_desc& g, int nu, int nv, double* lo, double* hi);
 
 // ---------------------------------------------------------------- kernels
 // geometry and assembly (wm_assembly.cu)

@@ -167,3 +167,54 @@ def test_host_queries_reject_bad_arguments(lib):
     assert lib.wm_geom_prolongation(g._h, 0, rp.ctypes.data, col.ctypes.data, val.ctypes.data,
                                     nnz - 1) == _capi.WM_ERR_INVALID_ARG
     assert lib.wm_geom_level_sizes(None, 0, None, None, None, None, None) == _capi.WM_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("lo,hi,n", [(1.0, 10.0, 4), (0.37, 37.0, 16), (2e-6, 0.3, 24), (1e-9, 0.33, 48),
+                                     (1.0, 1.0 + 1e-9, 3), (0.5, 2.0, 1)])
+def test_hht_rule_matches_oracle(lib, lo, hi, n):
+    # the library's elliptic functions (arithmetic-geometric mean scale) against
+    # scipy's through the oracle's rule; both reflect the nodes past K/2
+    import numpy as np
+    import paper_2605_24882_gb300 as wm
+    from oracle.sqrt_mass import hht_rule
+    w2, c = wm.hht_rule(lo, hi, n)
+    w2o, co = hht_rule(lo, hi, n)
+    np.testing.assert_allclose(w2, w2o, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(c, co, rtol=1e-12, atol=0)
+    lam = np.geomspace(lo, hi, 64)
+    s = lam * (c[None, :] / (lam[:, None] + w2[None, :])).sum(axis=1)
+    so = lam * (co[None, :] / (lam[:, None] + w2o[None, :])).sum(axis=1)
+    np.testing.assert_allclose(s, so, rtol=1e-13)
+
+
+def test_hht_rule_rejects_bad_arguments(lib):
+    import paper_2605_24882_gb300 as wm
+    from paper_2605_24882_gb300 import _capi
+    for args in [(0.0, 1.0, 4), (2.0, 1.0, 4), (1.0, 2.0, 0), (-1.0, 2.0, 4)]:
+        with pytest.raises(wm.WMError) as e:
+            wm.hht_rule(*args)
+        assert e.value.code == _capi.WM_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("kind,p,nu,nv", [("sphere", 1, 4, 4), ("sphere", 2, 8, 8), ("sphere", 3, 4, 4),
+                                           ("sphere", 2, 2, 2), ("torus", 3, 16, 8), ("torus", 2, 16, 16)])
+def test_mass_bounds_bracket_the_oracle_spectrum(lib, kind, p, nu, nv):
+    import numpy as np
+    import paper_2605_24882_gb300 as wm
+    from oracle import geometry as geo
+    from oracle.assembly import assemble
+    from oracle.space import GluedSpace
+    g = wm.Geometry(kind, p, nu, nv)
+    for level in range(2):
+        if kind == "torus" and (min(nu, nv) >> level) < 2 * p + 2:
+            break
+        sp_ = GluedSpace(geo.Surface(kind, p, nu >> level, None if kind == "sphere" else nv >> level))
+        _, M = assemble(sp_)
+        ev = np.linalg.eigvalsh(M.toarray())
+        lo, hi = g.mass_bounds(level)
+        assert 0.0 < lo <= ev[0] and ev[-1] <= hi, (level, lo, ev[0], ev[-1], hi)
+        # the bounds stay within small factors of the spectrum: the area element
+        # varies by 5.2 on the gnomonic sphere, 2.3 on this torus
+        assert ev[0] / lo < 40 and hi / ev[-1] < 20, (ev[0] / lo, hi / ev[-1])
+    with pytest.raises(wm.WMError):
+        g.mass_bounds(-1)
