@@ -248,6 +248,27 @@ int wm_noise_loads(wm_hier_t h, uint64_t seed, int n_samples, double* b, void* s
  */
 int wm_noise_loads_noalloc(wm_hier_t h, uint64_t seed, int n_samples, double* b, void* stream);
 
+/*
+ * White-noise loads by the matrix square root (Sec. 3.3, Eq. eq:sqrt):
+ * f_s = sqrt(M) y_s for samples s = 0..n_samples-1 on the finest level, with
+ * y_s[i] the Philox normal of index i (DOF) of sample s in stream 2 (counter
+ * layout of wm_normals), so Cov(f_s) = M up to the rule and solver errors.
+ * sqrt(M) y = M sum_k c_k (M + w_k^2 I)^{-1} y with the n_nodes-point rule of
+ * wm_hht_rule on [lo, hi], which must bracket the spectrum of M (e.g.
+ * wm_geom_mass_bounds of the same geometry).  The shifted systems of all nodes
+ * and samples are solved together by float64 conjugate gradients with Jacobi
+ * preconditioning until sqrt((r, D^{-1} r) / (r_0, D^{-1} r_0)) <= rtol, at
+ * most max_iter iterations.  f: device [n_samples][N] float64, caller-owned.
+ * iterations: host, may be NULL; receives the CG iterations of the slowest
+ * pass.  Device scratch is allocated per call (five float64 vectors per
+ * system, samples processed in passes that fit half the free memory) and the
+ * call returns after the stream has finished.
+ * Errors: WM_ERR_INVALID_ARG (sizes, bounds, host f), WM_ERR_OOM, WM_ERR_CUDA,
+ * WM_ERR_NONFINITE, WM_ERR_NOT_CONVERGED (f is still written).
+ */
+int wm_noise_loads_sqrt(wm_hier_t h, uint64_t seed, int n_samples, double lo, double hi, int n_nodes,
+                        double rtol, int max_iter, double* f, int* iterations, void* stream);
+
 /* ---- the sampler ------------------------------------------------------------ */
 typedef struct {
   double kappa;         /* kappa > 0                                                 */

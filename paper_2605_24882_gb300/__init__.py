@@ -217,6 +217,16 @@ class Hierarchy:
               "wm_noise_loads")
         return b
 
+    def noise_loads_sqrt(self, seed, n_samples, lo, hi, n_nodes, rtol=1e-12, max_iter=1000, stream=None):
+        """Loads f = sqrt(M) y [n_samples, N] (float64 CUDA tensor) by the n_nodes-point
+        Hale–Higham–Trefethen rule on [lo, hi]; returns (f, CG iterations)."""
+        f = torch.empty((n_samples, self.num_dofs(0)), dtype=torch.float64, device="cuda")
+        it = C.c_int()
+        check(lib().wm_noise_loads_sqrt(self._h, seed, n_samples, lo, hi, n_nodes, rtol, max_iter,
+                                        C.c_void_p(f.data_ptr()), C.byref(it), _stream(stream)),
+              "wm_noise_loads_sqrt")
+        return f, it.value
+
     @staticmethod
     def make_desc(kappa, beta, sinc_k=0.3, l_lo=-35, l_hi=35, n_samples=1, seed=0, split="standard",
                   precision="mixed", rtol=1e-8, max_iter=200, smoother_degree=4, cheb_ratio=12.0,

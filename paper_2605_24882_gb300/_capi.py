@@ -75,6 +75,7 @@ _PROTOS = {
     "wm_normals": (_i, [_u64, _i, _i, _i64, _i64, _vp, _vp]),
     "wm_noise_loads": (_i, [_vp, _u64, _i, _vp, _vp]),
     "wm_noise_loads_noalloc": (_i, [_vp, _u64, _i, _vp, _vp]),
+    "wm_noise_loads_sqrt": (_i, [_vp, _u64, _i, _d, _d, _i, _d, _i, _vp, C.POINTER(_i), _vp]),
     "wm_sample_fields": (_i, [_vp, C.POINTER(SampleDesc), _vp, _vp, C.POINTER(Stats), _vp]),
     "wm_sample_fields_batched": (_i, [_i, C.POINTER(_vp), C.POINTER(SampleDesc), C.POINTER(_vp),
                                       C.POINTER(Stats), _vp]),
