@@ -255,14 +255,15 @@ int wm_noise_loads_noalloc(wm_hier_t h, uint64_t seed, int n_samples, double* b,
  * layout of wm_normals), so Cov(f_s) = M up to the rule and solver errors.
  * sqrt(M) y = M sum_k c_k (M + w_k^2 I)^{-1} y with the n_nodes-point rule of
  * wm_hht_rule on [lo, hi], which must bracket the spectrum of M (e.g.
- * wm_geom_mass_bounds of the same geometry).  The shifted systems of all nodes
- * and samples are solved together by float64 conjugate gradients with Jacobi
- * preconditioning until sqrt((r, D^{-1} r) / (r_0, D^{-1} r_0)) <= rtol, at
+ * wm_geom_mass_bounds of the same geometry).  The n_nodes shifted systems of
+ * a sample share the Krylov space of (M, y_s) and are solved together by
+ * float64 multi-shift conjugate gradients (one mass apply per sample and
+ * iteration) until every shifted residual satisfies |r_k| <= rtol |y_s|, at
  * most max_iter iterations.  f: device [n_samples][N] float64, caller-owned.
  * iterations: host, may be NULL; receives the CG iterations of the slowest
- * pass.  Device scratch is allocated per call (five float64 vectors per
- * system, samples processed in passes that fit half the free memory) and the
- * call returns after the stream has finished.
+ * pass.  Device scratch is allocated per call (2 n_nodes + 7 float64 vectors
+ * per sample, samples processed in passes that fit half the free memory) and
+ * the call returns after the stream has finished.
  * Errors: WM_ERR_INVALID_ARG (sizes, bounds, host f), WM_ERR_OOM, WM_ERR_CUDA,
  * WM_ERR_NONFINITE, WM_ERR_NOT_CONVERGED (f is still written).
  */

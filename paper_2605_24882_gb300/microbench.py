@@ -10,6 +10,13 @@ geometrically over [25 + e^-10, 25 + e^10] (one shift per tile, as the
 sample-major packing of a sinc pass produces), and prints the mean time per
 V-cycle.  It is the driver for kernel profiles of the smoother, residual and
 transfer kernels.
+
+    python -m paper_2605_24882_gb300.microbench sqrt [--kind sphere] [--p 2]
+        [--elems 64] [--samples 64] [--nodes 12] [--rtol 1e-10] [--reps 2]
+
+`sqrt` draws `samples` loads f = sqrt(M) y with the `nodes`-point rule on the
+library's mass spectrum bounds `reps` times and prints the mean time per call
+and the CG iterations.
 """
 import argparse
 import json
@@ -39,9 +46,27 @@ def vcycle(args):
                       "max_abs_z": float(z.abs().max())}))
 
 
+def sqrt_noise(args):
+    g = wm.Geometry(args.kind, args.p, args.elems)
+    hier = wm.Hierarchy(g, 1)
+    lo, hi = g.mass_bounds(0)
+    f, it = hier.noise_loads_sqrt(1, args.samples, lo, hi, args.nodes, rtol=args.rtol)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for r in range(args.reps):
+        f, it = hier.noise_loads_sqrt(2 + r, args.samples, lo, hi, args.nodes, rtol=args.rtol)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"bench": "sqrt_noise", "dofs": hier.num_dofs(0), "samples": args.samples,
+                      "nodes": args.nodes, "systems": args.samples * args.nodes, "iterations": it,
+                      "ms_per_call": e0.elapsed_time(e1) / max(1, args.reps),
+                      "finite": bool(torch.isfinite(f).all())}))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["vcycle"])
+    ap.add_argument("what", choices=["vcycle", "sqrt"])
     ap.add_argument("--kind", default="sphere", choices=["sphere", "torus"])
     ap.add_argument("--p", type=int, default=2)
     ap.add_argument("--elems", type=int, default=64)
@@ -51,9 +76,14 @@ def main():
     ap.add_argument("--ratio", type=float, default=12.0)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--samples", type=int, default=64)
+    ap.add_argument("--nodes", type=int, default=12)
+    ap.add_argument("--rtol", type=float, default=1e-10)
     args = ap.parse_args()
     if args.what == "vcycle":
         vcycle(args)
+    else:
+        sqrt_noise(args)
 
 
 if __name__ == "__main__":
