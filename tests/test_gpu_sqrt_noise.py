@@ -90,3 +90,25 @@ def test_sqrt_noise_errors():
     with pytest.raises(wm.WMError) as e:
         hier.noise_loads_sqrt(1, 3, lo, hi, 8, rtol=1e-14, max_iter=1)
     assert e.value.code == wm._capi.WM_ERR_NOT_CONVERGED
+
+
+def test_fields_from_sqrt_noise_match_oracle():
+    # the paper's sampling chain with the square-root noise: f = sqrt(M) y
+    # (Eq. eq:sqrt), then u = L^{-beta} M^{-1} f; the library's loads enter its
+    # sampler as given loads, the oracle's loads enter the oracle's sampler
+    from oracle.fractional import sample_fields as oracle_fields
+    ns, n_nodes = 6, 32
+    sp_ = GluedSpace(geo.Surface("sphere", 2, 8))
+    S, M = assemble(sp_)
+    lo, hi = sq.mass_spectrum_bounds(sp_)
+    Y = np.stack([normals(13, s, np.arange(sp_.N), 2) for s in range(ns)])
+    f_or = sq.noise_loads_sqrt(M, lo, hi, n_nodes, Y)
+    u_or = oracle_fields(S, M, f_or, 2.0, 1.3, 0.4, -25, 25)
+    hier = wm.Hierarchy(wm.Geometry("sphere", 2, 8), 3)
+    f, _ = hier.noise_loads_sqrt(13, ns, lo, hi, n_nodes, rtol=1e-12)
+    u, st = hier.sample_fields(b=f, kappa=2.0, beta=1.3, sinc_k=0.4, l_lo=-25, l_hi=25, n_samples=ns,
+                               precision="mixed", rtol=1e-10)
+    torch.cuda.synchronize()
+    d = u.cpu().numpy() - u_or
+    err = np.sqrt(np.einsum("si,si->s", d, (M @ d.T).T) / np.einsum("si,si->s", u_or, (M @ u_or.T).T))
+    assert err.max() < 1e-6, (err, st)
