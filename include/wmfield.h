@@ -51,6 +51,8 @@ extern "C" {
 /* ---- enumerations --------------------------------------------------------- */
 #define WM_SPHERE6 0      /* unit sphere as six gnomonic cube-face patches     */
 #define WM_TORUS 1        /* one doubly periodic torus patch (R, r)            */
+#define WM_NURBS_PERIODIC 2 /* one NURBS patch, periodic in u and v (torus topology)  */
+#define WM_NURBS_CUBE 3     /* six NURBS patches in the cube-face arrangement          */
 
 #define WM_FP64 0         /* every step in float64                              */
 #define WM_MIXED 1        /* float64 outer CG, float32 multigrid preconditioner */
@@ -77,6 +79,20 @@ typedef struct wm_geom* wm_geom_t;
 typedef struct wm_hier* wm_hier_t;
 
 /*
+ * One NURBS patch of a geometry map (Sec. 2.2): F(u, v) on [0, 1]^2 is
+ * sum_ij N_i(u) M_j(v) w_ij P_ij / sum_ij N_i(u) M_j(v) w_ij with the B-splines
+ * N_i, M_j of Definition 2.1 on the knot vectors.  Host memory, read during
+ * wm_setup_geometry_nurbs and copied; the caller keeps ownership.
+ */
+typedef struct {
+  int degree_u, degree_v;  /* 1 .. 8                                                */
+  int n_u, n_v;            /* control points per direction (>= degree + 1)          */
+  const double* knots_u;   /* n_u + degree_u + 1 knots, nondecreasing, the first    */
+  const double* knots_v;   /*   degree+1 equal to 0 and the last degree+1 equal to 1 */
+  const double* cpw;       /* [n_v][n_u][4]: x, y, z and weight (> 0)               */
+} wm_nurbs_patch;
+
+/*
  * Validates a surface description and builds its patch table and the C0
  * gluing of the spline space S^0_{j,p} (Eq. def::space2) by combinatorial
  * matching of patch edges.  Host only.  Global DOF numbering: patches in
@@ -85,6 +101,35 @@ typedef struct wm_hier* wm_hier_t;
  * Errors: WM_ERR_INVALID_ARG for a bad kind/degree/size or NULL out.
  */
 int wm_setup_geometry(const wm_geom_desc* desc, wm_geom_t* out);
+
+/*
+ * A surface given by NURBS patches (Sec. 2.2, multi-patch NURBS
+ * parametrisations).  desc->kind is WM_NURBS_PERIODIC (n_patches = 1; the
+ * solution space is the torus's periodic spline space, so F must be periodic
+ * in u and v) or WM_NURBS_CUBE (n_patches = 6, glued like WM_SPHERE6: patch m
+ * covers the cube face whose coordinate a is 2u-1, b is 2v-1 and n is s, with
+ * (a, b, n, s) = (1,2,0,+), (2,1,0,-), (2,0,1,+), (0,2,1,-), (0,1,2,+), (1,0,2,-)
+ * for m = 0..5, and neighbouring patches must agree along their shared edges,
+ * parameter for parameter).  degree, elems_u, elems_v as for wm_setup_geometry;
+ * R and r are ignored.  The closure (periodic) or the edge agreement (cube) is
+ * checked at sample points to 1e-10 of the surface's size.  The geometry map
+ * is evaluated on the host at every Gauss point when a hierarchy is assembled;
+ * element boundaries should fall on the knots of the patches for full
+ * quadrature accuracy.
+ * Errors: WM_ERR_INVALID_ARG (kind, sizes, knots, weights, closure), WM_ERR_OOM.
+ */
+int wm_setup_geometry_nurbs(const wm_geom_desc* desc, const wm_nurbs_patch* patches, int n_patches,
+                            wm_geom_t* out);
+
+/*
+ * Host-only: the metric terms (a, G11, G12, G22) with G = a K^{-1} (Sec. 3.2)
+ * of a NURBS geometry at the Gauss points of a level, float64 [n_quad][4] in
+ * host memory (Gauss point order as wm_metric), exactly as the hierarchy
+ * uploads them.  `cap` is the capacity of `out` in doubles.
+ * Errors: WM_ERR_UNSUPPORTED for the analytic kinds (their metric is computed
+ * on the GPU, see wm_metric), WM_ERR_INVALID_ARG.
+ */
+int wm_geom_metric(wm_geom_t g, int level, double* out, int64_t cap);
 
 /*
  * Host-only queries of the discrete space of a geometry; no CUDA device is

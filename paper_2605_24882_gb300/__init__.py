@@ -39,7 +39,8 @@ def _dev_f64(t, name):
 
 
 class Geometry:
-    """Surface description: 'sphere' (six cube-face patches) or 'torus' (periodic)."""
+    """Surface description: 'sphere' (six cube-face patches) or 'torus' (periodic);
+    `Geometry.nurbs` builds one from NURBS patches."""
 
     def __init__(self, kind, degree, elems, elems_v=None, R=1.0, r=0.4):
         d = _capi.GeomDesc(kind=_capi.WM_SPHERE6 if kind == "sphere" else _capi.WM_TORUS, degree=degree,
@@ -48,6 +49,42 @@ class Geometry:
         check(lib().wm_setup_geometry(C.byref(d), C.byref(h)), "wm_setup_geometry")
         self._h = h
         self.desc = d
+
+    @classmethod
+    def nurbs(cls, topology, patches, degree, elems, elems_v=None):
+        """Surface from NURBS patches: topology 'periodic' (one patch) or 'cube' (six,
+        in the cube-face arrangement); each patch a dict with degree_u, degree_v,
+        knots_u, knots_v and cpw [n_v, n_u, 4] (x, y, z, weight)."""
+        kind = _capi.WM_NURBS_PERIODIC if topology == "periodic" else _capi.WM_NURBS_CUBE
+        d = _capi.GeomDesc(kind=kind, degree=degree, elems_u=elems, elems_v=elems if elems_v is None else elems_v,
+                           R=0.0, r=0.0)
+        keep = []
+        arr = (_capi.NurbsPatch * len(patches))()
+        for i, q in enumerate(patches):
+            ku = np.ascontiguousarray(q["knots_u"], dtype=np.float64)
+            kv = np.ascontiguousarray(q["knots_v"], dtype=np.float64)
+            cpw = np.ascontiguousarray(q["cpw"], dtype=np.float64)
+            if cpw.ndim != 3 or cpw.shape[2] != 4:
+                raise ValueError("cpw must be [n_v, n_u, 4]")
+            keep += [ku, kv, cpw]
+            arr[i] = _capi.NurbsPatch(degree_u=q["degree_u"], degree_v=q["degree_v"], n_u=cpw.shape[1],
+                                      n_v=cpw.shape[0], knots_u=ku.ctypes.data, knots_v=kv.ctypes.data,
+                                      cpw=cpw.ctypes.data)
+        self = cls.__new__(cls)
+        h = C.c_void_p()
+        check(lib().wm_setup_geometry_nurbs(C.byref(d), arr, len(patches), C.byref(h)), "wm_setup_geometry_nurbs")
+        self._h = h
+        self.desc = d
+        return self
+
+    def metric_host(self, level=0):
+        """Host-only (NURBS kinds): metric terms [n_quad, 4] = (a, G11, G12, G22) at the level's Gauss points."""
+        n_p = 6 if self.desc.kind in (_capi.WM_SPHERE6, _capi.WM_NURBS_CUBE) else 1
+        nq = self.desc.degree + 1
+        n_quad = n_p * (self.desc.elems_u >> level) * (self.desc.elems_v >> level) * nq * nq
+        out = np.empty((n_quad, 4), dtype=np.float64)
+        check(lib().wm_geom_metric(self._h, level, out.ctypes.data, out.size), "wm_geom_metric")
+        return out
 
     def level_sizes(self, level=0, prolongation=True):
         """Host-only: (N, n_loc_u, n_loc_v, elements, prolongation entries) of a level;
@@ -61,7 +98,7 @@ class Geometry:
         """Host-only: local-to-global map [patches, n_loc_v, n_loc_u] and element
         connectivity [elements, (p+1)^2] of a level (int32 numpy arrays)."""
         _, lu, lv, ne, _ = self.level_sizes(level, prolongation=False)
-        n_p = 6 if self.desc.kind == _capi.WM_SPHERE6 else 1
+        n_p = 6 if self.desc.kind in (_capi.WM_SPHERE6, _capi.WM_NURBS_CUBE) else 1
         l2g = np.empty((n_p, lv, lu), dtype=np.int32)
         conn = np.empty((ne, (self.desc.degree + 1) ** 2), dtype=np.int32)
         check(lib().wm_geom_dof_map(self._h, level, l2g.ctypes.data, l2g.size, conn.ctypes.data, conn.size),
@@ -157,11 +194,10 @@ class Hierarchy:
         return check(lib().wm_num_quad_points(self._h, level), "wm_num_quad_points")
 
     def dof_map(self, level=0):
-        import numpy as np
         g = self.geometry.desc
         p = g.degree
         n = (g.elems_u >> level), (g.elems_v >> level)
-        if g.kind == _capi.WM_TORUS:
+        if g.kind in (_capi.WM_TORUS, _capi.WM_NURBS_PERIODIC):
             shape = (1, n[1], n[0])
         else:
             shape = (6, n[1] + p, n[0] + p)

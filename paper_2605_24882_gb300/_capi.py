@@ -15,6 +15,8 @@ WM_ERR_UNSUPPORTED = -7
 
 WM_SPHERE6 = 0
 WM_TORUS = 1
+WM_NURBS_PERIODIC = 2
+WM_NURBS_CUBE = 3
 WM_FP64 = 0
 WM_MIXED = 1
 WM_SPLIT_STANDARD = 0
@@ -26,6 +28,11 @@ WM_NOISE_GIVEN = 1
 class GeomDesc(C.Structure):
     _fields_ = [("kind", C.c_int), ("degree", C.c_int), ("elems_u", C.c_int), ("elems_v", C.c_int),
                 ("R", C.c_double), ("r", C.c_double)]
+
+
+class NurbsPatch(C.Structure):
+    _fields_ = [("degree_u", C.c_int), ("degree_v", C.c_int), ("n_u", C.c_int), ("n_v", C.c_int),
+                ("knots_u", C.c_void_p), ("knots_v", C.c_void_p), ("cpw", C.c_void_p)]
 
 
 class SampleDesc(C.Structure):
@@ -54,6 +61,8 @@ _u64 = C.c_uint64
 
 _PROTOS = {
     "wm_setup_geometry": (_i, [C.POINTER(GeomDesc), C.POINTER(_vp)]),
+    "wm_setup_geometry_nurbs": (_i, [C.POINTER(GeomDesc), C.POINTER(NurbsPatch), _i, C.POINTER(_vp)]),
+    "wm_geom_metric": (_i, [_vp, _i, _vp, _i64]),
     "wm_assemble_hierarchy": (_i, [_vp, _i, _vp, C.POINTER(_vp)]),
     "wm_num_levels": (_i, [_vp]),
     "wm_num_dofs": (_i, [_vp, _i]),

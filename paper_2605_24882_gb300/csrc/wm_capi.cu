@@ -109,6 +109,62 @@ extern "C" int wm_setup_geometry(const wm_geom_desc* d, wm_geom_t* out) {
   return WM_OK;
 }
 
+extern "C" int wm_setup_geometry_nurbs(const wm_geom_desc* d, const wm_nurbs_patch* patches, int n_patches,
+                                       wm_geom_t* out) {
+  if (!d || !out || !patches) return WM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!wm_is_nurbs(d->kind)) {
+    wm_set_error("kind %d is not a NURBS kind", d->kind);
+    return WM_ERR_INVALID_ARG;
+  }
+  const bool periodic = wm_periodic(d->kind);
+  if (n_patches != (periodic ? 1 : 6)) {
+    wm_set_error("%s takes %d patches", periodic ? "WM_NURBS_PERIODIC" : "WM_NURBS_CUBE", periodic ? 1 : 6);
+    return WM_ERR_INVALID_ARG;
+  }
+  if (d->degree < 1 || d->degree > 4) {
+    wm_set_error("degree %d outside 1..4", d->degree);
+    return WM_ERR_INVALID_ARG;
+  }
+  if (d->elems_u < 1 || d->elems_v < 1 || (d->elems_u & (d->elems_u - 1)) || (d->elems_v & (d->elems_v - 1))) {
+    wm_set_error("element counts must be powers of two");
+    return WM_ERR_INVALID_ARG;
+  }
+  if (!periodic && d->elems_u != d->elems_v) {
+    wm_set_error("cube-arranged patches are square");
+    return WM_ERR_INVALID_ARG;
+  }
+  if (periodic && (d->elems_u < 2 * d->degree + 2 || d->elems_v < 2 * d->degree + 2)) {
+    wm_set_error("periodic patch needs at least 2p+2 elements per direction");
+    return WM_ERR_INVALID_ARG;
+  }
+  std::vector<WmNurbs> copy(n_patches);
+  for (int m = 0; m < n_patches; ++m) {
+    const wm_nurbs_patch& q = patches[m];
+    if (q.degree_u < 1 || q.degree_u > 8 || q.degree_v < 1 || q.degree_v > 8 || q.n_u < q.degree_u + 1 ||
+        q.n_v < q.degree_v + 1 || !q.knots_u || !q.knots_v || !q.cpw) {
+      wm_set_error("patch %d: degrees 1..8, n >= degree + 1 and all arrays given", m);
+      return WM_ERR_INVALID_ARG;
+    }
+    WmNurbs& c = copy[m];
+    c.pu = q.degree_u;
+    c.pv = q.degree_v;
+    c.nu = q.n_u;
+    c.nv = q.n_v;
+    c.ku.assign(q.knots_u, q.knots_u + q.n_u + q.degree_u + 1);
+    c.kv.assign(q.knots_v, q.knots_v + q.n_v + q.degree_v + 1);
+    c.cpw.assign(q.cpw, q.cpw + (size_t)q.n_u * q.n_v * 4);
+  }
+  WM_TRY(wm_host_nurbs_check(d->kind, copy));
+  wm_geom* g = new (std::nothrow) wm_geom;
+  if (!g) return WM_ERR_OOM;
+  g->d = *d;
+  g->np = n_patches;
+  g->nurbs.swap(copy);
+  *out = g;
+  return WM_OK;
+}
+
 extern "C" void wm_destroy_geom(wm_geom_t g) { delete g; }
 
 static void release_level(wm_level& L) {
@@ -168,7 +224,15 @@ static int assemble(wm_hier* h, int n_levels, cudaStream_t s) {
     WM_TRY(L.d_dM64.alloc(L.N));
     WM_TRY(L.d_dS32.alloc(L.N));
     WM_TRY(L.d_dM32.alloc(L.N));
-    WM_TRY(wm_k_metric(h, L, s));
+    if (wm_is_nurbs(g.kind)) {
+      // NURBS maps are evaluated on the host (wm_host_nurbs_metric) and uploaded
+      std::vector<double> met;
+      WM_TRY(wm_host_nurbs_metric(h->nurbs, nu, nv, h->gx, met));
+      WM_CUDA(cudaMemcpyAsync(L.d_metric.p, met.data(), met.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      WM_CUDA(cudaStreamSynchronize(s));
+    } else {
+      WM_TRY(wm_k_metric(h, L, s));
+    }
     WM_TRY(wm_k_element_matrices(h, L, s));
     WM_TRY(wm_k_assemble_rows(h, L, s));
     WM_TRY(wm_k_pack_rows(L, s));
@@ -232,7 +296,7 @@ static int assemble(wm_hier* h, int n_levels, cudaStream_t s) {
 // patch side (cube sphere) or to 2p+2 elements per side (periodic torus).
 static int max_levels(const wm_geom_desc& g) {
   int minside = std::min(g.elems_u, g.elems_v);
-  int lowest = g.kind == WM_TORUS ? 2 * g.degree + 2 : 1;
+  int lowest = wm_periodic(g.kind) ? 2 * g.degree + 2 : 1;
   int maxlev = 0;
   while ((minside >> maxlev) >= lowest) ++maxlev;
   return maxlev;
@@ -250,6 +314,7 @@ extern "C" int wm_assemble_hierarchy(wm_geom_t geom, int n_levels, void* stream,
   wm_hier* h = new (std::nothrow) wm_hier;
   if (!h) return WM_ERR_OOM;
   h->g = g;
+  h->nurbs = geom->nurbs;
   h->np = geom->np;
   h->p = g.degree;
   h->nq = g.degree + 1;
@@ -344,10 +409,41 @@ extern "C" int wm_geom_dof_map(wm_geom_t g, int level, int32_t* l2g, int64_t l2g
   return WM_OK;
 }
 
+static int geom_nurbs_metric(wm_geom_t g, int level, std::vector<double>& met) {
+  std::vector<double> gx, gw;
+  wm_gauss_legendre01(g->d.degree + 1, gx, gw);
+  return wm_host_nurbs_metric(g->nurbs, g->d.elems_u >> level, g->d.elems_v >> level, gx, met);
+}
+
 extern "C" int wm_geom_mass_bounds(wm_geom_t g, int level, double* lo, double* hi) {
   WM_TRY(check_geom_level(g, level, 0));
   if (!lo || !hi) return WM_ERR_INVALID_ARG;
-  return wm_host_mass_bounds(g->d, g->d.elems_u >> level, g->d.elems_v >> level, lo, hi);
+  const int nu = g->d.elems_u >> level, nv = g->d.elems_v >> level;
+  if (!wm_is_nurbs(g->d.kind)) return wm_host_mass_bounds(g->d, nu, nv, lo, hi);
+  std::vector<double> met;
+  WM_TRY(geom_nurbs_metric(g, level, met));
+  double amin = met[0], amax = met[0];
+  for (size_t q = 0; q < met.size(); q += 4) {
+    amin = std::min(amin, met[q]);
+    amax = std::max(amax, met[q]);
+  }
+  return wm_host_mass_bounds_metric(g->d, nu, nv, amin, amax, lo, hi);
+}
+
+extern "C" int wm_geom_metric(wm_geom_t g, int level, double* out, int64_t cap) {
+  WM_TRY(check_geom_level(g, level, 0));
+  if (!wm_is_nurbs(g->d.kind)) {
+    wm_set_error("the metric of the analytic kinds is computed on the GPU (wm_metric)");
+    return WM_ERR_UNSUPPORTED;
+  }
+  std::vector<double> met;
+  WM_TRY(geom_nurbs_metric(g, level, met));
+  if (!out || cap < (int64_t)met.size()) {
+    wm_set_error("output buffer too small");
+    return WM_ERR_INVALID_ARG;
+  }
+  std::memcpy(out, met.data(), met.size() * sizeof(double));
+  return WM_OK;
 }
 
 extern "C" int wm_geom_prolongation(wm_geom_t g, int level, int32_t* row_ptr, int32_t* col, double* val,

@@ -147,7 +147,7 @@ static void cardinal_eval(int p, double t, double* val, double* der) {
 
 void wm_host_tables(const wm_geom_desc& g, const std::vector<double>& gx, wm_level& L) {
   int p = g.degree, nq = (int)gx.size();
-  bool periodic = g.kind == WM_TORUS;
+  bool periodic = wm_periodic(g.kind);
   auto fill = [&](int n, std::vector<double>& b, std::vector<double>& d) {
     b.assign((size_t)n * (p + 1) * nq, 0.0);
     d.assign((size_t)n * (p + 1) * nq, 0.0);
@@ -187,7 +187,7 @@ int wm_host_build_level(const wm_geom_desc& g, int np, int nu, int nv, wm_level&
   L.nv = nv;
   L.nk = (p + 1) * (p + 1);
   L.E = np * nu * nv;
-  if (g.kind == WM_TORUS) {
+  if (wm_periodic(g.kind)) {
     L.nlu = nu;
     L.nlv = nv;
     L.N = nu * nv;
@@ -239,7 +239,7 @@ int wm_host_build_level(const wm_geom_desc& g, int np, int nu, int nv, wm_level&
         for (int kv = 0; kv <= p; ++kv)
           for (int ku = 0; ku <= p; ++ku) {
             int iu, iv;
-            if (g.kind == WM_TORUS) {
+            if (wm_periodic(g.kind)) {
               iu = ((eu - p + ku) % nu + nu) % nu;
               iv = ((ev - p + kv) % nv + nv) % nv;
             } else {
@@ -358,7 +358,7 @@ int wm_host_prolongation(const wm_geom_desc& g, int np, const wm_level& F, const
                          std::vector<int32_t>& Pptr, std::vector<int32_t>& Pcol, std::vector<double>& Pval,
                          std::vector<int32_t>& Rptr, std::vector<int32_t>& Rcol, std::vector<double>& Rval) {
   int p = g.degree;
-  bool periodic = g.kind == WM_TORUS;
+  bool periodic = wm_periodic(g.kind);
   std::vector<double> Pu, Pv;
   int nfu, ncu, nfv, ncv;
   refine_1d(C.nu, p, periodic, Pu, nfu, ncu);
@@ -514,7 +514,7 @@ extern "C" int wm_hht_rule(double lo, double hi, int n_nodes, double* w2, double
 static void mass_1d_extremes(const wm_geom_desc& g, int n, const std::vector<double>& gx,
                              const std::vector<double>& gw, double* lmin, double* lmax) {
   int p = g.degree, nq = (int)gx.size();
-  bool periodic = g.kind == WM_TORUS;
+  bool periodic = wm_periodic(g.kind);
   int nd = periodic ? n : n + p;
   // band storage: B[i][d] = A[i][i+d], d = 0..p (periodic: offsets mod n, c_d)
   std::vector<double> B((size_t)nd * (p + 1), 0.0);
@@ -587,31 +587,233 @@ static void mass_1d_extremes(const wm_geom_desc& g, int n, const std::vector<dou
 // between a_min and a_max times the flat form x^T (M_u (x) M_v) x, which the
 // p+1 point rule integrates exactly; the patches' DOF vectors x_m satisfy
 // |x|^2 <= sum_m |x_m|^2 <= mult |x|^2 (mult = 3 on the cube sphere, whose corner
-// DOFs lie on three patches).  Area elements: gnomonic 4 (1 + a^2 + b^2)^{-3/2},
-// a, b in [-1, 1], so a in [4 / 3^{3/2}, 4]; torus 4 pi^2 r (R + r cos 2 pi v).
-int wm_host_mass_bounds(const wm_geom_desc& g, int nu, int nv, double* lo, double* hi) {
+// DOFs lie on three patches).  amin, amax bound the area element at the Gauss
+// points (NURBS kinds: their extremes there).
+int wm_host_mass_bounds_metric(const wm_geom_desc& g, int nu, int nv, double amin, double amax, double* lo,
+                               double* hi) {
   std::vector<double> gx, gw;
   wm_gauss_legendre01(g.degree + 1, gx, gw);
   double umin, umax, vmin, vmax;
   mass_1d_extremes(g, nu, gx, gw, &umin, &umax);
   mass_1d_extremes(g, nv, gx, gw, &vmin, &vmax);
-  double amin, amax, mult;
-  if (g.kind == WM_TORUS) {
-    amin = 4.0 * M_PI * M_PI * g.r * (g.R - g.r);
-    amax = 4.0 * M_PI * M_PI * g.r * (g.R + g.r);
-    mult = 1.0;
-  } else {
-    amin = 4.0 / (3.0 * std::sqrt(3.0));
-    amax = 4.0;
-    mult = 3.0;
-  }
-  if (!(umin > 0.0 && vmin > 0.0)) {
-    wm_set_error("1D mass matrix not positive definite");
+  const double mult = wm_periodic(g.kind) ? 1.0 : 3.0;
+  if (!(umin > 0.0 && vmin > 0.0 && amin > 0.0)) {
+    wm_set_error("mass bounds need positive 1D spectra and area elements");
     return WM_ERR_INVALID_ARG;
   }
   // relative margins cover the rounding of the bisection and of the area elements
   *lo = amin * umin * vmin * (1.0 - 1e-9);
   *hi = mult * amax * umax * vmax * (1.0 + 1e-9);
+  return WM_OK;
+}
+
+// Analytic kinds, area elements in closed form: gnomonic 4 (1 + a^2 + b^2)^{-3/2},
+// a, b in [-1, 1], so a in [4 / 3^{3/2}, 4]; torus 4 pi^2 r (R + r cos 2 pi v).
+int wm_host_mass_bounds(const wm_geom_desc& g, int nu, int nv, double* lo, double* hi) {
+  double amin, amax;
+  if (g.kind == WM_TORUS) {
+    amin = 4.0 * M_PI * M_PI * g.r * (g.R - g.r);
+    amax = 4.0 * M_PI * M_PI * g.r * (g.R + g.r);
+  } else {
+    amin = 4.0 / (3.0 * std::sqrt(3.0));
+    amax = 4.0;
+  }
+  return wm_host_mass_bounds_metric(g, nu, nv, amin, amax, lo, hi);
+}
+
+// ------------------------------------------------------------ NURBS geometry
+// Span s of x in a clamped knot vector of n basis functions of degree p:
+// knots[s] <= x < knots[s+1], s in [p, n-1]; x at the right end takes the last
+// non-empty span.
+static int nurbs_span(const std::vector<double>& kn, int p, int n, double x) {
+  if (x >= kn[n]) {
+    int s = n - 1;
+    while (s > p && !(kn[s] < kn[s + 1])) --s;
+    return s;
+  }
+  int lo = p, hi = n;  // kn[lo] <= x < kn[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) / 2;
+    if (x < kn[mid]) hi = mid; else lo = mid;
+  }
+  return lo;
+}
+
+// Values N[a] and derivatives dN[a] of the p+1 B-splines s-p+a (a = 0..p) that
+// are non-zero on span s, by the Cox–de Boor recursion (Definition 2.1); the
+// derivative from the degree p-1 functions.
+static void nurbs_basis(const std::vector<double>& kn, int p, int s, double x, double* N, double* dN) {
+  double tri[9][9];
+  tri[0][0] = 1.0;
+  for (int d = 1; d <= p; ++d)
+    for (int j = 0; j <= d; ++j) {
+      int i = s - d + j;
+      double v = 0.0;
+      if (j >= 1) {
+        double den = kn[i + d] - kn[i];
+        if (den > 0) v += (x - kn[i]) / den * tri[d - 1][j - 1];
+      }
+      if (j <= d - 1) {
+        double den = kn[i + d + 1] - kn[i + 1];
+        if (den > 0) v += (kn[i + d + 1] - x) / den * tri[d - 1][j];
+      }
+      tri[d][j] = v;
+    }
+  for (int a = 0; a <= p; ++a) {
+    N[a] = tri[p][a];
+    int i = s - p + a;
+    double v = 0.0;
+    if (p > 0) {
+      if (a >= 1) {
+        double den = kn[i + p] - kn[i];
+        if (den > 0) v += p / den * tri[p - 1][a - 1];
+      }
+      if (a <= p - 1) {
+        double den = kn[i + p + 1] - kn[i + 1];
+        if (den > 0) v -= p / den * tri[p - 1][a];
+      }
+    }
+    dN[a] = v;
+  }
+}
+
+// F, d_u F, d_v F of a patch: F = A / W with A = sum N_i M_j w_ij P_ij and
+// W = sum N_i M_j w_ij; d F = (d A - F d W) / W.
+static void nurbs_eval(const WmNurbs& P, double u, double v, double F[3], double Fu[3], double Fv[3]) {
+  double Nu[9], dNu[9], Nv[9], dNv[9];
+  int su = nurbs_span(P.ku, P.pu, P.nu, u), sv = nurbs_span(P.kv, P.pv, P.nv, v);
+  nurbs_basis(P.ku, P.pu, su, u, Nu, dNu);
+  nurbs_basis(P.kv, P.pv, sv, v, Nv, dNv);
+  double A[3] = {0, 0, 0}, Au[3] = {0, 0, 0}, Av[3] = {0, 0, 0}, W = 0, Wu = 0, Wv = 0;
+  for (int b = 0; b <= P.pv; ++b)
+    for (int a = 0; a <= P.pu; ++a) {
+      const double* c = &P.cpw[((size_t)(sv - P.pv + b) * P.nu + (su - P.pu + a)) * 4];
+      double w = c[3];
+      double f = Nu[a] * Nv[b] * w, fu = dNu[a] * Nv[b] * w, fv = Nu[a] * dNv[b] * w;
+      for (int k = 0; k < 3; ++k) {
+        A[k] += f * c[k];
+        Au[k] += fu * c[k];
+        Av[k] += fv * c[k];
+      }
+      W += f;
+      Wu += fu;
+      Wv += fv;
+    }
+  for (int k = 0; k < 3; ++k) {
+    F[k] = A[k] / W;
+    Fu[k] = (Au[k] - F[k] * Wu) / W;
+    Fv[k] = (Av[k] - F[k] * Wv) / W;
+  }
+}
+
+int wm_host_nurbs_metric(const std::vector<WmNurbs>& patches, int nu, int nv, const std::vector<double>& gx,
+                         std::vector<double>& out) {
+  const int nq = (int)gx.size(), np = (int)patches.size();
+  out.assign((size_t)np * nu * nv * nq * nq * 4, 0.0);
+  for (int m = 0; m < np; ++m)
+    for (int ev = 0; ev < nv; ++ev)
+      for (int eu = 0; eu < nu; ++eu)
+        for (int gv = 0; gv < nq; ++gv)
+          for (int gu = 0; gu < nq; ++gu) {
+            double F[3], Fu[3], Fv[3];
+            nurbs_eval(patches[m], (eu + gx[gu]) / nu, (ev + gx[gv]) / nv, F, Fu, Fv);
+            double K11 = Fu[0] * Fu[0] + Fu[1] * Fu[1] + Fu[2] * Fu[2];
+            double K12 = Fu[0] * Fv[0] + Fu[1] * Fv[1] + Fu[2] * Fv[2];
+            double K22 = Fv[0] * Fv[0] + Fv[1] * Fv[1] + Fv[2] * Fv[2];
+            double det = K11 * K22 - K12 * K12;
+            if (!(det > 0.0) || !std::isfinite(det)) {
+              wm_set_error("degenerate NURBS map on patch %d element (%d, %d)", m, eu, ev);
+              return WM_ERR_INVALID_ARG;
+            }
+            double a = std::sqrt(det);
+            double* o = &out[((((size_t)m * nv + ev) * nu + eu) * nq * nq + gv * nq + gu) * 4];
+            o[0] = a;
+            o[1] = K22 / a;
+            o[2] = -K12 / a;
+            o[3] = K11 / a;
+          }
+  return WM_OK;
+}
+
+// Knots clamped to [0, 1] and nondecreasing, weights positive, coordinates
+// finite; then the closure of a periodic patch (F(0, t) = F(1, t), F(t, 0) =
+// F(t, 1)) or, for six cube-arranged patches, the agreement of every patch
+// edge with its neighbour at the same cube point, at 33 points per edge, to
+// 1e-10 of the largest control point coordinate.
+int wm_host_nurbs_check(int kind, const std::vector<WmNurbs>& P) {
+  double scale = 0.0;
+  for (size_t m = 0; m < P.size(); ++m) {
+    const WmNurbs& q = P[m];
+    for (int dir = 0; dir < 2; ++dir) {
+      const std::vector<double>& kn = dir ? q.kv : q.ku;
+      int p = dir ? q.pv : q.pu, n = dir ? q.nv : q.nu;
+      if (p < 1 || p > 8 || n < p + 1 || (int)kn.size() != n + p + 1) {
+        wm_set_error("patch %zu: degree 1..8 and n >= degree + 1 control points per direction", m);
+        return WM_ERR_INVALID_ARG;
+      }
+      for (int i = 0; i + 1 < (int)kn.size(); ++i)
+        if (!(kn[i] <= kn[i + 1])) {
+          wm_set_error("patch %zu: knots must be nondecreasing", m);
+          return WM_ERR_INVALID_ARG;
+        }
+      for (int i = 0; i <= p; ++i)
+        if (kn[i] != 0.0 || kn[n + i] != 1.0) {
+          wm_set_error("patch %zu: knot vectors must be clamped to [0, 1]", m);
+          return WM_ERR_INVALID_ARG;
+        }
+    }
+    for (size_t i = 0; i < q.cpw.size(); ++i) {
+      if (!std::isfinite(q.cpw[i]) || (i % 4 == 3 && !(q.cpw[i] > 0.0))) {
+        wm_set_error("patch %zu: control points must be finite and weights positive", m);
+        return WM_ERR_INVALID_ARG;
+      }
+      if (i % 4 != 3) scale = std::max(scale, std::fabs(q.cpw[i]));
+    }
+  }
+  const double tol = 1e-10 * std::max(scale, 1e-300);
+  auto dist = [](const double* a, const double* b) {
+    return std::sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) + (a[2] - b[2]) * (a[2] - b[2]));
+  };
+  const int ns = 33;
+  double F0[3], F1[3], du[3], dv[3];
+  if (kind == WM_NURBS_PERIODIC) {
+    for (int i = 0; i < ns; ++i) {
+      double t = (double)i / (ns - 1);
+      nurbs_eval(P[0], 0.0, t, F0, du, dv);
+      nurbs_eval(P[0], 1.0, t, F1, du, dv);
+      bool ok = dist(F0, F1) <= tol;
+      nurbs_eval(P[0], t, 0.0, F0, du, dv);
+      nurbs_eval(P[0], t, 1.0, F1, du, dv);
+      if (!ok || dist(F0, F1) > tol) {
+        wm_set_error("periodic NURBS patch is not closed (at t = %g)", t);
+        return WM_ERR_INVALID_ARG;
+      }
+    }
+    return WM_OK;
+  }
+  // cube arrangement: a boundary point of patch m sits at the cube point c with
+  // c[a] = 2u-1, c[b] = 2v-1, c[n] = s; every other patch m' with c[n'] = s' holds
+  // the same point at u' = (c[a'] + 1)/2, v' = (c[b'] + 1)/2
+  for (int m = 0; m < 6; ++m)
+    for (int e = 0; e < 4; ++e)
+      for (int i = 0; i < ns; ++i) {
+        double t = (double)i / (ns - 1);
+        double u = e == 0 ? t : e == 1 ? t : e == 2 ? 0.0 : 1.0;
+        double v = e == 0 ? 0.0 : e == 1 ? 1.0 : t;
+        double c[3];
+        c[kFace[m][0]] = 2.0 * u - 1.0;
+        c[kFace[m][1]] = 2.0 * v - 1.0;
+        c[kFace[m][2]] = kFace[m][3];
+        nurbs_eval(P[m], u, v, F0, du, dv);
+        for (int m2 = 0; m2 < 6; ++m2) {
+          if (m2 == m || c[kFace[m2][2]] != (double)kFace[m2][3]) continue;
+          nurbs_eval(P[m2], 0.5 * (c[kFace[m2][0]] + 1.0), 0.5 * (c[kFace[m2][1]] + 1.0), F1, du, dv);
+          if (dist(F0, F1) > tol) {
+            wm_set_error("NURBS patches %d and %d disagree on their shared edge (t = %g)", m, m2, t);
+            return WM_ERR_INVALID_ARG;
+          }
+        }
+      }
   return WM_OK;
 }
 
@@ -687,7 +889,7 @@ int wm_host_stencil(const wm_geom_desc& g, int np, const wm_level& L, std::vecto
   const int SW = 2 * p + 1;
   ext.assign((size_t)np * ELV * ELU, -1);
   own.assign((size_t)np * nlv * nlu, -1);
-  if (g.kind == WM_TORUS) {
+  if (wm_periodic(g.kind)) {
     for (int ev = 0; ev < ELV; ++ev)
       for (int eu = 0; eu < ELU; ++eu) {
         int iu = ((eu - p) % nlu + nlu) % nlu, iv = ((ev - p) % nlv + nlv) % nlv;

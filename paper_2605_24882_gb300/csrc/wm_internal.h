@@ -84,9 +84,20 @@ struct __align__(16) PkTr64 {
 };
 
 // ---------------------------------------------------------------- host setup
+// Topology of a surface kind: periodic single patch, or six cube-face patches.
+inline bool wm_periodic(int kind) { return kind == WM_TORUS || kind == WM_NURBS_PERIODIC; }
+inline bool wm_is_nurbs(int kind) { return kind == WM_NURBS_PERIODIC || kind == WM_NURBS_CUBE; }
+
+// Host copy of a NURBS patch of the geometry map.
+struct WmNurbs {
+  int pu = 0, pv = 0, nu = 0, nv = 0;
+  std::vector<double> ku, kv, cpw;  // knots, [nv][nu][4] control points and weights
+};
+
 struct wm_geom {
   wm_geom_desc d;
   int np;  // patches
+  std::vector<WmNurbs> nurbs;  // NURBS kinds only
 };
 
 // One level of the dyadic hierarchy.
@@ -148,6 +159,7 @@ struct WorkSpace;
 
 struct wm_hier {
   wm_geom_desc g;
+  std::vector<WmNurbs> nurbs;  // NURBS kinds only
   int np = 0, p = 0, nq = 0;
   std::vector<wm_level> lv;
   std::vector<double> gw, gx;  // Gauss weights and nodes on [0,1]
@@ -168,6 +180,15 @@ int wm_host_stencil(const wm_geom_desc& g, int np, const wm_level& L, std::vecto
                     std::vector<int32_t>& own, std::vector<int16_t>& slot);
 int wm_split_beta(double beta, int split, int* n, double* bp, int* passes);
 int wm_host_mass_bounds(const wm_geom_desc& g, int nu, int nv, double* lo, double* hi);
+// NURBS geometry: metric (a, G11, G12, G22) at the Gauss points gx of every
+// element of a level ([E][nq^2][4], element order (m nv + ev) nu + eu); checks
+// of a patch set (knots, weights, closure or edge agreement)
+int wm_host_nurbs_metric(const std::vector<WmNurbs>& patches, int nu, int nv, const std::vector<double>& gx,
+                         std::vector<double>& out);
+int wm_host_nurbs_check(int kind, const std::vector<WmNurbs>& patches);
+// bounds of the mass spectrum from the area element extremes at the Gauss points
+int wm_host_mass_bounds_metric(const wm_geom_desc& g, int nu, int nv, double amin, double amax, double* lo,
+                               double* hi);
 
 // ---------------------------------------------------------------- kernels
 // geometry and assembly (wm_assembly.cu)

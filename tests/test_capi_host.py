@@ -218,3 +218,95 @@ def test_mass_bounds_bracket_the_oracle_spectrum(lib, kind, p, nu, nv):
         assert ev[0] / lo < 40 and hi / ev[-1] < 20, (ev[0] / lo, hi / ev[-1])
     with pytest.raises(wm.WMError):
         g.mass_bounds(-1)
+
+
+def _nurbs_cases():
+    import wm_workloads as wl
+    return [("periodic", wl.nurbs_torus(1.0, 0.4), 2, 32, 16), ("periodic", wl.nurbs_torus(1.2, 0.3), 3, 16, 16),
+            ("cube", wl.nurbs_bulged_cube(0.3, 2.0), 2, 4, 4), ("cube", wl.nurbs_bulged_cube(0.0), 3, 2, 2),
+            ("cube", wl.nurbs_bulged_cube(0.5), 1, 8, 8)]
+
+
+@pytest.mark.parametrize("case", range(5))
+def test_nurbs_host_metric_and_maps_match_oracle(lib, case):
+    # the library evaluates the rational map on the host (span search, Cox–de Boor
+    # on the span, quotient rule); the oracle through its full-knot-vector bases
+    import numpy as np
+    import paper_2605_24882_gb300 as wm
+    from oracle.assembly import quadrature
+    from oracle.nurbs import NurbsSurface
+    from oracle.space import GluedSpace
+    topo, patches, p, nu, nv = _nurbs_cases()[case]
+    g = wm.Geometry.nurbs(topo, patches, p, nu, nv)
+    for level in range(2):
+        s = NurbsSurface(topo, patches, p, nu >> level, nv >> level)
+        q = quadrature(s)
+        ref = np.concatenate([np.stack([q[k][m] for k in ("a", "G11", "G12", "G22")], -1).reshape(-1, 4)
+                              for m in range(s.n_patches)])
+        met = g.metric_host(level)
+        np.testing.assert_allclose(met, ref, rtol=0, atol=1e-14 * np.abs(ref).max())
+        l2g, conn = g.dof_map(level)
+        sp_ = GluedSpace(s)
+        assert np.array_equal(l2g, sp_.l2g)
+        assert np.array_equal(conn, sp_.connectivity().reshape(conn.shape[0], -1))
+
+
+@pytest.mark.parametrize("case", range(5))
+def test_nurbs_mass_bounds_bracket_the_oracle_spectrum(lib, case):
+    import numpy as np
+    import paper_2605_24882_gb300 as wm
+    from oracle.assembly import assemble
+    from oracle.nurbs import NurbsSurface
+    from oracle.space import GluedSpace
+    topo, patches, p, nu, nv = _nurbs_cases()[case]
+    g = wm.Geometry.nurbs(topo, patches, p, nu, nv)
+    _, M = assemble(GluedSpace(NurbsSurface(topo, patches, p, nu, nv)))
+    ev = np.linalg.eigvalsh(M.toarray())
+    lo, hi = g.mass_bounds(0)
+    assert 0.0 < lo <= ev[0] and ev[-1] <= hi
+
+
+def test_nurbs_setup_rejects_bad_input(lib):
+    import numpy as np
+    import paper_2605_24882_gb300 as wm
+    import wm_workloads as wl
+    from paper_2605_24882_gb300 import _capi
+
+    def rejected(topo, patches, p=2, nu=16, nv=8):
+        with pytest.raises(wm.WMError) as e:
+            wm.Geometry.nurbs(topo, patches, p, nu, nv)
+        return e.value.code == _capi.WM_ERR_INVALID_ARG
+
+    torus = wl.nurbs_torus()
+    t = [dict(q) for q in torus]
+    t[0]["cpw"] = torus[0]["cpw"].copy()
+    t[0]["cpw"][0, 0, 0] += 1e-3                       # no longer closed
+    assert rejected("periodic", t)
+    t = [dict(q) for q in torus]
+    t[0]["knots_u"] = torus[0]["knots_u"][::-1].copy()  # decreasing
+    assert rejected("periodic", t)
+    t = [dict(q) for q in torus]
+    t[0]["knots_u"] = torus[0]["knots_u"] * 0.5         # not clamped to [0, 1]
+    assert rejected("periodic", t)
+    t = [dict(q) for q in torus]
+    t[0]["cpw"] = torus[0]["cpw"].copy()
+    t[0]["cpw"][4, 4, 3] = 0.0                          # non-positive weight
+    assert rejected("periodic", t)
+    assert rejected("periodic", torus, p=2, nu=4, nv=8)  # fewer than 2p+2 elements
+    assert rejected("periodic", torus + torus)           # two patches
+    cube = wl.nurbs_bulged_cube(0.2)
+    c = [dict(q) for q in cube]
+    c[3]["cpw"] = cube[3]["cpw"].copy()
+    c[3]["cpw"][0, 1, :3] += 1e-3                        # an edge control point off the shared edge
+    assert rejected("cube", c, nu=4, nv=4)
+    assert rejected("cube", cube[:5], nu=4, nv=4)
+    assert rejected("cube", cube, nu=4, nv=8)
+    # analytic kinds have no host metric; NURBS kinds need their own entry point
+    g = wm.Geometry("sphere", 2, 4)
+    with pytest.raises(wm.WMError) as e:
+        g.metric_host(0)
+    assert e.value.code == _capi.WM_ERR_UNSUPPORTED
+    d = _capi.GeomDesc(kind=_capi.WM_NURBS_CUBE, degree=2, elems_u=4, elems_v=4, R=0.0, r=0.0)
+    h = C.c_void_p()
+    assert lib.wm_setup_geometry(C.byref(d), C.byref(h)) == _capi.WM_ERR_INVALID_ARG
+    np.testing.assert_equal(h.value, None)

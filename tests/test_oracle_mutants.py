@@ -105,6 +105,14 @@ MUTANTS = [
     ("loss_drop_mass", "fractional.py", "L = float(np.sum(d * (M @ d)))", "L = float(np.sum(d * d))"),
     ("adjoint_rhs_drop_mass", "fractional.py", "gt = 2.0 * (M @ d)", "gt = 2.0 * d"),
     ("adjoint_kappa_sign", "fractional.py", "dk += -2.0 * kappa * cl * float(", "dk += 2.0 * kappa * cl * float("),
+    # NURBS geometry maps (Sec. 2.2)
+    ("nurbs_quotient_sign", "nurbs.py", "Fu = (Au - F * Wu) / W", "Fu = (Au + F * Wu) / W"),
+    ("nurbs_drop_weight", "nurbs.py", "wP = cpw[..., :3] * w[..., None]", "wP = cpw[..., :3]"),
+    ("nurbs_v_basis_for_u", "nurbs.py", 'Av = np.einsum("ni,nj,jic->nc", Nu, dNv, wP)',
+     'Av = np.einsum("ni,nj,jic->nc", dNu, Nv, wP)'),
+    ("nurbs_transposed_net", "nurbs.py", 'A = np.einsum("ni,nj,jic->nc", Nu, Nv, wP)',
+     'A = np.einsum("ni,nj,ijc->nc", Nu, Nv, wP)'),
+    ("nurbs_drop_weight_derivative", "nurbs.py", "Fv = (Av - F * Wv) / W", "Fv = Av / W"),
     # sqrt(M) by the Hale–Higham–Trefethen sum (Sec. 3.3)
     ("hht_midpoint", "sqrt_mass.py", "(np.arange(1, n_nodes + 1) - 0.5)", "(np.arange(1, n_nodes + 1) - 0.25)"),
     ("hht_prefactor", "sqrt_mass.py", "c = 2.0 * K * math.sqrt(lo)", "c = K * math.sqrt(lo)"),
@@ -144,6 +152,7 @@ def _copy_tree(dst):
     for f in _pin_files():
         shutil.copy(os.path.join(ROOT, "tests", f), td)
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(td, "golden"))
+    shutil.copy(os.path.join(ROOT, "wm_workloads.py"), dst)   # seeded inputs and geometry nets
     with open(os.path.join(td, "conftest.py"), "w") as fh:
         fh.write(CONFTEST)
 

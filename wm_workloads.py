@@ -80,3 +80,55 @@ def random_shifts(seed, n, lo=1e-2, hi=1e4):
     """n log-uniform shifts in [lo, hi]."""
     rng = np.random.default_rng(seed)
     return np.exp(rng.uniform(np.log(lo), np.log(hi), n))
+
+
+# ---------------------------------------------------------------- NURBS inputs
+# Geometry input for the NURBS surface kinds: control nets only (no method
+# arithmetic).  A patch is a dict with degree_u, degree_v, knots_u, knots_v and
+# cpw [n_v, n_u, 4] = (x, y, z, weight).
+
+# Cube-face arrangement of six-patch surfaces: patch m maps (u, v) to the cube
+# point whose coordinate a_axis is 2u-1, b_axis is 2v-1 and n_axis is n_sign
+# (the arrangement the library's six-patch gluing expects).
+CUBE_FACES = ((1, 2, 0, +1.0), (2, 1, 0, -1.0), (2, 0, 1, +1.0),
+              (0, 2, 1, -1.0), (0, 1, 2, +1.0), (1, 0, 2, -1.0))
+
+_H = np.sqrt(0.5)
+# full circle as a rational quadratic curve: 9 control points (x, y, w), knots at quarters
+_CIRCLE = np.array([[1, 0, 1], [1, 1, _H], [0, 1, 1], [-1, 1, _H], [-1, 0, 1],
+                    [-1, -1, _H], [0, -1, 1], [1, -1, _H], [1, 0, 1]], dtype=np.float64)
+_CIRCLE_KNOTS = np.array([0, 0, 0, .25, .25, .5, .5, .75, .75, 1, 1, 1], dtype=np.float64)
+
+
+def nurbs_torus(R=1.0, r=0.4):
+    """The torus ((R + r cos t) cos s, (R + r cos t) sin s, r sin t) exactly, as
+    the tensor product of two rational quadratic circles (one periodic patch)."""
+    cpw = np.zeros((9, 9, 4))
+    for j in range(9):          # tube circle (v)
+        cx, cz, wv = _CIRCLE[j]
+        for i in range(9):      # main circle (u)
+            ax, ay, wu = _CIRCLE[i]
+            rho = R + r * cx
+            cpw[j, i] = (ax * rho, ay * rho, r * cz, wu * wv)
+    return [dict(degree_u=2, degree_v=2, knots_u=_CIRCLE_KNOTS.copy(), knots_v=_CIRCLE_KNOTS.copy(), cpw=cpw)]
+
+
+def nurbs_bulged_cube(bulge=0.3, weight=1.0):
+    """Six biquadratic patches on the cube [-1, 1]^3 in the cube-face arrangement:
+    corner and edge-midpoint control points on the cube edges (shared exactly by
+    neighbouring patches), the face centre pushed outward by `bulge` with
+    weight `weight`.  bulge = 0 and weight = 1 give the flat cube surface."""
+    knots = np.array([0, 0, 0, 1, 1, 1], dtype=np.float64)
+    patches = []
+    for ax, bx, nx, sg in CUBE_FACES:
+        cpw = np.zeros((3, 3, 4))
+        for j in range(3):
+            for i in range(3):
+                c = np.zeros(3)
+                c[ax] = i - 1.0
+                c[bx] = j - 1.0
+                c[nx] = sg * (1.0 + (bulge if (i == 1 and j == 1) else 0.0))
+                cpw[j, i, :3] = c
+                cpw[j, i, 3] = weight if (i == 1 and j == 1) else 1.0
+        patches.append(dict(degree_u=2, degree_v=2, knots_u=knots.copy(), knots_v=knots.copy(), cpw=cpw))
+    return patches
