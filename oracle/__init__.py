@@ -22,6 +22,8 @@ It computes, in float64 with numpy/scipy, exactly what the sampler defines:
                     (Sec. 3.4), sinc nodes and weights (Eq. eq:beta-approx), and
                     the fields u_s by direct sparse solves and an explicit sum;
                     the field-loss gradient by the adjoint identity.
+* ``nurbs``      -- NURBS patches as geometry maps (Sec. 2.2) with the Surface
+                    interface, so the glued space and assembly apply to them.
 * ``sqrt_mass``  -- loads f = sqrt(M) y by the Hale–Higham–Trefethen sum
                     (Sec. 3.3, Eq. eq:sqrt) and bounds of the mass spectrum.
 
