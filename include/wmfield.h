@@ -160,6 +160,25 @@ int wm_geom_dof_map(wm_geom_t g, int level, int32_t* l2g, int64_t l2g_cap, int32
 int wm_geom_prolongation(wm_geom_t g, int level, int32_t* row_ptr, int32_t* col, double* val, int64_t nnz_cap);
 
 /*
+ * Host-only: the stencil form of a level's operator rows, as the shared-memory
+ * stencil kernels read it (no device used).
+ *   ext  [np][n_loc_v + 2p][n_loc_u + 2p]: global DOF of every cell of the patch
+ *        grids extended by a halo of p cells (across a cube edge the adjacent
+ *        patch's DOFs, periodic grids wrapped, beyond a cube corner -1);
+ *   own  [np][n_loc_v][n_loc_u]: the DOF whose row this patch position computes
+ *        (every DOF at its first patch), else -1;
+ *   col  [N][W]: the stored columns of each row, padded with the row index;
+ *   slot [N][W]: the window position (dv + p)(2p+1) + (du + p) of each stored
+ *        entry in the frame of the row's owner, -1 for padding.
+ * With all four arrays NULL only *W (the row width) is written.  Capacities are
+ * in entries (row_cap for col and slot).
+ * Errors: WM_ERR_UNSUPPORTED when the level has no stencil form (row kernels
+ * serve it), WM_ERR_INVALID_ARG for a bad level or a capacity too small.
+ */
+int wm_geom_stencil(wm_geom_t g, int level, int32_t* ext, int64_t ext_cap, int32_t* own, int64_t own_cap,
+                    int32_t* col, int16_t* slot, int64_t row_cap, int* W);
+
+/*
  * Host-only bounds lo <= lambda_min(M) and lambda_max(M) <= hi of the
  * assembled mass matrix of a level (the spectrum bounds m, M of Sec. 3.3 that
  * the sqrt(M) rule needs).  On each patch the quadrature mass form lies

@@ -116,6 +116,23 @@ class Geometry:
                                          nnz), "wm_geom_prolongation")
         return row_ptr, col, val
 
+    def stencil(self, level=0):
+        """Host-only: the stencil form (ext, own, col, slot) of a level's rows as int
+        numpy arrays (see wm_geom_stencil); raises WMError (unsupported) for levels
+        that the row kernels serve."""
+        n, lu, lv, _, _ = self.level_sizes(level, prolongation=False)
+        n_p = 6 if self.desc.kind in (_capi.WM_SPHERE6, _capi.WM_NURBS_CUBE) else 1
+        p = self.desc.degree
+        W = C.c_int()
+        check(lib().wm_geom_stencil(self._h, level, None, 0, None, 0, None, None, 0, C.byref(W)), "wm_geom_stencil")
+        ext = np.empty((n_p, lv + 2 * p, lu + 2 * p), dtype=np.int32)
+        own = np.empty((n_p, lv, lu), dtype=np.int32)
+        col = np.empty((n, W.value), dtype=np.int32)
+        slot = np.empty((n, W.value), dtype=np.int16)
+        check(lib().wm_geom_stencil(self._h, level, ext.ctypes.data, ext.size, own.ctypes.data, own.size,
+                                    col.ctypes.data, slot.ctypes.data, col.size, C.byref(W)), "wm_geom_stencil")
+        return ext, own, col, slot
+
     def mass_bounds(self, level=0):
         """Host-only: (lo, hi) bracketing the spectrum of the level's mass matrix."""
         lo, hi = C.c_double(), C.c_double()

@@ -73,6 +73,7 @@ _PROTOS = {
     "wm_geom_dof_map": (_i, [_vp, _i, _vp, _i64, _vp, _i64]),
     "wm_geom_prolongation": (_i, [_vp, _i, _vp, _vp, _vp, _i64]),
     "wm_geom_mass_bounds": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(_d)]),
+    "wm_geom_stencil": (_i, [_vp, _i, _vp, _i64, _vp, _i64, _vp, _vp, _i64, C.POINTER(_i)]),
     "wm_hht_rule": (_i, [_d, _d, _i, _vp, _vp]),
     "wm_metric": (_i, [_vp, _i, _vp, _vp]),
     "wm_apply_shifted": (_i, [_vp, _i, _i, C.POINTER(_d), _vp, _vp, _i, _vp]),

@@ -409,6 +409,27 @@ extern "C" int wm_geom_dof_map(wm_geom_t g, int level, int32_t* l2g, int64_t l2g
   return WM_OK;
 }
 
+extern "C" int wm_geom_stencil(wm_geom_t g, int level, int32_t* ext, int64_t ext_cap, int32_t* own,
+                               int64_t own_cap, int32_t* col, int16_t* slot, int64_t row_cap, int* W) {
+  wm_level L;
+  WM_TRY(geom_level(g, level, 0, L));
+  if (W) *W = L.W;
+  if (!ext && !own && !col && !slot) return WM_OK;
+  std::vector<int32_t> e, o;
+  std::vector<int16_t> sl;
+  WM_TRY(wm_host_stencil(g->d, g->np, L, e, o, sl));
+  if (!ext || !own || !col || !slot || ext_cap < (int64_t)e.size() || own_cap < (int64_t)o.size() ||
+      row_cap < (int64_t)L.col.size()) {
+    wm_set_error("output buffers too small");
+    return WM_ERR_INVALID_ARG;
+  }
+  std::memcpy(ext, e.data(), e.size() * sizeof(int32_t));
+  std::memcpy(own, o.data(), o.size() * sizeof(int32_t));
+  std::memcpy(col, L.col.data(), L.col.size() * sizeof(int32_t));
+  std::memcpy(slot, sl.data(), sl.size() * sizeof(int16_t));
+  return WM_OK;
+}
+
 static int geom_nurbs_metric(wm_geom_t g, int level, std::vector<double>& met) {
   std::vector<double> gx, gw;
   wm_gauss_legendre01(g->d.degree + 1, gx, gw);

@@ -310,3 +310,52 @@ def test_nurbs_setup_rejects_bad_input(lib):
     h = C.c_void_p()
     assert lib.wm_setup_geometry(C.byref(d), C.byref(h)) == _capi.WM_ERR_INVALID_ARG
     np.testing.assert_equal(h.value, None)
+
+
+def _stencil_cases():
+    import wm_workloads as wl
+    return [("sphere", 2, 8, 8, None), ("sphere", 3, 4, 4, None), ("sphere", 1, 8, 8, None),
+            ("torus", 3, 32, 16, None), ("torus", 2, 16, 16, None), ("cube", 2, 8, 8, wl.nurbs_bulged_cube(0.3))]
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_stencil_form_reproduces_the_operators(lib, case):
+    # The shared-memory kernels compute row i in the frame of its owner patch:
+    # y_i = sum over the (2p+1)^2 window cells s of coef_i[s] x[ext(cell s)], the
+    # coefficients placed by slot.  With the oracle's S and M in those slots this
+    # must give S x and M x exactly: every DOF owned once, every non-zero column
+    # of a row in exactly one window cell, padding and empty corner cells unused.
+    import numpy as np
+    import paper_2605_24882_gb300 as wm
+    from oracle import geometry as geo
+    from oracle.assembly import assemble
+    from oracle.nurbs import NurbsSurface
+    from oracle.space import GluedSpace
+    kind, p, nu, nv, patches = _stencil_cases()[case]
+    if patches is None:
+        g = wm.Geometry(kind, p, nu, nv)
+        surf = geo.Surface(kind, p, nu, None if kind == "sphere" else nv)
+    else:
+        g = wm.Geometry.nurbs(kind, patches, p, nu, nv)
+        surf = NurbsSurface(kind, patches, p, nu, nv)
+    S, M = assemble(GluedSpace(surf))
+    S, M = S.toarray(), M.toarray()
+    ext, own, col, slot = g.stencil(0)
+    N, SW = S.shape[0], 2 * p + 1
+    owned = own[own >= 0]
+    assert np.array_equal(np.sort(owned), np.arange(N))
+    x = np.random.default_rng(4).standard_normal(N)
+    yS, yM = np.zeros(N), np.zeros(N)
+    for m, iv, iu in zip(*np.nonzero(own >= 0)):
+        i = own[m, iv, iu]
+        s = slot[i]
+        assert len(set(s[s >= 0].tolist())) == (s >= 0).sum()         # one stored entry per cell
+        assert set(col[i][s >= 0].tolist()) == set(np.nonzero(M[i])[0].tolist())
+        for w in np.nonzero(s >= 0)[0]:
+            cell = ext[m, iv + s[w] // SW, iu + s[w] % SW]
+            assert cell == col[i, w]                                   # the slot's window cell holds the column
+            yS[i] += S[i, cell] * x[cell]
+            yM[i] += M[i, cell] * x[cell]
+        assert (col[i][s < 0] == i).all()                               # padding repeats the row index
+    np.testing.assert_allclose(yS, S @ x, rtol=0, atol=1e-13 * np.abs(S).max() * np.abs(x).sum())
+    np.testing.assert_allclose(yM, M @ x, rtol=0, atol=1e-13 * np.abs(M).max() * np.abs(x).sum())
