@@ -168,11 +168,22 @@ def _mutate(dst, fname, old, new):
         fh.write(src.replace(old, new))
 
 
-def _run_pins(dst):
+# pin files that exercise a module most directly run first (pytest -x stops at
+# the first failure); every pin file runs if those pass
+FIRST = {"bspline.py": ["test_oracle_bspline.py"], "geometry.py": ["test_oracle_geometry.py"],
+         "assembly.py": ["test_oracle_assembly.py"], "space.py": ["test_oracle_assembly.py"],
+         "noise.py": ["test_oracle_noise.py"], "philox.py": ["test_oracle_noise.py"],
+         "fractional.py": ["test_oracle_sinc.py", "test_oracle_fractional.py"],
+         "sqrt_mass.py": ["test_oracle_sqrt_mass.py"], "nurbs.py": ["test_oracle_nurbs.py"]}
+
+
+def _run_pins(dst, fname=None):
     env = dict(os.environ, PYTHONPATH=dst, PYTHONDONTWRITEBYTECODE="1", OMP_NUM_THREADS="1",
                OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
-           os.path.join(dst, "tests")]
+    first = FIRST.get(fname, [])
+    files = first + [f for f in _pin_files() if f not in first]
+    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]
+    cmd += [os.path.join(dst, "tests", f) for f in files]
     res = subprocess.run(cmd, cwd=dst, env=env, capture_output=True, text=True, timeout=600)
     return res.returncode, res.stdout[-2000:]
 
@@ -180,13 +191,16 @@ def _run_pins(dst):
 def _case(tmp, idx, mutant):
     dst = os.path.join(tmp, f"m{idx:02d}")
     _copy_tree(dst)
+    fname = None
     if mutant is not None:
         _, fname, old, new = mutant
         _mutate(dst, fname, old, new)
-    return _run_pins(dst)
+    return _run_pins(dst, fname)
 
 
 def test_mutant_fragments_are_unique():
+    pins = set(_pin_files())
+    assert set(FIRST) == {m[1] for m in MUTANTS} and all(set(v) <= pins for v in FIRST.values())
     for name, fname, old, new in MUTANTS:
         with open(os.path.join(ROOT, "oracle", fname)) as fh:
             assert fh.read().count(old) == 1, (name, old)
