@@ -55,3 +55,24 @@ def test_single_rank_helpers():
     assert bench.max_over_ranks(3.0, 1) == 3.0
     assert bench.rank_seed(7, 0) == 7
     assert bench.job_rate(1, 256, 250.0) == pytest.approx(1024.0)
+
+
+def test_reference_arm_json_contract():
+    # the reference arm times the oracle on the host cores and prints one JSON line
+    # with the contract's keys; it needs no GPU
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                         cwd=root, capture_output=True, text=True, timeout=300)
+    assert res.returncode == 0, res.stderr[-2000:]
+    line = json.loads(res.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "samples/s" and line["higher_is_better"] is True
+    assert line["n_gpus"] == 1 and line["steps"] == 1 and line["warmup"] == 0 and line["value"] > 0
+    assert line["ms_per_step"] > 0 and line["config"]["workload"] == "sphere_p2_j6_mixed_s256"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == line["value"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
