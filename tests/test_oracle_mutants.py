@@ -64,6 +64,10 @@ MUTANTS = [
     ("assembly_cols", "assembly.py", "cols = np.tile(c, (1, nk)).ravel()", "cols = np.repeat(c, nk, axis=1).ravel()"),
     ("load_drop_measure", "assembly.py", 'fq = f(X) * quad["W"] * quad["a"][m]', 'fq = f(X) * quad["W"]'),
     ("evaluate_transposed", "assembly.py", '"ni,ji,nj->n", Bu, C, Bv', '"ni,ij,nj->n", Bu, C, Bv'),
+    ("load_points_of_patch_zero", "assembly.py", 'X, _, _ = surf.map(m, quad["u"], quad["v"])',
+     'X, _, _ = surf.map(0, quad["u"], quad["v"])'),
+    ("load_local_index", "assembly.py", 'loc = np.einsum("yxkgh,yxgh->yxk", phi, fq)',
+     'loc = np.einsum("yxkgh,yxhg->yxk", phi, fq)'),
     # glued space (Sec. 2.3)
     ("greville_window", "space.py", "kn[i + 1:i + p + 1].mean()", "kn[i:i + p].mean()"),
     ("no_gluing", "space.py", "first[j] = min(first[j], first[i])", "pass"),
@@ -71,6 +75,8 @@ MUTANTS = [
     # white noise (Sec. 3.3)
     ("noise_no_sqrt", "noise.py", 'wq = np.sqrt(quad["W"] * quad["a"][m]) * xi[m]', 'wq = quad["W"] * quad["a"][m] * xi[m]'),
     ("noise_same_sample", "noise.py", "normals(seed, s, q, STREAM_NOISE)", "normals(seed, 0, q, STREAM_NOISE)"),
+    ("noise_local_index", "noise.py", 'loc = np.einsum("yxkgh,yxgh->yxk", phi, wq)',
+     'loc = np.einsum("yxkgh,yxhg->yxk", phi, wq)'),
     ("philox_multiplier", "philox.py", "_M0 = np.uint64(0xD2511F53)", "_M0 = np.uint64(0xD2511F35)"),
     ("philox_weyl", "philox.py", "k1 = (k1 + _W1) & _MASK", "k1 = (k1 + _W0) & _MASK"),
     ("philox_round_words", "philox.py", "c = [hi1 ^ c[1] ^ k0, lo1, hi0 ^ c[3] ^ k1, lo0]",

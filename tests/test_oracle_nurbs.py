@@ -117,3 +117,10 @@ def test_nurbs_torus_area_and_energies_of_physical_functions():
         errs.append(row)
     assert max(errs[1]) < 2e-4, errs
     assert all(e0 / e1 > 8 for e0, e1 in zip(*errs)), errs
+
+
+def test_cube_face_arrangement_is_one_table():
+    # the NURBS cube inputs, the oracle's gnomonic sphere and the library's six-patch
+    # gluing use one face arrangement (the library checks shared edges at set-up)
+    from oracle.geometry import CUBE_FACES
+    assert tuple(tuple(f) for f in wl.CUBE_FACES) == tuple(tuple(f) for f in CUBE_FACES)
