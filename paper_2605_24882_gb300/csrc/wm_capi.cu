@@ -602,6 +602,27 @@ static int set_batch_meta(WorkSpace& ws, int tiles, const std::vector<double>& s
     n_uni += uni[t];
   }
   ws.n_uni_tiles = n_uni;
+  // groups of at most kUniGroup consecutive one-shift tiles with the same shift
+  // index (one block of the one-shift kernel per group and spatial block)
+  std::vector<int2> grp;
+  for (int t = 0; t < tiles; ++t) {
+    if (!uni[t]) continue;
+    const int st = si[(size_t)t * WM_LANES];
+    if (!grp.empty()) {
+      int2& last = grp.back();
+      const int lt = last.x + last.y;  // tile after the last group
+      if (lt == t && last.y < kUniGroup && si[(size_t)last.x * WM_LANES] == st) {
+        last.y += 1;
+        continue;
+      }
+    }
+    grp.push_back(make_int2(t, 1));
+  }
+  ws.n_uni_groups = (int)grp.size();
+  if (!grp.empty()) {
+    WM_TRY(ws.uni_groups.alloc(grp.size()));
+    WM_CUDA(cudaMemcpyAsync(ws.uni_groups.p, grp.data(), grp.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  }
   WM_CUDA(cudaMemcpyAsync(ws.sigma.p, sg.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
   WM_CUDA(cudaMemcpyAsync(ws.sid.p, si.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
   WM_CUDA(cudaMemcpyAsync(ws.src_of.p, sr.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));

@@ -918,6 +918,16 @@ int Batch::chunks_for(int N) const {
 // over the SMs instead of running a few long, latency-bound warps
 static int vcycle_chunks(int N) { return std::max(1, std::min(64, (N + 15) / 16)); }
 
+// the one-shift tiles of the current batch
+static UniTiles uni_of(const WorkSpace& ws) {
+  UniTiles u;
+  u.flag = ws.tile_uni.p;
+  u.n = ws.n_uni_tiles;
+  u.groups = ws.uni_groups.p;
+  u.n_groups = ws.n_uni_groups;
+  return u;
+}
+
 template <typename T>
 static T* vb(VBuf& b);
 template <>
@@ -988,7 +998,7 @@ void WorkSpace::release() {
   }
   lvl.clear();
   sigma.release(); sid.release(); src_of.release(); active.release(); rep.release(); restart.release();
-  tile_active.release(); tile_rep.release(); tile_uni.release();
+  tile_active.release(); tile_rep.release(); tile_uni.release(); uni_groups.release();
   rho.release(); alpha.release(); beta.release(); bb.release(); rr.release(); rr_ref.release();
   for (auto& pp : part) pp.release();
   flags.release(); counters.release(); lmax.release(); ainv.release(); shifts.release(); statd.release();
@@ -1158,7 +1168,7 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
     if (Lv.sten) {
       const bool fuse = dd && ws.n_uni_tiles > 0;
       int e = wm_sten_cheb_step<T>(Lv, h->np, h->p, tiles, k, ws.sigma.p, ctab, ws.sid.p, rin, zin, prev, zo, ta,
-                                   ws.tile_uni.p, ws.n_uni_tiles, csm, s, fuse ? dd->q : nullptr,
+                                   uni_of(ws), csm, s, fuse ? dd->q : nullptr,
                                    fuse ? dd->prz : nullptr, fuse ? dd->pzq : nullptr);
       if (fuse) dd->fused = true;
       if (e != WM_OK) step_rc = e;
@@ -1174,14 +1184,14 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   T* oth = zb;
   int k1 = 1;
   if (Lv.sten && ws.n_uni_tiles > 0 && nu >= 2) {
-    WM_TRY(wm_sten_cheb_first2<T>(Lv, h->np, h->p, tiles, ws.sigma.p, ctab, ws.sid.p, rin, za, zb, ta, ws.tile_uni.p,
+    WM_TRY(wm_sten_cheb_first2<T>(Lv, h->np, h->p, tiles, ws.sigma.p, ctab, ws.sid.p, rin, za, zb, ta, uni_of(ws),
                                   csm, s));
     units(csm, bt, 3.0 * Tb * Lv.N, 2.0 * Lv.nnz + 8.0 * Lv.N);
     if (ws.n_uni_tiles < tiles) {
       WM_LAUNCH(csm, s, k_cheb_first<T><<<ggrid, kBlk, 0, s>>>(Lv.N, ch, tiles, rin, dS, dM, ws.sigma.p, ctab,
                                                                ws.sid.p, za, ta, ws.tile_uni.p));
       int e = wm_sten_cheb_step<T>(Lv, h->np, h->p, tiles, 1, ws.sigma.p, ctab, ws.sid.p, rin, za, nullptr, zb, ta,
-                                   ws.tile_uni.p, ws.n_uni_tiles, csm, s, nullptr, nullptr, nullptr, true);
+                                   uni_of(ws), csm, s, nullptr, nullptr, nullptr, true);
       if (e != WM_OK) return e;
     }
     std::swap(cur, oth);  // cur = z2, oth = z1
@@ -1197,8 +1207,7 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   }
   // residual, restriction, coarse correction
   if (Lv.sten) {
-    WM_TRY(wm_sten_residual<T>(Lv, h->np, h->p, tiles, ws.sigma.p, rin, cur, res, ta, ws.tile_uni.p, ws.n_uni_tiles,
-                               cre, s));
+    WM_TRY(wm_sten_residual<T>(Lv, h->np, h->p, tiles, ws.sigma.p, rin, cur, res, ta, uni_of(ws), cre, s));
   } else {
     WM_LAUNCH(cre, s, k_residual<T><<<ggrid, kBlk, 0, s>>>(Lv.N, Lv.W, ch, tiles, pk, ws.sigma.p, rin, cur, res,
                                                            ta));
@@ -1332,8 +1341,8 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
   bool df_res = bt.df_residual;
   for (it = 1; it <= bt.max_iter; ++it) {
     if (L0.sten) {
-      WM_TRY(wm_sten_apply_pq<T>(L0, h->np, h->p, tiles, ws.sigma.p, p, q, ws.tile_active.p, ws.tile_uni.p,
-                                 ws.n_uni_tiles, ws.part[0].p, s));
+      WM_TRY(wm_sten_apply_pq<T>(L0, h->np, h->p, tiles, ws.sigma.p, p, q, ws.tile_active.p, uni_of(ws),
+                                 ws.part[0].p, s));
     } else {
       WM_LAUNCH(WM_PC_APPLY64, s, k_apply_pq<T><<<ggrid, kBlk, 0, s>>>(N, L0.W, ch, tiles, rows_of<T>(L0),
                                                                        ws.sigma.p, p, q, ws.tile_active.p,

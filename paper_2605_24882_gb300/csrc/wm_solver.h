@@ -66,6 +66,8 @@ struct WorkSpace {
   DevBuf<int> active, rep, restart, tile_active, tile_rep;
   DevBuf<int> tile_uni;       // 1 where the 32 shifts of a tile are equal
   int n_uni_tiles = 0;        // host count of such tiles in the current batch
+  DevBuf<int2> uni_groups;    // runs of at most 8 consecutive such tiles of one shift: (first tile, count)
+  int n_uni_groups = 0;
   DevBuf<double> rho, alpha, beta, bb, rr, rr_ref;
   DevBuf<double> part[3];
   DevBuf<int> flags, counters;

@@ -381,27 +381,29 @@ __global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGe
 }
 
 // ------------------------------------------- operator steps, one shift per tile
-// Operator-type steps for blocks of one tile whose 32 systems share a shift
-// sigma (sample-major packing puts the 32 samples of one sinc node in a
-// tile):
-//   UNI_CHEB   three-term Chebyshev step  out = z + c1 (z - z_prev) + w (r - A z)
-//   UNI_RESID  residual                   out = r - A z
-//   UNI_APPLY  outer apply                out = A z, per-block partial (z, A z)
-// After the DOF ids of the window are known, every global input of the block
-// (window of z, the rows of r and z_prev, coefficient rows (S, M), the
-// diagonals) is requested in one batch of asynchronous copies; the block then
-// combines its rows once into A = S + sigma M (and w = c2 / (dS + sigma dM)),
-// so an output costs one FMA per stencil entry and no division, each combined
-// row being read back with 16-byte shared loads.  One tile per block keeps
-// the register window at (2p+1)^2 values; for p = 2 in float the Chebyshev
-// block holds 50 KB of shared memory and four blocks share an SM (p = 3: 68 KB,
-// three blocks).
+// Operator-type steps for runs of consecutive tiles whose 32 systems share one
+// shift sigma (sample-major packing puts the 32 samples of one sinc node in a
+// tile, and the ns / 32 tiles of a node next to each other):
+//   UNI_CHEB     three-term Chebyshev step  out = z + c1 (z - z_prev) + w (r - A z)
+//   UNI_RESID    residual                   out = r - A z
+//   UNI_APPLY    outer apply                out = A z, per-block partial (z, A z)
 //   UNI_CHEBDOT  the Chebyshev step that ends a V-cycle, also forming the
 //                per-block partials (r, z_new) and (z_new, q) of the outer CG
 //                (q staged as a third row)
 //   UNI_CHEB1    the first two pre-smoothing steps from z = 0 in one pass:
 //                z1 = c2_0 Dinv r (written to out1), out = z1 + c1 z1 + c2 Dinv (r - A z1),
 //                A z1 formed from the window of r with c2_0 Dinv folded into the rows
+// A block owns one spatial block of one patch and a group of at most
+// kUniGroup consecutive tiles of one shift (a host-built list of (first tile,
+// count); `split` blocks share a group when the grid would be too small).
+// Everything that depends only on the spatial block and the shift is done
+// once for the group: the DOF ids of the window and of the output rows, every
+// thread's source offsets of its 16-byte copies, and the combined rows
+// A = S + sigma M (with the Chebyshev weights w = c2 / (dS + sigma dM)), so an
+// output costs one FMA per stencil entry and no division.  The group's tiles
+// then stream through shared memory: in float the window and rows of the next
+// tile are copied (cp.async) while the current tile is computed (two stage
+// buffers); in double a single stage buffer keeps two blocks on an SM.
 enum { UNI_CHEB = 0, UNI_RESID = 1, UNI_APPLY = 2, UNI_CHEBDOT = 3, UNI_CHEB1 = 4 };
 template <int MODE>
 struct UniCheb {
@@ -419,16 +421,25 @@ struct UniLayout {
   static constexpr int CS = CoefStride<T, P>::value;          // (S, M) row stride of the level tables
   static constexpr int NR = UniRows<MODE>::value;
   static constexpr int ND = UniCheb<MODE>::value ? 2 : 0;     // staged diagonals dS, dM
-  static constexpr size_t win = (size_t)NC * 32 * sizeof(T);
-  static constexpr size_t rows = (size_t)NR * BU * BV * 32 * sizeof(T);
-  static constexpr size_t raw = (size_t)BU * BV * CS * sizeof(typename V2<T>::type);  // (S, M) rows
-  static constexpr size_t coef = 0;  // the combined rows overwrite the (S, M) rows (fewer bytes)
-  static_assert((size_t)BU * BV * S2P * sizeof(T) <= raw, "combined rows must fit over the (S, M) rows");
+  static constexpr int NST = sizeof(T) == 4 ? 2 : 1;          // stage buffers
+  static constexpr size_t win = (size_t)NC * 32 * sizeof(T);  // window of the input vector
+  static constexpr size_t rows = (size_t)NR * BU * BV * 32 * sizeof(T);  // staged rows of the outputs
+  static constexpr size_t stage = win + rows;
+  // raw (S, M) rows, needed at set-up only: they sit in the last stage buffer
+  static constexpr size_t raw = (size_t)BU * BV * CS * sizeof(typename V2<T>::type);
+  static constexpr size_t last = stage > raw ? stage : raw;
+  static constexpr size_t stages = (NST - 1) * stage + last;
+  static constexpr size_t coef = (size_t)BU * BV * S2P * sizeof(T);  // combined rows
   static constexpr size_t diag = MODE == UNI_CHEB1 ? (size_t)3 * NC * sizeof(T)  // dS, dM, Dinv of the cells
                                                    : (size_t)(ND + 1) * BU * BV * sizeof(T);  // dS, dM, w
   static constexpr size_t diag16 = (diag + 15) / 16 * 16;
   static constexpr size_t ids = (size_t)(NC + BU * BV) * sizeof(int);
-  static constexpr size_t total = win + rows + raw + coef + diag16 + ids;
+  static constexpr size_t total = stages + coef + diag16 + ids;
+  // 16-byte copies of one staged tile: window chunks and row chunks, and per thread
+  static constexpr int ROWCH = 32 * sizeof(T) / 16;
+  static constexpr int WCH = NC * ROWCH, RCH = BU * BV * ROWCH;
+  static constexpr int WPT = (WCH + BU * 32 - 1) / (BU * 32), RPT = (RCH + BU * 32 - 1) / (BU * 32);
+  static_assert(stage % 16 == 0 && raw % 16 == 0 && coef % 16 == 0, "16-byte aligned regions");
 };
 template <typename T>
 struct Vec16;
@@ -444,11 +455,16 @@ struct Vec16<double> {
   using type = double2;
   static __device__ __forceinline__ double at(const double2& v, int k) { return k == 0 ? v.x : v.y; }
 };
-// blocks per SM the register budget is sized for
+// blocks per SM that the shared memory allows (with the 2 KB of the partial-sum
+// reduction and the 1 KB the runtime reserves per block), at most four (float)
+// or two (double: its copy offsets and window need the registers); this is
+// also the register budget
 template <typename T, int P, int MODE>
 struct UniMinBlocks {
-  static constexpr int value =
-      sizeof(T) == 4 ? (P == 2 ? 4 : ((MODE == UNI_CHEB || MODE == UNI_RESID) ? 3 : 2)) : (P == 2 ? 2 : 1);
+  static constexpr size_t per = UniLayout<T, P, MODE>::total + 3 * 1024;
+  static constexpr int fit = (int)((228 * 1024) / per);
+  static constexpr int cap = sizeof(T) == 4 ? 4 : 2;
+  static constexpr int value = fit >= cap ? cap : (fit < 1 ? 1 : fit);
 };
 // 4- or 8-byte asynchronous copy through L1 (diagonal entries)
 template <int BYTES>
@@ -457,13 +473,18 @@ __device__ __forceinline__ void cp_async_ca(void* smem, const void* gmem, int sr
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sa), "l"(gmem), "n"(BYTES), "r"(src_bytes)
                : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 template <typename T, int P, int MODE>
 __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
     k_sten_uni(StenGeo G, const typename V2<T>::type* __restrict__ csm, const T* __restrict__ dS,
                const T* __restrict__ dM, const double* __restrict__ sigma, const typename V2<T>::type* __restrict__ ctab,
                const int* __restrict__ sid, int kstep, const T* __restrict__ z, const T* __restrict__ r, const T* prev,
-               T* out, int tiles, const int* __restrict__ tile_active, const int* __restrict__ tile_uni,
+               T* out, int tiles, const int* __restrict__ tile_active, const int2* __restrict__ groups, int split,
                double* __restrict__ part, const T* __restrict__ qd, double* __restrict__ part2,
                T* __restrict__ out1) {
   using C2 = typename V2<T>::type;
@@ -471,16 +492,18 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
   constexpr bool CHEB = UniCheb<MODE>::value;
   using VT = typename Vec16<T>::type;
   constexpr int SW = 2 * P + 1, CU = LY::CU, NC = LY::NC, S2 = LY::S2, S2P = LY::S2P, VEC = LY::VEC, CS = LY::CS;
-  constexpr int NR = LY::NR;
+  constexpr int NR = LY::NR, NST = LY::NST, ROWCH = LY::ROWCH;
+  constexpr int EPT = 16 / sizeof(T);  // values per 16-byte chunk
+  constexpr int NT = BU * 32;          // threads per block
+  constexpr size_t STAGE = LY::stage / sizeof(T);  // stage buffer length in T
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* sm = reinterpret_cast<T*>(smraw);
-  T* srw = reinterpret_cast<T*>(smraw + LY::win);                                   // [NR][64][32]
-  C2* sraw = reinterpret_cast<C2*>(smraw + LY::win + LY::rows);                     // [64][CS]
-  T* scf = reinterpret_cast<T*>(smraw + LY::win + LY::rows);                        // [64][S2P] over sraw
-  T* sdg = reinterpret_cast<T*>(smraw + LY::win + LY::rows + LY::raw + LY::coef);   // [ND][64], then w [64]
-  T* swt = sdg + LY::ND * BU * BV;
-  int* sid_ = reinterpret_cast<int*>(smraw + LY::win + LY::rows + LY::raw + LY::coef + LY::diag16);
-  int* srow = sid_ + NC;
+  T* const stg = reinterpret_cast<T*>(smraw);  // [NST] x ([NC][32] window, [NR][64][32] rows)
+  C2* const sraw = reinterpret_cast<C2*>(smraw + (NST - 1) * LY::stage);  // [64][CS], set-up only
+  T* const scf = reinterpret_cast<T*>(smraw + LY::stages);                // [64][S2P]
+  T* const sdg = reinterpret_cast<T*>(smraw + LY::stages + LY::coef);     // [ND][64], then w [64]
+  T* const swt = sdg + LY::ND * BU * BV;
+  int* const sid_ = reinterpret_cast<int*>(smraw + LY::stages + LY::coef + LY::diag16);
+  int* const srow = sid_ + NC;
   const int lane = threadIdx.x, w = threadIdx.y;
   const int tid = w * 32 + lane;
   int b = blockIdx.x;
@@ -488,11 +511,19 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
   b /= G.nbu;
   const int bv = b % G.nbv;
   const int m = b / G.nbv;
-  const int t = blockIdx.y;
-  if (t >= tiles || !tile_active[t] || !tile_uni[t]) return;  // mixed-shift tiles are done by k_sten
+  // this block's tiles [ta, tb): part `sp` of group blockIdx.y / split
+  const int2 gr = groups[blockIdx.y / split];
+  const int sp = blockIdx.y % split;
+  const int per = (gr.y + split - 1) / split;
+  const int ta = gr.x + sp * per;
+  const int tb = min(min(gr.x + gr.y, ta + per), tiles);
+  unsigned todo = 0;  // active tiles of the range, bit t - ta (at most kUniGroup bits)
+  for (int t = ta; t < tb; ++t)
+    if (tile_active[t]) todo |= 1u << (t - ta);
+  if (todo == 0) return;
   T sg, c1 = 0, c2 = 0, c20 = 0;
   {
-    const int g = t * 32;  // every lane of the tile has this shift
+    const int g = gr.x * 32;  // every system of the group has this shift
     if constexpr (CHEB) {
       const C2 c = ctab[sid[g] * WM_MAX_CHEB + kstep];
       c1 = kstep == 0 ? (T)0 : c.x;
@@ -506,10 +537,10 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
     }
     sg = (T)sigma[g];
   }
-  // phase 0: global DOF of every window cell and every output row
+  // set-up 1: global DOF of every window cell and every output row
   const int32_t* E = G.ext + (size_t)m * G.ELV * G.ELU;
   const int32_t* OWN = G.own + (size_t)m * G.nlv * G.nlu;
-  for (int c = tid; c < NC + BU * BV; c += BU * 32) {
+  for (int c = tid; c < NC + BU * BV; c += NT) {
     int v = -1;
     if (c < NC) {
       int eu = bu * BU + c % CU, ev = bv * BV + c / CU;
@@ -522,30 +553,11 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
     sid_[c] = v;
   }
   __syncthreads();
-  // phase 1: every global input in one batch of asynchronous copies
-  constexpr int ROWCH = 32 * sizeof(T) / 16;        // 16-byte chunks per staged row
+  // set-up 2: (S, M) rows and diagonals, and each thread's source offsets
+  // (within a tile) of its window and row chunks: -1 zero-fills a cell
+  // outside the surface, -2 marks no chunk
   constexpr int RAWCH = CS * (int)sizeof(C2) / 16;  // 16-byte chunks per (S, M) row
-  constexpr int EPT = 16 / sizeof(T);               // values per chunk
-  const T* zt = z + (size_t)t * G.N * 32;
-  for (int c = tid; c < NC * ROWCH; c += BU * 32) {
-    const int part16 = c % ROWCH, cell = c / ROWCH;
-    const int gi = sid_[cell];
-    cp_async16(sm + cell * 32 + part16 * EPT, gi >= 0 ? zt + (size_t)gi * 32 + part16 * EPT : z, gi >= 0 ? 16 : 0);
-  }
-  if constexpr (NR > 0) {
-    const T* rt = r + (size_t)t * G.N * 32;
-    const T* pt = prev ? prev + (size_t)t * G.N * 32 : nullptr;
-    const T* qt = (MODE == UNI_CHEBDOT && qd) ? qd + (size_t)t * G.N * 32 : nullptr;
-    for (int c = tid; c < NR * BU * BV * ROWCH; c += BU * 32) {
-      const int part16 = c % ROWCH, o = (c / ROWCH) % (BU * BV), a = c / (ROWCH * BU * BV);
-      const int gi = srow[o];
-      const T* base = a == 0 ? rt : (a == 1 ? pt : qt);
-      const bool ok = gi >= 0 && base != nullptr;
-      cp_async16(srw + (a * BU * BV + o) * 32 + part16 * EPT, ok ? base + (size_t)gi * 32 + part16 * EPT : z,
-                 ok ? 16 : 0);
-    }
-  }
-  for (int c = tid; c < BU * BV * RAWCH; c += BU * 32) {
+  for (int c = tid; c < BU * BV * RAWCH; c += NT) {
     const int part16 = c % RAWCH, o = c / RAWCH;
     const int gi = srow[o];
     cp_async16(reinterpret_cast<unsigned char*>(sraw) + o * (CS * sizeof(C2)) + part16 * 16,
@@ -554,117 +566,184 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
                gi >= 0 ? 16 : 0);
   }
   if constexpr (MODE == UNI_CHEB1) {  // diagonals of every window cell
-    for (int c = tid; c < 2 * NC; c += BU * 32) {
-      const int cell = c % NC;
-      const int gi = sid_[cell];
+    for (int c = tid; c < 2 * NC; c += NT) {
+      const int gi = sid_[c % NC];
       const T* base = c < NC ? dS : dM;
       cp_async_ca<sizeof(T)>(sdg + c, gi >= 0 ? base + gi : dS, gi >= 0 ? (int)sizeof(T) : 0);
     }
   }
   if constexpr (CHEB) {
-    for (int c = tid; c < 2 * BU * BV; c += BU * 32) {
-      const int o = c % (BU * BV);
-      const int gi = srow[o];
+    for (int c = tid; c < 2 * BU * BV; c += NT) {
+      const int gi = srow[c % (BU * BV)];
       const T* base = c < BU * BV ? dS : dM;
       cp_async_ca<sizeof(T)>(sdg + c, gi >= 0 ? base + gi : dS, gi >= 0 ? (int)sizeof(T) : 0);
     }
   }
-  cp_async_wait_all();
+  cp_async_commit();
+  int woff[LY::WPT];
+#pragma unroll
+  for (int k = 0; k < LY::WPT; ++k) {
+    const int c = tid + k * NT;
+    int o = -2;
+    if (c < LY::WCH) {
+      const int gi = sid_[c / ROWCH];
+      o = gi >= 0 ? gi * 32 + (c % ROWCH) * EPT : -1;
+    }
+    woff[k] = o;
+  }
+  int roff[NR > 0 ? LY::RPT : 1];
+#pragma unroll
+  for (int k = 0; k < (NR > 0 ? LY::RPT : 1); ++k) {
+    const int c = tid + k * NT;
+    int o = -2;
+    if (NR > 0 && c < LY::RCH) {
+      const int gi = srow[c / ROWCH];
+      o = gi >= 0 ? gi * 32 + (c % ROWCH) * EPT : -1;
+    }
+    roff[k] = o;
+  }
+  // the 16-byte copies of tile t into stage buffer `buf` (chunk c of the
+  // window lands at element c * EPT, chunk c of row input a at NC * 32 +
+  // a * 64 * 32 + c * EPT); absent inputs (z_prev, q) are not copied
+  auto issue = [&](int t, T* buf) {
+    const size_t to = (size_t)t * G.N * 32;
+#pragma unroll
+    for (int k = 0; k < LY::WPT; ++k) {
+      const int o = woff[k];
+      if (o != -2) cp_async16(buf + (tid + k * NT) * EPT, o >= 0 ? z + to + o : z, o >= 0 ? 16 : 0);
+    }
+#pragma unroll
+    for (int a = 0; a < NR; ++a) {
+      const T* base = a == 0 ? r : (a == 1 ? prev : qd);
+      if (base == nullptr) continue;
+#pragma unroll
+      for (int k = 0; k < LY::RPT; ++k) {
+        const int o = roff[k];
+        if (o != -2)
+          cp_async16(buf + NC * 32 + a * BU * BV * 32 + (tid + k * NT) * EPT, o >= 0 ? base + to + o : base,
+                     o >= 0 ? 16 : 0);
+      }
+    }
+    cp_async_commit();
+  };
+  int cur = __ffs(todo) - 1;
+  todo &= todo - 1;
+  if constexpr (NST == 2) {  // the first tile goes to buffer 0 (the raw rows sit in buffer 1)
+    issue(ta + cur, stg);
+    cp_async_wait<1>();
+  } else {
+    cp_async_wait<0>();
+  }
   __syncthreads();
   T* sdc = sdg + 2 * NC;  // UNI_CHEB1: Dinv of every window cell
   if constexpr (MODE == UNI_CHEB1) {
-    for (int c = tid; c < NC; c += BU * 32) sdc[c] = sid_[c] >= 0 ? (T)1 / (sdg[c] + sg * sdg[NC + c]) : (T)0;
+    for (int c = tid; c < NC; c += NT) sdc[c] = sid_[c] >= 0 ? (T)1 / (sdg[c] + sg * sdg[NC + c]) : (T)0;
     __syncthreads();
   }
-  // combined rows (and the Chebyshev diagonal weights): every thread reads its
-  // (S, M) entries first, then, after the barrier, writes the combined rows over them
-  constexpr int CPT = (BU * BV * S2P + BU * 32 - 1) / (BU * 32);
-  T av[CPT];
-#pragma unroll
-  for (int k = 0; k < CPT; ++k) {
-    const int c = tid + k * BU * 32;
+  // set-up 3: combined rows and the Chebyshev diagonal weights
+  for (int c = tid; c < BU * BV * S2P; c += NT) {
     const int o = c / S2P, sl = c - o * S2P;
-    av[k] = 0;
-    if (c < BU * BV * S2P && sl < S2) {
+    T a = 0;
+    if (sl < S2) {
       const C2 q = sraw[o * CS + sl];
-      av[k] = q.x + sg * q.y;
+      a = q.x + sg * q.y;
       if constexpr (MODE == UNI_CHEB1)  // times c2_0 Dinv of the neighbour's cell: A z1 from r
-        av[k] *= c20 * sdc[((o / BU) + sl / SW) * CU + (o % BU) + sl % SW];
+        a *= c20 * sdc[((o / BU) + sl / SW) * CU + (o % BU) + sl % SW];
     }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < CPT; ++k) {
-    const int c = tid + k * BU * 32;
-    if (c < BU * BV * S2P) scf[c] = av[k];
+    scf[c] = a;
   }
   if constexpr (CHEB)
-    for (int c = tid; c < BU * BV; c += BU * 32)
-      swt[c] = srow[c] >= 0 ? c2 / (sdg[c] + sg * sdg[BU * BV + c]) : (T)0;
-  __syncthreads();
-  // phase 2: each warp sweeps the column iu with a ring of SW staged rows
+    for (int c = tid; c < BU * BV; c += NT) swt[c] = srow[c] >= 0 ? c2 / (sdg[c] + sg * sdg[BU * BV + c]) : (T)0;
+  __syncthreads();  // the raw rows are dead from here on (buffer 1 may be refilled)
   const int iu = bu * BU + w;
-  DAcc<T> dot;   // UNI_APPLY: (z, A z); UNI_CHEBDOT: (r, z_new) over this thread's outputs
-  DAcc<T> dot2;  // UNI_CHEBDOT: (z_new, q)
-  if (iu < G.nlu) {
-    T win[SW][SW];
+  int bsel = 0;
+  for (;;) {
+    const bool more = todo != 0;
+    const int nxt = more ? __ffs(todo) - 1 : 0;
+    T* const buf = stg + bsel * STAGE;
+    if constexpr (NST == 2) {
+      if (more) {
+        issue(ta + nxt, stg + (bsel ^ 1) * STAGE);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+    } else {
+      issue(ta + cur, buf);
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    // each warp sweeps the column iu with a ring of SW staged rows
+    const int t = ta + cur;
+    const T* const sm = buf;
+    const T* const srw = buf + NC * 32;
+    DAcc<T> dot;   // UNI_APPLY: (z, A z); UNI_CHEBDOT: (r, z_new) over this thread's outputs
+    DAcc<T> dot2;  // UNI_CHEBDOT: (z_new, q)
+    if (iu < G.nlu) {
+      T win[SW][SW];
 #pragma unroll
-    for (int rr = 0; rr < SW - 1; ++rr)
+      for (int rr = 0; rr < SW - 1; ++rr)
 #pragma unroll
-      for (int du = 0; du < SW; ++du) win[rr][du] = sm[(rr * CU + w + du) * 32 + lane];
+        for (int du = 0; du < SW; ++du) win[rr][du] = sm[(rr * CU + w + du) * 32 + lane];
 #pragma unroll
-    for (int j = 0; j < BV; ++j) {
-      const int rnx = j + SW - 1;  // staged row entering the window
+      for (int j = 0; j < BV; ++j) {
+        const int rnx = j + SW - 1;  // staged row entering the window
 #pragma unroll
-      for (int du = 0; du < SW; ++du) win[rnx % SW][du] = sm[(rnx * CU + w + du) * 32 + lane];
-      const int o = j * BU + w;
-      const int i = srow[o];
-      if (i >= 0) {
-        const VT* cf = reinterpret_cast<const VT*>(scf + o * S2P);
-        T acc = 0;
+        for (int du = 0; du < SW; ++du) win[rnx % SW][du] = sm[(rnx * CU + w + du) * 32 + lane];
+        const int o = j * BU + w;
+        const int i = srow[o];
+        if (i >= 0) {
+          const VT* cf = reinterpret_cast<const VT*>(scf + o * S2P);
+          T acc = 0;
 #pragma unroll
-        for (int q = 0; q < S2P / VEC; ++q) {
-          const VT a = cf[q];
+          for (int q = 0; q < S2P / VEC; ++q) {
+            const VT a = cf[q];
 #pragma unroll
-          for (int e = 0; e < VEC; ++e) {
-            const int sl = q * VEC + e;
-            if (sl < S2) acc = fma(Vec16<T>::at(a, e), win[(j + sl / SW) % SW][sl % SW], acc);
+            for (int e = 0; e < VEC; ++e) {
+              const int sl = q * VEC + e;
+              if (sl < S2) acc = fma(Vec16<T>::at(a, e), win[(j + sl / SW) % SW][sl % SW], acc);
+            }
           }
-        }
-        const T zc = win[(j + P) % SW][P];
-        T res;
-        if constexpr (CHEB) {
-          const T rv = srw[o * 32 + lane];
-          const T zp = prev ? srw[(BU * BV + o) * 32 + lane] : (T)0;
-          res = zc + c1 * (zc - zp) + swt[o] * (rv - acc);
-          if constexpr (MODE == UNI_CHEBDOT) {
-            dot.add(rv * res);
-            if (qd) dot2.add(res * srw[(2 * BU * BV + o) * 32 + lane]);
+          const T zc = win[(j + P) % SW][P];
+          T res;
+          if constexpr (CHEB) {
+            const T rv = srw[o * 32 + lane];
+            const T zp = prev ? srw[(BU * BV + o) * 32 + lane] : (T)0;
+            res = zc + c1 * (zc - zp) + swt[o] * (rv - acc);
+            if constexpr (MODE == UNI_CHEBDOT) {
+              dot.add(rv * res);
+              if (qd) dot2.add(res * srw[(2 * BU * BV + o) * 32 + lane]);
+            }
+          } else if constexpr (MODE == UNI_CHEB1) {
+            const T dc = sdc[(j + P) * CU + w + P];  // Dinv of the output row
+            const T z1 = c20 * dc * zc;              // zc is r here
+            out1[((size_t)t * G.N + i) * 32 + lane] = z1;
+            res = z1 + c1 * z1 + c2 * dc * (zc - acc);
+          } else if constexpr (MODE == UNI_RESID) {
+            res = srw[o * 32 + lane] - acc;
+          } else {
+            res = acc;
+            dot.add(zc * acc);
           }
-        } else if constexpr (MODE == UNI_CHEB1) {
-          const T dc = sdc[(j + P) * CU + w + P];  // Dinv of the output row
-          const T z1 = c20 * dc * zc;              // zc is r here
-          out1[((size_t)t * G.N + i) * 32 + lane] = z1;
-          res = z1 + c1 * z1 + c2 * dc * (zc - acc);
-        } else if constexpr (MODE == UNI_RESID) {
-          res = srw[o * 32 + lane] - acc;
-        } else {
-          res = acc;
-          dot.add(zc * acc);
+          out[((size_t)t * G.N + i) * 32 + lane] = res;
         }
-        out[((size_t)t * G.N + i) * 32 + lane] = res;
       }
     }
-  }
-  if constexpr (MODE == UNI_APPLY || MODE == UNI_CHEBDOT) {
-    const bool one[1] = {true};
-    double a1[1] = {dot.get()};
-    block_reduce<1>(a1, part, t, tiles, one);
-    if (MODE == UNI_CHEBDOT && qd) {
-      __syncthreads();
-      a1[0] = dot2.get();
-      block_reduce<1>(a1, part2, t, tiles, one);
+    if constexpr (MODE == UNI_APPLY || MODE == UNI_CHEBDOT) {
+      const bool one[1] = {true};
+      double a1[1] = {dot.get()};
+      block_reduce<1>(a1, part, t, tiles, one);
+      if (MODE == UNI_CHEBDOT && qd) {
+        __syncthreads();
+        a1[0] = dot2.get();
+        block_reduce<1>(a1, part2, t, tiles, one);
+      }
     }
+    __syncthreads();  // this stage buffer (and the reduction buffer) may be refilled
+    if (!more) break;
+    todo &= todo - 1;
+    cur = nxt;
+    if constexpr (NST == 2) bsel ^= 1;
   }
 }
 
@@ -1059,10 +1138,20 @@ int wm_sten_chunks(const wm_level& L, int np) { return L.sten ? np * L.nbu * L.n
     default: return WM_ERR_UNSUPPORTED;            \
   }
 
+// SMs of the current device (grid sizing of the one-shift kernel)
+static int device_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 152;
+  }
+  return n > 0 ? n : 152;
+}
+
 template <typename T, int P, int MODE>
-static int launch_uni(const wm_level& L, int np, int tiles, int kstep, const double* sigma,
+static int launch_uni(const wm_level& L, int np, int tiles, const UniTiles& ut, int kstep, const double* sigma,
                       const typename V2<T>::type* ctab, const int* sid, const T* r, const T* z, const T* prev,
-                      T* out, const int* tile_active, const int* tile_uni, double* part, int cat, cudaStream_t s,
+                      T* out, const int* tile_active, double* part, int cat, cudaStream_t s,
                       const T* qd = nullptr, double* part2 = nullptr, T* out1 = nullptr) {
   constexpr size_t sm = UniLayout<T, P, MODE>::total;
   static bool configured = false;
@@ -1070,33 +1159,42 @@ static int launch_uni(const wm_level& L, int np, int tiles, int kstep, const dou
     WM_CUDA(cudaFuncSetAttribute(k_sten_uni<T, P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     configured = true;
   }
+  if (ut.n_groups <= 0) return WM_OK;
+  static const int sms = device_sms();
+  const int bx = np * L.nbu * L.nbv;
+  // blocks that share a group: enough blocks for about four waves
+  const int64_t want = 4LL * sms * UniMinBlocks<T, P, MODE>::value;
+  int split = 1;
+  while (split < kUniGroup && (int64_t)bx * ut.n_groups * split < want) split *= 2;
   const T* dS = std::is_same<T, double>::value ? (const T*)L.d_dS64.p : (const T*)L.d_dS32.p;
   const T* dM = std::is_same<T, double>::value ? (const T*)L.d_dM64.p : (const T*)L.d_dM32.p;
-  dim3 grid(np * L.nbu * L.nbv, tiles);
-  WM_LAUNCH(cat, s, k_sten_uni<T, P, MODE><<<grid, dim3(32, BU), sm, s>>>(geo_of(L), csm_of<T>(L), dS, dM, sigma,
-                                                                         ctab, sid, kstep, z, r, prev, out, tiles,
-                                                                         tile_active, tile_uni, part, qd, part2,
-                                                                         out1));
-  WM_CUDA(cudaGetLastError());
+  const int gmax = 65535 / split;  // grid.y limit
+  for (int g0 = 0; g0 < ut.n_groups; g0 += gmax) {
+    const int ng = std::min(gmax, ut.n_groups - g0);
+    dim3 grid(bx, ng * split);
+    WM_LAUNCH(cat, s, k_sten_uni<T, P, MODE><<<grid, dim3(32, BU), sm, s>>>(
+                          geo_of(L), csm_of<T>(L), dS, dM, sigma, ctab, sid, kstep, z, r, prev, out, tiles,
+                          tile_active, ut.groups + g0, split, part, qd, part2, out1));
+    WM_CUDA(cudaGetLastError());
+  }
   return WM_OK;
 }
 
 template <typename T>
 int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, const double* sigma,
                       const typename StenC2<T>::type* ctab, const int* sid, const T* r, const T* z, const T* prev,
-                      T* out, const int* tile_active, const int* tile_uni, int n_uni, int cat, cudaStream_t s,
+                      T* out, const int* tile_active, const UniTiles& ut, int cat, cudaStream_t s,
                       const T* q, double* part_rz, double* part_zq, bool generic_only) {
   if (generic_only) {
     // the one-shift tiles were done elsewhere: generic kernel for the others only
-  } else if (n_uni > 0 && part_rz) {
-    WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_CHEBDOT>(L, np, tiles, kstep, sigma, ctab, sid, r, z, prev,
-                                                              out, tile_active, tile_uni, part_rz, cat, s, q,
-                                                              part_zq))); });
-  } else if (n_uni > 0) {
-    WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_CHEB>(L, np, tiles, kstep, sigma, ctab, sid, r, z, prev, out,
-                                                           tile_active, tile_uni, nullptr, cat, s))); });
+  } else if (ut.n > 0 && part_rz) {
+    WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_CHEBDOT>(L, np, tiles, ut, kstep, sigma, ctab, sid, r, z, prev,
+                                                              out, tile_active, part_rz, cat, s, q, part_zq))); });
+  } else if (ut.n > 0) {
+    WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_CHEB>(L, np, tiles, ut, kstep, sigma, ctab, sid, r, z, prev,
+                                                           out, tile_active, nullptr, cat, s))); });
   }
-  if (n_uni >= tiles) return WM_OK;
+  if (ut.n >= tiles) return WM_OK;
   ChebEpi<T, 2> e2;
   ChebEpi<T, 1> e1;
   auto fill = [&](auto& e) {
@@ -1113,7 +1211,7 @@ int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, co
   };
   fill(e2);
   fill(e1);
-  const int* skip = n_uni > 0 ? tile_uni : nullptr;
+  const int* skip = ut.n > 0 ? ut.flag : nullptr;
   WM_DISPATCH_P(p, {
     if constexpr (Tpb<T, PP>::value == 2)
       return launch<T, PP>(L, np, tiles, z, tile_active, e2, cat, s, skip);
@@ -1126,20 +1224,20 @@ int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, co
 template <typename T>
 int wm_sten_cheb_first2(const wm_level& L, int np, int p, int tiles, const double* sigma,
                         const typename StenC2<T>::type* ctab, const int* sid, const T* r, T* z1, T* z2,
-                        const int* tile_active, const int* tile_uni, int cat, cudaStream_t s) {
-  WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_CHEB1>(L, np, tiles, 1, sigma, ctab, sid, nullptr, r, nullptr, z2,
-                                                          tile_active, tile_uni, nullptr, cat, s, nullptr, nullptr,
+                        const int* tile_active, const UniTiles& ut, int cat, cudaStream_t s) {
+  WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_CHEB1>(L, np, tiles, ut, 1, sigma, ctab, sid, nullptr, r, nullptr,
+                                                          z2, tile_active, nullptr, cat, s, nullptr, nullptr,
                                                           z1))); });
   return WM_OK;
 }
 
 template <typename T>
 int wm_sten_residual(const wm_level& L, int np, int p, int tiles, const double* sigma, const T* r, const T* z,
-                     T* res, const int* tile_active, const int* tile_uni, int n_uni, int cat, cudaStream_t s) {
-  if (n_uni > 0) {
-    WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_RESID>(L, np, tiles, 0, sigma, nullptr, nullptr, r, z, nullptr,
-                                                            res, tile_active, tile_uni, nullptr, cat, s))); });
-    if (n_uni >= tiles) return WM_OK;
+                     T* res, const int* tile_active, const UniTiles& ut, int cat, cudaStream_t s) {
+  if (ut.n > 0) {
+    WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_RESID>(L, np, tiles, ut, 0, sigma, nullptr, nullptr, r, z,
+                                                            nullptr, res, tile_active, nullptr, cat, s))); });
+    if (ut.n >= tiles) return WM_OK;
   }
   ResidEpi<T, 2> e2;
   ResidEpi<T, 1> e1;
@@ -1148,7 +1246,7 @@ int wm_sten_residual(const wm_level& L, int np, int p, int tiles, const double* 
   e2.res = e1.res = res;
   e2.sigma = e1.sigma = sigma;
   e2.in[0] = e1.in[0] = r;
-  const int* skip = n_uni > 0 ? tile_uni : nullptr;
+  const int* skip = ut.n > 0 ? ut.flag : nullptr;
   WM_DISPATCH_P(p, {
     if constexpr (Tpb<T, PP>::value == 2)
       return launch<T, PP>(L, np, tiles, z, tile_active, e2, cat, s, skip);
@@ -1160,12 +1258,12 @@ int wm_sten_residual(const wm_level& L, int np, int p, int tiles, const double* 
 
 template <typename T>
 int wm_sten_apply_pq(const wm_level& L, int np, int p, int tiles, const double* sigma, const T* pv, T* q,
-                     const int* tile_active, const int* tile_uni, int n_uni, double* part, cudaStream_t s) {
-  if (n_uni > 0) {
-    WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_APPLY>(L, np, tiles, 0, sigma, nullptr, nullptr, nullptr, pv,
-                                                            nullptr, q, tile_active, tile_uni, part, WM_PC_APPLY64,
+                     const int* tile_active, const UniTiles& ut, double* part, cudaStream_t s) {
+  if (ut.n > 0) {
+    WM_DISPATCH_P(p, { WM_TRY((launch_uni<T, PP, UNI_APPLY>(L, np, tiles, ut, 0, sigma, nullptr, nullptr, nullptr,
+                                                            pv, nullptr, q, tile_active, part, WM_PC_APPLY64,
                                                             s))); });
-    if (n_uni >= tiles) return WM_OK;
+    if (ut.n >= tiles) return WM_OK;
   }
   ApplyEpi<T, 2> e2;
   ApplyEpi<T, 1> e1;
@@ -1173,7 +1271,7 @@ int wm_sten_apply_pq(const wm_level& L, int np, int p, int tiles, const double* 
   e2.q = e1.q = q;
   e2.sigma = e1.sigma = sigma;
   e2.part = e1.part = part;
-  const int* skip = n_uni > 0 ? tile_uni : nullptr;
+  const int* skip = ut.n > 0 ? ut.flag : nullptr;
   WM_DISPATCH_P(p, {
     if constexpr (Tpb<T, PP>::value == 2)
       return launch<T, PP>(L, np, tiles, pv, tile_active, e2, WM_PC_APPLY64, s, skip);
@@ -1228,22 +1326,23 @@ int wm_sten_true_residual_df(const wm_level& L, int np, int p, int tiles, const 
 
 template int wm_sten_cheb_step<float>(const wm_level&, int, int, int, int, const double*, const float2*,
                                       const int*, const float*, const float*, const float*, float*, const int*,
-                                      const int*, int, int, cudaStream_t, const float*, double*, double*, bool);
+                                      const UniTiles&, int, cudaStream_t, const float*, double*, double*, bool);
 template int wm_sten_cheb_step<double>(const wm_level&, int, int, int, int, const double*, const double2*,
                                        const int*, const double*, const double*, const double*, double*, const int*,
-                                       const int*, int, int, cudaStream_t, const double*, double*, double*, bool);
+                                       const UniTiles&, int, cudaStream_t, const double*, double*, double*, bool);
 template int wm_sten_cheb_first2<float>(const wm_level&, int, int, int, const double*, const float2*, const int*,
-                                        const float*, float*, float*, const int*, const int*, int, cudaStream_t);
+                                        const float*, float*, float*, const int*, const UniTiles&, int, cudaStream_t);
 template int wm_sten_cheb_first2<double>(const wm_level&, int, int, int, const double*, const double2*, const int*,
-                                         const double*, double*, double*, const int*, const int*, int, cudaStream_t);
+                                         const double*, double*, double*, const int*, const UniTiles&, int,
+                                         cudaStream_t);
 template int wm_sten_residual<float>(const wm_level&, int, int, int, const double*, const float*, const float*, float*,
-                                     const int*, const int*, int, int, cudaStream_t);
+                                     const int*, const UniTiles&, int, cudaStream_t);
 template int wm_sten_residual<double>(const wm_level&, int, int, int, const double*, const double*, const double*,
-                                      double*, const int*, const int*, int, int, cudaStream_t);
+                                      double*, const int*, const UniTiles&, int, cudaStream_t);
 template int wm_sten_apply_pq<float>(const wm_level&, int, int, int, const double*, const float*, float*, const int*,
-                                     const int*, int, double*, cudaStream_t);
+                                     const UniTiles&, double*, cudaStream_t);
 template int wm_sten_apply_pq<double>(const wm_level&, int, int, int, const double*, const double*, double*,
-                                      const int*, const int*, int, double*, cudaStream_t);
+                                      const int*, const UniTiles&, double*, cudaStream_t);
 template int wm_sten_true_residual<float>(const wm_level&, int, int, int, const double*, const double*, const double*,
                                           const int*, const int*, const int*, float*, double*, cudaStream_t);
 template int wm_sten_true_residual<double>(const wm_level&, int, int, int, const double*, const double*,

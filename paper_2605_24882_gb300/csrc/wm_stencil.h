@@ -7,6 +7,19 @@
 #define WM_MAX_CHEB 8
 #endif
 
+// Tiles whose 32 systems share one shift (sample-major packing: the 32 samples
+// of one sinc node), for the combined-coefficient kernel: a per-tile flag (the
+// generic kernel skips those tiles) and groups of at most kUniGroup
+// consecutive such tiles with the same shift index, each (first tile, count).
+// A block of the one-shift kernel serves one group (or part of one).
+constexpr int kUniGroup = 8;
+struct UniTiles {
+  const int* flag = nullptr;     // [tiles] 1 where the 32 shifts of the tile are equal
+  int n = 0;                     // number of such tiles
+  const int2* groups = nullptr;  // [n_groups] (first tile, count), count in 1..kUniGroup
+  int n_groups = 0;
+};
+
 // Builds the stencil form of a level (extended grids, owner map, coefficient
 // slots) after its rows are assembled; leaves L.sten = false when the level
 // keeps the row kernels (degree outside 2..3, patches narrower than 8).
@@ -27,13 +40,12 @@ struct StenC2<double> {
 // Three-term Chebyshev step out = z + c1 (z - prev) + c2 D^{-1} (r - A z)
 // (c1 = 0 at kstep 0, prev = nullptr for z_prev = 0; out may alias prev).
 // ctab: (c1, c2) per [shift][step] of the level (WM_MAX_CHEB steps per shift).
-// tile_uni[t] = 1 when the 32 shifts of tile t are equal; those tiles
-// (n_uni of them) go to the combined-coefficient kernel (one tile per
-// block), the others to the generic one.
+// The one-shift tiles of `ut` go to the combined-coefficient kernel, the
+// others to the generic one.
 template <typename T>
 int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, const double* sigma,
                       const typename StenC2<T>::type* ctab, const int* sid, const T* r, const T* z, const T* prev,
-                      T* out, const int* tile_active, const int* tile_uni, int n_uni, int cat, cudaStream_t s,
+                      T* out, const int* tile_active, const UniTiles& ut, int cat, cudaStream_t s,
                       const T* q = nullptr, double* part_rz = nullptr, double* part_zq = nullptr,
                       bool generic_only = false);
 // With part_rz set, the one-shift tiles of the step also leave per-block partial
@@ -47,16 +59,16 @@ int wm_sten_cheb_step(const wm_level& L, int np, int p, int tiles, int kstep, co
 template <typename T>
 int wm_sten_cheb_first2(const wm_level& L, int np, int p, int tiles, const double* sigma,
                         const typename StenC2<T>::type* ctab, const int* sid, const T* r, T* z1, T* z2,
-                        const int* tile_active, const int* tile_uni, int cat, cudaStream_t s);
+                        const int* tile_active, const UniTiles& ut, int cat, cudaStream_t s);
 // residual res = r - A z and outer apply q = A p with per-block partial sums
-// (p, q) in `part` ([tile][chunk][32], chunk = spatial block); one-shift
-// tiles (tile_uni, n_uni of them) take the combined-coefficient kernel
+// (p, q) in `part` ([tile][chunk][32], chunk = spatial block); the one-shift
+// tiles of `ut` take the combined-coefficient kernel
 template <typename T>
 int wm_sten_residual(const wm_level& L, int np, int p, int tiles, const double* sigma, const T* r, const T* z,
-                     T* res, const int* tile_active, const int* tile_uni, int n_uni, int cat, cudaStream_t s);
+                     T* res, const int* tile_active, const UniTiles& ut, int cat, cudaStream_t s);
 template <typename T>
 int wm_sten_apply_pq(const wm_level& L, int np, int p, int tiles, const double* sigma, const T* pv, T* q,
-                     const int* tile_active, const int* tile_uni, int n_uni, double* part, cudaStream_t s);
+                     const int* tile_active, const UniTiles& ut, double* part, cudaStream_t s);
 template <typename Tr>
 int wm_sten_true_residual(const wm_level& L, int np, int p, int tiles, const double* sigma, const double* x,
                           const double* rhs, const int* src_of, const int* rep, const int* tile_rep, Tr* r,

@@ -1,14 +1,14 @@
 """Component micro-benchmarks of the sampler's kernels on synthetic inputs.
 
     python -m paper_2605_24882_gb300.microbench vcycle [--kind sphere] [--p 2]
-        [--elems 64] [--levels 6] [--tiles 71] [--degree 4] [--ratio 12]
-        [--precision mixed] [--reps 3]
+        [--elems 64] [--levels 6] [--tiles 71] [--tiles-per-shift 1] [--degree 4]
+        [--ratio 12] [--precision mixed] [--reps 3]
 
 `vcycle` runs `reps` V-cycles (the preconditioner of the batched solves) on
-`tiles` x 32 seeded random residuals, 32 per shift with `tiles` shifts spread
-geometrically over [25 + e^-10, 25 + e^10] (one shift per tile, as the
-sample-major packing of a sinc pass produces), and prints the mean time per
-V-cycle.  It is the driver for kernel profiles of the smoother, residual and
+`tiles` x 32 seeded random residuals, 32 x `tiles-per-shift` per shift, the
+shifts spread geometrically over [25 + e^-10, 25 + e^10] (sample-major packing
+of a sinc pass puts n_s / 32 consecutive tiles on one shift), and prints the
+mean time per V-cycle.  It is the driver for kernel profiles of the smoother, residual and
 transfer kernels.
 
     python -m paper_2605_24882_gb300.microbench sqrt [--kind sphere] [--p 2]
@@ -30,7 +30,8 @@ import paper_2605_24882_gb300 as wm
 def vcycle(args):
     hier = wm.Hierarchy(wm.Geometry(args.kind, args.p, args.elems), args.levels)
     n = hier.num_dofs(0)
-    sig = np.repeat(np.exp(np.linspace(-10.0, 10.0, args.tiles)) + 25.0, 32)
+    nsh = (args.tiles + args.tiles_per_shift - 1) // args.tiles_per_shift
+    sig = np.repeat(np.exp(np.linspace(-10.0, 10.0, nsh)) + 25.0, 32 * args.tiles_per_shift)[:args.tiles * 32]
     g = torch.Generator(device="cuda").manual_seed(0)
     r = torch.randn((args.tiles * 32, n), dtype=torch.float64, device="cuda", generator=g)
     z = hier.vcycle(r, sig, precision=args.precision, smoother_degree=args.degree, cheb_ratio=args.ratio)
@@ -42,6 +43,7 @@ def vcycle(args):
     e1.record()
     torch.cuda.synchronize()
     print(json.dumps({"bench": "vcycle", "dofs": n, "systems": args.tiles * 32, "levels": args.levels,
+                      "tiles_per_shift": args.tiles_per_shift,
                       "degree": args.degree, "ms_per_vcycle": e0.elapsed_time(e1) / max(1, args.reps),
                       "max_abs_z": float(z.abs().max())}))
 
@@ -72,6 +74,7 @@ def main():
     ap.add_argument("--elems", type=int, default=64)
     ap.add_argument("--levels", type=int, default=6)
     ap.add_argument("--tiles", type=int, default=71)
+    ap.add_argument("--tiles-per-shift", type=int, default=1)
     ap.add_argument("--degree", type=int, default=4)
     ap.add_argument("--ratio", type=float, default=12.0)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
