@@ -8,8 +8,8 @@ six-patch unit sphere with 64 x 64 bi-quadratic elements per patch.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun every rank samples its own 256 fields (independent seeds, no
-collective on the data path: weak scaling); rank 0 prints one JSON line.
+Under torchrun rank r samples fields r*256 .. r*256+255 of one noise sequence
+(no collective on the data path: weak scaling); rank 0 prints one JSON line.
 """
 import argparse
 import hashlib
@@ -132,9 +132,11 @@ def max_over_ranks(x, world, device="cuda"):
     return float(t.item())
 
 
-def rank_seed(seed, rank):
-    """Noise seed of a rank's replica: the replicas draw independent samples."""
-    return seed + 1000003 * rank
+def rank_samples(rank, samples_per_rank):
+    """Sample range [first, first + n) of a rank: the job's samples 0 .. N n - 1
+    under one noise seed, split into contiguous blocks (rank r draws the same
+    loads and fields as rows r n .. (r + 1) n - 1 of a one-GPU run of N n)."""
+    return rank * samples_per_rank, samples_per_rank
 
 
 def job_rate(world, samples_per_rank, ms_per_step):
@@ -208,8 +210,8 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "dofs": N},
-            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
-                             "sample": "per step: " + sample},
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "host_cores": os.cpu_count(),
+                             "kind": "oracle", "sample": "per step: " + sample},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -323,7 +325,8 @@ def our_arm(args):
     N = hier.num_dofs(0)
     ns = args.samples or c["n_samples"]
     kw = dict(kappa=c["kappa"], beta=c["beta"], sinc_k=c["k"], l_lo=c["l_lo"], l_hi=c["l_hi"], n_samples=ns,
-              seed=rank_seed(c["seed"], rank), split=c["split"], precision=c["precision"], rtol=c["rtol"],
+              seed=c["seed"], sample0=rank_samples(rank, ns)[0], split=c["split"], precision=c["precision"],
+              rtol=c["rtol"],
               smoother_degree=args.smoother_degree or c.get("smoother_degree", 4),
               cheb_ratio=args.cheb_ratio or c.get("cheb_ratio", 12.0), preconditioner=args.preconditioner)
     u = torch.empty((ns, N), dtype=torch.float64, device="cuda")
@@ -395,6 +398,8 @@ def our_arm(args):
             "gpu_launches": launches,
             "roofline": rl,
             "kernel_ms_per_step": {k: v["ms"] / args.profile_steps for k, v in prof.items() if v["ms"] > 0},
+            "kernel_alg_gbs": {k: v["bytes"] / (v["ms"] * 1e6) for k, v in prof.items()
+                               if v["ms"] > 0 and v["bytes"] > 0},
             "profiled_steps": args.profile_steps if prof else 0,
             "clocks": clocks}
     if not args.no_fp64_legs:
@@ -404,8 +409,8 @@ def our_arm(args):
         line["fp64_comparison"] = legs
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, total, sample, _ = oracle_estimate(c)
-        line["cpu_baseline"] = {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle", "sample": sample,
-                                "extrapolated_seconds_per_step": total}
+        line["cpu_baseline"] = {"value": v, "unit": "samples/s", "cores": 1, "host_cores": os.cpu_count(),
+                                "kind": "oracle", "sample": sample, "extrapolated_seconds_per_step": total}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -296,19 +296,22 @@ int wm_noise_loads(wm_hier_t h, uint64_t seed, int n_samples, double* b, void* s
 
 /*
  * wm_noise_loads without any device allocation, for callers that cannot
- * allocate device memory (code inside a CUDA graph being captured, or a host
- * framework whose allocator owns all device memory).  The paper has no
- * counterpart: this is a packaging variant of wm_noise_loads with the same
- * result (b: device [n_samples][N], caller-owned).  Its element-local scratch
- * is a fixed file-scope device array of 2^22 doubles (32 MiB) that every GPU
- * which loads the library holds until process exit; a call needs
- * elements x (p+1)^2 x n_samples <= 2^22 and otherwise returns
- * WM_ERR_INVALID_ARG without launching anything.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) and caches it:
- * make that first call before any stream capture.  Every call writes all the
- * scratch it reads, so nothing needs to start at zero; all calls share the
- * array, so calls whose work overlaps on the GPU (different streams, or
- * different host threads) race.  Stream-ordered, no synchronisation.
+ * allocate device memory: a host framework whose caching allocator owns the
+ * device memory, or code that may not call cudaMalloc because cudaMalloc can
+ * synchronise the device.  The paper has no counterpart: this is a packaging
+ * variant of wm_noise_loads with the same result (b: device [n_samples][N],
+ * caller-owned; the hierarchy's device must be the current device).  Its
+ * element-local scratch is a fixed file-scope device array of 2^22 doubles
+ * (32 MiB) that every GPU which loads the library holds until process exit; a
+ * call needs elements x (p+1)^2 x n_samples <= 2^22 and otherwise returns
+ * WM_ERR_INVALID_ARG without launching anything (so does a b that is not
+ * device memory, or a current device other than the hierarchy's).  The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it: make that first call before any stream
+ * capture.  Every call writes all the scratch it reads, so nothing needs to
+ * start at zero; all calls share the array, so calls whose work overlaps on
+ * the GPU (different streams, or different host threads) race.
+ * Stream-ordered, no synchronisation.
  */
 int wm_noise_loads_noalloc(wm_hier_t h, uint64_t seed, int n_samples, double* b, void* stream);
 
@@ -356,6 +359,11 @@ typedef struct {
                            the BPX preconditioner the paper's experiments favour
                            (Sec. 3.5): sum over levels of P D^{-1} P^T with the
                            dense coarse solve on the coarsest level              */
+  int sample0;          /* index of the first sample: the call computes the fields
+                           of samples sample0 .. sample0 + n_samples - 1 (their
+                           Philox counters), stored as rows 0 .. n_samples - 1;
+                           >= 0.  Splitting one sample range over calls (or
+                           GPUs) gives the loads of the whole range bit for bit */
 } wm_sample_desc;
 
 typedef struct {

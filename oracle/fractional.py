@@ -86,7 +86,12 @@ def scalar_sinc(beta_frac, K, lam):
 
 
 class Shifted:
-    """Factorisations of S + sigma M, cached per shift."""
+    """Factorisations of S + sigma M, cached per shift.
+
+    S + sigma M is symmetric (both bilinear forms of Sec. 3.2 are), so the LU
+    factorisation takes the symmetric minimum-degree ordering of its pattern;
+    the solve is the same direct solve, with far less fill on large meshes.
+    """
 
     def __init__(self, S, M):
         self.S = S.tocsc()
@@ -96,7 +101,7 @@ class Shifted:
     def solve(self, sigma, rhs):
         key = float(sigma)
         if key not in self.cache:
-            self.cache[key] = spla.splu((self.S + sigma * self.M).tocsc())
+            self.cache[key] = spla.splu((self.S + sigma * self.M).tocsc(), permc_spec="MMD_AT_PLUS_A")
         return self.cache[key].solve(rhs)
 
 

@@ -283,9 +283,9 @@ class Hierarchy:
     @staticmethod
     def make_desc(kappa, beta, sinc_k=0.3, l_lo=-35, l_hi=35, n_samples=1, seed=0, split="standard",
                   precision="mixed", rtol=1e-8, max_iter=200, smoother_degree=4, cheb_ratio=12.0,
-                  max_systems=0, noise_given=False, preconditioner="vcycle"):
+                  max_systems=0, noise_given=False, preconditioner="vcycle", sample0=0):
         return _capi.SampleDesc(kappa=kappa, beta=beta, split=_SPLIT[split], sinc_k=sinc_k, l_lo=l_lo, l_hi=l_hi,
-                                seed=seed, n_samples=n_samples,
+                                seed=seed, n_samples=n_samples, sample0=sample0,
                                 noise_mode=_capi.WM_NOISE_GIVEN if noise_given else _capi.WM_NOISE_DRAW,
                                 precision=_PREC[precision], rtol=rtol, max_iter=max_iter,
                                 smoother_degree=smoother_degree, cheb_ratio=cheb_ratio, max_systems=max_systems,

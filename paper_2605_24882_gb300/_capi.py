@@ -40,7 +40,7 @@ class SampleDesc(C.Structure):
                 ("l_lo", C.c_int), ("l_hi", C.c_int), ("seed", C.c_uint64), ("n_samples", C.c_int),
                 ("noise_mode", C.c_int), ("precision", C.c_int), ("rtol", C.c_double), ("max_iter", C.c_int),
                 ("smoother_degree", C.c_int), ("cheb_ratio", C.c_double), ("max_systems", C.c_int),
-                ("preconditioner", C.c_int)]
+                ("preconditioner", C.c_int), ("sample0", C.c_int)]
 
 
 class Stats(C.Structure):

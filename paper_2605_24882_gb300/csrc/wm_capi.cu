@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <new>
 
 #include "wm_solver.h"
@@ -313,6 +314,12 @@ extern "C" int wm_assemble_hierarchy(wm_geom_t geom, int n_levels, void* stream,
   }
   wm_hier* h = new (std::nothrow) wm_hier;
   if (!h) return WM_ERR_OOM;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    wm_set_error("no current CUDA device");
+    return WM_ERR_CUDA;
+  }
   h->g = g;
   h->nurbs = geom->nurbs;
   h->np = geom->np;
@@ -646,14 +653,30 @@ extern "C" int wm_vcycle(wm_hier_t h, int n_vec, const double* sigma, const doub
   int tiles = (n_vec + WM_LANES - 1) / WM_LANES;
   WM_TRY(ws.reserve(h, tiles, n_vec, precision == WM_FP64));
   std::vector<double> sg(sigma, sigma + n_vec);
+  // systems with the same shift (bit for bit) share its index: one coarse
+  // inverse and one smoother bound per distinct shift
+  std::vector<double> shl;
   std::vector<int> sid(n_vec), src(n_vec);
-  for (int g = 0; g < n_vec; ++g) sid[g] = src[g] = g;
+  {
+    std::map<uint64_t, int> index;
+    for (int g = 0; g < n_vec; ++g) {
+      uint64_t key;
+      std::memcpy(&key, &sg[g], sizeof(key));
+      auto it = index.find(key);
+      if (it == index.end()) {
+        it = index.emplace(key, (int)shl.size()).first;
+        shl.push_back(sg[g]);
+      }
+      sid[g] = it->second;
+      src[g] = g;
+    }
+  }
   WM_TRY(set_batch_meta(ws, tiles, sg, sid, src, s));
-  WM_TRY(wm_prepare_shifts(h, ws, sg, s));
+  WM_TRY(wm_prepare_shifts(h, ws, shl, s));
   Batch bt;
   bt.tiles = tiles;
   bt.nsys = n_vec;
-  bt.nshift = n_vec;
+  bt.nshift = (int)shl.size();
   bt.precision = precision;
   bt.degree = smoother_degree;
   bt.cheb_ratio = cheb_ratio;
@@ -680,8 +703,8 @@ extern "C" int wm_normals(uint64_t seed, int sample, int stream_id, int64_t q0, 
   return WM_OK;
 }
 
-// loads of samples [0, ns) into the sample-tiled buffer b_t
-static int draw_loads(wm_hier_t h, WorkSpace& ws, uint64_t seed, int ns, double* b_t, cudaStream_t s) {
+// loads of samples sample0 + [0, ns) into rows [0, ns) of the sample-tiled buffer b_t
+static int draw_loads(wm_hier_t h, WorkSpace& ws, uint64_t seed, int sample0, int ns, double* b_t, cudaStream_t s) {
   const wm_level& L = h->lv[0];
   // sample chunks bounded so that the element scratch stays below ~1 GiB
   size_t per_sample = (size_t)L.E * L.nk;
@@ -689,7 +712,7 @@ static int draw_loads(wm_hier_t h, WorkSpace& ws, uint64_t seed, int ns, double*
   WM_TRY(ws.noise_scratch.alloc(per_sample * chunk));
   for (int s0 = 0; s0 < ns; s0 += chunk) {
     int c = std::min(chunk, ns - s0);
-    WM_TRY(wm_k_noise_tiled(h, seed, s0, c, b_t, ws.noise_scratch.p, s));
+    WM_TRY(wm_k_noise_tiled(h, seed, sample0, s0, c, b_t, ws.noise_scratch.p, s));
   }
   return WM_OK;
 }
@@ -701,7 +724,7 @@ extern "C" int wm_noise_loads(wm_hier_t h, uint64_t seed, int n_samples, double*
   WorkSpace& ws = workspace(h);
   int stiles = (n_samples + WM_LANES - 1) / WM_LANES;
   WM_TRY(ws.samp[0].alloc((size_t)stiles * h->lv[0].N * WM_LANES));
-  WM_TRY(draw_loads(h, ws, seed, n_samples, ws.samp[0].p, s));
+  WM_TRY(draw_loads(h, ws, seed, 0, n_samples, ws.samp[0].p, s));
   WM_TRY(wm_k_from_tiled(ws.samp[0].p, stiles, h->lv[0].N, b, n_samples, s));
   WM_CUDA(cudaStreamSynchronize(s));
   return WM_OK;
@@ -734,7 +757,8 @@ int make_plan(const wm_sample_desc* d, Plan& P) {
 int validate_desc(wm_hier_t h, const wm_sample_desc* d) {
   if (!h || !d) return WM_ERR_INVALID_ARG;
   if (d->n_samples < 0 || d->max_iter < 1 || !(d->rtol > 0) || d->smoother_degree < 1 ||
-      d->smoother_degree > 8 || !(d->cheb_ratio > 1.0) || d->max_systems < 0) {
+      d->smoother_degree > 8 || !(d->cheb_ratio > 1.0) || d->max_systems < 0 || d->sample0 < 0 ||
+      (int64_t)d->sample0 + d->n_samples > (int64_t)INT32_MAX) {
     wm_set_error("invalid sample descriptor");
     return WM_ERR_INVALID_ARG;
   }
@@ -890,7 +914,7 @@ static int sample_fields_impl(wm_hier_t h, const wm_sample_desc* d, double* u, d
   if ((!u_dev || !b_dev)) WM_TRY(ws.samp[4].alloc((size_t)ns * N));
   // loads
   if (d->noise_mode == WM_NOISE_DRAW) {
-    WM_TRY(draw_loads(h, ws, d->seed, ns, b_t, s));
+    WM_TRY(draw_loads(h, ws, d->seed, d->sample0, ns, b_t, s));
     if (b) {
       if (b_dev) {
         WM_TRY(wm_k_from_tiled(b_t, stiles, N, b, ns, s));

@@ -165,6 +165,7 @@ struct wm_hier {
   std::vector<double> gw, gx;  // Gauss weights and nodes on [0,1]
   DevBuf<double> d_gw, d_gx;
   WorkSpace* ws = nullptr;
+  int device = 0;  // the CUDA device holding the hierarchy's buffers
 };
 
 // host helpers (wm_host_setup.cpp)
@@ -202,9 +203,10 @@ int wm_k_pack_rows(wm_level& L, cudaStream_t s);
 int wm_k_philox(const uint32_t* ctr, uint64_t key, uint32_t* out, int64_t n, cudaStream_t s);
 int wm_k_normals(uint64_t seed, int sample, int stream_id, int64_t q0, int64_t n, double* out,
                  cudaStream_t s);
-// loads of samples [s0, s0+ns) into a tiled [tiles][N][32] buffer (sample s at
-// tile s/32, lane s%32); `bl` is scratch of E*nk*ns_pad doubles
-int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int s0, int ns, double* b_tiled,
+// loads of rows [s0, s0+ns) into a tiled [tiles][N][32] buffer (row s at tile
+// s/32, lane s%32), row s holding the loads of sample sample0 + s (its Philox
+// counters); `bl` is scratch of E*nk*ns_pad doubles
+int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int sample0, int s0, int ns, double* b_tiled,
                      double* bl, cudaStream_t s);
 
 // batched operators (wm_operator.cu); vectors are [tiles][N][32]

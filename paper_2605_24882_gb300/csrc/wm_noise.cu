@@ -79,8 +79,8 @@ __global__ void k_normals(uint64_t seed, int sample, int stream, int64_t q0, int
 }
 
 // One thread per (element e, sample s0+sl): the (p+1)^2 local load
-// contributions sum_q sqrt(w_q a_q) xi_q phi_k(x_q) of the element.
-// bl layout [E][nk][ns].
+// contributions sum_q sqrt(w_q a_q) xi_q phi_k(x_q) of the element, xi the
+// Philox normals of sample s0 + sl.  bl layout [E][nk][ns].
 template <int P>
 __global__ void k_noise_local(int E, int nu, int nv, int ns, int s0, uint64_t seed,
                               const double* __restrict__ metric, const double* __restrict__ gw,
@@ -159,13 +159,13 @@ int wm_k_normals(uint64_t seed, int sample, int stream_id, int64_t q0, int64_t n
   return WM_OK;
 }
 
-int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int s0, int ns, double* b_tiled, double* bl,
+int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int sample0, int s0, int ns, double* b_tiled, double* bl,
                      cudaStream_t s) {
   const wm_level& L = h->lv[0];
   int64_t n1 = (int64_t)L.E * ns;
   unsigned g1 = (unsigned)((n1 + 127) / 128);
 #define WM_NL(PP)                                                                                        \
-  k_noise_local<PP><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, ns, s0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, \
+  k_noise_local<PP><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, ns, sample0 + s0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, \
                                        L.d_bv.p, bl)
   wm_prof_begin(WM_PC_NOISE, s);
   switch (h->p) {
@@ -186,11 +186,11 @@ int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int s0, int ns, double* b_
 }
 
 // ---------------------------------------------------------------- no-alloc entry
-// White-noise loads for callers that cannot allocate device memory (for
-// example code running inside a CUDA graph being captured, or a host framework
-// whose allocator owns all device memory).  The element-local contributions go
-// to a fixed file-scope device array instead of workspace memory; the loads are
-// gathered straight into the caller's [n][N] output.
+// White-noise loads for callers that cannot allocate device memory: a host
+// framework whose caching allocator owns the device memory, or code that may
+// not call cudaMalloc because it synchronises the device.  The element-local
+// contributions go to a fixed file-scope device array instead of workspace
+// memory; the loads are gathered straight into the caller's [n][N] output.
 #include <mutex>
 
 #define WM_NOALLOC_SCRATCH_DOUBLES (1 << 22) /* 32 MiB, resident on every device that loads the library */
@@ -213,11 +213,9 @@ __global__ void k_noise_gather_rows(int N, int ns, const int32_t* __restrict__ p
 
 // Device address of the scratch array, looked up once per device with that
 // device current (a host-side name of a __device__ array is not its address).
-int noalloc_scratch(double** out) {
+int noalloc_scratch(int dev, double** out) {
   static std::mutex mu;
   static double* addr[256] = {};
-  int dev = 0;
-  WM_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 256) return WM_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> g(mu);
   if (!addr[dev]) {
@@ -229,11 +227,31 @@ int noalloc_scratch(double** out) {
   return WM_OK;
 }
 
+// device (or managed) memory the kernels may write
+bool device_writable(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 }  // namespace
 
 extern "C" int wm_noise_loads_noalloc(wm_hier_t h, uint64_t seed, int n_samples, double* b, void* stream) {
   if (!h || n_samples < 0 || (n_samples > 0 && !b)) return WM_ERR_INVALID_ARG;
   if (n_samples == 0) return WM_OK;
+  int dev = 0;
+  WM_CUDA(cudaGetDevice(&dev));
+  if (dev != h->device) {
+    wm_set_error("wm_noise_loads_noalloc: the hierarchy lives on device %d but device %d is current", h->device, dev);
+    return WM_ERR_INVALID_ARG;
+  }
+  if (!device_writable(b)) {
+    wm_set_error("wm_noise_loads_noalloc: b must be device memory");
+    return WM_ERR_INVALID_ARG;
+  }
   const wm_level& L = h->lv[0];
   int64_t need = (int64_t)L.E * L.nk * n_samples;
   if (need > (int64_t)WM_NOALLOC_SCRATCH_DOUBLES) {
@@ -243,20 +261,21 @@ extern "C" int wm_noise_loads_noalloc(wm_hier_t h, uint64_t seed, int n_samples,
     return WM_ERR_INVALID_ARG;
   }
   double* bl = nullptr;
-  WM_TRY(noalloc_scratch(&bl));
+  WM_TRY(noalloc_scratch(dev, &bl));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int64_t n1 = (int64_t)L.E * n_samples;
   unsigned g1 = (unsigned)((n1 + 127) / 128);
   switch (h->p) {
-    case 1: k_noise_local<1><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, n_samples, 0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, L.d_bv.p, bl); break;
-    case 2: k_noise_local<2><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, n_samples, 0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, L.d_bv.p, bl); break;
-    case 3: k_noise_local<3><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, n_samples, 0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, L.d_bv.p, bl); break;
-    case 4: k_noise_local<4><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, n_samples, 0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, L.d_bv.p, bl); break;
+    case 1: WM_LAUNCH(WM_PC_NOISE, s, k_noise_local<1><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, n_samples, 0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, L.d_bv.p, bl)); break;
+    case 2: WM_LAUNCH(WM_PC_NOISE, s, k_noise_local<2><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, n_samples, 0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, L.d_bv.p, bl)); break;
+    case 3: WM_LAUNCH(WM_PC_NOISE, s, k_noise_local<3><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, n_samples, 0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, L.d_bv.p, bl)); break;
+    case 4: WM_LAUNCH(WM_PC_NOISE, s, k_noise_local<4><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, n_samples, 0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, L.d_bv.p, bl)); break;
     default: return WM_ERR_UNSUPPORTED;
   }
   WM_CUDA(cudaGetLastError());
   int64_t n2 = (int64_t)L.N * n_samples;
-  k_noise_gather_rows<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(L.N, n_samples, L.d_ng_ptr.p, L.d_ng_idx.p, bl, b);
+  WM_LAUNCH(WM_PC_NOISE, s, k_noise_gather_rows<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(
+                                L.N, n_samples, L.d_ng_ptr.p, L.d_ng_idx.p, bl, b));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }

@@ -397,14 +397,30 @@ __global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGe
 // kUniGroup consecutive tiles of one shift (a host-built list of (first tile,
 // count); `split` blocks share a group when the grid would be too small).
 // Everything that depends only on the spatial block and the shift is done
-// once for the group: the DOF ids of the window and of the output rows, every
-// thread's source offsets of its 16-byte copies, and the combined rows
+// once for the group: the DOF ids of the window and of the output rows and the
+// combined rows
 // A = S + sigma M (with the Chebyshev weights w = c2 / (dS + sigma dM)), so an
 // output costs one FMA per stencil entry and no division.  The group's tiles
-// then stream through shared memory: in float the window and rows of the next
-// tile are copied (cp.async) while the current tile is computed (two stage
-// buffers); in double a single stage buffer keeps two blocks on an SM.
+// then stream through one shared-memory stage buffer (cp.async copies of the
+// window and the output rows), four blocks to an SM in float hiding each
+// other's copy latency; two stage buffers (the next tile copied while the
+// current one is computed) measured slower at the two blocks per SM they allow.
 enum { UNI_CHEB = 0, UNI_RESID = 1, UNI_APPLY = 2, UNI_CHEBDOT = 3, UNI_CHEB1 = 4 };
+// schedule constants of the one-shift kernel: stage buffers in float, output
+// rows per step of a warp (0: two where the register budget allows), partial
+// sums per output
+#ifndef WM_UNI_NST_F32
+#define WM_UNI_NST_F32 1
+#endif
+#ifndef WM_UNI_RPS
+#define WM_UNI_RPS 1
+#endif
+#ifndef WM_UNI_NACC
+#define WM_UNI_NACC 1
+#endif
+#ifndef WM_UNI_MAXB_F32
+#define WM_UNI_MAXB_F32 4
+#endif
 template <int MODE>
 struct UniCheb {
   static constexpr bool value = MODE == UNI_CHEB || MODE == UNI_CHEBDOT;
@@ -421,7 +437,7 @@ struct UniLayout {
   static constexpr int CS = CoefStride<T, P>::value;          // (S, M) row stride of the level tables
   static constexpr int NR = UniRows<MODE>::value;
   static constexpr int ND = UniCheb<MODE>::value ? 2 : 0;     // staged diagonals dS, dM
-  static constexpr int NST = sizeof(T) == 4 ? 2 : 1;          // stage buffers
+  static constexpr int NST = sizeof(T) == 4 ? WM_UNI_NST_F32 : 1;  // stage buffers
   static constexpr size_t win = (size_t)NC * 32 * sizeof(T);  // window of the input vector
   static constexpr size_t rows = (size_t)NR * BU * BV * 32 * sizeof(T);  // staged rows of the outputs
   static constexpr size_t stage = win + rows;
@@ -463,7 +479,7 @@ template <typename T, int P, int MODE>
 struct UniMinBlocks {
   static constexpr size_t per = UniLayout<T, P, MODE>::total + 3 * 1024;
   static constexpr int fit = (int)((228 * 1024) / per);
-  static constexpr int cap = sizeof(T) == 4 ? 4 : 2;
+  static constexpr int cap = sizeof(T) == 4 ? WM_UNI_MAXB_F32 : 2;
   static constexpr int value = fit >= cap ? cap : (fit < 1 ? 1 : fit);
 };
 // 4- or 8-byte asynchronous copy through L1 (diagonal entries)
@@ -493,6 +509,10 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
   using VT = typename Vec16<T>::type;
   constexpr int SW = 2 * P + 1, CU = LY::CU, NC = LY::NC, S2 = LY::S2, S2P = LY::S2P, VEC = LY::VEC, CS = LY::CS;
   constexpr int NR = LY::NR, NST = LY::NST, ROWCH = LY::ROWCH;
+  constexpr int RPS = WM_UNI_RPS > 0 ? WM_UNI_RPS : (UniMinBlocks<T, P, MODE>::value >= 3 ? 1 : 2);
+  constexpr int NACC = WM_UNI_NACC;
+  constexpr int RW = SW + RPS - 1;     // rows of the register ring
+  static_assert(BV % RPS == 0, "rows per step divide the block height");
   constexpr int EPT = 16 / sizeof(T);  // values per 16-byte chunk
   constexpr int NT = BU * 32;          // threads per block
   constexpr size_t STAGE = LY::stage / sizeof(T);  // stage buffer length in T
@@ -553,9 +573,7 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
     sid_[c] = v;
   }
   __syncthreads();
-  // set-up 2: (S, M) rows and diagonals, and each thread's source offsets
-  // (within a tile) of its window and row chunks: -1 zero-fills a cell
-  // outside the surface, -2 marks no chunk
+  // set-up 2: (S, M) rows and diagonals, copy offsets
   constexpr int RAWCH = CS * (int)sizeof(C2) / 16;  // 16-byte chunks per (S, M) row
   for (int c = tid; c < BU * BV * RAWCH; c += NT) {
     const int part16 = c % RAWCH, o = c / RAWCH;
@@ -580,6 +598,8 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
     }
   }
   cp_async_commit();
+  // each thread's source offsets (within a tile) of its window and row
+  // chunks: -1 zero-fills a cell outside the surface, -2 marks no chunk
   int woff[LY::WPT];
 #pragma unroll
   for (int k = 0; k < LY::WPT; ++k) {
@@ -673,57 +693,79 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
       cp_async_wait<0>();
     }
     __syncthreads();
-    // each warp sweeps the column iu with a ring of SW staged rows
+    // each warp sweeps the column iu, RPS output rows per step, with a ring of
+    // RW staged rows in registers; every output sums its stencil in NACC
+    // partial sums (stencil rows dv mod NACC), so a step has NACC x RPS
+    // independent FMA chains
     const int t = ta + cur;
     const T* const sm = buf;
     const T* const srw = buf + NC * 32;
     DAcc<T> dot;   // UNI_APPLY: (z, A z); UNI_CHEBDOT: (r, z_new) over this thread's outputs
     DAcc<T> dot2;  // UNI_CHEBDOT: (z_new, q)
     if (iu < G.nlu) {
-      T win[SW][SW];
+      T win[RW][SW];
 #pragma unroll
       for (int rr = 0; rr < SW - 1; ++rr)
 #pragma unroll
         for (int du = 0; du < SW; ++du) win[rr][du] = sm[(rr * CU + w + du) * 32 + lane];
 #pragma unroll
-      for (int j = 0; j < BV; ++j) {
-        const int rnx = j + SW - 1;  // staged row entering the window
+      for (int j = 0; j < BV; j += RPS) {
 #pragma unroll
-        for (int du = 0; du < SW; ++du) win[rnx % SW][du] = sm[(rnx * CU + w + du) * 32 + lane];
-        const int o = j * BU + w;
-        const int i = srow[o];
-        if (i >= 0) {
-          const VT* cf = reinterpret_cast<const VT*>(scf + o * S2P);
-          T acc = 0;
+        for (int e = 0; e < RPS; ++e) {
+          const int rn = j + SW - 1 + e;  // staged rows entering the window
 #pragma unroll
-          for (int q = 0; q < S2P / VEC; ++q) {
-            const VT a = cf[q];
+          for (int du = 0; du < SW; ++du) win[rn % RW][du] = sm[(rn * CU + w + du) * 32 + lane];
+        }
+        T acc[RPS][NACC];
 #pragma unroll
-            for (int e = 0; e < VEC; ++e) {
-              const int sl = q * VEC + e;
-              if (sl < S2) acc = fma(Vec16<T>::at(a, e), win[(j + sl / SW) % SW][sl % SW], acc);
+        for (int k = 0; k < RPS; ++k)
+#pragma unroll
+          for (int h = 0; h < NACC; ++h) acc[k][h] = 0;
+#pragma unroll
+        for (int q = 0; q < S2P / VEC; ++q) {
+          VT a[RPS];
+#pragma unroll
+          for (int k = 0; k < RPS; ++k) a[k] = reinterpret_cast<const VT*>(scf + ((j + k) * BU + w) * S2P)[q];
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) {
+            const int sl = q * VEC + e;
+            if (sl < S2) {
+              const int dv = sl / SW, du = sl % SW;
+#pragma unroll
+              for (int k = 0; k < RPS; ++k)
+                acc[k][dv % NACC] = fma(Vec16<T>::at(a[k], e), win[(j + k + dv) % RW][du], acc[k][dv % NACC]);
             }
           }
-          const T zc = win[(j + P) % SW][P];
+        }
+#pragma unroll
+        for (int k = 0; k < RPS; ++k) {
+          const int jj = j + k;
+          const int o = jj * BU + w;
+          const int i = srow[o];
+          if (i < 0) continue;
+          T az = acc[k][0];
+#pragma unroll
+          for (int h = 1; h < NACC; ++h) az += acc[k][h];
+          const T zc = win[(jj + P) % RW][P];
           T res;
           if constexpr (CHEB) {
             const T rv = srw[o * 32 + lane];
             const T zp = prev ? srw[(BU * BV + o) * 32 + lane] : (T)0;
-            res = zc + c1 * (zc - zp) + swt[o] * (rv - acc);
+            res = zc + c1 * (zc - zp) + swt[o] * (rv - az);
             if constexpr (MODE == UNI_CHEBDOT) {
               dot.add(rv * res);
               if (qd) dot2.add(res * srw[(2 * BU * BV + o) * 32 + lane]);
             }
           } else if constexpr (MODE == UNI_CHEB1) {
-            const T dc = sdc[(j + P) * CU + w + P];  // Dinv of the output row
-            const T z1 = c20 * dc * zc;              // zc is r here
+            const T dc = sdc[(jj + P) * CU + w + P];  // Dinv of the output row
+            const T z1 = c20 * dc * zc;               // zc is r here
             out1[((size_t)t * G.N + i) * 32 + lane] = z1;
-            res = z1 + c1 * z1 + c2 * dc * (zc - acc);
+            res = z1 + c1 * z1 + c2 * dc * (zc - az);
           } else if constexpr (MODE == UNI_RESID) {
-            res = srw[o * 32 + lane] - acc;
+            res = srw[o * 32 + lane] - az;
           } else {
-            res = acc;
-            dot.add(zc * acc);
+            res = az;
+            dot.add(zc * az);
           }
           out[((size_t)t * G.N + i) * 32 + lane] = res;
         }
@@ -1072,6 +1114,7 @@ __global__ void __launch_bounds__(BU * 32, 2)
   a2[0] = tiny && mine ? HUGE_VAL : (double)accb;  // fails the caller's error check
   block_reduce<1>(a2, part_bound, t, tiles, one);
 }
+
 
 __global__ void k_build_csm(int N, int W, int cs32, int cs64, const int16_t* __restrict__ slot,
                             const double* __restrict__ S, const double* __restrict__ M, float2* __restrict__ c32,

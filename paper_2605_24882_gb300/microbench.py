@@ -42,8 +42,18 @@ def vcycle(args):
         z = hier.vcycle(r, sig, precision=args.precision, smoother_degree=args.degree, cheb_ratio=args.ratio)
     e1.record()
     torch.cuda.synchronize()
+    cats = {}
+    if args.profile:  # per-category device time of one more V-cycle (CUDA events per launch)
+        wm.profile_enable(True)
+        hier.vcycle(r, sig, precision=args.precision, smoother_degree=args.degree, cheb_ratio=args.ratio)
+        torch.cuda.synchronize()
+        prof = wm.profile_read()
+        wm.profile_enable(False)
+        cats = {k: {"ms": round(v["ms"], 4), "launches": v["timed"],
+                    "gbs": round(v["bytes"] / (v["ms"] * 1e6), 1) if v["ms"] > 0 else None}
+                for k, v in prof.items() if v["timed"] > 0}
     print(json.dumps({"bench": "vcycle", "dofs": n, "systems": args.tiles * 32, "levels": args.levels,
-                      "tiles_per_shift": args.tiles_per_shift,
+                      "tiles_per_shift": args.tiles_per_shift, "categories": cats,
                       "degree": args.degree, "ms_per_vcycle": e0.elapsed_time(e1) / max(1, args.reps),
                       "max_abs_z": float(z.abs().max())}))
 
@@ -75,6 +85,7 @@ def main():
     ap.add_argument("--levels", type=int, default=6)
     ap.add_argument("--tiles", type=int, default=71)
     ap.add_argument("--tiles-per-shift", type=int, default=1)
+    ap.add_argument("--profile", action="store_true", help="per-category times of one extra V-cycle")
     ap.add_argument("--degree", type=int, default=4)
     ap.add_argument("--ratio", type=float, default=12.0)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])

@@ -1,6 +1,6 @@
 """The bench's multi-rank logic (one replica per GPU, no data-path collective)
 on two CPU processes with the gloo backend: group set-up, barrier, the
-max-over-ranks step time, per-rank noise seeds and the whole-job rate."""
+max-over-ranks step time, the per-rank sample ranges and the whole-job rate."""
 import os
 import socket
 import sys
@@ -25,9 +25,9 @@ def _worker(rank, world, port, q):
     bench.init_group(world, rank, "gloo")
     bench.barrier(world)
     ms = bench.max_over_ranks(100.0 + 50.0 * rank, world, device="cpu")
-    seeds = [None] * world
-    dist.all_gather_object(seeds, bench.rank_seed(0, rank))
-    q.put((rank, ms, seeds, bench.job_rate(world, 256, ms)))
+    ranges = [None] * world
+    dist.all_gather_object(ranges, bench.rank_samples(rank, 256))
+    q.put((rank, ms, ranges, bench.job_rate(world, 256, ms)))
     dist.destroy_process_group()
 
 
@@ -43,9 +43,11 @@ def test_two_rank_replicas_on_gloo():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    for rank, ms, seeds, rate in out:
+    for rank, ms, ranges, rate in out:
         assert ms == 150.0                      # the slowest rank's time on every rank
-        assert len(set(seeds)) == world         # independent noise per replica
+        # the ranks' sample ranges are disjoint and together cover 0 .. world*256 - 1
+        covered = sorted(s for first, n in ranges for s in range(first, first + n))
+        assert covered == list(range(world * 256))
         assert rate == pytest.approx(2 * 256 / 0.15)
 
 
@@ -53,7 +55,7 @@ def test_single_rank_helpers():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.max_over_ranks(3.0, 1) == 3.0
-    assert bench.rank_seed(7, 0) == 7
+    assert bench.rank_samples(0, 256) == (0, 256) and bench.rank_samples(3, 64) == (192, 64)
     assert bench.job_rate(1, 256, 250.0) == pytest.approx(1024.0)
 
 

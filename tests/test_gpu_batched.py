@@ -6,9 +6,9 @@
 * The periodic bicubic torus 512 x 256 (131,072 DOFs) at full size: the
   problem is invariant under a rotation about the torus axis by one element,
   so shifting the loads by one DOF column along u must shift the fields the
-  same way (to the solver tolerance); and the mixed fields must agree with the
-  float64 path.  Neither check needs the oracle, which cannot factor 71
-  shifted matrices of this size in test time.
+  same way (to the solver tolerance); the mixed fields must agree with the
+  float64 path; and on a two-node set (two sparse LU factorisations of the
+  oracle) both precisions must match the oracle.
 """
 import numpy as np
 import pytest
@@ -19,7 +19,7 @@ from oracle.assembly import assemble
 from oracle.fractional import sample_fields as oracle_fields
 from oracle.noise import noise_loads
 from oracle.space import GluedSpace
-from wm_workloads import uneven_instances
+from wm_workloads import WORKLOADS, uneven_instances
 
 pytestmark = pytest.mark.gpu
 
@@ -86,3 +86,25 @@ def test_torus_full_size_rotation_and_fp64(wm):
     u64, st64 = hier.sample_fields(b=b, **dict(kw, precision="fp64"))
     assert st64["n_not_converged"] == 0
     assert float(rel(u, u64).max()) < 1e-6
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", 1e-6), ("fp64", 1e-9)])
+def test_torus_full_size_against_the_oracle(wm, precision, tol):
+    # the 512 x 256 bicubic torus of the torus workload, through its whole
+    # hierarchy and kernel configuration, against the oracle's direct solves on
+    # a two-node set (one sparse LU per shift) and two samples
+    c = WORKLOADS["torus_p3_512x256_s1024"]
+    kw = dict(kappa=c["kappa"], beta=c["beta"], sinc_k=c["k"], l_lo=-1, l_hi=0, n_samples=2, seed=c["seed"],
+              precision=precision, rtol=1e-10 if precision == "mixed" else 1e-12,
+              smoother_degree=c["smoother_degree"], cheb_ratio=c["cheb_ratio"])
+    hier = wm.Hierarchy(wm.Geometry("torus", 3, c["n_u"], c["n_v"], c["R"], c["r"]), c["levels"])
+    u, b, st = hier.sample_fields(return_loads=True, **kw)
+    assert st["n_not_converged"] == 0 and st["n_systems"] == 2 * 2
+    sp_ = GluedSpace(geo.Surface("torus", 3, c["n_u"], c["n_v"], c["R"], c["r"]))
+    S, M = assemble(sp_)
+    b_or = noise_loads(sp_, c["seed"], 2)
+    np.testing.assert_allclose(b.cpu().numpy(), b_or, rtol=1e-11, atol=1e-13 * np.abs(b_or).max())
+    u_or = oracle_fields(S, M, b_or, c["kappa"], c["beta"], c["k"], -1, 0)
+    d = u.cpu().numpy() - u_or
+    err = np.sqrt(np.einsum("si,si->s", d, (M @ d.T).T) / np.einsum("si,si->s", u_or, (M @ u_or.T).T))
+    assert err.max() < tol, (err, st)

@@ -200,3 +200,21 @@ def test_failure_reporting_not_converged_and_nonfinite(wm):
     with pytest.raises(wm.WMError) as e:
         hier.sample_fields(b=b, **kw)
     assert e.value.code == _capi.WM_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sample_range_split_reproduces_the_whole_run(wm, precision):
+    # A replica job splits one sample range: the rank holding samples n .. 2n - 1
+    # calls with sample0 = n.  Its loads must be rows n .. 2n - 1 of a 2n-sample
+    # run bit for bit (and the oracle's loads of those samples), its fields the same.
+    from oracle.noise import noise_loads
+    n = 32
+    hier = wm.Hierarchy(wm.Geometry("sphere", 2, 16), 4)
+    kw = dict(kappa=3.0, beta=1.3, sinc_k=0.4, l_lo=-20, l_hi=20, seed=9, precision=precision, rtol=1e-10)
+    u2, b2, st2 = hier.sample_fields(return_loads=True, n_samples=2 * n, **kw)
+    u1, b1, st1 = hier.sample_fields(return_loads=True, n_samples=n, sample0=n, **kw)
+    assert torch.equal(b1, b2[n:])
+    sp_ = GluedSpace(geo.Surface("sphere", 2, 16))
+    b_or = noise_loads(sp_, 9, 2 * n)[n:]
+    np.testing.assert_allclose(b1.cpu().numpy(), b_or, rtol=1e-11, atol=1e-13 * np.abs(b_or).max())
+    torch.testing.assert_close(u1, u2[n:], rtol=1e-12, atol=1e-14 * float(u2.abs().max()))

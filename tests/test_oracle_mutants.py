@@ -98,8 +98,8 @@ MUTANTS = [
      "y_lo = math.log(tol * (1.0 - g) * mu / (3.0 * s)) / g"),
     ("scalar_sinc_step", "fractional.py", "sinc_rule(beta_frac, 2.0 / math.sqrt(K), -K, K)",
      "sinc_rule(beta_frac, 1.0 / math.sqrt(K), -K, K)"),
-    ("shifted_operands_swapped", "fractional.py", "spla.splu((self.S + sigma * self.M).tocsc())",
-     "spla.splu((self.M + sigma * self.S).tocsc())"),
+    ("shifted_operands_swapped", "fractional.py", "spla.splu((self.S + sigma * self.M).tocsc(), permc_spec",
+     "spla.splu((self.M + sigma * self.S).tocsc(), permc_spec"),
     ("apply_drop_mass", "fractional.py", "    rhs = M @ v\n", "    rhs = v\n"),
     ("apply_shift_kappa", "fractional.py", "x = sh.solve(math.exp(yl) + kappa**2, rhs)", "x = sh.solve(math.exp(yl) + kappa, rhs)"),
     ("integer_extra_solve", "fractional.py", "        for _ in range(n - 1):\n            w = sh.solve(kappa**2, M @ w)\n        v = w",
