@@ -312,6 +312,48 @@ def fp64_legs(hier, kw, u_mixed, N, systems_per_sample, args):
     return out
 
 
+def secondary_leg(wm, name, pk, pk_kind, args):
+    """A second workload on the same GPU, same protocol at fewer steps: one
+    warm-up step, `secondary_steps` timed steps with profiling off, then one
+    profiled step for the per-kernel times and the dominant kernel's roofline."""
+    import torch
+    c = WORKLOADS[name]
+    hier = wm.Hierarchy(wm.Geometry(c["kind"], c["p"], c["n_u"], c["n_v"], c.get("R", 1.0), c.get("r", 0.4)),
+                        c["levels"])
+    N = hier.num_dofs(0)
+    ns = c["n_samples"]
+    kw = dict(kappa=c["kappa"], beta=c["beta"], sinc_k=c["k"], l_lo=c["l_lo"], l_hi=c["l_hi"], n_samples=ns,
+              seed=c["seed"], split=c["split"], precision=c["precision"], rtol=c["rtol"],
+              smoother_degree=c.get("smoother_degree", 4), cheb_ratio=c.get("cheb_ratio", 12.0))
+    u = torch.empty((ns, N), dtype=torch.float64, device="cuda")
+    _, stats = hier.sample_fields(out=u, **kw)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.secondary_steps):
+        _, stats = hier.sample_fields(out=u, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.secondary_steps
+    wm.profile_enable(True)
+    hier.sample_fields(out=u, **kw)
+    torch.cuda.synchronize()
+    prof = wm.profile_read()
+    wm.profile_enable(False)
+    rl, _ = roofline(prof, pk, pk_kind)
+    n_int, _, passes = wm.beta_plan(c["beta"], c["split"])
+    systems = ns * (n_int + passes * (c["l_hi"] - c["l_lo"] + 1))
+    out = {"workload": name, "surface": surface_text(c), "dofs": N, "samples": ns, "systems_per_step": systems,
+           "value": ns / (ms / 1e3), "unit": "samples/s", "ms_per_step": ms, "steps": args.secondary_steps,
+           "warmup": 1, "dof_solves_per_s": N * systems / (ms / 1e3), "precision": c["precision"],
+           "solver": {k: stats[k] for k in ("max_iterations", "n_not_converged", "max_rel_residual", "n_batches")},
+           "roofline": rl, "kernel_ms_per_step": {k: v["ms"] for k, v in prof.items() if v["ms"] > 0}}
+    del u, hier
+    torch.cuda.empty_cache()
+    return out
+
+
 def our_arm(args):
     import torch
 
@@ -407,6 +449,10 @@ def our_arm(args):
         legs["speedup_batched_mixed_vs_plain_fp64"] = value / world / legs["plain_fp64_one_system_at_a_time"]["value"]
         legs["speedup_batched_mixed_vs_batched_fp64"] = value / world / legs["batched_fp64"]["value"]
         line["fp64_comparison"] = legs
+    if world == 1 and args.secondary and args.secondary != args.workload:
+        del u, hier
+        torch.cuda.empty_cache()
+        line["secondary"] = secondary_leg(wm, args.secondary, pk, pk_kind, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, total, sample, _ = oracle_estimate(c)
         line["cpu_baseline"] = {"value": v, "unit": "samples/s", "cores": 1, "host_cores": os.cpu_count(),
@@ -437,6 +483,9 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=2,
                     help="steps of the separate profiled pass (per-kernel times, roofline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--secondary", default="torus_p3_512x256_s1024",
+                    help="a second workload reported in the line's `secondary` object ('' for none)")
+    ap.add_argument("--secondary-steps", type=int, default=2)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

@@ -1374,8 +1374,8 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
         bool done = false;
         if constexpr (std::is_same<T, float>::value) {
           if (df_res) {
-            WM_TRY(wm_sten_true_residual_df(L0, h->np, h->p, tiles, ws.sigma.p, ws.x.p, rhs_tiled, ws.src_of.p,
-                                               ws.rep.p, ws.tile_rep.p, r, ws.part[1].p, ws.part[2].p, s));
+            WM_TRY(wm_sten_true_residual_df(L0, h->np, h->p, tiles, uni_of(ws), ws.sigma.p, ws.x.p, rhs_tiled,
+                                            ws.src_of.p, ws.rep.p, ws.tile_rep.p, r, ws.part[1].p, ws.part[2].p, s));
             WM_CUDA(cudaMemsetAsync(cnt + 5, 0, sizeof(int), s));
             WM_LAUNCH(WM_PC_SCALAR, s, k_df_check<<<sb, 128, 0, s>>>(nsys_pad, ch_op, ws.part[2].p, ws.bb.p,
                                                                      0.01 * rtol2, ws.rep.p, cnt + 5));

@@ -421,6 +421,9 @@ enum { UNI_CHEB = 0, UNI_RESID = 1, UNI_APPLY = 2, UNI_CHEBDOT = 3, UNI_CHEB1 = 
 #ifndef WM_UNI_MAXB_F32
 #define WM_UNI_MAXB_F32 4
 #endif
+#ifndef WM_UNI_MAXB_F32_P3
+#define WM_UNI_MAXB_F32_P3 4
+#endif
 template <int MODE>
 struct UniCheb {
   static constexpr bool value = MODE == UNI_CHEB || MODE == UNI_CHEBDOT;
@@ -479,7 +482,7 @@ template <typename T, int P, int MODE>
 struct UniMinBlocks {
   static constexpr size_t per = UniLayout<T, P, MODE>::total + 3 * 1024;
   static constexpr int fit = (int)((228 * 1024) / per);
-  static constexpr int cap = sizeof(T) == 4 ? WM_UNI_MAXB_F32 : 2;
+  static constexpr int cap = sizeof(T) == 4 ? (P == 3 ? WM_UNI_MAXB_F32_P3 : WM_UNI_MAXB_F32) : 2;
   static constexpr int value = fit >= cap ? cap : (fit < 1 ? 1 : fit);
 };
 // 4- or 8-byte asynchronous copy through L1 (diagonal entries)
@@ -955,7 +958,8 @@ __global__ void __launch_bounds__(BU * 32, 2)
     k_sten_trueres_df(StenGeo G, const float4* __restrict__ cdf, const double* __restrict__ x, int tiles,
                       const int* __restrict__ tile_rep, const double* __restrict__ sigma,
                       const double* __restrict__ rhs, const int* __restrict__ src_of, const int* __restrict__ rep,
-                      float* __restrict__ r, double* __restrict__ part, double* __restrict__ part_bound) {
+                      float* __restrict__ r, double* __restrict__ part, double* __restrict__ part_bound,
+                      const int* __restrict__ skip_uni) {
   using LY = DfLayout<P>;
   constexpr int SW = 2 * P + 1, CU = LY::CU, NC = LY::NC, S2 = LY::S2;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -972,7 +976,7 @@ __global__ void __launch_bounds__(BU * 32, 2)
   const int bv = b % G.nbv;
   const int m = b / G.nbv;
   const int t = blockIdx.y;
-  if (t >= tiles || !tile_rep[t]) return;
+  if (t >= tiles || !tile_rep[t] || (skip_uni && skip_uni[t])) return;  // skip: done by the group kernel
   const int g = t * 32 + lane;
   const double sg = sigma[g];
   bool tiny = false;  // a value of this system too small for float pairs
@@ -1115,6 +1119,154 @@ __global__ void __launch_bounds__(BU * 32, 2)
   block_reduce<1>(a2, part_bound, t, tiles, one);
 }
 
+// The same residual for groups of one-shift tiles (the list of the one-shift
+// kernel): a block computes its window's DOF ids and the combined double-float
+// rows A = S + sigma M of its shift once, then streams the x windows of the
+// group's flagged tiles through shared memory.
+template <int P>
+struct DfUniLayout {
+  static constexpr int CU = BU + 2 * P, CV = BV + 2 * P, NC = CU * CV, S2 = (2 * P + 1) * (2 * P + 1);
+  static constexpr size_t win = (size_t)NC * 32 * sizeof(double);          // x window (raw rows at set-up)
+  static constexpr size_t raw = (size_t)BU * BV * S2 * sizeof(float4);      // (S_hi, S_lo, M_hi, M_lo) rows
+  static constexpr size_t pairs = (size_t)BU * (BV / 2) * S2 * sizeof(float4);  // combined row pairs
+  static constexpr size_t ids = (size_t)(NC + BU * BV) * sizeof(int);
+  static constexpr size_t total = win + pairs + ids;
+  static_assert(raw <= win, "the raw rows are staged in the window area");
+};
+
+template <int P>
+__global__ void __launch_bounds__(BU * 32, 3)
+    k_sten_trueres_df_uni(StenGeo G, const float4* __restrict__ cdf, const double* __restrict__ x, int tiles,
+                          const int* __restrict__ tile_rep, const int2* __restrict__ groups, int split,
+                          const double* __restrict__ sigma, const double* __restrict__ rhs,
+                          const int* __restrict__ src_of, const int* __restrict__ rep, float* __restrict__ r,
+                          double* __restrict__ part, double* __restrict__ part_bound) {
+  using LY = DfUniLayout<P>;
+  constexpr int SW = 2 * P + 1, CU = LY::CU, NC = LY::NC, S2 = LY::S2;
+  constexpr int NT = BU * 32;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* smd = reinterpret_cast<double*>(smraw);
+  float2* smf = reinterpret_cast<float2*>(smraw);  // the same cells after the split
+  float4* sraw = reinterpret_cast<float4*>(smraw);  // set-up only
+  float4* scf = reinterpret_cast<float4*>(smraw + LY::win);
+  int* sid = reinterpret_cast<int*>(smraw + LY::win + LY::pairs);
+  int* srow = sid + NC;
+  __shared__ int s_tiny[BU][32];
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int tid = w * 32 + lane;
+  int b = blockIdx.x;
+  const int bu = b % G.nbu;
+  b /= G.nbu;
+  const int bv = b % G.nbv;
+  const int m = b / G.nbv;
+  const int2 gr = groups[blockIdx.y / split];
+  const int sp = blockIdx.y % split;
+  const int per = (gr.y + split - 1) / split;
+  const int ta = gr.x + sp * per;
+  const int tb = min(min(gr.x + gr.y, ta + per), tiles);
+  unsigned todo = 0;  // flagged tiles of the range, bit t - ta
+  for (int t = ta; t < tb; ++t)
+    if (tile_rep[t]) todo |= 1u << (t - ta);
+  if (todo == 0) return;
+  bool tiny = false;
+  const float2 sgp = split_bits(sigma[gr.x * 32], tiny);  // the group's shift (a tiny shift only loses itself)
+  // set-up: global DOF of every window cell and every output row
+  const int32_t* E = G.ext + (size_t)m * G.ELV * G.ELU;
+  const int32_t* OWN = G.own + (size_t)m * G.nlv * G.nlu;
+  for (int c = tid; c < NC + BU * BV; c += NT) {
+    int v = -1;
+    if (c < NC) {
+      int eu = bu * BU + c % CU, ev = bv * BV + c / CU;
+      if (eu < G.ELU && ev < G.ELV) v = E[(size_t)ev * G.ELU + eu];
+    } else {
+      int o = c - NC;
+      int iu = bu * BU + o % BU, iv = bv * BV + o / BU;
+      if (iu < G.nlu && iv < G.nlv) v = OWN[(size_t)iv * G.nlu + iu];
+    }
+    sid[c] = v;
+  }
+  __syncthreads();
+  for (int c = tid; c < BU * BV * S2; c += NT) {
+    const int o = c / S2, k = c % S2;
+    const int gi = srow[o];
+    cp_async16(sraw + c, gi >= 0 ? cdf + (size_t)gi * S2 + k : cdf, gi >= 0 ? 16 : 0);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // combined rows A = S + sigma M as row pairs: entry (pair jj*BU + w, slot) =
+  // (A_hi of rows 2jj and 2jj+1, A_lo of both), the operands of the packed loop
+  for (int c = tid; c < BU * (BV / 2) * S2; c += NT) {
+    const int pi = c / S2, sl = c - pi * S2;
+    const int o0 = (pi / BU) * 2 * BU + pi % BU;  // rows 2jj and 2jj+1 of column w
+    const float4 q0 = sraw[o0 * S2 + sl], q1 = sraw[(o0 + BU) * S2 + sl];
+    const float2 a0 = df_axpy(q0.x, q0.y, sgp.x, sgp.y, q0.z, q0.w);
+    const float2 a1 = df_axpy(q1.x, q1.y, sgp.x, sgp.y, q1.z, q1.w);
+    scf[c] = make_float4(a0.x, a1.x, a0.y, a1.y);
+  }
+  __syncthreads();  // the raw rows are dead: the window area is free
+  const int iu = bu * BU + w;
+  while (todo) {
+    const int t = ta + __ffs(todo) - 1;
+    todo &= todo - 1;
+    const int g = t * 32 + lane;
+    const bool mine = rep[g] != 0;
+    const int src = src_of[g];
+    for (int c = tid; c < NC * 16; c += NT) {  // x window: 16 chunks of 16 bytes per cell
+      const int part16 = c % 16, cell = c / 16;
+      const int gi = sid[cell];
+      cp_async16(smd + (size_t)cell * 32 + part16 * 2, gi >= 0 ? x + ((size_t)t * G.N + gi) * 32 + part16 * 2 : x,
+                 gi >= 0 ? 16 : 0);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    tiny = false;
+    for (int c = tid; c < NC * 32; c += NT) smf[c] = split_bits(smd[c], tiny);  // lane c % 32 == lane
+    s_tiny[w][lane] = tiny;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BU; ++k) tiny |= s_tiny[k][lane] != 0;
+    float acc = 0.f, accb = 0.f;
+    auto emit = [&](int i, float s, float c, float bnd) {
+      if (!mine) return;
+      const float2 bp = split_bits(src >= 0 ? rhs[((size_t)(src / 32) * G.N + i) * 32 + (src % 32)] : 0.0, tiny);
+      float d, de;
+      two_sum(bp.x, -s, d, de);
+      const float rt = __fadd_rn(d, __fadd_rn(de, __fsub_rn(bp.y, c)));
+      r[((size_t)t * G.N + i) * 32 + lane] = rt;
+      acc = fmaf(rt, rt, acc);
+      accb = fmaf(bnd, bnd, accb);
+    };
+    if (iu < G.nlu) {
+#pragma unroll 1
+      for (int j = 0; j < BV; j += 2) {
+        const int i0 = srow[j * BU + w], i1 = srow[(j + 1) * BU + w];
+        if (i0 < 0 && i1 < 0) continue;  // rows past the patch edge or owned by another patch
+        const float4* cf = scf + (size_t)((j / 2) * BU + w) * S2;  // row pair (j, j+1)
+        const float2* zw = smf + ((size_t)j * CU + w) * 32 + lane;
+        float2 spp = make_float2(0.f, 0.f), cpp = make_float2(0.f, 0.f);
+        float b0 = 0.f, b1 = 0.f;
+#pragma unroll
+        for (int dv = 0; dv < SW; ++dv)
+#pragma unroll
+          for (int du = 0; du < SW; ++du) {
+            const float4 q = cf[dv * SW + du];
+            const float2 z0 = zw[(dv * CU + du) * 32], z1 = zw[((dv + 1) * CU + du) * 32];
+            df_acc2(spp, cpp, b0, b1, make_float2(q.x, q.y), make_float2(q.z, q.w), make_float2(z0.x, z1.x),
+                    make_float2(z0.y, z1.y));
+          }
+        if (i0 >= 0) emit(i0, spp.x, cpp.x, b0);
+        if (i1 >= 0) emit(i1, spp.y, cpp.y, b1);
+      }
+    }
+    const bool one[1] = {true};
+    double a2[1] = {(double)acc};
+    block_reduce<1>(a2, part, t, tiles, one);
+    __syncthreads();
+    a2[0] = tiny && mine ? HUGE_VAL : (double)accb;  // fails the caller's error check
+    block_reduce<1>(a2, part_bound, t, tiles, one);
+    __syncthreads();  // the window and the reduction buffer may be refilled
+  }
+}
 
 __global__ void k_build_csm(int N, int W, int cs32, int cs64, const int16_t* __restrict__ slot,
                             const double* __restrict__ S, const double* __restrict__ M, float2* __restrict__ c32,
@@ -1341,28 +1493,47 @@ int wm_sten_true_residual(const wm_level& L, int np, int p, int tiles, const dou
 }
 
 template <int P>
-static int launch_df(const wm_level& L, int np, int tiles, const double* sigma, const double* x, const double* rhs,
-                     const int* src_of, const int* rep, const int* tile_rep, float* r, double* part,
+static int launch_df(const wm_level& L, int np, int tiles, const UniTiles& ut, const double* sigma, const double* x,
+                     const double* rhs, const int* src_of, const int* rep, const int* tile_rep, float* r, double* part,
                      double* part_bound, cudaStream_t s) {
   constexpr size_t sm = DfLayout<P>::total;
+  constexpr size_t smu = DfUniLayout<P>::total;
   static bool configured = false;
   if (!configured) {
     WM_CUDA(cudaFuncSetAttribute(k_sten_trueres_df<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    WM_CUDA(cudaFuncSetAttribute(k_sten_trueres_df_uni<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smu));
     configured = true;
   }
-  dim3 grid(np * L.nbu * L.nbv, tiles);
-  WM_LAUNCH(WM_PC_TRUERES, s, k_sten_trueres_df<P><<<grid, dim3(32, BU), sm, s>>>(
-                                  geo_of(L), L.d_csmdf.p, x, tiles, tile_rep, sigma, rhs, src_of, rep, r, part,
-                                  part_bound));
-  WM_CUDA(cudaGetLastError());
+  const int bx = np * L.nbu * L.nbv;
+  if (ut.n_groups > 0) {
+    static const int sms = device_sms();
+    const int64_t want = 4LL * sms * 3;
+    int split = 1;
+    while (split < kUniGroup && (int64_t)bx * ut.n_groups * split < want) split *= 2;
+    const int gmax = 65535 / split;
+    for (int g0 = 0; g0 < ut.n_groups; g0 += gmax) {
+      const int ng = std::min(gmax, ut.n_groups - g0);
+      WM_LAUNCH(WM_PC_TRUERES, s, k_sten_trueres_df_uni<P><<<dim3(bx, ng * split), dim3(32, BU), smu, s>>>(
+                                      geo_of(L), L.d_csmdf.p, x, tiles, tile_rep, ut.groups + g0, split, sigma, rhs,
+                                      src_of, rep, r, part, part_bound));
+      WM_CUDA(cudaGetLastError());
+    }
+  }
+  if (ut.n < tiles) {
+    dim3 grid(bx, tiles);
+    WM_LAUNCH(WM_PC_TRUERES, s, k_sten_trueres_df<P><<<grid, dim3(32, BU), sm, s>>>(
+                                    geo_of(L), L.d_csmdf.p, x, tiles, tile_rep, sigma, rhs, src_of, rep, r, part,
+                                    part_bound, ut.n > 0 ? ut.flag : nullptr));
+    WM_CUDA(cudaGetLastError());
+  }
   return WM_OK;
 }
 
-int wm_sten_true_residual_df(const wm_level& L, int np, int p, int tiles, const double* sigma, const double* x,
-                             const double* rhs, const int* src_of, const int* rep, const int* tile_rep, float* r,
-                             double* part, double* part_bound, cudaStream_t s) {
+int wm_sten_true_residual_df(const wm_level& L, int np, int p, int tiles, const UniTiles& ut, const double* sigma,
+                             const double* x, const double* rhs, const int* src_of, const int* rep,
+                             const int* tile_rep, float* r, double* part, double* part_bound, cudaStream_t s) {
   WM_DISPATCH_P(p, {
-    return launch_df<PP>(L, np, tiles, sigma, x, rhs, src_of, rep, tile_rep, r, part, part_bound, s);
+    return launch_df<PP>(L, np, tiles, ut, sigma, x, rhs, src_of, rep, tile_rep, r, part, part_bound, s);
   });
   return WM_OK;
 }

@@ -77,6 +77,7 @@ int wm_sten_true_residual(const wm_level& L, int np, int p, int tiles, const dou
 // arithmetic on the FP32 pipes; part_bound receives the per-block partial
 // sums of ||B||^2 with B_i = sum_j |a_ij| |x_j| (the rounding error of entry i
 // is below 2^-42 B_i), or +inf for a system with a value below 2^-102
-int wm_sten_true_residual_df(const wm_level& L, int np, int p, int tiles, const double* sigma, const double* x,
-                             const double* rhs, const int* src_of, const int* rep, const int* tile_rep, float* r,
-                             double* part, double* part_bound, cudaStream_t s);
+// (one-shift tiles of `ut` by groups, the others one tile per block)
+int wm_sten_true_residual_df(const wm_level& L, int np, int p, int tiles, const UniTiles& ut, const double* sigma,
+                             const double* x, const double* rhs, const int* src_of, const int* rep,
+                             const int* tile_rep, float* r, double* part, double* part_bound, cudaStream_t s);
