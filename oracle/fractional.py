@@ -151,44 +151,57 @@ def sample_fields(S, M, b, kappa, beta, k, l_lo, l_hi, mode=STANDARD, sh=None):
 def field_loss_grad(S, M, b, g, kappa, beta, k, l_lo, l_hi, mode=STANDARD):
     """Loss L = sum_s ||u_s - g_s||_M^2 and its gradients by the adjoint identity.
 
-    Returns (L, dL/db [ns, N], dL/dkappa).  Covers the standard split with
-    n = 0 or n >= 1 and one fractional pass.  Derivation: u = sum_l c_l x_l,
-    x_l = A_l^{-1} r, A_l = S + sigma_l M, sigma_l = e^{y_l} + kappa^2, with the
-    symmetric A_l: dL/dr = sum_l c_l z_l, z_l = A_l^{-1} gt, gt = 2 M (u - g);
-    dx_l/dkappa = -A_l^{-1} (2 kappa M) x_l.  The integer chain w_i = A0^{-1} M w_{i-1}
-    (A0 = S + kappa^2 M, w_1 = A0^{-1} b, r = M w_n) is differentiated the same way.
+    Returns (L, dL/db [ns, N], dL/dkappa) for every split: n >= 0 integer
+    solves and 0, 1 or 2 fractional passes (the improved split of Sec. 3.4
+    applies the sinc map twice, the second time to M times the first result).
+    Derivation: a pass maps its right-hand side r to v = sum_l c_l x_l,
+    x_l = A_l^{-1} r, A_l = S + sigma_l M, sigma_l = e^{y_l} + kappa^2.  With
+    the symmetric A_l its adjoint maps dL/dv to dL/dr = sum_l c_l z_l,
+    z_l = A_l^{-1} dL/dv, and dx_l/dkappa = -A_l^{-1} (2 kappa M) x_l adds
+    -2 kappa c_l z_l^T M x_l to dL/dkappa; dL/du = gt = 2 M (u - g).  A pass
+    after the first (or after integer solves) takes r = M v_prev, so
+    dL/dv_prev = M dL/dr.  The integer chain w_i = A0^{-1} M w_{i-1}
+    (A0 = S + kappa^2 M, w_1 = A0^{-1} b) is differentiated the same way.
     """
     sh = Shifted(S, M)
     n, bp, passes = split_beta(beta, mode)
-    if passes != 1:
-        raise NotImplementedError("gradient for one fractional pass")
     y, c = sinc_rule(bp, k, l_lo, l_hi)
     sig = np.exp(y) + kappa**2
     B = np.asarray(b, dtype=np.float64).T
     ws = []
+    v = None
     if n >= 1:
         w = sh.solve(kappa**2, B)
         ws.append(w)
         for _ in range(n - 1):
             w = sh.solve(kappa**2, M @ w)
             ws.append(w)
-        r = M @ w
-    else:
-        r = B
-    xs = [sh.solve(s, r) for s in sig]
-    u = sum(cl * x for cl, x in zip(c, xs))
+        v = w
+    # fractional passes: the right-hand side is b (first pass with n = 0) or M v
+    xss = []
+    for _ in range(passes):
+        r = B if v is None else M @ v
+        xs = [sh.solve(s, r) for s in sig]
+        v = sum(cl * x for cl, x in zip(c, xs))
+        xss.append(xs)
+    u = v
     G = np.asarray(g, dtype=np.float64).T
     d = u - G
     L = float(np.sum(d * (M @ d)))
     gt = 2.0 * (M @ d)
-    zs = [sh.solve(s, gt) for s in sig]
-    dLdr = sum(cl * z for cl, z in zip(c, zs))
     dk = 0.0
-    for cl, x, z in zip(c, xs, zs):
-        dk += -2.0 * kappa * cl * float(np.sum(z * (M @ x)))
+    dout = gt  # dL/d(output of the step being differentiated)
+    dLdr = None
+    for p_ in range(passes - 1, -1, -1):
+        zs = [sh.solve(s, dout) for s in sig]
+        dLdr = sum(cl * z for cl, z in zip(c, zs))
+        for cl, x, z in zip(c, xss[p_], zs):
+            dk += -2.0 * kappa * cl * float(np.sum(z * (M @ x)))
+        if p_ > 0 or n >= 1:
+            dout = M @ dLdr  # r = M v_prev
     if n >= 1:
-        # r = M w_n; w_i = A0^{-1} M w_{i-1}; adjoint lambda_n = A0^{-1} M dLdr
-        lam = sh.solve(kappa**2, M @ dLdr)
+        # dL/dw_n = dout; w_i = A0^{-1} (M w_{i-1}) (w_1 = A0^{-1} b): lambda_i = A0^{-1} dL/dw_i
+        lam = sh.solve(kappa**2, dout)
         for i in range(n - 1, -1, -1):
             # w_{i+1} depends on kappa through A0: dw/dkappa = -A0^{-1} 2 kappa M w
             dk += -2.0 * kappa * float(np.sum(lam * (M @ ws[i])))

@@ -69,23 +69,27 @@ def test_harmonic_rhs_scalar_sinc():
     np.testing.assert_allclose(u, fr.scalar_sinc(beta, K, lam) * y_coef, rtol=0, atol=3e-3 * np.abs(y_coef).max())
 
 
-@pytest.mark.parametrize("beta", [0.8, 1.3])
-def test_gradient_matches_finite_differences(tiny, beta):
+@pytest.mark.parametrize("beta,mode", [(0.8, fr.STANDARD), (1.3, fr.STANDARD), (2.0, fr.STANDARD),
+                                       (0.9, fr.IMPROVED), (1.5, fr.IMPROVED), (1.9, fr.IMPROVED)])
+def test_gradient_matches_finite_differences(tiny, beta, mode):
+    # every split: one pass (0.8, 1.3), integer beta (2.0: no pass), two passes
+    # with n = 0, 0 and 1 integer solves (improved split: 0.9, 1.5, 1.9)
     sp_, S, M, mu, V, b = tiny
     kappa, k, lo, hi = 1.7, 0.5, -12, 12
     g = np.random.default_rng(1).standard_normal(b.shape)
-    L, dLdb, dLdk = fr.field_loss_grad(S, M, b, g, kappa, beta, k, lo, hi)
+    L, dLdb, dLdk = fr.field_loss_grad(S, M, b, g, kappa, beta, k, lo, hi, mode)
     h = 1e-6
-    Lp = fr.field_loss_grad(S, M, b, g, kappa + h, beta, k, lo, hi)[0]
-    Lm = fr.field_loss_grad(S, M, b, g, kappa - h, beta, k, lo, hi)[0]
+    Lp = fr.field_loss_grad(S, M, b, g, kappa + h, beta, k, lo, hi, mode)[0]
+    Lm = fr.field_loss_grad(S, M, b, g, kappa - h, beta, k, lo, hi, mode)[0]
     assert dLdk == pytest.approx((Lp - Lm) / (2 * h), rel=1e-6)
     d = np.random.default_rng(2).standard_normal(b.shape)
-    Lp = fr.field_loss_grad(S, M, b + h * d, g, kappa, beta, k, lo, hi)[0]
-    Lm = fr.field_loss_grad(S, M, b - h * d, g, kappa, beta, k, lo, hi)[0]
+    Lp = fr.field_loss_grad(S, M, b + h * d, g, kappa, beta, k, lo, hi, mode)[0]
+    Lm = fr.field_loss_grad(S, M, b - h * d, g, kappa, beta, k, lo, hi, mode)[0]
     assert float(np.sum(dLdb * d)) == pytest.approx((Lp - Lm) / (2 * h), rel=1e-6)
-    # closed form of the loss through the eigen-decomposition
-    n, bp, _ = fr.split_beta(beta)
-    sym = (kappa ** 2 + mu) ** -float(n) * _sinc_symbol(bp, kappa, k, lo, hi, mu)
+    # closed form of the loss through the eigen-decomposition: each pass
+    # multiplies mode mu by the sinc symbol, each integer solve by 1/(kappa^2 + mu)
+    n, bp, passes = fr.split_beta(beta, mode)
+    sym = (kappa ** 2 + mu) ** -float(n) * _sinc_symbol(bp, kappa, k, lo, hi, mu) ** passes
     u = (V @ (sym[:, None] * (V.T @ b.T))).T
     dd = u - g
     assert L == pytest.approx(float(np.sum(dd * (M @ dd.T).T)), rel=1e-10)

@@ -135,6 +135,10 @@ MUTANTS = [
     ("bounds_unscaled", "sqrt_mass.py", "A / d[:, :, None] / d[:, None, :]", "A / d[:, :, None]"),
     ("adjoint_drop_integer_term", "fractional.py", "dk += -2.0 * kappa * float(np.sum(lam * (M @ ws[i])))",
      "pass"),
+    ("adjoint_pass_drop_mass", "fractional.py", "            dout = M @ dLdr  # r = M v_prev",
+     "            dout = dLdr  # r = M v_prev"),
+    ("adjoint_pass_wrong_iterates", "fractional.py", "for cl, x, z in zip(c, xss[p_], zs):",
+     "for cl, x, z in zip(c, xss[0], zs):"),
 ]
 
 CONFTEST = (
