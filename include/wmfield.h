@@ -66,6 +66,10 @@ extern "C" {
 #define WM_PRECOND_VCYCLE 0  /* multiplicative: one V-cycle per CG iteration       */
 #define WM_PRECOND_BPX 1     /* additive: BPX multilevel diagonal scaling           */
 
+#define WM_CKPT_RECOMPUTE 0  /* the backward re-solves the forward systems it needs */
+#define WM_CKPT_KEEP 1       /* forward solutions are kept for the backward when
+                                they fit in half of the free device memory         */
+
 /* ---- geometry ------------------------------------------------------------- */
 typedef struct {
   int kind;      /* WM_SPHERE6 or WM_TORUS                                        */
@@ -364,6 +368,18 @@ typedef struct {
                            Philox counters), stored as rows 0 .. n_samples - 1;
                            >= 0.  Splitting one sample range over calls (or
                            GPUs) gives the loads of the whole range bit for bit */
+  int ckpt;             /* WM_CKPT_RECOMPUTE or WM_CKPT_KEEP.  In wm_sample_fields,
+                           KEEP keeps the per-node solutions x_{l,s} of every
+                           fractional pass, the pass right-hand sides, the
+                           integer iterates and the loads in the hierarchy's
+                           workspace (replacing an earlier checkpoint) when they
+                           fit in half of the free device memory; a following
+                           wm_sample_fields_backward with the same descriptor
+                           and the same loads then solves the adjoint systems
+                           only.  In the backward, KEEP also keeps the solutions
+                           of a first pass (improved split) between its forward
+                           and adjoint sweeps when they fit, instead of solving
+                           them twice                                           */
 } wm_sample_desc;
 
 typedef struct {
@@ -379,6 +395,10 @@ typedef struct {
   int n_replacements;     /* float64 true-residual evaluations (system count)       */
   int n_df_fallbacks;     /* batches whose double-float residual failed its error
                              check and switched to float64 (mixed precision)        */
+  int ckpt_kept;          /* wm_sample_fields: 1 when the forward solutions were
+                             kept (WM_CKPT_KEEP and enough memory)                   */
+  int ckpt_used;          /* wm_sample_fields_backward: 1 when it took the forward
+                             solutions from a matching checkpoint                   */
 } wm_stats;
 
 /*
@@ -408,16 +428,23 @@ int wm_sample_fields_batched(int n_inst, const wm_hier_t* h, const wm_sample_des
  * [n_samples][N] (device) for the fields of `desc` with loads b (device,
  * [n_samples][N], e.g. those returned by wm_sample_fields), returns
  * grad_b = dL/db (device [n_samples][N], may be NULL) and *grad_kappa = dL/dkappa
- * (host, may be NULL).  The operator is symmetric, so the adjoint reuses the
- * batched shifted solves on grad_u:  z_{l,s} = (S + sigma_l M)^{-1} grad_u_s,
- * dL/db_s = sum_l c_l z_{l,s} (chained through the integer solves), and
- * dL/dkappa = -2 kappa sum_{l,s} c_l z_{l,s}^T M x_{l,s} (+ integer-solve terms).
- * The forward solutions x_{l,s} are recomputed per batch of max_systems.
- * Standard split with one fractional pass (or integer beta) only.
+ * (host, may be NULL), for every split (integer beta, one fractional pass, or
+ * the improved split's two passes, Sec. 3.4).  The operator is symmetric, so
+ * the adjoint reuses the batched shifted solves: a pass with right-hand side
+ * r and nodes (c_l, sigma_l) maps dL/d(out) to dL/dr = sum_l c_l z_l,
+ * z_l = (S + sigma_l M)^{-1} dL/d(out), and adds
+ * -2 kappa sum_l c_l z_l^T M x_l (x_l its forward solutions) to dL/dkappa; a
+ * pass fed by M v passes M dL/dr back to v; the integer solves
+ * w_i = (S + kappa^2 M)^{-1} M w_{i-1} are chained the same way.  The forward
+ * solutions come from a matching WM_CKPT_KEEP checkpoint of wm_sample_fields
+ * (same descriptor fields and bit-identical loads), else they are recomputed
+ * per batch of max_systems.  stats: host, may be NULL (systems, iterations,
+ * ckpt_used).  The stream is synchronised before return.
+ * Errors as wm_sample_fields; WM_ERR_INVALID_ARG also for host buffers.
  */
 int wm_sample_fields_backward(wm_hier_t h, const wm_sample_desc* desc, const double* b,
                               const double* grad_u, double* grad_b, double* grad_kappa,
-                              void* stream);
+                              wm_stats* stats, void* stream);
 
 /* Integer/fractional split of beta (Sec. 3.4): n_int, beta_frac, n_passes. */
 int wm_beta_plan(double beta, int split, int* n_int, double* beta_frac, int* n_passes);

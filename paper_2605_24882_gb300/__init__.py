@@ -283,9 +283,10 @@ class Hierarchy:
     @staticmethod
     def make_desc(kappa, beta, sinc_k=0.3, l_lo=-35, l_hi=35, n_samples=1, seed=0, split="standard",
                   precision="mixed", rtol=1e-8, max_iter=200, smoother_degree=4, cheb_ratio=12.0,
-                  max_systems=0, noise_given=False, preconditioner="vcycle", sample0=0):
+                  max_systems=0, noise_given=False, preconditioner="vcycle", sample0=0, ckpt="recompute"):
         return _capi.SampleDesc(kappa=kappa, beta=beta, split=_SPLIT[split], sinc_k=sinc_k, l_lo=l_lo, l_hi=l_hi,
                                 seed=seed, n_samples=n_samples, sample0=sample0,
+                                ckpt={"recompute": _capi.WM_CKPT_RECOMPUTE, "keep": _capi.WM_CKPT_KEEP}[ckpt],
                                 noise_mode=_capi.WM_NOISE_GIVEN if noise_given else _capi.WM_NOISE_DRAW,
                                 precision=_PREC[precision], rtol=rtol, max_iter=max_iter,
                                 smoother_degree=smoother_degree, cheb_ratio=cheb_ratio, max_systems=max_systems,
@@ -313,13 +314,17 @@ class Hierarchy:
             return u, b, st.as_dict()
         return u, st.as_dict()
 
-    def sample_fields_backward(self, b, grad_u, stream=None, **kw):
+    def sample_fields_backward(self, b, grad_u, stream=None, return_stats=False, **kw):
+        """(dL/db, dL/dkappa) for loads b and dL/du = grad_u (and the stats dict)."""
         d = self.make_desc(noise_given=True, **kw)
         gb = torch.empty_like(b)
         gk = C.c_double(0.0)
+        st = _capi.Stats()
         check(lib().wm_sample_fields_backward(self._h, C.byref(d), _dev_f64(b, "b"), _dev_f64(grad_u, "grad_u"),
-                                              _dev_f64(gb, "grad_b"), C.byref(gk), _stream(stream)),
+                                              _dev_f64(gb, "grad_b"), C.byref(gk), C.byref(st), _stream(stream)),
               "wm_sample_fields_backward")
+        if return_stats:
+            return gb, gk.value, st.as_dict()
         return gb, gk.value
 
 
@@ -358,12 +363,17 @@ class WMField(torch.autograd.Function):
     runs the adjoint solves (wm_sample_fields_backward) for dL/db and dL/dkappa.
 
     ``kw`` holds the remaining sampler parameters (beta, sinc_k, l_lo, l_hi,
-    n_samples, precision, rtol, ...), without kappa and b.
+    n_samples, precision, rtol, ...), without kappa and b.  The forward keeps
+    its per-node solutions in the hierarchy's workspace when they fit
+    (``ckpt="keep"``, the default here), so that the backward solves only the
+    adjoint systems; ``ckpt="recompute"`` re-solves them in the backward.
     """
 
     @staticmethod
     def forward(ctx, b, kappa, hier, kw):
         kappa_f = float(kappa)
+        kw = dict(kw)
+        kw.setdefault("ckpt", "keep")
         u, _ = hier.sample_fields(b=b.detach().contiguous(), kappa=kappa_f, **kw)
         ctx.save_for_backward(b)
         ctx.hier, ctx.kw, ctx.kappa = hier, kw, kappa_f

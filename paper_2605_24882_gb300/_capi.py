@@ -23,6 +23,8 @@ WM_SPLIT_STANDARD = 0
 WM_SPLIT_IMPROVED = 1
 WM_NOISE_DRAW = 0
 WM_NOISE_GIVEN = 1
+WM_CKPT_RECOMPUTE = 0
+WM_CKPT_KEEP = 1
 
 
 class GeomDesc(C.Structure):
@@ -40,14 +42,15 @@ class SampleDesc(C.Structure):
                 ("l_lo", C.c_int), ("l_hi", C.c_int), ("seed", C.c_uint64), ("n_samples", C.c_int),
                 ("noise_mode", C.c_int), ("precision", C.c_int), ("rtol", C.c_double), ("max_iter", C.c_int),
                 ("smoother_degree", C.c_int), ("cheb_ratio", C.c_double), ("max_systems", C.c_int),
-                ("preconditioner", C.c_int), ("sample0", C.c_int)]
+                ("preconditioner", C.c_int), ("sample0", C.c_int), ("ckpt", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("n_systems", C.c_int), ("n_batches", C.c_int), ("max_iterations", C.c_int),
                 ("total_iterations", C.c_int), ("n_not_converged", C.c_int), ("max_rel_residual", C.c_double),
                 ("n_int_solves", C.c_int), ("n_frac_passes", C.c_int), ("n_nodes", C.c_int),
-                ("n_replacements", C.c_int), ("n_df_fallbacks", C.c_int)]
+                ("n_replacements", C.c_int), ("n_df_fallbacks", C.c_int), ("ckpt_kept", C.c_int),
+                ("ckpt_used", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,7 +92,8 @@ _PROTOS = {
     "wm_sample_fields": (_i, [_vp, C.POINTER(SampleDesc), _vp, _vp, C.POINTER(Stats), _vp]),
     "wm_sample_fields_batched": (_i, [_i, C.POINTER(_vp), C.POINTER(SampleDesc), C.POINTER(_vp),
                                       C.POINTER(Stats), _vp]),
-    "wm_sample_fields_backward": (_i, [_vp, C.POINTER(SampleDesc), _vp, _vp, _vp, C.POINTER(_d), _vp]),
+    "wm_sample_fields_backward": (_i, [_vp, C.POINTER(SampleDesc), _vp, _vp, _vp, C.POINTER(_d), C.POINTER(Stats),
+                                       _vp]),
     "wm_beta_plan": (_i, [_d, _i, C.POINTER(_i), C.POINTER(_d), C.POINTER(_i)]),
     "wm_sinc_nodes": (_i, [_d, _i, _d, _d, C.POINTER(_d), C.POINTER(_i), C.POINTER(_i)]),
     "wm_profile_enable": (_i, [_i]),

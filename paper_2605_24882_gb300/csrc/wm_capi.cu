@@ -764,6 +764,10 @@ int validate_desc(wm_hier_t h, const wm_sample_desc* d) {
   }
   if (d->precision != WM_FP64 && d->precision != WM_MIXED) return WM_ERR_INVALID_ARG;
   if (d->noise_mode != WM_NOISE_DRAW && d->noise_mode != WM_NOISE_GIVEN) return WM_ERR_INVALID_ARG;
+  if (d->ckpt != WM_CKPT_RECOMPUTE && d->ckpt != WM_CKPT_KEEP) {
+    wm_set_error("unknown checkpoint policy %d", d->ckpt);
+    return WM_ERR_INVALID_ARG;
+  }
   if (d->preconditioner != WM_PRECOND_VCYCLE && d->preconditioner != WM_PRECOND_BPX) {
     wm_set_error("unknown preconditioner %d", d->preconditioner);
     return WM_ERR_INVALID_ARG;
@@ -884,6 +888,59 @@ int run_pass(wm_hier_t h, WorkSpace& ws, const wm_sample_desc* d, const Pass& ps
 
 // Sample-tiled buffers: samp[0] loads, samp[1] current iterate, samp[2]
 // accumulator, samp[3] pass right-hand side, samp[4] staging of host outputs.
+
+namespace {
+
+// descriptor fields that decide the forward solutions (the loads are compared
+// separately, bit for bit)
+bool same_solutions(const wm_sample_desc& a, const wm_sample_desc& b) {
+  return a.kappa == b.kappa && a.beta == b.beta && a.split == b.split && a.sinc_k == b.sinc_k && a.l_lo == b.l_lo &&
+         a.l_hi == b.l_hi && a.n_samples == b.n_samples && a.sample0 == b.sample0 && a.precision == b.precision &&
+         a.rtol == b.rtol && a.max_iter == b.max_iter && a.smoother_degree == b.smoother_degree &&
+         a.cheb_ratio == b.cheb_ratio && a.max_systems == b.max_systems && a.preconditioner == b.preconditioner;
+}
+
+__global__ void k_count_diff(size_t n, const double* __restrict__ a, const double* __restrict__ b, int* cnt) {
+  size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (k < n && __double_as_longlong(a[k]) != __double_as_longlong(b[k])) atomicAdd(cnt, 1);
+}
+
+// true when the n doubles of a and b are identical bit for bit
+int equal_bits(WorkSpace& ws, const double* a, const double* b, size_t n, bool* eq, cudaStream_t s) {
+  int* cnt = ws.counters.p + 7;
+  WM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+  WM_LAUNCH(WM_PC_SINC, s, k_count_diff<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, a, b, cnt));
+  WM_CUDA(cudaGetLastError());
+  WM_CUDA(cudaMemcpyAsync(ws.host_small + 12, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+  WM_CUDA(cudaStreamSynchronize(s));
+  *eq = ws.host_small[12] == 0;
+  return WM_OK;
+}
+
+// whether `bytes` more may be kept: at most half of the free device memory
+bool may_keep(size_t bytes) {
+  size_t freeb = 0, totb = 0;
+  if (cudaMemGetInfo(&freeb, &totb) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return bytes <= freeb / 2;
+}
+
+// the fractional pass of a plan: all nodes x samples
+Pass frac_pass(const Plan& P, int ns, int nshift_total) {
+  Pass fp;
+  fp.sigma = P.sigma;
+  fp.ns = ns;
+  fp.sid_base = 0;
+  fp.nshift_total = nshift_total;
+  return fp;
+}
+
+size_t pass_tiles(const Plan& P, int ns) { return ((size_t)P.sigma.size() * ns + WM_LANES - 1) / WM_LANES; }
+
+}  // namespace
+
 static int sample_fields_impl(wm_hier_t h, const wm_sample_desc* d, double* u, double* b, wm_stats* st,
                               cudaStream_t s) {
   WM_TRY(validate_desc(h, d));
@@ -940,6 +997,26 @@ static int sample_fields_impl(wm_hier_t h, const wm_sample_desc* d, double* u, d
                       d->precision == WM_FP64));
     WM_TRY(wm_prepare_shifts(h, ws, shifts, s));
   }
+  // checkpoint for the backward: loads, integer iterates, pass right-hand sides
+  // and every pass's solutions, when asked for and when they fit
+  WorkSpace::Ckpt& ck = ws.ck;
+  bool keep = false;
+  if (d->ckpt == WM_CKPT_KEEP) {
+    ck.release();
+    const size_t xt = pass_tiles(P, ns) * N * WM_LANES;
+    const size_t bytes = sizeof(double) * (sn * (1 + P.n_int + P.passes) + xt * P.passes);
+    keep = may_keep(bytes);
+    if (keep) {
+      WM_TRY(ck.b.alloc(sn));
+      WM_TRY(wm_copy(b_t, ck.b.p, sn, s));
+      ck.w.resize(P.n_int);
+      for (int i = 0; i < P.n_int; ++i) WM_TRY(ck.w[i].alloc(sn));
+      for (int p = 0; p < P.passes; ++p) {
+        WM_TRY(ck.r[p].alloc(sn));
+        WM_TRY(ck.x[p].alloc(xt));
+      }
+    }
+  }
   // integer part: (S + kappa^2 M) w_1 = b, (S + kappa^2 M) w_i = M w_{i-1}
   Pass ip;
   ip.sigma = {d->kappa * d->kappa};
@@ -959,28 +1036,37 @@ static int sample_fields_impl(wm_hier_t h, const wm_sample_desc* d, double* u, d
       return wm_copy(ws.x.p, cur + off, n, ss);
     };
     WM_TRY(run_pass(h, ws, d, ip, r, st, &worst, sink, s));
+    if (keep) WM_TRY(wm_copy(cur, ck.w[i].p, sn, s));
   }
   // fractional passes
   if (P.passes > 0) {
     WM_TRY(ws.coef.upload(P.c, s));
-    Pass fp;
-    fp.sigma = P.sigma;
-    fp.ns = ns;
-    fp.sid_base = 0;
-    fp.nshift_total = (int)shifts.size();
+    const Pass fp = frac_pass(P, ns, (int)shifts.size());
     for (int pass = 0; pass < P.passes; ++pass) {
       const double* r = b_t;
       if (P.n_int > 0 || pass > 0) {
         WM_TRY(wm_k_apply_mass64(L0, stiles, cur, rhs, nullptr, s));
         r = rhs;
       }
+      if (keep) WM_TRY(wm_copy(r, ck.r[pass].p, sn, s));
       WM_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * sn, s));
+      double* xk = keep ? ck.x[pass].p : nullptr;
       auto sink = [&](int g0, int g1, cudaStream_t ss) -> int {
+        if (xk) {
+          size_t off = (size_t)(g0 / WM_LANES) * N * WM_LANES;
+          size_t n = (size_t)((g1 - g0 + WM_LANES - 1) / WM_LANES) * N * WM_LANES;
+          WM_TRY(wm_copy(ws.x.p, xk + off, n, ss));
+        }
         return wm_sinc_accumulate(h, ns, g0, g1, ws.coef.p, ws.x.p, acc, ss);
       };
       WM_TRY(run_pass(h, ws, d, fp, r, st, &worst, sink, s));
       std::swap(cur, acc);
     }
+  }
+  if (keep) {
+    ck.desc = *d;
+    ck.valid = true;
+    if (st) st->ckpt_kept = 1;
   }
   // fields
   if (u_dev) {
@@ -1015,23 +1101,22 @@ extern "C" int wm_sample_fields_batched(int n_inst, const wm_hier_t* h, const wm
   return worst;
 }
 
-// Adjoint of the sampler for a scalar loss L(u): with A_l = S + sigma_l M
-// symmetric, dL/dr_s = sum_l c_l A_l^{-1} dL/du_s and
-// dL/dkappa = -2 kappa sum_{l,s} c_l z_{l,s}^T M x_{l,s} (x: forward solutions,
-// z: adjoint solutions; sigma_l = e^{y_l} + kappa^2).  Through the integer part
-// r = M w_n, w_i = A0^{-1} M w_{i-1}, w_1 = A0^{-1} b: lambda_n = A0^{-1} M dL/dr,
-// lambda_{i-1} = A0^{-1} M lambda_i, dL/db = lambda_1, and each solve adds
-// -2 kappa lambda_i^T M w_i.  Each batch of shifted systems is solved forward
-// (its solutions kept as the batch checkpoint) and then adjoint.
+// Adjoint of the sampler for a scalar loss L(u) (see the header).  Buffers:
+// samp[0] loads, samp[1] dL/du, samp[2] dL/dr of the current pass (then the
+// integer-chain adjoints lambda_i), samp[3] M-products; per batch ws.x holds
+// the forward solutions (when recomputed) and then the adjoint solutions, and
+// ws.mx the M-products of the forward ones.
 extern "C" int wm_sample_fields_backward(wm_hier_t h, const wm_sample_desc* d, const double* b, const double* grad_u,
-                                         double* grad_b, double* grad_kappa, void* stream) {
+                                         double* grad_b, double* grad_kappa, wm_stats* st, void* stream) {
   WM_TRY(validate_desc(h, d));
   if (!b || !grad_u) return WM_ERR_INVALID_ARG;
   Plan P;
   WM_TRY(make_plan(d, P));
-  if (P.passes > 1) {
-    wm_set_error("backward supports one fractional pass (standard split)");
-    return WM_ERR_UNSUPPORTED;
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->n_int_solves = P.n_int;
+    st->n_frac_passes = P.passes;
+    st->n_nodes = (int)P.c.size();
   }
   int ns = d->n_samples;
   if (ns == 0) {
@@ -1050,10 +1135,10 @@ extern "C" int wm_sample_fields_backward(wm_hier_t h, const wm_sample_desc* d, c
   const double kappa = d->kappa;
   WorkSpace& ws = workspace(h);
   for (int k = 0; k < 4; ++k) WM_TRY(ws.samp[k].alloc(sn));
-  double* b_t = ws.samp[0].p;   // loads
-  double* g_t = ws.samp[1].p;   // dL/du
-  double* dr = ws.samp[2].p;    // dL/dr accumulator, then lambda
-  double* tmp = ws.samp[3].p;   // M-products
+  double* b_t = ws.samp[0].p;
+  double* g_t = ws.samp[1].p;
+  double* dr = ws.samp[2].p;
+  double* tmp = ws.samp[3].p;
   WM_TRY(wm_k_to_tiled(b, ns, N, b_t, stiles, s));
   WM_TRY(wm_k_to_tiled(grad_u, ns, N, g_t, stiles, s));
   int worst = WM_OK;
@@ -1064,89 +1149,138 @@ extern "C" int wm_sample_fields_backward(wm_hier_t h, const wm_sample_desc* d, c
   int tiles_max_f = (int)((per_batch_f + WM_LANES - 1) / WM_LANES);
   WM_TRY(ws.reserve(h, tiles_max_f, (int)shifts.size(), d->precision == WM_FP64));
   WM_TRY(wm_prepare_shifts(h, ws, shifts, s));
-  // forward integer chain, keeping every iterate
-  ws.chain.resize(P.n_int);
+  WM_TRY(ws.mx.alloc((size_t)tiles_max_f * N * WM_LANES));
   Pass ip;
   ip.sigma = {kappa * kappa};
   ip.ns = ns;
   ip.sid_base = (int)P.sigma.size();
   ip.nshift_total = (int)shifts.size();
-  for (int i = 0; i < P.n_int; ++i) {
-    WM_TRY(ws.chain[i].alloc(sn));
-    const double* r = b_t;
-    if (i > 0) {
-      WM_TRY(wm_k_apply_mass64(L0, stiles, ws.chain[i - 1].p, tmp, nullptr, s));
-      r = tmp;
+  const Pass fp = frac_pass(P, ns, (int)shifts.size());
+  if (P.passes > 0) WM_TRY(ws.coef.upload(P.c, s));
+  // forward quantities: integer iterates w_i, pass right-hand sides r_p and
+  // (where kept) every system's pass solution x_p
+  std::vector<const double*> wv(P.n_int, nullptr);
+  const double* rp[2] = {nullptr, nullptr};
+  const double* xp[2] = {nullptr, nullptr};
+  bool use_ck = false;
+  if (d->ckpt == WM_CKPT_KEEP && ws.ck.valid && same_solutions(ws.ck.desc, *d) && ws.ck.b.n == sn)
+    WM_TRY(equal_bits(ws, b_t, ws.ck.b.p, sn, &use_ck, s));
+  if (use_ck) {
+    for (int i = 0; i < P.n_int; ++i) wv[i] = ws.ck.w[i].p;
+    for (int p = 0; p < P.passes; ++p) {
+      rp[p] = ws.ck.r[p].p;
+      xp[p] = ws.ck.x[p].p;
     }
-    double* wi = ws.chain[i].p;
-    auto sink = [&](int g0, int g1, cudaStream_t ss) -> int {
-      size_t off = (size_t)(g0 / WM_LANES) * N * WM_LANES;
-      size_t n = (size_t)((g1 - g0 + WM_LANES - 1) / WM_LANES) * N * WM_LANES;
-      return wm_copy(ws.x.p, wi + off, n, ss);
-    };
-    WM_TRY(run_pass(h, ws, d, ip, r, nullptr, &worst, sink, s));
+    if (st) st->ckpt_used = 1;
+  } else {
+    // integer chain, keeping every iterate
+    ws.chain.resize(P.n_int);
+    for (int i = 0; i < P.n_int; ++i) {
+      WM_TRY(ws.chain[i].alloc(sn));
+      const double* r = b_t;
+      if (i > 0) {
+        WM_TRY(wm_k_apply_mass64(L0, stiles, ws.chain[i - 1].p, tmp, nullptr, s));
+        r = tmp;
+      }
+      double* wi = ws.chain[i].p;
+      auto sink = [&](int g0, int g1, cudaStream_t ss) -> int {
+        size_t off = (size_t)(g0 / WM_LANES) * N * WM_LANES;
+        size_t n = (size_t)((g1 - g0 + WM_LANES - 1) / WM_LANES) * N * WM_LANES;
+        return wm_copy(ws.x.p, wi + off, n, ss);
+      };
+      WM_TRY(run_pass(h, ws, d, ip, r, st, &worst, sink, s));
+      wv[i] = wi;
+    }
+    // pass right-hand sides; every pass but the last is solved forward for the
+    // next one's right-hand side (its solutions kept when asked for and they fit)
+    const double* v = P.n_int > 0 ? wv[P.n_int - 1] : nullptr;
+    for (int p = 0; p < P.passes; ++p) {
+      if (v == nullptr) {
+        rp[p] = b_t;
+      } else {
+        WM_TRY(ws.rpass[p].alloc(sn));
+        WM_TRY(wm_k_apply_mass64(L0, stiles, v, ws.rpass[p].p, nullptr, s));
+        rp[p] = ws.rpass[p].p;
+      }
+      if (p + 1 == P.passes) break;
+      const size_t xt = pass_tiles(P, ns) * N * WM_LANES;
+      double* xk = nullptr;
+      if (d->ckpt == WM_CKPT_KEEP && (ws.xpass[p].n >= xt || may_keep(sizeof(double) * xt))) {
+        WM_TRY(ws.xpass[p].alloc(xt));
+        xk = ws.xpass[p].p;
+      }
+      WM_TRY(ws.vpass.alloc(sn));
+      WM_CUDA(cudaMemsetAsync(ws.vpass.p, 0, sizeof(double) * sn, s));
+      auto sink = [&](int g0, int g1, cudaStream_t ss) -> int {
+        if (xk) {
+          size_t off = (size_t)(g0 / WM_LANES) * N * WM_LANES;
+          size_t n = (size_t)((g1 - g0 + WM_LANES - 1) / WM_LANES) * N * WM_LANES;
+          WM_TRY(wm_copy(ws.x.p, xk + off, n, ss));
+        }
+        return wm_sinc_accumulate(h, ns, g0, g1, ws.coef.p, ws.x.p, ws.vpass.p, ss);
+      };
+      WM_TRY(run_pass(h, ws, d, fp, rp[p], st, &worst, sink, s));
+      xp[p] = xk;
+      v = ws.vpass.p;
+    }
   }
-  // fractional pass: forward then adjoint per batch
-  WM_CUDA(cudaMemsetAsync(dr, 0, sizeof(double) * sn, s));
-  if (P.passes == 1) {
-    // r = M w_n (or b); kept in tmp for the whole pass
-    const double* r = b_t;
-    if (P.n_int > 0) {
-      WM_TRY(wm_k_apply_mass64(L0, stiles, ws.chain[P.n_int - 1].p, tmp, nullptr, s));
-      r = tmp;
-    }
-    WM_TRY(ws.coef.upload(P.c, s));
-    Pass fp;
-    fp.sigma = P.sigma;
-    fp.ns = ns;
-    fp.sid_base = 0;
-    fp.nshift_total = (int)shifts.size();
-    int nj = (int)P.sigma.size();
-    int64_t nsys = (int64_t)nj * ns;
-    int64_t per_batch = per_batch_f;
-    int tiles_max = tiles_max_f;
-    WM_TRY(ws.mx.alloc((size_t)tiles_max * N * WM_LANES));
-    for (int64_t g0 = 0; g0 < nsys; g0 += per_batch) {
-      int64_t g1 = std::min(nsys, g0 + per_batch);
-      int tiles = (int)((g1 - g0 + WM_LANES - 1) / WM_LANES);
-      size_t n = (size_t)tiles * N * WM_LANES;
-      WM_TRY(solve_range(h, ws, d, fp, g0, g1, r, nullptr, &worst, s));
-      WM_TRY(wm_k_apply_mass64(L0, tiles, ws.x.p, ws.mx.p, nullptr, s));  // M x (checkpoint as M x)
-      WM_TRY(solve_range(h, ws, d, fp, g0, g1, g_t, nullptr, &worst, s));
+  // adjoint of the passes, last first: dL/d(out) -> dL/dr = sum_l c_l z_l, with
+  // z_l = A_l^{-1} dL/d(out); dL/dkappa += -2 kappa sum_l c_l z_l^T M x_l
+  const double* dout = g_t;
+  for (int p = P.passes - 1; p >= 0; --p) {
+    const int64_t nsys = (int64_t)P.sigma.size() * ns;
+    WM_CUDA(cudaMemsetAsync(dr, 0, sizeof(double) * sn, s));
+    for (int64_t g0 = 0; g0 < nsys; g0 += per_batch_f) {
+      const int64_t g1 = std::min(nsys, g0 + per_batch_f);
+      const int tiles = (int)((g1 - g0 + WM_LANES - 1) / WM_LANES);
+      if (grad_kappa) {
+        const double* xb = nullptr;
+        if (xp[p]) {
+          xb = xp[p] + (size_t)(g0 / WM_LANES) * N * WM_LANES;
+        } else {
+          WM_TRY(solve_range(h, ws, d, fp, g0, g1, rp[p], st, &worst, s));
+          xb = ws.x.p;
+        }
+        WM_TRY(wm_k_apply_mass64(L0, tiles, xb, ws.mx.p, nullptr, s));
+      }
+      WM_TRY(solve_range(h, ws, d, fp, g0, g1, dout, st, &worst, s));
       WM_TRY(wm_sinc_accumulate(h, ns, (int)g0, (int)g1, ws.coef.p, ws.x.p, dr, s));
       if (grad_kappa) {
         WM_TRY(wm_system_dots(ws, tiles, N, ws.x.p, ws.mx.p, dots, s));
         for (int64_t g = g0; g < g1; ++g) dk += -2.0 * kappa * P.c[(size_t)(g / ns)] * dots[(size_t)(g - g0)];
       }
-      (void)n;
     }
-  } else {
-    // integer beta: dL/dw_n = dL/du
-    WM_TRY(wm_copy(g_t, dr, sn, s));
-  }
-  // integer chain adjoint
-  if (P.n_int > 0) {
-    for (int i = P.n_int - 1; i >= 0; --i) {
-      // lambda_{i+1} = A0^{-1} (M * incoming), incoming = dL/dr for the last solve
-      const double* incoming = dr;
-      if (P.passes == 1 || i < P.n_int - 1) {
-        WM_TRY(wm_k_apply_mass64(L0, stiles, dr, tmp, nullptr, s));
-        incoming = tmp;
-      }
-      auto sink = [&](int g0, int g1, cudaStream_t ss) -> int {
-        size_t off = (size_t)(g0 / WM_LANES) * N * WM_LANES;
-        size_t nn = (size_t)((g1 - g0 + WM_LANES - 1) / WM_LANES) * N * WM_LANES;
-        return wm_copy(ws.x.p, dr + off, nn, ss);
-      };
-      WM_TRY(run_pass(h, ws, d, ip, incoming, nullptr, &worst, sink, s));
-      if (grad_kappa) {
-        WM_TRY(wm_k_apply_mass64(L0, stiles, ws.chain[i].p, tmp, nullptr, s));
-        WM_TRY(wm_system_dots(ws, stiles, N, dr, tmp, dots, s));
-        for (int g = 0; g < ns; ++g) dk += -2.0 * kappa * dots[g];
-      }
+    if (p > 0 || P.n_int > 0) {  // this pass's right-hand side was M v: dL/dv = M dL/dr
+      WM_TRY(wm_k_apply_mass64(L0, stiles, dr, tmp, nullptr, s));
+      dout = tmp;
+    } else {
+      dout = dr;  // n = 0: the first pass took the loads themselves
     }
   }
-  if (grad_b) WM_TRY(wm_k_from_tiled(dr, stiles, N, grad_b, ns, s));
+  // integer chain: dL/dw_n = dout; lambda_i = A0^{-1} dL/dw_i, dL/dw_{i-1} = M lambda_i,
+  // dL/dkappa += -2 kappa lambda_i^T M w_i, dL/db = lambda_1
+  for (int i = P.n_int - 1; i >= 0; --i) {
+    // dout is M dL/dr of the first pass (or dL/du for integer beta), never dr
+    const double* incoming = dout;
+    if (i < P.n_int - 1) {
+      WM_TRY(wm_k_apply_mass64(L0, stiles, dr, tmp, nullptr, s));
+      incoming = tmp;
+    }
+    auto sink = [&](int g0, int g1, cudaStream_t ss) -> int {
+      size_t off = (size_t)(g0 / WM_LANES) * N * WM_LANES;
+      size_t nn = (size_t)((g1 - g0 + WM_LANES - 1) / WM_LANES) * N * WM_LANES;
+      return wm_copy(ws.x.p, dr + off, nn, ss);
+    };
+    WM_TRY(run_pass(h, ws, d, ip, incoming, st, &worst, sink, s));
+    if (grad_kappa) {
+      WM_TRY(wm_k_apply_mass64(L0, stiles, wv[i], tmp, nullptr, s));
+      WM_TRY(wm_system_dots(ws, stiles, N, dr, tmp, dots, s));
+      for (int g = 0; g < ns; ++g) dk += -2.0 * kappa * dots[g];
+    }
+  }
+  // dL/db: lambda_1 with integer solves, else dL/dr of the first pass
+  const double* gb = P.n_int > 0 ? dr : (P.passes > 0 ? dout : g_t);
+  if (grad_b) WM_TRY(wm_k_from_tiled(gb, stiles, N, grad_b, ns, s));
   WM_CUDA(cudaStreamSynchronize(s));
   if (grad_kappa) *grad_kappa = dk;
   return worst;

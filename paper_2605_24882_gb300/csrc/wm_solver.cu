@@ -1009,6 +1009,12 @@ void WorkSpace::release() {
   ckpt.release(); mx.release(); dots.release();
   for (auto& c : chain) c.release();
   chain.clear();
+  for (int k = 0; k < 2; ++k) {
+    rpass[k].release();
+    xpass[k].release();
+  }
+  vpass.release();
+  ck.release();
   if (host_small) cudaFreeHost(host_small);
   host_small = nullptr;
 }

@@ -82,6 +82,28 @@ struct WorkSpace {
   DevBuf<double> coef;        // sinc weights of the current pass
   DevBuf<double> ckpt, mx, dots;  // adjoint: forward solutions of a batch, M x, per-system dots
   std::vector<DevBuf<double>> chain;  // adjoint: integer-part iterates w_1..w_n (sample-tiled)
+  DevBuf<double> rpass[2], xpass[2], vpass;  // adjoint: pass right-hand sides, kept pass solutions, pass result
+  // Forward checkpoint for the backward (WM_CKPT_KEEP): the loads, the integer
+  // iterates w_1..w_n and the pass right-hand sides (sample-tiled), and the
+  // solution of every system of each fractional pass ([tiles][N][32], system
+  // g = j n_s + s of the pass); valid for the descriptor `desc`.
+  struct Ckpt {
+    bool valid = false;
+    wm_sample_desc desc{};
+    DevBuf<double> b;
+    std::vector<DevBuf<double>> w;
+    DevBuf<double> r[2], x[2];
+    void release() {
+      valid = false;
+      b.release();
+      for (auto& v : w) v.release();
+      w.clear();
+      for (int k = 0; k < 2; ++k) {
+        r[k].release();
+        x[k].release();
+      }
+    }
+  } ck;
   // shifts whose smoother bounds and coarse inverses are in lmax / ainv
   std::vector<double> prep_shifts;
   const double* prep_lmax = nullptr;

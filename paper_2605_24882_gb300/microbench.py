@@ -14,6 +14,13 @@ transfer kernels.
     python -m paper_2605_24882_gb300.microbench sqrt [--kind sphere] [--p 2]
         [--elems 64] [--samples 64] [--nodes 12] [--rtol 1e-10] [--reps 2]
 
+    python -m paper_2605_24882_gb300.microbench adjoint [--precision fp64]
+
+`adjoint` times the differentiation workload (sphere 6 x 128 x 128, p = 3,
+101,402 DOFs, 64 samples, kappa = 4, beta = 0.8, loss against target fields of
+seed 7): the forward call keeping its per-node solutions, the backward that
+reuses them, and the backward that re-solves them, each after a warm-up.
+
 `sqrt` draws `samples` loads f = sqrt(M) y with the `nodes`-point rule on the
 library's mass spectrum bounds `reps` times and prints the mean time per call
 and the CG iterations.
@@ -76,9 +83,42 @@ def sqrt_noise(args):
                       "finite": bool(torch.isfinite(f).all())}))
 
 
+def adjoint(args):
+    from wm_workloads import WORKLOADS
+    c = WORKLOADS["sphere_p3_j7_adjoint_s64"]
+    hier = wm.Hierarchy(wm.Geometry(c["kind"], c["p"], c["n_u"]), c["levels"])
+    ns, N = c["n_samples"], hier.num_dofs(0)
+    kw = dict(beta=c["beta"], sinc_k=c["k"], l_lo=c["l_lo"], l_hi=c["l_hi"], n_samples=ns, kappa=c["kappa"],
+              precision=args.precision, rtol=c["rtol"] if args.precision == "fp64" else 1e-8, max_iter=400)
+    b = hier.noise_loads(c["seed"], ns)
+    g = torch.stack([wm.normals(c["target_seed"], s, 1, 0, N) for s in range(ns)])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"bench": "adjoint", "dofs": N, "samples": ns, "precision": args.precision}
+
+    def timed(fn):
+        fn()  # warm-up
+        torch.cuda.synchronize()
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    ms_f, (u, st) = timed(lambda: hier.sample_fields(b=b, ckpt="keep", **kw))
+    grad_u = 2.0 * hier.apply_mass(u - g)
+    ms_b, (_, gk, sb) = timed(lambda: hier.sample_fields_backward(b, grad_u, ckpt="keep", return_stats=True, **kw))
+    ms_r, (_, gk_r, sr) = timed(lambda: hier.sample_fields_backward(b, grad_u, return_stats=True, **kw))
+    out.update({"forward_ms": ms_f, "forward_kept": st["ckpt_kept"], "backward_from_checkpoint_ms": ms_b,
+                "backward_ckpt_used": sb["ckpt_used"], "backward_recompute_ms": ms_r,
+                "samples_per_s_forward_plus_backward": ns / ((ms_f + ms_b) / 1e3),
+                "dLdkappa": gk, "dLdkappa_recompute": gk_r,
+                "systems_backward": sb["n_systems"], "systems_backward_recompute": sr["n_systems"]})
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["vcycle", "sqrt"])
+    ap.add_argument("what", choices=["vcycle", "sqrt", "adjoint"])
     ap.add_argument("--kind", default="sphere", choices=["sphere", "torus"])
     ap.add_argument("--p", type=int, default=2)
     ap.add_argument("--elems", type=int, default=64)
@@ -96,6 +136,8 @@ def main():
     args = ap.parse_args()
     if args.what == "vcycle":
         vcycle(args)
+    elif args.what == "adjoint":
+        adjoint(args)
     else:
         sqrt_noise(args)
 

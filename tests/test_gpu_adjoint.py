@@ -28,8 +28,11 @@ def gpu_loss(hier, b, g, **kw):
     return float((d * hier.apply_mass(d)).sum()), u
 
 
-@pytest.mark.parametrize("beta", [0.8, 1.3])
-def test_adjoint_matches_oracle_and_fd(wm, beta):
+@pytest.mark.parametrize("beta,split", [(0.8, "standard"), (1.3, "standard"), (2.0, "standard"),
+                                        (0.9, "improved"), (1.5, "improved"), (1.9, "improved")])
+def test_adjoint_matches_oracle_and_fd(wm, beta, split):
+    # one fractional pass (0.8, 1.3), integer beta (2.0), and the improved
+    # split's two passes with 0, 0 and 1 integer solves (0.9, 1.5, 1.9)
     kind, p, n = "sphere", 3, 4
     hier = wm.Hierarchy(wm.Geometry(kind, p, n), 2)
     sp_ = GluedSpace(geo.Surface(kind, p, n))
@@ -37,8 +40,9 @@ def test_adjoint_matches_oracle_and_fd(wm, beta):
     ns, kappa, k, lo, hi = 3, 1.7, 0.5, -12, 12
     b_or = noise_loads(sp_, 4, ns)
     g_or = target_fields(sp_, 7, ns)
-    L_or, dLdb_or, dLdk_or = field_loss_grad(S, M, b_or, g_or, kappa, beta, k, lo, hi)
-    kw = dict(beta=beta, sinc_k=k, l_lo=lo, l_hi=hi, n_samples=ns, precision="fp64", rtol=1e-13, max_iter=400)
+    L_or, dLdb_or, dLdk_or = field_loss_grad(S, M, b_or, g_or, kappa, beta, k, lo, hi, split)
+    kw = dict(beta=beta, split=split, sinc_k=k, l_lo=lo, l_hi=hi, n_samples=ns, precision="fp64", rtol=1e-13,
+              max_iter=400)
     b = torch.tensor(b_or, device="cuda")
     g = torch.tensor(g_or, device="cuda")
     L, u = gpu_loss(hier, b, g, kappa=kappa, **kw)
@@ -52,6 +56,33 @@ def test_adjoint_matches_oracle_and_fd(wm, beta):
     Lp, _ = gpu_loss(hier, b, g, kappa=kappa + h, **kw)
     Lm, _ = gpu_loss(hier, b, g, kappa=kappa - h, **kw)
     assert gk == pytest.approx((Lp - Lm) / (2 * h), rel=1e-5)
+
+
+@pytest.mark.parametrize("beta,split", [(1.3, "standard"), (1.9, "improved")])
+def test_checkpointed_backward(wm, beta, split):
+    # a forward call with ckpt="keep" leaves every per-node solution in the
+    # workspace; the backward with the same descriptor and loads then solves the
+    # adjoint systems only and gives the gradients of the recomputing backward
+    hier = wm.Hierarchy(wm.Geometry("sphere", 2, 8), 3)
+    ns, kappa = 5, 2.0
+    kw = dict(beta=beta, split=split, sinc_k=0.4, l_lo=-12, l_hi=12, n_samples=ns, precision="fp64", rtol=1e-12)
+    b = hier.noise_loads(3, ns)
+    g = torch.tensor(random_vectors(8, ns, hier.num_dofs(0)), device="cuda")
+    u, st = hier.sample_fields(b=b, kappa=kappa, ckpt="keep", **kw)
+    assert st["ckpt_kept"] == 1
+    grad_u = 2.0 * hier.apply_mass(u - g)
+    gb1, gk1, s1 = hier.sample_fields_backward(b, grad_u, kappa=kappa, ckpt="keep", return_stats=True, **kw)
+    gb0, gk0, s0 = hier.sample_fields_backward(b, grad_u, kappa=kappa, return_stats=True, **kw)
+    assert s1["ckpt_used"] == 1 and s0["ckpt_used"] == 0
+    assert s1["n_systems"] < s0["n_systems"]  # no forward solves
+    torch.testing.assert_close(gb1, gb0, rtol=1e-12, atol=1e-14 * float(gb0.abs().max()))
+    assert gk1 == pytest.approx(gk0, rel=1e-12)
+    # other loads or another kappa: the checkpoint does not match and is not used
+    b2 = b.clone()
+    b2[0, 0] += 1e-3
+    _, _, s2 = hier.sample_fields_backward(b2, grad_u, kappa=kappa, ckpt="keep", return_stats=True, **kw)
+    _, _, s3 = hier.sample_fields_backward(b, grad_u, kappa=kappa + 0.1, ckpt="keep", return_stats=True, **kw)
+    assert s2["ckpt_used"] == 0 and s3["ckpt_used"] == 0
 
 
 def test_autograd_function(wm):
