@@ -417,8 +417,19 @@ int wm_sample_fields(wm_hier_t h, const wm_sample_desc* desc, double* u, double*
 
 /*
  * Several independent problems (surfaces, levels, kappa, beta, samples) in one
- * call: u[i] receives the fields of problem i (same rules as wm_sample_fields,
- * device memory).  stats: host [n_inst] or NULL.
+ * call: u[i] receives the fields of problem i ([n_samples_i][N_i] device memory;
+ * loads drawn, WM_NOISE_DRAW).  Instances with the same hierarchy handle and the
+ * same solver settings (precision, rtol, max_iter, smoother, preconditioner,
+ * max_systems) form a group whose instances share every batched solve: stage k
+ * (an instance's k-th integer solve, then its fractional passes; Sec. 3.4) of
+ * all the group's instances is one list of shifted systems, each with its own
+ * shift, sample and sinc weight, solved in memory-sized batches; the first
+ * stage takes the loads, every later one M times the previous stage's result.
+ * Groups run one after another on the stream.  ckpt is not used here.
+ * stats: host [n_inst] or NULL; per instance: its systems, convergence and
+ * largest final relative residual exactly; iterations, batches, replacements
+ * and fallbacks of the batches it took part in.  The stream is synchronised
+ * before return.  Errors as wm_sample_fields (the worst over the instances).
  */
 int wm_sample_fields_batched(int n_inst, const wm_hier_t* h, const wm_sample_desc* desc,
                              double* const* u, wm_stats* stats, void* stream);

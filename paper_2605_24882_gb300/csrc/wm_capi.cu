@@ -703,8 +703,9 @@ extern "C" int wm_normals(uint64_t seed, int sample, int stream_id, int64_t q0, 
   return WM_OK;
 }
 
-// loads of samples sample0 + [0, ns) into rows [0, ns) of the sample-tiled buffer b_t
-static int draw_loads(wm_hier_t h, WorkSpace& ws, uint64_t seed, int sample0, int ns, double* b_t, cudaStream_t s) {
+// loads of samples sample0 + [0, ns) into rows row0 + [0, ns) of the sample-tiled buffer b_t
+static int draw_loads(wm_hier_t h, WorkSpace& ws, uint64_t seed, int sample0, int ns, double* b_t, cudaStream_t s,
+                      int row0 = 0) {
   const wm_level& L = h->lv[0];
   // sample chunks bounded so that the element scratch stays below ~1 GiB
   size_t per_sample = (size_t)L.E * L.nk;
@@ -712,7 +713,7 @@ static int draw_loads(wm_hier_t h, WorkSpace& ws, uint64_t seed, int sample0, in
   WM_TRY(ws.noise_scratch.alloc(per_sample * chunk));
   for (int s0 = 0; s0 < ns; s0 += chunk) {
     int c = std::min(chunk, ns - s0);
-    WM_TRY(wm_k_noise_tiled(h, seed, sample0, s0, c, b_t, ws.noise_scratch.p, s));
+    WM_TRY(wm_k_noise_tiled(h, seed, sample0 + s0, row0 + s0, c, b_t, ws.noise_scratch.p, s));
   }
   return WM_OK;
 }
@@ -1086,12 +1087,295 @@ extern "C" int wm_sample_fields(wm_hier_t h, const wm_sample_desc* d, double* u,
   return sample_fields_impl(h, d, u, b, st, as_stream(stream));
 }
 
+namespace {
+
+// rows [row0, row0 + n) of a sample-tiled buffer to [n][N] (caller layout)
+__global__ void k_rows_from_tiled(const double* __restrict__ src, int N, int row0, int n, double* __restrict__ dst) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= (int64_t)n * N) return;
+  int v = (int)(k / N), i = (int)(k - (int64_t)v * N);
+  int r = row0 + v;
+  dst[k] = src[((size_t)(r / WM_LANES) * N + i) * WM_LANES + (r % WM_LANES)];
+}
+
+// rows of a sample-tiled buffer whose flag is set become zero
+__global__ void k_zero_rows(int N, const int* __restrict__ flag, double* __restrict__ v) {
+  int st = blockIdx.y;
+  int r = st * WM_LANES + threadIdx.x;
+  if (!flag[r]) return;
+  for (int i = blockIdx.x * blockDim.y + threadIdx.y; i < N; i += gridDim.x * blockDim.y)
+    v[((size_t)st * N + i) * WM_LANES + threadIdx.x] = 0.0;
+}
+
+// acc[row r] += sum over the entries e of row r (CSR ptr over rows) of
+// coef[e] x[system sys[e]], systems of the batch stored [tiles][N][32]; the
+// entries of a row are summed in order (deterministic)
+__global__ void k_rows_accumulate(int N, const int* __restrict__ ptr, const int* __restrict__ sys,
+                                  const double* __restrict__ coef, const double* __restrict__ x,
+                                  double* __restrict__ acc) {
+  int st = blockIdx.y;
+  int r = st * WM_LANES + threadIdx.x;
+  int e0 = ptr[r], e1 = ptr[r + 1];
+  if (e0 == e1) return;
+  for (int i = blockIdx.x * blockDim.y + threadIdx.y; i < N; i += gridDim.x * blockDim.y) {
+    double a = 0.0;
+    for (int e = e0; e < e1; ++e) {
+      int g = sys[e];
+      a += coef[e] * x[((size_t)(g / WM_LANES) * N + i) * WM_LANES + (g % WM_LANES)];
+    }
+    acc[((size_t)st * N + i) * WM_LANES + threadIdx.x] += a;
+  }
+}
+
+// solver settings that instances must share to be packed into one batch
+bool same_solver(const wm_sample_desc& a, const wm_sample_desc& b) {
+  return a.precision == b.precision && a.rtol == b.rtol && a.max_iter == b.max_iter &&
+         a.smoother_degree == b.smoother_degree && a.cheb_ratio == b.cheb_ratio &&
+         a.preconditioner == b.preconditioner && a.max_systems == b.max_systems;
+}
+
+// Instances of one hierarchy with the same solver settings, solved together.
+// Their samples are rows off_i .. off_i + n_i - 1 of shared sample-tiled
+// buffers.  Stage k of an instance is its k-th integer solve or, after those,
+// its fractional passes; every stage but the first takes M times the previous
+// stage's result, the first takes the loads.  Stage k of all instances that
+// have one is a single list of systems (the instances' shifts and weights side
+// by side), solved in batches by the batched PCG; each batch's solutions are
+// summed into the rows of their samples with their weights (1 for an integer
+// solve).
+int sample_fields_group(wm_hier_t h, const std::vector<const wm_sample_desc*>& D, const std::vector<double*>& U,
+                        const std::vector<wm_stats*>& ST, cudaStream_t s) {
+  const int m = (int)D.size();
+  std::vector<Plan> P(m);
+  std::vector<int> off(m + 1, 0);
+  for (int i = 0; i < m; ++i) {
+    WM_TRY(validate_desc(h, D[i]));
+    if (D[i]->noise_mode != WM_NOISE_DRAW) {
+      wm_set_error("wm_sample_fields_batched draws the loads (WM_NOISE_DRAW)");
+      return WM_ERR_INVALID_ARG;
+    }
+    WM_TRY(make_plan(D[i], P[i]));
+    if (ST[i]) {
+      std::memset(ST[i], 0, sizeof(*ST[i]));
+      ST[i]->n_int_solves = P[i].n_int;
+      ST[i]->n_frac_passes = P[i].passes;
+      ST[i]->n_nodes = (int)P[i].c.size();
+    }
+    if (D[i]->n_samples > 0 && (!U[i] || !is_device_ptr(U[i]))) {
+      wm_set_error("wm_sample_fields_batched: u[%d] must be device memory", i);
+      return WM_ERR_INVALID_ARG;
+    }
+    off[i + 1] = off[i] + D[i]->n_samples;
+  }
+  const int S = off[m];
+  if (S == 0) return WM_OK;
+  const wm_level& L0 = h->lv[0];
+  const int N = L0.N;
+  const int stiles = (S + WM_LANES - 1) / WM_LANES;
+  const size_t sn = (size_t)stiles * N * WM_LANES;
+  WorkSpace& ws = workspace(h);
+  for (int k = 0; k < 3; ++k) WM_TRY(ws.samp[k].alloc(sn));
+  double* b_t = ws.samp[0].p;
+  double* cur = ws.samp[1].p;
+  double* rhs = ws.samp[2].p;
+  for (int i = 0; i < m; ++i)
+    if (D[i]->n_samples > 0) WM_TRY(draw_loads(h, ws, D[i]->seed, D[i]->sample0, D[i]->n_samples, b_t, s, off[i]));
+  // the call's shift list: every distinct shift of every instance
+  std::vector<double> shl;
+  std::map<uint64_t, int> index;
+  auto shift_id = [&](double v) {
+    uint64_t key;
+    std::memcpy(&key, &v, sizeof(key));
+    auto it = index.find(key);
+    if (it == index.end()) {
+      it = index.emplace(key, (int)shl.size()).first;
+      shl.push_back(v);
+    }
+    return it->second;
+  };
+  std::vector<std::vector<int>> node_sid(m);
+  std::vector<int> kappa_sid(m);
+  int K = 0;
+  for (int i = 0; i < m; ++i) {
+    for (double v : P[i].sigma) node_sid[i].push_back(shift_id(v));
+    kappa_sid[i] = shift_id(D[i]->kappa * D[i]->kappa);
+    if (D[i]->n_samples > 0) K = std::max(K, P[i].n_int + P[i].passes);
+  }
+  const wm_sample_desc& d0 = *D[0];
+  int64_t most = 0;
+  for (int i = 0; i < m; ++i) most += (int64_t)std::max<size_t>(1, P[i].sigma.size()) * D[i]->n_samples;
+  const int64_t per_batch = batch_size(h, ws, &d0, most, 0);
+  WM_TRY(ws.reserve(h, (int)((per_batch + WM_LANES - 1) / WM_LANES), (int)shl.size(), d0.precision == WM_FP64));
+  WM_TRY(wm_prepare_shifts(h, ws, shl, s));
+  DevBuf<int> d_flag, d_ptr, d_sys;
+  DevBuf<double> d_coef;
+  WM_TRY(d_flag.alloc((size_t)stiles * WM_LANES));
+  WM_TRY(d_ptr.alloc((size_t)stiles * WM_LANES + 1));
+  int worst = WM_OK;
+  const unsigned gx = (unsigned)std::max(1, std::min(256, (N + 7) / 8));
+  for (int k = 0; k < K; ++k) {
+    // right-hand sides: the loads, or M times the previous stage's result
+    const double* r = b_t;
+    if (k > 0) {
+      WM_TRY(wm_k_apply_mass64(L0, stiles, cur, rhs, nullptr, s));
+      r = rhs;
+    }
+    // systems of stage k: (shift, shift index, sample row, weight, instance)
+    std::vector<double> sg, cf;
+    std::vector<int> sid, src, inst;
+    std::vector<int> flag((size_t)stiles * WM_LANES, 0);
+    for (int i = 0; i < m; ++i) {
+      const int ns = D[i]->n_samples;
+      if (ns == 0 || k >= P[i].n_int + P[i].passes) continue;
+      for (int v = 0; v < ns; ++v) flag[off[i] + v] = 1;
+      if (k < P[i].n_int) {
+        for (int v = 0; v < ns; ++v) {
+          sg.push_back(D[i]->kappa * D[i]->kappa);
+          sid.push_back(kappa_sid[i]);
+          src.push_back(off[i] + v);
+          cf.push_back(1.0);
+          inst.push_back(i);
+        }
+      } else {
+        for (size_t j = 0; j < P[i].sigma.size(); ++j)
+          for (int v = 0; v < ns; ++v) {
+            sg.push_back(P[i].sigma[j]);
+            sid.push_back(node_sid[i][j]);
+            src.push_back(off[i] + v);
+            cf.push_back(P[i].c[j]);
+            inst.push_back(i);
+          }
+      }
+    }
+    WM_CUDA(cudaMemcpyAsync(d_flag.p, flag.data(), flag.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    // the rows of this stage start from zero; the others keep their result
+    WM_LAUNCH(WM_PC_SINC, s, k_zero_rows<<<dim3(gx, stiles), dim3(WM_LANES, 8), 0, s>>>(N, d_flag.p, cur));
+    WM_CUDA(cudaGetLastError());
+    const int64_t nsys = (int64_t)sg.size();
+    for (int64_t g0 = 0; g0 < nsys; g0 += per_batch) {
+      const int64_t g1 = std::min(nsys, g0 + per_batch);
+      const int nb = (int)(g1 - g0);
+      const int tiles = (nb + WM_LANES - 1) / WM_LANES;
+      std::vector<double> bsg(sg.begin() + g0, sg.begin() + g1);
+      std::vector<int> bsid(sid.begin() + g0, sid.begin() + g1), bsrc(src.begin() + g0, src.begin() + g1);
+      WM_TRY(set_batch_meta(ws, tiles, bsg, bsid, bsrc, s));
+      Batch bt;
+      bt.tiles = tiles;
+      bt.nsys = nb;
+      bt.nshift = (int)shl.size();
+      bt.precision = d0.precision;
+      bt.rtol = d0.rtol;
+      bt.max_iter = d0.max_iter;
+      bt.degree = d0.smoother_degree;
+      bt.cheb_ratio = d0.cheb_ratio;
+      bt.replace_drop = d0.precision == WM_FP64 ? 0.0 : 1e-4;
+      bt.df_residual = d0.precision != WM_FP64;
+      bt.precond = d0.preconditioner;
+      BatchResult br;
+      WM_TRY(wm_solve_batch(h, ws, bt, r, &br, s));
+      if (br.flags & 1) worst = std::min(worst, WM_ERR_NONFINITE);
+      if ((br.n_not_converged > 0 || (br.flags & 2)) && worst == WM_OK) worst = WM_ERR_NOT_CONVERGED;
+      // per-instance statistics from the per-system state of the batch
+      std::vector<int> act(nb);
+      std::vector<double> rr(nb), bb(nb);
+      WM_CUDA(cudaMemcpyAsync(act.data(), ws.active.p, nb * sizeof(int), cudaMemcpyDeviceToHost, s));
+      WM_CUDA(cudaMemcpyAsync(rr.data(), ws.rr.p, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+      WM_CUDA(cudaMemcpyAsync(bb.data(), ws.bb.p, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+      // weighted sums of this batch's solutions into their sample rows (CSR over rows)
+      std::vector<int> ptr((size_t)stiles * WM_LANES + 1, 0), esys(nb);
+      std::vector<double> ecf(nb);
+      for (int q = 0; q < nb; ++q) ptr[bsrc[q] + 1]++;
+      for (size_t v = 0; v + 1 < ptr.size(); ++v) ptr[v + 1] += ptr[v];
+      {
+        std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+        for (int q = 0; q < nb; ++q) {
+          esys[fill[bsrc[q]]] = q;
+          ecf[fill[bsrc[q]]++] = cf[g0 + q];
+        }
+      }
+      WM_TRY(d_sys.alloc(nb));
+      WM_TRY(d_coef.alloc(nb));
+      WM_CUDA(cudaMemcpyAsync(d_ptr.p, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      WM_CUDA(cudaMemcpyAsync(d_sys.p, esys.data(), nb * sizeof(int), cudaMemcpyHostToDevice, s));
+      WM_CUDA(cudaMemcpyAsync(d_coef.p, ecf.data(), nb * sizeof(double), cudaMemcpyHostToDevice, s));
+      WM_LAUNCH(WM_PC_SINC, s, k_rows_accumulate<<<dim3(gx, stiles), dim3(WM_LANES, 8), 0, s>>>(
+                                   N, d_ptr.p, d_sys.p, d_coef.p, ws.x.p, cur));
+      WM_CUDA(cudaGetLastError());
+      WM_CUDA(cudaStreamSynchronize(s));  // the host vectors above go out of scope
+      std::vector<char> seen(m, 0);
+      for (int q = 0; q < nb; ++q) {
+        const int i = inst[g0 + q];
+        wm_stats* st = ST[i];
+        if (!st) continue;
+        st->n_systems += 1;
+        st->n_not_converged += act[q] ? 1 : 0;
+        if (bb[q] > 0) st->max_rel_residual = std::max(st->max_rel_residual, std::sqrt(rr[q] / bb[q]));
+        if (!seen[i]) {
+          seen[i] = 1;
+          st->n_batches += 1;
+          st->max_iterations = std::max(st->max_iterations, br.iterations);
+          st->total_iterations += br.iterations;
+          st->n_replacements += br.replacements;
+          st->n_df_fallbacks += br.df_fallbacks;
+        }
+      }
+    }
+  }
+  // fields: each instance's rows to its [n_i][N] output
+  for (int i = 0; i < m; ++i) {
+    const int ns = D[i]->n_samples;
+    if (ns == 0) continue;
+    const int64_t n = (int64_t)ns * N;
+    WM_LAUNCH(WM_PC_LAYOUT, s, k_rows_from_tiled<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cur, N, off[i], ns,
+                                                                                            U[i]));
+    WM_CUDA(cudaGetLastError());
+  }
+  WM_CUDA(cudaStreamSynchronize(s));
+  return worst;
+}
+
+}  // namespace
+
 extern "C" int wm_sample_fields_batched(int n_inst, const wm_hier_t* h, const wm_sample_desc* d, double* const* u,
                                         wm_stats* st, void* stream) {
   if (n_inst < 0 || (n_inst > 0 && (!h || !d || !u))) return WM_ERR_INVALID_ARG;
-  int worst = WM_OK;
+  for (int i = 0; i < n_inst; ++i)
+    if (!h[i]) return WM_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  // groups: instances with the same hierarchy and solver settings, in order of first appearance
+  std::vector<char> done(n_inst, 0);
+  std::vector<std::vector<int>> groups;
   for (int i = 0; i < n_inst; ++i) {
-    int rc = sample_fields_impl(h[i], &d[i], u[i], nullptr, st ? &st[i] : nullptr, as_stream(stream));
+    if (done[i]) continue;
+    groups.emplace_back();
+    for (int j = i; j < n_inst; ++j) {
+      if (done[j] || h[j] != h[i] || !same_solver(d[j], d[i])) continue;
+      done[j] = 1;
+      groups.back().push_back(j);
+    }
+  }
+  int worst = WM_OK;
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const std::vector<int>& G = groups[gi];
+    std::vector<const wm_sample_desc*> D;
+    std::vector<double*> U;
+    std::vector<wm_stats*> ST;
+    for (int j : G) {
+      D.push_back(&d[j]);
+      U.push_back(u[j]);
+      ST.push_back(st ? &st[j] : nullptr);
+    }
+    int rc = sample_fields_group(h[G[0]], D, U, ST, s);
+    // with several groups each one sizes its batches to the free memory: hand the
+    // workspace of a hierarchy back once its last group is done
+    if (groups.size() > 1 && h[G[0]]->ws) {
+      bool later = false;
+      for (size_t gj = gi + 1; gj < groups.size(); ++gj) later |= h[groups[gj][0]] == h[G[0]];
+      if (!later) {
+        cudaStreamSynchronize(s);
+        h[G[0]]->ws->release();
+      }
+    }
     if (rc == WM_ERR_NOT_CONVERGED || rc == WM_ERR_NONFINITE) {
       worst = std::min(worst, rc);
       continue;

@@ -203,10 +203,10 @@ int wm_k_pack_rows(wm_level& L, cudaStream_t s);
 int wm_k_philox(const uint32_t* ctr, uint64_t key, uint32_t* out, int64_t n, cudaStream_t s);
 int wm_k_normals(uint64_t seed, int sample, int stream_id, int64_t q0, int64_t n, double* out,
                  cudaStream_t s);
-// loads of rows [s0, s0+ns) into a tiled [tiles][N][32] buffer (row s at tile
-// s/32, lane s%32), row s holding the loads of sample sample0 + s (its Philox
-// counters); `bl` is scratch of E*nk*ns_pad doubles
-int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int sample0, int s0, int ns, double* b_tiled,
+// loads of rows [row0, row0+ns) of a tiled [tiles][N][32] buffer (row v at tile
+// v/32, lane v%32), row row0 + k holding the loads of sample sample_first + k
+// (its Philox counters); `bl` is scratch of E*nk*ns doubles
+int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int sample_first, int row0, int ns, double* b_tiled,
                      double* bl, cudaStream_t s);
 
 // batched operators (wm_operator.cu); vectors are [tiles][N][32]

@@ -127,7 +127,7 @@ __global__ void k_noise_local(int E, int nu, int nv, int ns, int s0, uint64_t se
     }
 }
 
-// One thread per (DOF i, sample s0+sl): b[tile][i][lane] = sum over the element
+// One thread per (DOF i, row s0+sl): b[tile][i][lane] = sum over the element
 // functions containing i of their local contributions, in element order.
 __global__ void k_noise_gather(int N, int ns, int s0, const int32_t* __restrict__ ptr,
                                const int32_t* __restrict__ idx, const double* __restrict__ bl,
@@ -159,13 +159,13 @@ int wm_k_normals(uint64_t seed, int sample, int stream_id, int64_t q0, int64_t n
   return WM_OK;
 }
 
-int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int sample0, int s0, int ns, double* b_tiled, double* bl,
-                     cudaStream_t s) {
+int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int sample_first, int row0, int ns, double* b_tiled,
+                     double* bl, cudaStream_t s) {
   const wm_level& L = h->lv[0];
   int64_t n1 = (int64_t)L.E * ns;
   unsigned g1 = (unsigned)((n1 + 127) / 128);
 #define WM_NL(PP)                                                                                        \
-  k_noise_local<PP><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, ns, sample0 + s0, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, \
+  k_noise_local<PP><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, ns, sample_first, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, \
                                        L.d_bv.p, bl)
   wm_prof_begin(WM_PC_NOISE, s);
   switch (h->p) {
@@ -179,7 +179,7 @@ int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int sample0, int s0, int n
   wm_prof_end(WM_PC_NOISE, s);
   WM_CUDA(cudaGetLastError());
   int64_t n2 = (int64_t)L.N * ns;
-  WM_LAUNCH(WM_PC_NOISE, s, k_noise_gather<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(L.N, ns, s0, L.d_ng_ptr.p, L.d_ng_idx.p, bl,
+  WM_LAUNCH(WM_PC_NOISE, s, k_noise_gather<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(L.N, ns, row0, L.d_ng_ptr.p, L.d_ng_idx.p, bl,
                                                               b_tiled));
   WM_CUDA(cudaGetLastError());
   return WM_OK;

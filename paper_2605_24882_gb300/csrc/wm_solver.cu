@@ -321,7 +321,8 @@ __global__ void k_dots_rz_zq(int N, int chunks, int tiles, const T* __restrict__
   block_reduce_store<2, 1>(v, parts, chunks, t, tiles);
 }
 
-// p = z + beta p
+// p = z + beta p; with beta = 0 (the first direction, a restart) p = z without
+// reading p, which may hold anything before the first direction is formed
 template <typename T>
 __global__ void k_update_p(int N, int chunks, const double* __restrict__ beta, const T* __restrict__ z,
                            T* __restrict__ p, const int* __restrict__ tile_active) {
@@ -331,7 +332,7 @@ __global__ void k_update_p(int N, int chunks, const double* __restrict__ beta, c
   RowRange rr = chunk_rows(N, chunks);
   for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
     size_t k = vidx(t, N, i);
-    p[k] = z[k] + b * p[k];
+    p[k] = b == (T)0 ? z[k] : z[k] + b * p[k];
   }
 }
 
@@ -1017,6 +1018,10 @@ void WorkSpace::release() {
   ck.release();
   if (host_small) cudaFreeHost(host_small);
   host_small = nullptr;
+  // the prepared bounds and inverses went with their buffers
+  prep_shifts.clear();
+  prep_lmax = prep_ainv = nullptr;
+  n_uni_tiles = n_uni_groups = 0;
 }
 
 // lambda_max(D^{-1}(S + sigma M)) on every non-coarsest level for each shift,

@@ -108,3 +108,71 @@ def test_torus_full_size_against_the_oracle(wm, precision, tol):
     d = u.cpu().numpy() - u_or
     err = np.sqrt(np.einsum("si,si->s", d, (M @ d.T).T) / np.einsum("si,si->s", u_or, (M @ u_or.T).T))
     assert err.max() < tol, (err, st)
+
+
+def test_instances_sharing_a_hierarchy_share_the_solves(wm):
+    # five instances on one hierarchy (kappa, beta under both splits, 1..40
+    # samples, seeds, first samples all different) are solved stage by stage in
+    # the same batched solves; each must match the oracle and its own run
+    hier = wm.Hierarchy(wm.Geometry("sphere", 2, 8), 3)
+    sp_ = GluedSpace(geo.Surface("sphere", 2, 8))
+    S, M = assemble(sp_)
+    cases = [(2.0, 0.75, "standard", 3, 1, 0), (5.0, 1.3, "standard", 40, 2, 7), (1.5, 1.5, "improved", 17, 3, 0),
+             (8.0, 0.9, "improved", 1, 4, 5), (3.0, 2.0, "standard", 33, 5, 0)]
+    descs = [wm.Hierarchy.make_desc(kap, beta, 0.4, -20, 20, ns, seed, split, "mixed", 1e-9, sample0=s0)
+             for kap, beta, split, ns, seed, s0 in cases]
+    outs, stats = wm.sample_fields_batched([hier] * len(cases), descs)
+    for (kap, beta, split, ns, seed, s0), u, st in zip(cases, outs, stats):
+        n_int, _, passes = wm.beta_plan(beta, split)
+        assert st["n_not_converged"] == 0 and st["n_systems"] == ns * (n_int + passes * 41), st
+        b = noise_loads(sp_, seed, s0 + ns)[s0:]
+        ref = oracle_fields(S, M, b, kap, beta, 0.4, -20, 20, split)
+        assert mnorm_rel(u.cpu().numpy(), ref, M).max() < 1e-6, (kap, beta, split)
+        alone, _ = hier.sample_fields(kappa=kap, beta=beta, sinc_k=0.4, l_lo=-20, l_hi=20, n_samples=ns, seed=seed,
+                                      split=split, precision="mixed", rtol=1e-9, sample0=s0)
+        assert mnorm_rel(u.cpu().numpy(), alone.cpu().numpy(), M).max() < 1e-7
+
+
+def test_uneven_batch_96_instances(wm):
+    # the uneven configuration: 96 spheres (p = 2) and tori (p = 3) at levels
+    # 3..9 (488 .. 1,579,016 DOFs), kappa ~ U[1, 20], beta ~ U[0.55, 1.95] with
+    # the improved split, 1..64 samples, seed 11; one hierarchy per distinct
+    # surface, so the instances of a surface share their batched solves.
+    # Checks: instances up to 6,536 DOFs against the oracle; for every larger
+    # one, its first and last samples against the float64 path run alone.
+    import collections
+    insts = uneven_instances()
+    hiers = {}
+    H, D = [], []
+    for c in insts:
+        key = (c["kind"], c["n_u"], c["n_v"])
+        if key not in hiers:
+            g = wm.Geometry(c["kind"], c["p"], c["n_u"], c["n_v"], c.get("R", 1.0), c.get("r", 0.4))
+            hiers[key] = wm.Hierarchy(g, c["levels"])
+        H.append(hiers[key])
+        D.append(wm.Hierarchy.make_desc(c["kappa"], c["beta"], c["k"], c["l_lo"], c["l_hi"], c["n_samples"],
+                                        c["seed"], c["split"], c["precision"], c["rtol"]))
+    assert len(hiers) == 14
+    outs, stats = wm.sample_fields_batched(H, D)
+    assert all(st["n_not_converged"] == 0 for st in stats)
+    oracle_cache = collections.OrderedDict()
+    for c, h, u, st in zip(insts, H, outs, stats):
+        N = h.num_dofs(0)
+        assert u.shape == (c["n_samples"], N)
+        if N <= 6536:
+            key = (c["kind"], c["n_u"])
+            if key not in oracle_cache:
+                sp_ = GluedSpace(geo.Surface(c["kind"], c["p"], c["n_u"], c["n_v"], c.get("R", 1.0), c.get("r", 0.4)))
+                oracle_cache[key] = (sp_,) + tuple(assemble(sp_))
+            sp_, S, M = oracle_cache[key]
+            b = noise_loads(sp_, c["seed"], c["n_samples"])
+            ref = oracle_fields(S, M, b, c["kappa"], c["beta"], c["k"], c["l_lo"], c["l_hi"], c["split"])
+            assert mnorm_rel(u.cpu().numpy(), ref, M).max() < 1e-6, (c["kind"], c["n_u"], c["beta"])
+        else:
+            for s0 in sorted({0, c["n_samples"] - 1}):
+                u64, st64 = h.sample_fields(kappa=c["kappa"], beta=c["beta"], sinc_k=c["k"], l_lo=c["l_lo"],
+                                            l_hi=c["l_hi"], n_samples=1, seed=c["seed"], split=c["split"],
+                                            precision="fp64", rtol=1e-10, sample0=s0)
+                d = u[s0:s0 + 1] - u64
+                rel = torch.sqrt((d * h.apply_mass(d)).sum() / (u64 * h.apply_mass(u64)).sum())
+                assert float(rel) < 1e-6, (c["kind"], c["n_u"], c["beta"], s0, float(rel))
