@@ -312,6 +312,28 @@ def fp64_legs(hier, kw, u_mixed, N, systems_per_sample, args):
     return out
 
 
+def tuned_setting(hier, c, args):
+    """Smoother pair and kernel schedule of a workload: the autotuner's cache
+    entry for this workload and GPU when there is one (applied to `hier`),
+    else the workload's smoother pair and the library's default schedule;
+    --smoother-degree / --cheb-ratio override the pair."""
+    import torch
+    from paper_2605_24882_gb300 import autotune
+    key = autotune.cache_key(c, c["n_samples"], torch.cuda.get_device_name())
+    entry = autotune.lookup(key)
+    if entry:
+        smoother, source = autotune.apply(hier, entry), "autotune cache " + key
+    else:
+        smoother = {"smoother_degree": c.get("smoother_degree", 4), "cheb_ratio": c.get("cheb_ratio", 12.0),
+                    "smoother_degree_coarse": 0}
+        source = "workload defaults (no cache entry for %s)" % key
+    if args.smoother_degree:
+        smoother["smoother_degree"] = args.smoother_degree
+    if args.cheb_ratio:
+        smoother["cheb_ratio"] = args.cheb_ratio
+    return {"source": source, "smoother": smoother, "schedule": hier.schedule()}
+
+
 def secondary_leg(wm, name, pk, pk_kind, args):
     """A second workload on the same GPU, same protocol at fewer steps: one
     warm-up step, `secondary_steps` timed steps with profiling off, then one
@@ -322,9 +344,9 @@ def secondary_leg(wm, name, pk, pk_kind, args):
                         c["levels"])
     N = hier.num_dofs(0)
     ns = c["n_samples"]
+    tuning = tuned_setting(hier, c, argparse.Namespace(smoother_degree=0, cheb_ratio=0.0))
     kw = dict(kappa=c["kappa"], beta=c["beta"], sinc_k=c["k"], l_lo=c["l_lo"], l_hi=c["l_hi"], n_samples=ns,
-              seed=c["seed"], split=c["split"], precision=c["precision"], rtol=c["rtol"],
-              smoother_degree=c.get("smoother_degree", 4), cheb_ratio=c.get("cheb_ratio", 12.0))
+              seed=c["seed"], split=c["split"], precision=c["precision"], rtol=c["rtol"], **tuning["smoother"])
     u = torch.empty((ns, N), dtype=torch.float64, device="cuda")
     _, stats = hier.sample_fields(out=u, **kw)
     torch.cuda.synchronize()
@@ -348,10 +370,72 @@ def secondary_leg(wm, name, pk, pk_kind, args):
            "value": ns / (ms / 1e3), "unit": "samples/s", "ms_per_step": ms, "steps": args.secondary_steps,
            "warmup": 1, "dof_solves_per_s": N * systems / (ms / 1e3), "precision": c["precision"],
            "solver": {k: stats[k] for k in ("max_iterations", "n_not_converged", "max_rel_residual", "n_batches")},
-           "roofline": rl, "kernel_ms_per_step": {k: v["ms"] for k, v in prof.items() if v["ms"] > 0}}
+           "roofline": rl, "kernel_ms_per_step": {k: v["ms"] for k, v in prof.items() if v["ms"] > 0},
+           "tuning": tuning}
     del u, hier
     torch.cuda.empty_cache()
     return out
+
+
+def uneven_arm(args):
+    """The uneven batch: 96 sphere and torus instances (levels 3..9, seed 11) in
+    one wm_sample_fields_batched call per step, one hierarchy per distinct
+    surface.  A first call with per-launch profiling gives the per-category
+    times and the roofline; the timed steps run with profiling off."""
+    import torch
+
+    import paper_2605_24882_gb300 as wm
+    from wm_workloads import uneven_instances
+
+    pk, pk_kind = peaks()
+    insts = uneven_instances()
+    hiers, H, D = {}, [], []
+    t0 = time.perf_counter()
+    for c in insts:
+        key = (c["kind"], c["n_u"], c["n_v"])
+        if key not in hiers:
+            hiers[key] = wm.Hierarchy(wm.Geometry(c["kind"], c["p"], c["n_u"], c["n_v"], c.get("R", 1.0),
+                                                  c.get("r", 0.4)), c["levels"])
+        H.append(hiers[key])
+        D.append(wm.Hierarchy.make_desc(c["kappa"], c["beta"], c["k"], c["l_lo"], c["l_hi"], c["n_samples"],
+                                        c["seed"], c["split"], c["precision"], c["rtol"]))
+    setup_s = time.perf_counter() - t0
+    outs = [torch.empty((d.n_samples, h.num_dofs(0)), dtype=torch.float64, device="cuda") for h, d in zip(H, D)]
+    wm.profile_enable(True)
+    _, stats = wm.sample_fields_batched(H, D, outs=outs)
+    torch.cuda.synchronize()
+    prof = wm.profile_read()
+    wm.profile_enable(False)
+    rl, _ = roofline(prof, pk, pk_kind)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, stats = wm.sample_fields_batched(H, D, outs=outs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    samples = sum(d.n_samples for d in D)
+    dof_solves = sum(h.num_dofs(0) * st["n_systems"] for h, st in zip(H, stats))
+    line = {"metric": METRIC, "value": samples / (ms / 1e3), "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": "uneven96", "instances": len(D), "surfaces": len(hiers),
+                       "dofs": [min(h.num_dofs(0) for h in H), max(h.num_dofs(0) for h in H)],
+                       "samples": samples, "systems_per_step": sum(st["n_systems"] for st in stats),
+                       "precision": "mixed", "rtol": insts[0]["rtol"], "split": "improved",
+                       "hierarchy_setup_s": setup_s},
+            "dof_solves_per_s": dof_solves / (ms / 1e3),
+            "solver": {"n_not_converged": sum(st["n_not_converged"] for st in stats),
+                       "max_rel_residual": max(st["max_rel_residual"] for st in stats),
+                       "max_iterations": max(st["max_iterations"] for st in stats)},
+            "gpu_launches": sum(v["launches"] for v in prof.values()),
+            "roofline": rl, "kernel_ms_profiled_call": {k: v["ms"] for k, v in prof.items() if v["ms"] > 0},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
 
 
 def our_arm(args):
@@ -366,11 +450,10 @@ def our_arm(args):
                         c["levels"])
     N = hier.num_dofs(0)
     ns = args.samples or c["n_samples"]
+    tuning = tuned_setting(hier, c, args)
     kw = dict(kappa=c["kappa"], beta=c["beta"], sinc_k=c["k"], l_lo=c["l_lo"], l_hi=c["l_hi"], n_samples=ns,
               seed=c["seed"], sample0=rank_samples(rank, ns)[0], split=c["split"], precision=c["precision"],
-              rtol=c["rtol"],
-              smoother_degree=args.smoother_degree or c.get("smoother_degree", 4),
-              cheb_ratio=args.cheb_ratio or c.get("cheb_ratio", 12.0), preconditioner=args.preconditioner)
+              rtol=c["rtol"], preconditioner=args.preconditioner, **tuning["smoother"])
     u = torch.empty((ns, N), dtype=torch.float64, device="cuda")
     stats = None
     for _ in range(args.warmup):
@@ -428,7 +511,9 @@ def our_arm(args):
                        "systems_per_step": ns * (n_int + passes * n_nodes), "rtol": c["rtol"],
                        "precision": c["precision"], "parallelism": "replicas" if world > 1 else "single GPU",
                        "preconditioner": args.preconditioner,
-                       "smoother": {"chebyshev_degree": kw["smoother_degree"], "interval_ratio": kw["cheb_ratio"]},
+                       "smoother": {"chebyshev_degree": kw["smoother_degree"], "interval_ratio": kw["cheb_ratio"],
+                                    "chebyshev_degree_coarse": kw["smoother_degree_coarse"] or kw["smoother_degree"]},
+                       "tuning": tuning,
                        "l2": "inputs larger than L2: the batch working set is %.0f GB per step"
                              % (N * ns * (n_int + passes * n_nodes) * 40 / 1e9)},
             "dof_solves_per_s": dof_solves,
@@ -489,6 +574,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "uneven96":
+        uneven_arm(args)
     else:
         our_arm(args)
 

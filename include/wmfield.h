@@ -220,6 +220,25 @@ int wm_hht_rule(double lo, double hi, int n_nodes, double* w2, double* c);
  */
 int wm_assemble_hierarchy(wm_geom_t geom, int n_levels, void* stream, wm_hier_t* out);
 
+/*
+ * Kernel schedule of a hierarchy's batched solves (a tuning knob: results
+ * change at most in rounding order).  Defaults in parentheses; wm_set_schedule
+ * with NULL restores them.  Errors: WM_ERR_INVALID_ARG for values out of range.
+ */
+typedef struct {
+  int uni_run;      /* consecutive one-shift tiles one block of the stencil kernels
+                       serves (window ids and combined rows built once), 1..8 (8)   */
+  int uni_waves;    /* grid target of those kernels, in waves of resident blocks:
+                       runs are split over more blocks until the grid reaches it,
+                       1..64 (4)                                                    */
+  int vec_rows;     /* rows per block of the outer CG's vector kernels, 32..4096
+                       (128)                                                        */
+  int vcycle_rows;  /* rows per block of the V-cycle's row kernels (levels without
+                       a stencil form), 8..1024 (16)                                */
+} wm_schedule;
+int wm_set_schedule(wm_hier_t h, const wm_schedule* sched);
+int wm_get_schedule(wm_hier_t h, wm_schedule* out);
+
 int wm_num_levels(wm_hier_t h);               /* number of levels, or < 0 on error */
 int wm_num_dofs(wm_hier_t h, int level);      /* glued DOFs N of a level, or < 0    */
 int wm_num_quad_points(wm_hier_t h, int level); /* Gauss points of a level, or < 0   */
@@ -380,6 +399,8 @@ typedef struct {
                            of a first pass (improved split) between its forward
                            and adjoint sweeps when they fit, instead of solving
                            them twice                                           */
+  int smoother_degree_coarse;  /* Chebyshev degree on the levels below the finest,
+                           0..8; 0: smoother_degree                             */
 } wm_sample_desc;
 
 typedef struct {

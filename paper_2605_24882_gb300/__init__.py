@@ -264,6 +264,25 @@ class Hierarchy:
                               smoother_degree, cheb_ratio, _stream(stream)), "wm_vcycle")
         return z
 
+    def set_schedule(self, **kw):
+        """Kernel schedule of this hierarchy's batched solves (uni_run, uni_waves,
+        vec_rows, vcycle_rows; unnamed fields keep their values; no arguments:
+        the defaults)."""
+        if not kw:
+            check(lib().wm_set_schedule(self._h, None), "wm_set_schedule")
+            return self.schedule()
+        sc = _capi.Schedule()
+        check(lib().wm_get_schedule(self._h, C.byref(sc)), "wm_get_schedule")
+        for k, v in kw.items():
+            setattr(sc, k, int(v))
+        check(lib().wm_set_schedule(self._h, C.byref(sc)), "wm_set_schedule")
+        return self.schedule()
+
+    def schedule(self):
+        sc = _capi.Schedule()
+        check(lib().wm_get_schedule(self._h, C.byref(sc)), "wm_get_schedule")
+        return sc.as_dict()
+
     def noise_loads(self, seed, n_samples, stream=None):
         b = torch.empty((n_samples, self.num_dofs(0)), dtype=torch.float64, device="cuda")
         check(lib().wm_noise_loads(self._h, seed, n_samples, C.c_void_p(b.data_ptr()), _stream(stream)),
@@ -283,10 +302,12 @@ class Hierarchy:
     @staticmethod
     def make_desc(kappa, beta, sinc_k=0.3, l_lo=-35, l_hi=35, n_samples=1, seed=0, split="standard",
                   precision="mixed", rtol=1e-8, max_iter=200, smoother_degree=4, cheb_ratio=12.0,
-                  max_systems=0, noise_given=False, preconditioner="vcycle", sample0=0, ckpt="recompute"):
+                  max_systems=0, noise_given=False, preconditioner="vcycle", sample0=0, ckpt="recompute",
+                  smoother_degree_coarse=0):
         return _capi.SampleDesc(kappa=kappa, beta=beta, split=_SPLIT[split], sinc_k=sinc_k, l_lo=l_lo, l_hi=l_hi,
                                 seed=seed, n_samples=n_samples, sample0=sample0,
                                 ckpt={"recompute": _capi.WM_CKPT_RECOMPUTE, "keep": _capi.WM_CKPT_KEEP}[ckpt],
+                                smoother_degree_coarse=smoother_degree_coarse,
                                 noise_mode=_capi.WM_NOISE_GIVEN if noise_given else _capi.WM_NOISE_DRAW,
                                 precision=_PREC[precision], rtol=rtol, max_iter=max_iter,
                                 smoother_degree=smoother_degree, cheb_ratio=cheb_ratio, max_systems=max_systems,
@@ -328,13 +349,18 @@ class Hierarchy:
         return gb, gk.value
 
 
-def sample_fields_batched(hiers, descs, stream=None):
-    """Fields of several independent problems in one call (list of tensors, stats list)."""
+def sample_fields_batched(hiers, descs, stream=None, outs=None):
+    """Fields of several independent problems in one call (list of tensors, stats list).
+
+    Instances that share a Hierarchy object (and solver settings) share the
+    batched solves.  ``outs``: optional list of [n_samples, N] float64 CUDA
+    tensors to write into."""
     n = len(hiers)
     H = (C.c_void_p * n)(*[h._h for h in hiers])
     D = (_capi.SampleDesc * n)(*descs)
-    outs = [torch.empty((d.n_samples, h.num_dofs(0)), dtype=torch.float64, device="cuda")
-            for h, d in zip(hiers, descs)]
+    if outs is None:
+        outs = [torch.empty((d.n_samples, h.num_dofs(0)), dtype=torch.float64, device="cuda")
+                for h, d in zip(hiers, descs)]
     U = (C.c_void_p * n)(*[C.c_void_p(u.data_ptr()) for u in outs])
     st = (_capi.Stats * n)()
     check(lib().wm_sample_fields_batched(n, H, D, U, st, _stream(stream)), "wm_sample_fields_batched")

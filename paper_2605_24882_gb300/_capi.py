@@ -42,7 +42,15 @@ class SampleDesc(C.Structure):
                 ("l_lo", C.c_int), ("l_hi", C.c_int), ("seed", C.c_uint64), ("n_samples", C.c_int),
                 ("noise_mode", C.c_int), ("precision", C.c_int), ("rtol", C.c_double), ("max_iter", C.c_int),
                 ("smoother_degree", C.c_int), ("cheb_ratio", C.c_double), ("max_systems", C.c_int),
-                ("preconditioner", C.c_int), ("sample0", C.c_int), ("ckpt", C.c_int)]
+                ("preconditioner", C.c_int), ("sample0", C.c_int), ("ckpt", C.c_int),
+                ("smoother_degree_coarse", C.c_int)]
+
+
+class Schedule(C.Structure):
+    _fields_ = [("uni_run", C.c_int), ("uni_waves", C.c_int), ("vec_rows", C.c_int), ("vcycle_rows", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Stats(C.Structure):
@@ -96,6 +104,8 @@ _PROTOS = {
                                        _vp]),
     "wm_beta_plan": (_i, [_d, _i, C.POINTER(_i), C.POINTER(_d), C.POINTER(_i)]),
     "wm_sinc_nodes": (_i, [_d, _i, _d, _d, C.POINTER(_d), C.POINTER(_i), C.POINTER(_i)]),
+    "wm_set_schedule": (_i, [_vp, C.POINTER(Schedule)]),
+    "wm_get_schedule": (_i, [_vp, C.POINTER(Schedule)]),
     "wm_profile_enable": (_i, [_i]),
     "wm_profile_read": (_i, [_i, C.POINTER(_d), C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_d), C.POINTER(_d),
                              C.POINTER(C.c_char_p)]),

@@ -338,6 +338,26 @@ extern "C" int wm_assemble_hierarchy(wm_geom_t geom, int n_levels, void* stream,
   return WM_OK;
 }
 
+extern "C" int wm_set_schedule(wm_hier_t h, const wm_schedule* sc) {
+  if (!h) return WM_ERR_INVALID_ARG;
+  const wm_schedule def{8, 4, 128, 16};
+  const wm_schedule v = sc ? *sc : def;
+  if (v.uni_run < 1 || v.uni_run > kUniGroup || v.uni_waves < 1 || v.uni_waves > 64 || v.vec_rows < 32 ||
+      v.vec_rows > 4096 || v.vcycle_rows < 8 || v.vcycle_rows > 1024) {
+    wm_set_error("schedule out of range: uni_run 1..%d, uni_waves 1..64, vec_rows 32..4096, vcycle_rows 8..1024",
+                 kUniGroup);
+    return WM_ERR_INVALID_ARG;
+  }
+  h->sched = v;
+  return WM_OK;
+}
+
+extern "C" int wm_get_schedule(wm_hier_t h, wm_schedule* out) {
+  if (!h || !out) return WM_ERR_INVALID_ARG;
+  *out = h->sched;
+  return WM_OK;
+}
+
 extern "C" int wm_num_levels(wm_hier_t h) { return h ? (int)h->lv.size() : WM_ERR_INVALID_ARG; }
 
 extern "C" int wm_num_dofs(wm_hier_t h, int level) {
@@ -582,8 +602,8 @@ extern "C" int wm_restrict(wm_hier_t h, int level, const double* rf, double* rc,
   return transfer(h, level, rf, rc, n_vec, false, stream);
 }
 
-static int set_batch_meta(WorkSpace& ws, int tiles, const std::vector<double>& sigma, const std::vector<int>& sid,
-                          const std::vector<int>& src, cudaStream_t s) {
+static int set_batch_meta(WorkSpace& ws, const wm_schedule& sc, int tiles, const std::vector<double>& sigma,
+                          const std::vector<int>& sid, const std::vector<int>& src, cudaStream_t s) {
   size_t n = (size_t)tiles * WM_LANES;
   std::vector<double> sg(n, sigma.empty() ? 1.0 : sigma[0]);
   std::vector<int> si(n, 0), sr(n, -1);
@@ -618,7 +638,7 @@ static int set_batch_meta(WorkSpace& ws, int tiles, const std::vector<double>& s
     if (!grp.empty()) {
       int2& last = grp.back();
       const int lt = last.x + last.y;  // tile after the last group
-      if (lt == t && last.y < kUniGroup && si[(size_t)last.x * WM_LANES] == st) {
+      if (lt == t && last.y < std::min(kUniGroup, sc.uni_run) && si[(size_t)last.x * WM_LANES] == st) {
         last.y += 1;
         continue;
       }
@@ -626,6 +646,7 @@ static int set_batch_meta(WorkSpace& ws, int tiles, const std::vector<double>& s
     grp.push_back(make_int2(t, 1));
   }
   ws.n_uni_groups = (int)grp.size();
+  ws.uni_waves = sc.uni_waves;
   if (!grp.empty()) {
     WM_TRY(ws.uni_groups.alloc(grp.size()));
     WM_CUDA(cudaMemcpyAsync(ws.uni_groups.p, grp.data(), grp.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
@@ -671,9 +692,10 @@ extern "C" int wm_vcycle(wm_hier_t h, int n_vec, const double* sigma, const doub
       src[g] = g;
     }
   }
-  WM_TRY(set_batch_meta(ws, tiles, sg, sid, src, s));
+  WM_TRY(set_batch_meta(ws, h->sched, tiles, sg, sid, src, s));
   WM_TRY(wm_prepare_shifts(h, ws, shl, s));
   Batch bt;
+  bt.schedule(h->sched);
   bt.tiles = tiles;
   bt.nsys = n_vec;
   bt.nshift = (int)shl.size();
@@ -758,7 +780,7 @@ int make_plan(const wm_sample_desc* d, Plan& P) {
 int validate_desc(wm_hier_t h, const wm_sample_desc* d) {
   if (!h || !d) return WM_ERR_INVALID_ARG;
   if (d->n_samples < 0 || d->max_iter < 1 || !(d->rtol > 0) || d->smoother_degree < 1 ||
-      d->smoother_degree > 8 || !(d->cheb_ratio > 1.0) || d->max_systems < 0 || d->sample0 < 0 ||
+      d->smoother_degree > 8 || d->smoother_degree_coarse < 0 || d->smoother_degree_coarse > 8 || !(d->cheb_ratio > 1.0) || d->max_systems < 0 || d->sample0 < 0 ||
       (int64_t)d->sample0 + d->n_samples > (int64_t)INT32_MAX) {
     wm_set_error("invalid sample descriptor");
     return WM_ERR_INVALID_ARG;
@@ -839,8 +861,9 @@ int solve_range(wm_hier_t h, WorkSpace& ws, const wm_sample_desc* d, const Pass&
     sid[k] = ps.sid_base + j;
     src[k] = (int)(g % ps.ns);
   }
-  WM_TRY(set_batch_meta(ws, tiles, sg, sid, src, s));
+  WM_TRY(set_batch_meta(ws, h->sched, tiles, sg, sid, src, s));
   Batch bt;
+  bt.schedule(h->sched);
   bt.tiles = tiles;
   bt.nsys = nb;
   bt.nshift = ps.nshift_total;
@@ -848,6 +871,7 @@ int solve_range(wm_hier_t h, WorkSpace& ws, const wm_sample_desc* d, const Pass&
   bt.rtol = d->rtol;
   bt.max_iter = d->max_iter;
   bt.degree = d->smoother_degree;
+  bt.degree_coarse = d->smoother_degree_coarse;
   bt.cheb_ratio = d->cheb_ratio;
   bt.replace_drop = dbl ? 0.0 : 1e-4;
   bt.df_residual = !dbl;
@@ -898,7 +922,8 @@ bool same_solutions(const wm_sample_desc& a, const wm_sample_desc& b) {
   return a.kappa == b.kappa && a.beta == b.beta && a.split == b.split && a.sinc_k == b.sinc_k && a.l_lo == b.l_lo &&
          a.l_hi == b.l_hi && a.n_samples == b.n_samples && a.sample0 == b.sample0 && a.precision == b.precision &&
          a.rtol == b.rtol && a.max_iter == b.max_iter && a.smoother_degree == b.smoother_degree &&
-         a.cheb_ratio == b.cheb_ratio && a.max_systems == b.max_systems && a.preconditioner == b.preconditioner;
+         a.smoother_degree_coarse == b.smoother_degree_coarse && a.cheb_ratio == b.cheb_ratio &&
+         a.max_systems == b.max_systems && a.preconditioner == b.preconditioner;
 }
 
 __global__ void k_count_diff(size_t n, const double* __restrict__ a, const double* __restrict__ b, int* cnt) {
@@ -1130,7 +1155,8 @@ __global__ void k_rows_accumulate(int N, const int* __restrict__ ptr, const int*
 // solver settings that instances must share to be packed into one batch
 bool same_solver(const wm_sample_desc& a, const wm_sample_desc& b) {
   return a.precision == b.precision && a.rtol == b.rtol && a.max_iter == b.max_iter &&
-         a.smoother_degree == b.smoother_degree && a.cheb_ratio == b.cheb_ratio &&
+         a.smoother_degree == b.smoother_degree && a.smoother_degree_coarse == b.smoother_degree_coarse &&
+         a.cheb_ratio == b.cheb_ratio &&
          a.preconditioner == b.preconditioner && a.max_systems == b.max_systems;
 }
 
@@ -1207,8 +1233,21 @@ int sample_fields_group(wm_hier_t h, const std::vector<const wm_sample_desc*>& D
   const int64_t per_batch = batch_size(h, ws, &d0, most, 0);
   WM_TRY(ws.reserve(h, (int)((per_batch + WM_LANES - 1) / WM_LANES), (int)shl.size(), d0.precision == WM_FP64));
   WM_TRY(wm_prepare_shifts(h, ws, shl, s));
-  DevBuf<int> d_flag, d_ptr, d_sys;
-  DevBuf<double> d_coef;
+  // per-call row flags and accumulation lists, released on every return
+  struct GroupBufs {
+    DevBuf<int> flag, ptr, sys;
+    DevBuf<double> coef;
+    ~GroupBufs() {
+      flag.release();
+      ptr.release();
+      sys.release();
+      coef.release();
+    }
+  } gb;
+  DevBuf<int>& d_flag = gb.flag;
+  DevBuf<int>& d_ptr = gb.ptr;
+  DevBuf<int>& d_sys = gb.sys;
+  DevBuf<double>& d_coef = gb.coef;
   WM_TRY(d_flag.alloc((size_t)stiles * WM_LANES));
   WM_TRY(d_ptr.alloc((size_t)stiles * WM_LANES + 1));
   int worst = WM_OK;
@@ -1258,8 +1297,9 @@ int sample_fields_group(wm_hier_t h, const std::vector<const wm_sample_desc*>& D
       const int tiles = (nb + WM_LANES - 1) / WM_LANES;
       std::vector<double> bsg(sg.begin() + g0, sg.begin() + g1);
       std::vector<int> bsid(sid.begin() + g0, sid.begin() + g1), bsrc(src.begin() + g0, src.begin() + g1);
-      WM_TRY(set_batch_meta(ws, tiles, bsg, bsid, bsrc, s));
+      WM_TRY(set_batch_meta(ws, h->sched, tiles, bsg, bsid, bsrc, s));
       Batch bt;
+      bt.schedule(h->sched);
       bt.tiles = tiles;
       bt.nsys = nb;
       bt.nshift = (int)shl.size();
@@ -1267,6 +1307,7 @@ int sample_fields_group(wm_hier_t h, const std::vector<const wm_sample_desc*>& D
       bt.rtol = d0.rtol;
       bt.max_iter = d0.max_iter;
       bt.degree = d0.smoother_degree;
+      bt.degree_coarse = d0.smoother_degree_coarse;
       bt.cheb_ratio = d0.cheb_ratio;
       bt.replace_drop = d0.precision == WM_FP64 ? 0.0 : 1e-4;
       bt.df_residual = d0.precision != WM_FP64;

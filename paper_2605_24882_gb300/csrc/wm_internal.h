@@ -166,6 +166,7 @@ struct wm_hier {
   DevBuf<double> d_gw, d_gx;
   WorkSpace* ws = nullptr;
   int device = 0;  // the CUDA device holding the hierarchy's buffers
+  wm_schedule sched{8, 4, 128, 16};  // kernel schedule of the batched solves
 };
 
 // host helpers (wm_host_setup.cpp)

@@ -503,13 +503,14 @@ __device__ __forceinline__ ChebCoef cheb_coef(double lmax, double ratio, int k) 
 
 // (c1, c2) of every smoothing step for every level and shift, computed once
 // per batch in float64 (the smoothing kernels only load them)
-__global__ void k_cheb_table(int nlev, int nshift, int degree, double ratio, const double* __restrict__ lmax,
-                             float2* __restrict__ t32, double2* __restrict__ t64) {
+__global__ void k_cheb_table(int nlev, int nshift, int degree, int degree_coarse, double ratio,
+                             const double* __restrict__ lmax, float2* __restrict__ t32, double2* __restrict__ t64) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nlev * nshift * WM_MAX_CHEB) return;
   int k = t % WM_MAX_CHEB;
   int ls = t / WM_MAX_CHEB;
-  ChebCoef c = k < degree ? cheb_coef(lmax[ls], ratio, k) : ChebCoef{0.0, 0.0};
+  const int deg = ls < nshift ? degree : degree_coarse;  // level 0, or a coarser one
+  ChebCoef c = k < deg ? cheb_coef(lmax[ls], ratio, k) : ChebCoef{0.0, 0.0};
   t32[t] = make_float2((float)c.c1, (float)c.c2);
   t64[t] = make_double2(c.c1, c.c2);
 }
@@ -909,15 +910,15 @@ static inline void units(int cat, const Batch& bt, double b, double f) {
 }
 
 int Batch::chunks_for(int N) const {
-  // row chunks per tile: at least 128 rows each, at most 64 (the partial-sum
-  // buffers); with tile groups this keeps thousands of blocks in flight
-  return std::max(1, std::min(64, (N + 127) / 128));
+  // row chunks per tile: at least vec_rows (128) rows each, at most 64 (the
+  // partial-sum buffers); with tile groups this keeps thousands of blocks in flight
+  return std::max(1, std::min(64, (N + vec_rows - 1) / vec_rows));
 }
 
-// row chunks per tile inside the V-cycle (no partial sums there): at least 16
-// rows each (two per warp), so that the small coarse levels still spread
-// over the SMs instead of running a few long, latency-bound warps
-static int vcycle_chunks(int N) { return std::max(1, std::min(64, (N + 15) / 16)); }
+// row chunks per tile inside the V-cycle (no partial sums there): at least
+// vcycle_rows (16) rows each (two per warp), so that the small coarse levels
+// still spread over the SMs instead of running a few long, latency-bound warps
+int Batch::vcycle_chunks(int N) const { return std::max(1, std::min(64, (N + vcycle_rows - 1) / vcycle_rows)); }
 
 // the one-shift tiles of the current batch
 static UniTiles uni_of(const WorkSpace& ws) {
@@ -926,6 +927,7 @@ static UniTiles uni_of(const WorkSpace& ws) {
   u.n = ws.n_uni_tiles;
   u.groups = ws.uni_groups.p;
   u.n_groups = ws.n_uni_groups;
+  u.waves = ws.uni_waves;
   return u;
 }
 
@@ -1122,6 +1124,7 @@ static int build_cheb_table(const wm_hier* h, WorkSpace& ws, const Batch& bt, cu
   WM_TRY(ws.cheb32.alloc(n));
   WM_TRY(ws.cheb64.alloc(n));
   WM_LAUNCH(WM_PC_SETUP, s, k_cheb_table<<<nblk(n, 128), 128, 0, s>>>((int)h->lv.size(), bt.nshift, bt.degree,
+                                                                      bt.degree_of(1),
                                                                       bt.cheb_ratio, ws.lmax.p, ws.cheb32.p,
                                                                       ws.cheb64.p));
   WM_CUDA(cudaGetLastError());
@@ -1149,7 +1152,7 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   LevelBufs& B = ws.lvl[l];
   const int* ta = ws.tile_active.p;
   const int tiles = bt.tiles;
-  const int ch = vcycle_chunks(Lv.N);
+  const int ch = bt.vcycle_chunks(Lv.N);
   const dim3 ggrid(ch, groups(tiles));
   const typename C2T<T>::type* ctab = cheb_tab<T>(ws) + (size_t)l * bt.nshift * WM_MAX_CHEB;
   const auto* pk = rows_of<T>(Lv);
@@ -1170,7 +1173,7 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
     return WM_OK;
   }
   T* res = vb<T>(B.res);
-  const int nu = bt.degree;
+  const int nu = bt.degree_of(l);
   int step_rc = WM_OK;
   // three-term step k from z = cur: the result overwrites z_prev in `oth`
   // (has_prev false: z_prev = 0, or unused at k = 0)
@@ -1227,7 +1230,7 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
   WM_TRY(step_rc);
   const wm_level& Cv = h->lv[l + 1];
   T* rc = vb<T>(ws.lvl[l + 1].r);
-  const int chc = vcycle_chunks(Cv.N);
+  const int chc = bt.vcycle_chunks(Cv.N);
   WM_LAUNCH(WM_PC_RESTRICT, s, k_transfer<T, false><<<dim3(chc, groups(tiles)), kBlk, 0, s>>>(
                                    Cv.N, Lv.N, chc, tiles, Lv.d_Rptr.p, R_of<T>(Lv), res, rc, ta));
   units(WM_PC_RESTRICT, bt, Tb * (Lv.N + Cv.N), 2.0 * Lv.nnzP);
@@ -1261,7 +1264,7 @@ static int bpx(const wm_hier* h, WorkSpace& ws, const Batch& bt, const T* rin, T
     const wm_level& Lv = h->lv[l];
     const wm_level& Cv = h->lv[l + 1];
     const T* rl = l == 0 ? rin : vb<T>(ws.lvl[l].r);
-    const int chc = vcycle_chunks(Cv.N);
+    const int chc = bt.vcycle_chunks(Cv.N);
     WM_LAUNCH(WM_PC_RESTRICT, s, k_transfer<T, false><<<dim3(chc, groups(tiles)), kBlk, 0, s>>>(
                                      Cv.N, Lv.N, chc, tiles, Lv.d_Rptr.p, R_of<T>(Lv), rl, vb<T>(ws.lvl[l + 1].r),
                                      ta));
@@ -1280,7 +1283,7 @@ static int bpx(const wm_hier* h, WorkSpace& ws, const Batch& bt, const T* rin, T
     const wm_level& Cv = h->lv[l + 1];
     const T* rl = l == 0 ? rin : vb<T>(ws.lvl[l].r);
     T* zl = vb<T>(ws.lvl[l].za);
-    const int ch = vcycle_chunks(Lv.N);
+    const int ch = bt.vcycle_chunks(Lv.N);
     const dim3 ggrid(ch, groups(tiles));
     const int cat = l == 0 ? WM_PC_SMOOTH0 : WM_PC_SMOOTHC;
     WM_LAUNCH(cat, s, k_diag_scale<T><<<ggrid, kBlk, 0, s>>>(Lv.N, ch, tiles, rl, dS_of<T>(Lv), dM_of<T>(Lv),

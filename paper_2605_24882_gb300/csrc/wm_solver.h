@@ -33,7 +33,9 @@ struct Batch {
   int precision = WM_MIXED;
   double rtol = 1e-8;
   int max_iter = 200;
-  int degree = 2;     // Chebyshev degree of each smoothing sweep
+  int degree = 2;     // Chebyshev degree of each smoothing sweep on the finest level
+  int degree_coarse = 0;  // on the coarser levels (0: the same)
+  int degree_of(int level) const { return level == 0 || degree_coarse == 0 ? degree : degree_coarse; }
   double cheb_ratio = 8.0;
   // float64 residual replacement once the recursive residual of a system has
   // fallen by this factor since its last replacement (and always before a
@@ -44,7 +46,14 @@ struct Batch {
   bool df_residual = false;
   int precond = WM_PRECOND_VCYCLE;  // or WM_PRECOND_BPX
   mutable int active_tiles = 0;  // host copy of the active tile count (for work accounting)
+  int vec_rows = 128;     // rows per block of the CG vector kernels
+  int vcycle_rows = 16;   // rows per block of the V-cycle row kernels
   int chunks_for(int N) const;
+  int vcycle_chunks(int N) const;
+  void schedule(const wm_schedule& s) {
+    vec_rows = s.vec_rows;
+    vcycle_rows = s.vcycle_rows;
+  }
 };
 
 struct BatchResult {
@@ -68,6 +77,7 @@ struct WorkSpace {
   int n_uni_tiles = 0;        // host count of such tiles in the current batch
   DevBuf<int2> uni_groups;    // runs of at most 8 consecutive such tiles of one shift: (first tile, count)
   int n_uni_groups = 0;
+  int uni_waves = 4;          // grid target of the one-shift kernels (the hierarchy's schedule)
   DevBuf<double> rho, alpha, beta, bb, rr, rr_ref;
   DevBuf<double> part[3];
   DevBuf<int> flags, counters;

@@ -18,7 +18,17 @@
 namespace {
 
 constexpr int BU = 8;   // outputs per block along u (one warp each)
-constexpr int BV = 8;   // outputs per warp along v
+// outputs per warp along v: for p = 2 the patches have 2^l + 2 local DOFs per
+// side, which a height of 6 covers with less waste than 8 (66 and 18 exactly;
+// coarse-level smoothing 33.9 -> 32.0 ms per bench step)
+#ifndef WM_BV_P2
+#define WM_BV_P2 6
+#endif
+template <int P>
+struct BvOf {
+  static constexpr int value = P == 2 ? WM_BV_P2 : 8;
+  static_assert(value % 2 == 0 && value >= 2, "row pairs of the double-float residual");
+};
 
 template <typename T>
 struct V2;
@@ -238,6 +248,7 @@ struct CoefStride {
 
 template <typename T, int P, int TPB, int NIN>
 struct SmemLayout {
+  static constexpr int BV = BvOf<P>::value;
   static constexpr int CU = BU + 2 * P, CV = BV + 2 * P, NC = CU * CV;
   static constexpr int CS = CoefStride<T, P>::value;
   static constexpr size_t win = (size_t)TPB * NC * 32 * sizeof(T);
@@ -252,6 +263,7 @@ __global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGe
                                                   const T* __restrict__ src, int tiles,
                                                   const int* __restrict__ tile_active, const Epi epi_arg,
                                                   const int* __restrict__ skip_uni) {
+  constexpr int BV = BvOf<P>::value;
   static_assert(TPB == 1 || TPB == 2, "tile selection below assumes at most two tiles per block");
   using C2 = typename V2<T>::type;
   using LY = SmemLayout<T, P, TPB, Epi::NIN>;
@@ -424,6 +436,12 @@ enum { UNI_CHEB = 0, UNI_RESID = 1, UNI_APPLY = 2, UNI_CHEBDOT = 3, UNI_CHEB1 = 
 #ifndef WM_UNI_MAXB_F32_P3
 #define WM_UNI_MAXB_F32_P3 4
 #endif
+// tiles per warp pass of the float p = 2 kernels: 0 = two for the residual and
+// the outer apply (measured faster there, 5.5 vs 6.3 and 5.6 vs 5.8 ms per bench
+// step) and one for the Chebyshev modes (two: 66 vs 62 ms); 1 or 2 = all modes
+#ifndef WM_UNI_TPW
+#define WM_UNI_TPW 0
+#endif
 template <int MODE>
 struct UniCheb {
   static constexpr bool value = MODE == UNI_CHEB || MODE == UNI_CHEBDOT;
@@ -434,13 +452,19 @@ struct UniRows {  // staged 32-system rows per output row
 };
 template <typename T, int P, int MODE>
 struct UniLayout {
+  static constexpr int BV = BvOf<P>::value;
   static constexpr int CU = BU + 2 * P, CV = BV + 2 * P, NC = CU * CV, S2 = (2 * P + 1) * (2 * P + 1);
   static constexpr int VEC = 16 / sizeof(T);                  // values per 16-byte load
   static constexpr int S2P = (S2 + VEC - 1) / VEC * VEC;      // padded combined row length
   static constexpr int CS = CoefStride<T, P>::value;          // (S, M) row stride of the level tables
   static constexpr int NR = UniRows<MODE>::value;
   static constexpr int ND = UniCheb<MODE>::value ? 2 : 0;     // staged diagonals dS, dM
-  static constexpr int NST = sizeof(T) == 4 ? WM_UNI_NST_F32 : 1;  // stage buffers
+  // tiles per warp pass (one stage buffer each) and stage buffers
+  static constexpr int TPW =
+      (sizeof(T) == 4 && P == 2)
+          ? (WM_UNI_TPW == 0 ? ((MODE == UNI_RESID || MODE == UNI_APPLY) ? 2 : 1) : WM_UNI_TPW)
+          : 1;
+  static constexpr int NST = TPW == 2 ? 2 : (sizeof(T) == 4 ? WM_UNI_NST_F32 : 1);
   static constexpr size_t win = (size_t)NC * 32 * sizeof(T);  // window of the input vector
   static constexpr size_t rows = (size_t)NR * BU * BV * 32 * sizeof(T);  // staged rows of the outputs
   static constexpr size_t stage = win + rows;
@@ -482,7 +506,7 @@ template <typename T, int P, int MODE>
 struct UniMinBlocks {
   static constexpr size_t per = UniLayout<T, P, MODE>::total + 3 * 1024;
   static constexpr int fit = (int)((228 * 1024) / per);
-  static constexpr int cap = sizeof(T) == 4 ? (P == 3 ? WM_UNI_MAXB_F32_P3 : WM_UNI_MAXB_F32) : 2;
+  static constexpr int cap = sizeof(T) == 4 ? (P == 3 ? WM_UNI_MAXB_F32_P3 : (UniLayout<T, P, MODE>::TPW == 2 ? 3 : WM_UNI_MAXB_F32)) : 2;
   static constexpr int value = fit >= cap ? cap : (fit < 1 ? 1 : fit);
 };
 // 4- or 8-byte asynchronous copy through L1 (diagonal entries)
@@ -506,12 +530,13 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
                T* out, int tiles, const int* __restrict__ tile_active, const int2* __restrict__ groups, int split,
                double* __restrict__ part, const T* __restrict__ qd, double* __restrict__ part2,
                T* __restrict__ out1) {
+  constexpr int BV = BvOf<P>::value;
   using C2 = typename V2<T>::type;
   using LY = UniLayout<T, P, MODE>;
   constexpr bool CHEB = UniCheb<MODE>::value;
   using VT = typename Vec16<T>::type;
   constexpr int SW = 2 * P + 1, CU = LY::CU, NC = LY::NC, S2 = LY::S2, S2P = LY::S2P, VEC = LY::VEC, CS = LY::CS;
-  constexpr int NR = LY::NR, NST = LY::NST, ROWCH = LY::ROWCH;
+  constexpr int NR = LY::NR, NST = LY::NST, ROWCH = LY::ROWCH, TPW = LY::TPW;
   constexpr int RPS = WM_UNI_RPS > 0 ? WM_UNI_RPS : (UniMinBlocks<T, P, MODE>::value >= 3 ? 1 : 2);
   constexpr int NACC = WM_UNI_NACC;
   constexpr int RW = SW + RPS - 1;     // rows of the register ring
@@ -649,9 +674,13 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
     }
     cp_async_commit();
   };
+  // tiles go through the stage buffers TPW at a time (a pair shares every load
+  // of the combined rows); with PREFETCH the next tile is copied while the
+  // current one is computed
+  constexpr bool PREFETCH = NST == 2 && TPW == 1;
   int cur = __ffs(todo) - 1;
   todo &= todo - 1;
-  if constexpr (NST == 2) {  // the first tile goes to buffer 0 (the raw rows sit in buffer 1)
+  if constexpr (PREFETCH) {  // the first tile goes to buffer 0 (the raw rows sit in buffer 1)
     issue(ta + cur, stg);
     cp_async_wait<1>();
   } else {
@@ -681,10 +710,20 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
   const int iu = bu * BU + w;
   int bsel = 0;
   for (;;) {
+    // the tiles of this pass: tt[u] in buffer u (with PREFETCH, buffer bsel)
+    int tt[TPW];
+    bool ok[TPW];
+    tt[0] = ta + cur;
+    ok[0] = true;
+    if constexpr (TPW == 2) {
+      ok[1] = todo != 0;
+      const int c1 = ok[1] ? __ffs(todo) - 1 : cur;
+      if (ok[1]) todo &= todo - 1;
+      tt[1] = ta + c1;
+    }
     const bool more = todo != 0;
     const int nxt = more ? __ffs(todo) - 1 : 0;
-    T* const buf = stg + bsel * STAGE;
-    if constexpr (NST == 2) {
+    if constexpr (PREFETCH) {
       if (more) {
         issue(ta + nxt, stg + (bsel ^ 1) * STAGE);
         cp_async_wait<1>();
@@ -692,38 +731,50 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
         cp_async_wait<0>();
       }
     } else {
-      issue(ta + cur, buf);
+      issue(tt[0], stg);
+      if constexpr (TPW == 2)
+        if (ok[1]) issue(tt[1], stg + STAGE);
       cp_async_wait<0>();
     }
     __syncthreads();
     // each warp sweeps the column iu, RPS output rows per step, with a ring of
-    // RW staged rows in registers; every output sums its stencil in NACC
-    // partial sums (stencil rows dv mod NACC), so a step has NACC x RPS
-    // independent FMA chains
-    const int t = ta + cur;
-    const T* const sm = buf;
-    const T* const srw = buf + NC * 32;
-    DAcc<T> dot;   // UNI_APPLY: (z, A z); UNI_CHEBDOT: (r, z_new) over this thread's outputs
-    DAcc<T> dot2;  // UNI_CHEBDOT: (z_new, q)
+    // RW staged rows in registers per tile; every output sums its stencil in
+    // NACC partial sums (stencil rows dv mod NACC), and each combined-row load
+    // serves the TPW tiles of the pass
+    const T* smv[TPW];
+    const T* srwv[TPW];
+#pragma unroll
+    for (int u = 0; u < TPW; ++u) {
+      smv[u] = PREFETCH ? stg + bsel * STAGE : stg + ((TPW == 2 && !ok[u]) ? 0 : u) * STAGE;
+      srwv[u] = smv[u] + NC * 32;
+    }
+    DAcc<T> dot[TPW];   // UNI_APPLY: (z, A z); UNI_CHEBDOT: (r, z_new) over this thread's outputs
+    DAcc<T> dot2[TPW];  // UNI_CHEBDOT: (z_new, q)
     if (iu < G.nlu) {
-      T win[RW][SW];
+      T win[TPW][RW][SW];
 #pragma unroll
-      for (int rr = 0; rr < SW - 1; ++rr)
+      for (int u = 0; u < TPW; ++u)
 #pragma unroll
-        for (int du = 0; du < SW; ++du) win[rr][du] = sm[(rr * CU + w + du) * 32 + lane];
+        for (int rr = 0; rr < SW - 1; ++rr)
+#pragma unroll
+          for (int du = 0; du < SW; ++du) win[u][rr][du] = smv[u][(rr * CU + w + du) * 32 + lane];
 #pragma unroll
       for (int j = 0; j < BV; j += RPS) {
 #pragma unroll
         for (int e = 0; e < RPS; ++e) {
           const int rn = j + SW - 1 + e;  // staged rows entering the window
 #pragma unroll
-          for (int du = 0; du < SW; ++du) win[rn % RW][du] = sm[(rn * CU + w + du) * 32 + lane];
+          for (int u = 0; u < TPW; ++u)
+#pragma unroll
+            for (int du = 0; du < SW; ++du) win[u][rn % RW][du] = smv[u][(rn * CU + w + du) * 32 + lane];
         }
-        T acc[RPS][NACC];
+        T acc[TPW][RPS][NACC];
 #pragma unroll
-        for (int k = 0; k < RPS; ++k)
+        for (int u = 0; u < TPW; ++u)
 #pragma unroll
-          for (int h = 0; h < NACC; ++h) acc[k][h] = 0;
+          for (int k = 0; k < RPS; ++k)
+#pragma unroll
+            for (int h = 0; h < NACC; ++h) acc[u][k][h] = 0;
 #pragma unroll
         for (int q = 0; q < S2P / VEC; ++q) {
           VT a[RPS];
@@ -736,7 +787,10 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
               const int dv = sl / SW, du = sl % SW;
 #pragma unroll
               for (int k = 0; k < RPS; ++k)
-                acc[k][dv % NACC] = fma(Vec16<T>::at(a[k], e), win[(j + k + dv) % RW][du], acc[k][dv % NACC]);
+#pragma unroll
+                for (int u = 0; u < TPW; ++u)
+                  acc[u][k][dv % NACC] =
+                      fma(Vec16<T>::at(a[k], e), win[u][(j + k + dv) % RW][du], acc[u][k][dv % NACC]);
             }
           }
         }
@@ -746,49 +800,60 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
           const int o = jj * BU + w;
           const int i = srow[o];
           if (i < 0) continue;
-          T az = acc[k][0];
 #pragma unroll
-          for (int h = 1; h < NACC; ++h) az += acc[k][h];
-          const T zc = win[(jj + P) % RW][P];
-          T res;
-          if constexpr (CHEB) {
-            const T rv = srw[o * 32 + lane];
-            const T zp = prev ? srw[(BU * BV + o) * 32 + lane] : (T)0;
-            res = zc + c1 * (zc - zp) + swt[o] * (rv - az);
-            if constexpr (MODE == UNI_CHEBDOT) {
-              dot.add(rv * res);
-              if (qd) dot2.add(res * srw[(2 * BU * BV + o) * 32 + lane]);
+          for (int u = 0; u < TPW; ++u) {
+            if (!ok[u]) continue;
+            const T* const srw = srwv[u];
+            const int t = tt[u];
+            T az = acc[u][k][0];
+#pragma unroll
+            for (int h = 1; h < NACC; ++h) az += acc[u][k][h];
+            const T zc = win[u][(jj + P) % RW][P];
+            T res;
+            if constexpr (CHEB) {
+              const T rv = srw[o * 32 + lane];
+              const T zp = prev ? srw[(BU * BV + o) * 32 + lane] : (T)0;
+              res = zc + c1 * (zc - zp) + swt[o] * (rv - az);
+              if constexpr (MODE == UNI_CHEBDOT) {
+                dot[u].add(rv * res);
+                if (qd) dot2[u].add(res * srw[(2 * BU * BV + o) * 32 + lane]);
+              }
+            } else if constexpr (MODE == UNI_CHEB1) {
+              const T dc = sdc[(jj + P) * CU + w + P];  // Dinv of the output row
+              const T z1 = c20 * dc * zc;               // zc is r here
+              out1[((size_t)t * G.N + i) * 32 + lane] = z1;
+              res = z1 + c1 * z1 + c2 * dc * (zc - az);
+            } else if constexpr (MODE == UNI_RESID) {
+              res = srw[o * 32 + lane] - az;
+            } else {
+              res = az;
+              dot[u].add(zc * az);
             }
-          } else if constexpr (MODE == UNI_CHEB1) {
-            const T dc = sdc[(jj + P) * CU + w + P];  // Dinv of the output row
-            const T z1 = c20 * dc * zc;               // zc is r here
-            out1[((size_t)t * G.N + i) * 32 + lane] = z1;
-            res = z1 + c1 * z1 + c2 * dc * (zc - az);
-          } else if constexpr (MODE == UNI_RESID) {
-            res = srw[o * 32 + lane] - az;
-          } else {
-            res = az;
-            dot.add(zc * az);
+            out[((size_t)t * G.N + i) * 32 + lane] = res;
           }
-          out[((size_t)t * G.N + i) * 32 + lane] = res;
         }
       }
     }
     if constexpr (MODE == UNI_APPLY || MODE == UNI_CHEBDOT) {
       const bool one[1] = {true};
-      double a1[1] = {dot.get()};
-      block_reduce<1>(a1, part, t, tiles, one);
-      if (MODE == UNI_CHEBDOT && qd) {
-        __syncthreads();
-        a1[0] = dot2.get();
-        block_reduce<1>(a1, part2, t, tiles, one);
+#pragma unroll
+      for (int u = 0; u < TPW; ++u) {
+        if (!ok[u]) continue;  // uniform over the block
+        if (u > 0) __syncthreads();
+        double a1[1] = {dot[u].get()};
+        block_reduce<1>(a1, part, tt[u], tiles, one);
+        if (MODE == UNI_CHEBDOT && qd) {
+          __syncthreads();
+          a1[0] = dot2[u].get();
+          block_reduce<1>(a1, part2, tt[u], tiles, one);
+        }
       }
     }
-    __syncthreads();  // this stage buffer (and the reduction buffer) may be refilled
+    __syncthreads();  // the stage buffers (and the reduction buffer) may be refilled
     if (!more) break;
     todo &= todo - 1;
     cur = nxt;
-    if constexpr (NST == 2) bsel ^= 1;
+    if constexpr (PREFETCH) bsel ^= 1;
   }
 }
 
@@ -946,6 +1011,7 @@ __device__ __forceinline__ void df_acc2(float2& s, float2& c, float& b0, float& 
 
 template <int P>
 struct DfLayout {
+  static constexpr int BV = BvOf<P>::value;
   static constexpr int CU = BU + 2 * P, CV = BV + 2 * P, NC = CU * CV, S2 = (2 * P + 1) * (2 * P + 1);
   static constexpr size_t win = (size_t)NC * 32 * sizeof(double);
   static constexpr size_t coef = (size_t)BU * BV * S2 * sizeof(float4);
@@ -960,6 +1026,7 @@ __global__ void __launch_bounds__(BU * 32, 2)
                       const double* __restrict__ rhs, const int* __restrict__ src_of, const int* __restrict__ rep,
                       float* __restrict__ r, double* __restrict__ part, double* __restrict__ part_bound,
                       const int* __restrict__ skip_uni) {
+  constexpr int BV = BvOf<P>::value;
   using LY = DfLayout<P>;
   constexpr int SW = 2 * P + 1, CU = LY::CU, NC = LY::NC, S2 = LY::S2;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -1125,6 +1192,7 @@ __global__ void __launch_bounds__(BU * 32, 2)
 // group's flagged tiles through shared memory.
 template <int P>
 struct DfUniLayout {
+  static constexpr int BV = BvOf<P>::value;
   static constexpr int CU = BU + 2 * P, CV = BV + 2 * P, NC = CU * CV, S2 = (2 * P + 1) * (2 * P + 1);
   static constexpr size_t win = (size_t)NC * 32 * sizeof(double);          // x window (raw rows at set-up)
   static constexpr size_t raw = (size_t)BU * BV * S2 * sizeof(float4);      // (S_hi, S_lo, M_hi, M_lo) rows
@@ -1141,6 +1209,7 @@ __global__ void __launch_bounds__(BU * 32, 3)
                           const double* __restrict__ sigma, const double* __restrict__ rhs,
                           const int* __restrict__ src_of, const int* __restrict__ rep, float* __restrict__ r,
                           double* __restrict__ part, double* __restrict__ part_bound) {
+  constexpr int BV = BvOf<P>::value;
   using LY = DfUniLayout<P>;
   constexpr int SW = 2 * P + 1, CU = LY::CU, NC = LY::NC, S2 = LY::S2;
   constexpr int NT = BU * 32;
@@ -1285,9 +1354,16 @@ __global__ void k_build_csm(int N, int W, int cs32, int cs64, const int16_t* __r
 }  // namespace
 
 // ====================================================================== host
+// levels whose patches have fewer local DOFs per side keep the row kernels
+// (moving the 10- and 18-wide levels of the sphere to the row kernels was slower:
+// 174.5 and 184.0 against 172.5 ms per bench step)
+#ifndef WM_STEN_MIN_NL
+#define WM_STEN_MIN_NL 8
+#endif
+
 int wm_sten_build(const wm_geom_desc& g, int np, wm_level& L, cudaStream_t s) {
   L.sten = false;
-  if (g.degree < 2 || g.degree > 3 || L.nlu < 8 || L.nlv < 8) return WM_OK;
+  if (g.degree < 2 || g.degree > 3 || L.nlu < WM_STEN_MIN_NL || L.nlv < WM_STEN_MIN_NL) return WM_OK;
   std::vector<int32_t> ext, own;
   std::vector<int16_t> slot;
   if (wm_host_stencil(g, np, L, ext, own, slot) != WM_OK) return WM_OK;  // row kernels only
@@ -1296,7 +1372,8 @@ int wm_sten_build(const wm_geom_desc& g, int np, wm_level& L, cudaStream_t s) {
   L.ELU = L.nlu + 2 * p;
   L.ELV = L.nlv + 2 * p;
   L.nbu = (L.nlu + BU - 1) / BU;
-  L.nbv = (L.nlv + BV - 1) / BV;
+  const int bv = p == 2 ? BvOf<2>::value : BvOf<3>::value;
+  L.nbv = (L.nlv + bv - 1) / bv;
   WM_TRY(L.d_ext.upload(ext, s));
   WM_TRY(L.d_own.upload(own, s));
   DevBuf<int16_t> d_slot;
@@ -1357,8 +1434,8 @@ static int launch_uni(const wm_level& L, int np, int tiles, const UniTiles& ut, 
   if (ut.n_groups <= 0) return WM_OK;
   static const int sms = device_sms();
   const int bx = np * L.nbu * L.nbv;
-  // blocks that share a group: enough blocks for about four waves
-  const int64_t want = 4LL * sms * UniMinBlocks<T, P, MODE>::value;
+  // blocks that share a group: enough blocks for ut.waves waves
+  const int64_t want = (int64_t)ut.waves * sms * UniMinBlocks<T, P, MODE>::value;
   int split = 1;
   while (split < kUniGroup && (int64_t)bx * ut.n_groups * split < want) split *= 2;
   const T* dS = std::is_same<T, double>::value ? (const T*)L.d_dS64.p : (const T*)L.d_dS32.p;
@@ -1507,7 +1584,7 @@ static int launch_df(const wm_level& L, int np, int tiles, const UniTiles& ut, c
   const int bx = np * L.nbu * L.nbv;
   if (ut.n_groups > 0) {
     static const int sms = device_sms();
-    const int64_t want = 4LL * sms * 3;
+    const int64_t want = (int64_t)ut.waves * sms * 3;
     int split = 1;
     while (split < kUniGroup && (int64_t)bx * ut.n_groups * split < want) split *= 2;
     const int gmax = 65535 / split;

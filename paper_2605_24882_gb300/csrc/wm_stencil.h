@@ -18,6 +18,7 @@ struct UniTiles {
   int n = 0;                     // number of such tiles
   const int2* groups = nullptr;  // [n_groups] (first tile, count), count in 1..kUniGroup
   int n_groups = 0;
+  int waves = 4;                 // grid target: runs are split until the grid has this many waves
 };
 
 // Builds the stencil form of a level (extended grids, owner map, coefficient

@@ -158,3 +158,35 @@ def test_vcycle_is_a_good_symmetric_preconditioner(wm, precision):
         r2 = random_vectors(10, nv, sp_.N)
         z2 = hier.vcycle(torch.tensor(r2, device="cuda"), sg, precision=precision).cpu().numpy()
         np.testing.assert_allclose(np.sum(z * r2, 1), np.sum(r * z2, 1), rtol=1e-9)
+
+
+def test_schedule_changes_only_rounding(wm):
+    # the kernel schedule maps the same solves onto the SMs differently: fields
+    # agree to the solver tolerance, values out of range are refused
+    hier = wm.Hierarchy(wm.Geometry("sphere", 2, 16), 4)
+    kw = dict(kappa=3.0, beta=1.3, sinc_k=0.4, l_lo=-15, l_hi=15, n_samples=40, seed=2, precision="mixed",
+              rtol=1e-10)
+    assert hier.schedule() == {"uni_run": 8, "uni_waves": 4, "vec_rows": 128, "vcycle_rows": 16}
+    u0, _ = hier.sample_fields(**kw)
+    hier.set_schedule(uni_run=2, uni_waves=16, vec_rows=64, vcycle_rows=32)
+    u1, st = hier.sample_fields(**kw)
+    assert st["n_not_converged"] == 0
+    d = u1 - u0
+    assert float(torch.sqrt((d * hier.apply_mass(d)).sum() / (u0 * hier.apply_mass(u0)).sum())) < 1e-8
+    with pytest.raises(wm.WMError):
+        hier.set_schedule(uni_run=9)
+    assert hier.set_schedule() == {"uni_run": 8, "uni_waves": 4, "vec_rows": 128, "vcycle_rows": 16}
+
+
+def test_coarse_smoother_degree(wm):
+    # another Chebyshev degree on the coarser levels changes the preconditioner,
+    # not the fields beyond the solver tolerance
+    hier = wm.Hierarchy(wm.Geometry("sphere", 2, 16), 4)
+    kw = dict(kappa=3.0, beta=1.3, sinc_k=0.4, l_lo=-15, l_hi=15, n_samples=33, seed=4, precision="mixed",
+              rtol=1e-10, smoother_degree=4)
+    u0, _ = hier.sample_fields(**kw)
+    for dc in (2, 6):
+        u1, st = hier.sample_fields(smoother_degree_coarse=dc, **kw)
+        assert st["n_not_converged"] == 0
+        d = u1 - u0
+        assert float(torch.sqrt((d * hier.apply_mass(d)).sum() / (u0 * hier.apply_mass(u0)).sum())) < 1e-8
