@@ -446,7 +446,10 @@ int wm_sample_fields(wm_hier_t h, const wm_sample_desc* desc, double* u, double*
  * all the group's instances is one list of shifted systems, each with its own
  * shift, sample and sinc weight, solved in memory-sized batches; the first
  * stage takes the loads, every later one M times the previous stage's result.
- * Groups run one after another on the stream.  ckpt is not used here.
+ * Groups run one after another on the stream; when the call has several
+ * groups, each hierarchy's workspace (with any checkpoint it held) is released
+ * after its last group, so later groups can size their batches to the free
+ * memory.  ckpt is not used here.
  * stats: host [n_inst] or NULL; per instance: its systems, convergence and
  * largest final relative residual exactly; iterations, batches, replacements
  * and fallbacks of the batches it took part in.  The stream is synchronised
