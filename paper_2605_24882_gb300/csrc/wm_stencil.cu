@@ -477,12 +477,16 @@ struct UniLayout {
                                                    : (size_t)(ND + 1) * BU * BV * sizeof(T);  // dS, dM, w
   static constexpr size_t diag16 = (diag + 15) / 16 * 16;
   static constexpr size_t ids = (size_t)(NC + BU * BV) * sizeof(int);
-  static constexpr size_t total = stages + coef + diag16 + ids;
+  // float Chebyshev modes: (row id, weight) of every output as one 8-byte entry
+  static constexpr bool PACK_IW = UniCheb<MODE>::value && sizeof(T) == 4;
+  static constexpr size_t iw = PACK_IW ? (size_t)BU * BV * sizeof(int2) : 0;
+  static constexpr size_t total = stages + coef + diag16 + ids + iw;
   // 16-byte copies of one staged tile: window chunks and row chunks, and per thread
   static constexpr int ROWCH = 32 * sizeof(T) / 16;
   static constexpr int WCH = NC * ROWCH, RCH = BU * BV * ROWCH;
   static constexpr int WPT = (WCH + BU * 32 - 1) / (BU * 32), RPT = (RCH + BU * 32 - 1) / (BU * 32);
   static_assert(stage % 16 == 0 && raw % 16 == 0 && coef % 16 == 0, "16-byte aligned regions");
+  static_assert(!PACK_IW || (stages + coef + diag16 + ids) % 8 == 0, "8-byte aligned (row id, weight) entries");
 };
 template <typename T>
 struct Vec16;
@@ -552,6 +556,7 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
   T* const swt = sdg + LY::ND * BU * BV;
   int* const sid_ = reinterpret_cast<int*>(smraw + LY::stages + LY::coef + LY::diag16);
   int* const srow = sid_ + NC;
+  int2* const siw = reinterpret_cast<int2*>(smraw + LY::stages + LY::coef + LY::diag16 + LY::ids);  // PACK_IW
   const int lane = threadIdx.x, w = threadIdx.y;
   const int tid = w * 32 + lane;
   int b = blockIdx.x;
@@ -705,7 +710,11 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
     scf[c] = a;
   }
   if constexpr (CHEB)
-    for (int c = tid; c < BU * BV; c += NT) swt[c] = srow[c] >= 0 ? c2 / (sdg[c] + sg * sdg[BU * BV + c]) : (T)0;
+    for (int c = tid; c < BU * BV; c += NT) {
+      const T wc = srow[c] >= 0 ? c2 / (sdg[c] + sg * sdg[BU * BV + c]) : (T)0;
+      swt[c] = wc;
+      if constexpr (LY::PACK_IW) siw[c] = make_int2(srow[c], __float_as_int((float)wc));
+    }
   __syncthreads();  // the raw rows are dead from here on (buffer 1 may be refilled)
   const int iu = bu * BU + w;
   int bsel = 0;
@@ -798,7 +807,16 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
         for (int k = 0; k < RPS; ++k) {
           const int jj = j + k;
           const int o = jj * BU + w;
-          const int i = srow[o];
+          int i;
+          T wo = 0;  // the output's Chebyshev weight (one 8-byte load with its row id in float)
+          if constexpr (LY::PACK_IW) {
+            const int2 iw = siw[o];
+            i = iw.x;
+            wo = __int_as_float(iw.y);
+          } else {
+            i = srow[o];
+            if constexpr (CHEB) wo = swt[o];
+          }
           if (i < 0) continue;
 #pragma unroll
           for (int u = 0; u < TPW; ++u) {
@@ -813,7 +831,7 @@ __global__ void __launch_bounds__(BU * 32, UniMinBlocks<T, P, MODE>::value)
             if constexpr (CHEB) {
               const T rv = srw[o * 32 + lane];
               const T zp = prev ? srw[(BU * BV + o) * 32 + lane] : (T)0;
-              res = zc + c1 * (zc - zp) + swt[o] * (rv - az);
+              res = zc + c1 * (zc - zp) + wo * (rv - az);
               if constexpr (MODE == UNI_CHEBDOT) {
                 dot[u].add(rv * res);
                 if (qd) dot2[u].add(res * srw[(2 * BU * BV + o) * 32 + lane]);
