@@ -235,6 +235,11 @@ typedef struct {
                        (128)                                                        */
   int vcycle_rows;  /* rows per block of the V-cycle's row kernels (levels without
                        a stencil form), 8..1024 (16)                                */
+  int tail_fused;   /* float solves: the V-cycle from the first level without a
+                       stencil form down to the coarse solve and back in one
+                       kernel per tile (vectors in shared memory), where those
+                       levels fit a block's shared memory; 0: one launch per
+                       level and step.  0 or 1 (1)                                  */
 } wm_schedule;
 int wm_set_schedule(wm_hier_t h, const wm_schedule* sched);
 int wm_get_schedule(wm_hier_t h, wm_schedule* out);

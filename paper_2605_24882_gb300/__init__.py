@@ -266,8 +266,8 @@ class Hierarchy:
 
     def set_schedule(self, **kw):
         """Kernel schedule of this hierarchy's batched solves (uni_run, uni_waves,
-        vec_rows, vcycle_rows; unnamed fields keep their values; no arguments:
-        the defaults)."""
+        vec_rows, vcycle_rows, tail_fused; unnamed fields keep their values; no
+        arguments: the defaults)."""
         if not kw:
             check(lib().wm_set_schedule(self._h, None), "wm_set_schedule")
             return self.schedule()

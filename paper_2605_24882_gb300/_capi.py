@@ -47,7 +47,8 @@ class SampleDesc(C.Structure):
 
 
 class Schedule(C.Structure):
-    _fields_ = [("uni_run", C.c_int), ("uni_waves", C.c_int), ("vec_rows", C.c_int), ("vcycle_rows", C.c_int)]
+    _fields_ = [("uni_run", C.c_int), ("uni_waves", C.c_int), ("vec_rows", C.c_int), ("vcycle_rows", C.c_int),
+                ("tail_fused", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

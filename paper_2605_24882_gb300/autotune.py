@@ -6,7 +6,8 @@ and the ratio r of its interval [lambda_max / r, 1.1 lambda_max].  A higher degr
 saves outer iterations; the best pair depends on the spline degree, the mesh
 and the shifts.  The kernel schedule of a hierarchy (wm_schedule: tiles per
 run of the one-shift stencil kernels, their grid target in waves, rows per
-block of the vector and coarse-level kernels) changes how the batched solves
+block of the vector and coarse-level kernels, the fused coarse end of the
+V-cycle) changes how the batched solves
 map onto the SMs, not their results beyond rounding order.
 
 `tune` times `sample_fields` on the caller's problem (CUDA events, after a
@@ -32,6 +33,7 @@ SCHEDULE_CHOICES = {
     "uni_waves": (2, 4, 8, 16),
     "vec_rows": (64, 128, 256, 512),
     "vcycle_rows": (8, 16, 32),
+    "tail_fused": (0, 1),
 }
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 

@@ -340,11 +340,12 @@ extern "C" int wm_assemble_hierarchy(wm_geom_t geom, int n_levels, void* stream,
 
 extern "C" int wm_set_schedule(wm_hier_t h, const wm_schedule* sc) {
   if (!h) return WM_ERR_INVALID_ARG;
-  const wm_schedule def{8, 4, 128, 16};
+  const wm_schedule def{8, 4, 128, 16, 1};
   const wm_schedule v = sc ? *sc : def;
   if (v.uni_run < 1 || v.uni_run > kUniGroup || v.uni_waves < 1 || v.uni_waves > 64 || v.vec_rows < 32 ||
-      v.vec_rows > 4096 || v.vcycle_rows < 8 || v.vcycle_rows > 1024) {
-    wm_set_error("schedule out of range: uni_run 1..%d, uni_waves 1..64, vec_rows 32..4096, vcycle_rows 8..1024",
+      v.vec_rows > 4096 || v.vcycle_rows < 8 || v.vcycle_rows > 1024 || v.tail_fused < 0 || v.tail_fused > 1) {
+    wm_set_error("schedule out of range: uni_run 1..%d, uni_waves 1..64, vec_rows 32..4096, vcycle_rows 8..1024, "
+                 "tail_fused 0..1",
                  kUniGroup);
     return WM_ERR_INVALID_ARG;
   }

@@ -166,7 +166,7 @@ struct wm_hier {
   DevBuf<double> d_gw, d_gx;
   WorkSpace* ws = nullptr;
   int device = 0;  // the CUDA device holding the hierarchy's buffers
-  wm_schedule sched{8, 4, 128, 16};  // kernel schedule of the batched solves
+  wm_schedule sched{8, 4, 128, 16, 1};  // kernel schedule of the batched solves
 };
 
 // host helpers (wm_host_setup.cpp)
@@ -248,6 +248,7 @@ enum {
   WM_PC_ASSEMBLY,      // metric, element matrices, rows
   WM_PC_APPLY,         // component operator applies
   WM_PC_TRUERES,       // float64 true residual b - A x (residual replacement)
+  WM_PC_VTAIL,         // fused coarse end of the V-cycle (levels without a stencil form, coarse solve)
   WM_PC_COUNT
 };
 void wm_prof_begin(int cat, cudaStream_t s);

@@ -14,7 +14,7 @@ namespace {
 const char* kNames[WM_PC_COUNT] = {
     "apply_outer", "smooth_level0", "smooth_coarse", "residual_level0", "residual_coarse", "restrict",
     "prolong", "coarse_solve", "cg_vectors", "cg_scalars", "noise", "sinc_mass_copy", "setup_bounds_inverse",
-    "layout", "assembly", "apply_component", "true_residual_f64"};
+    "layout", "assembly", "apply_component", "true_residual_f64", "coarse_tail"};
 
 constexpr int kPool = 1 << 16;
 

@@ -708,10 +708,33 @@ __global__ void __launch_bounds__(256) k_transfer(int Nout, int Nin, int chunks,
   if (!ts.any) return;
   RowRange rr = chunk_rows(Nout, chunks);
   for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
-    T acc[kTPW];
+    T acc[kTPW], old[kTPW];
 #pragma unroll
-    for (int k = 0; k < kTPW; ++k) acc[k] = 0;
-    for (int j = ptr[i]; j < ptr[i + 1]; ++j) {
+    for (int k = 0; k < kTPW; ++k) {
+      acc[k] = 0;
+      old[k] = ADD && ts.act[k] ? out[((size_t)(t0 + k) * Nout + i) * WM_LANES + lane] : (T)0;
+    }
+    // entries four at a time: their loads and gathers in flight together,
+    // the products summed in entry order
+    const int j1 = ptr[i + 1];
+    int j = ptr[i];
+    for (; j + 4 <= j1; j += 4) {
+      typename TrT<T>::type en[4];
+      T v[4][kTPW];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) en[u] = ld_tr(ent + j + u);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int k = 0; k < kTPW; ++k)
+          v[u][k] = ts.act[k] ? in[((size_t)(t0 + k) * Nin + en[u].col) * WM_LANES + lane] : (T)0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int k = 0; k < kTPW; ++k)
+          if (ts.act[k]) acc[k] += en[u].v * v[u][k];
+    }
+    for (; j < j1; ++j) {
       auto en = ld_tr(ent + j);
 #pragma unroll
       for (int k = 0; k < kTPW; ++k)
@@ -722,7 +745,7 @@ __global__ void __launch_bounds__(256) k_transfer(int Nout, int Nin, int chunks,
       if (ts.act[k]) {
         size_t o = ((size_t)(t0 + k) * Nout + i) * WM_LANES + lane;
         if (ADD)
-          out[o] += acc[k];
+          out[o] = old[k] + acc[k];
         else
           out[o] = acc[k];
       }
@@ -743,6 +766,193 @@ __global__ void k_coarse_solve(int N, const double* __restrict__ Ainv, const int
     for (int j = 0; j < N; ++j) acc += A[(size_t)i * N + j] * (double)r[vidx(t, N, j)];
     z[vidx(t, N, i)] = (T)acc;
   }
+}
+
+// ------------------------------------------------ fused coarse end of a V-cycle
+// From the first level without a stencil form down to the dense coarse solve
+// and back up in one kernel (float): one block per tile of 32 systems, every
+// vector of those levels in shared memory (lane = system, warps over rows),
+// each step the arithmetic of the per-level kernels above in their order
+// (k_cheb_first, k_cheb_step, k_residual, k_transfer, k_coarse_solve) with a
+// block barrier in place of a launch boundary.  Vectors are rows of 32 floats
+// at row offsets of the dynamic shared area.
+constexpr int kTailMax = 6;    // smoothing levels of a fused tail
+// One block of 32 warps per SM: each warp walks its rows one at a time, so the
+// rows per warp set the latency of a step, and the shared-memory carve-out is
+// kept to what the block needs so that the level tables (rows, transfers)
+// stay in L1.
+#ifndef WM_TAIL_WARPS
+#define WM_TAIL_WARPS 32
+#endif
+constexpr int kTailWarps = WM_TAIL_WARPS;
+struct TailLv {
+  int N = 0, W = 0, nu = 0;
+  int oz0 = 0, oz1 = 0, orr = -1;   // rows of the two iterates and of r (orr < 0: r in global memory)
+  const PkRow32* pk = nullptr;
+  const float* dS = nullptr;
+  const float* dM = nullptr;
+  const float2* ctab = nullptr;     // this level's Chebyshev table [nshift][WM_MAX_CHEB]
+  const int32_t* Pptr = nullptr;    // z_l += P z_{l+1}, rows of this level
+  const PkTr32* P = nullptr;
+  const int32_t* Rptr = nullptr;    // r_{l+1} = R res_l, rows of the next level
+  const PkTr32* R = nullptr;
+};
+struct TailDesc {
+  int nl = 0, Nc = 0;
+  int orc = 0, ozc = 0, ores = 0;   // rows of the coarse r and z, and of the residual scratch
+  const double* ainv = nullptr;     // [nshift][Nc][Nc]
+  TailLv lv[kTailMax];
+};
+
+__global__ void __launch_bounds__(WM_LANES * kTailWarps, 1)
+    k_vcycle_tail(const TailDesc D, const double* __restrict__ sigma, const int* __restrict__ sid,
+                  const float* __restrict__ rin, float* __restrict__ zout, const int* __restrict__ tile_active) {
+  extern __shared__ float sh[];
+  const int t = blockIdx.x;
+  if (!tile_active[t]) return;  // the whole block
+  const int lane = threadIdx.x, wy = threadIdx.y;
+  const int g = t * WM_LANES + lane;
+  const float sg = (float)sigma[g];
+  const int sd = sid[g];
+  const float* rg = rin + (size_t)t * D.lv[0].N * WM_LANES + lane;
+  auto V = [&](int row0, int i) -> float& { return sh[(row0 + i) * WM_LANES + lane]; };
+  auto rval = [&](const TailLv& L, int i) { return L.orr < 0 ? rg[(size_t)i * WM_LANES] : V(L.orr, i); };
+  // (the entries of a row are loaded eight at a time, then summed in order:
+  // one block works a row at a time per warp, so the loads must overlap)
+  auto apply_row = [&](const TailLv& L, int zin, int i, float& aS, float& aM) {
+    aS = 0.f;
+    aM = 0.f;
+    const PkRow32* e = L.pk + (size_t)i * L.W;
+    int w = 0;
+    for (; w + 8 <= L.W; w += 8) {
+      PkRow32 en[8];
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) en[u] = ld_row(e + w + u);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = V(zin, en[u].col);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        aS += en[u].s * v[u];
+        aM += en[u].m * v[u];
+      }
+    }
+    for (; w < L.W; ++w) {
+      const PkRow32 en = ld_row(e + w);
+      const float v = V(zin, en.col);
+      aS += en.s * v;
+      aM += en.m * v;
+    }
+  };
+  // three-term step k from z = zin; out may be prev (each row reads prev before it writes out)
+  auto cheb = [&](const TailLv& L, int k, int zin, int prev, int out) {
+    const float2 cf = L.ctab[sd * WM_MAX_CHEB + k];
+    const float c1 = k > 0 ? cf.x : 0.f, c2 = cf.y;
+    for (int i = wy; i < L.N; i += kTailWarps) {
+      float aS, aM;
+      apply_row(L, zin, i, aS, aM);
+      const float ds = L.dS[i], dm = L.dM[i];
+      const float res = rval(L, i) - (aS + sg * aM);
+      const float zc = V(zin, i);
+      const float zp = prev >= 0 ? V(prev, i) : 0.f;
+      V(out, i) = zc + c1 * (zc - zp) + c2 * res / (ds + sg * dm);
+    }
+    __syncthreads();
+  };
+  auto transfer = [&](const int32_t* ptr, const PkTr32* ent, int nout, int in, int out, bool add) {
+    for (int i = wy; i < nout; i += kTailWarps) {
+      float acc = 0.f;
+      const int j1 = ptr[i + 1];
+      int j = ptr[i];
+      for (; j + 4 <= j1; j += 4) {
+        PkTr32 en[4];
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) en[u] = ld_tr(ent + j + u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = V(in, en[u].col);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc += en[u].v * v[u];
+      }
+      for (; j < j1; ++j) {
+        const PkTr32 en = ld_tr(ent + j);
+        acc += en.v * V(in, en.col);
+      }
+      if (add)
+        V(out, i) += acc;
+      else
+        V(out, i) = acc;
+    }
+    __syncthreads();
+  };
+  int cur[kTailMax], oth[kTailMax];
+  // down: pre-smoothing from z = 0, residual, restriction
+  for (int l = 0; l < D.nl; ++l) {
+    const TailLv& L = D.lv[l];
+    {
+      const float c2 = L.ctab[sd * WM_MAX_CHEB].y;
+      for (int i = wy; i < L.N; i += kTailWarps) {
+        const float ds = L.dS[i], dm = L.dM[i];
+        V(L.oz0, i) = c2 * rval(L, i) / (ds + sg * dm);
+      }
+      __syncthreads();
+    }
+    int c = L.oz0, o = L.oz1;
+    for (int k = 1; k < L.nu; ++k) {
+      cheb(L, k, c, k >= 2 ? o : -1, o);
+      const int x = c;
+      c = o;
+      o = x;
+    }
+    for (int i = wy; i < L.N; i += kTailWarps) {
+      float aS, aM;
+      apply_row(L, c, i, aS, aM);
+      V(D.ores, i) = rval(L, i) - (aS + sg * aM);
+    }
+    __syncthreads();
+    const bool last = l + 1 == D.nl;
+    transfer(L.Rptr, L.R, last ? D.Nc : D.lv[l + 1].N, D.ores, last ? D.orc : D.lv[l + 1].orr, false);
+    cur[l] = c;
+    oth[l] = o;
+  }
+  // dense coarse solve in float64 with the inverse of the system's shift
+  {
+    const double* A = D.ainv + (size_t)sd * D.Nc * D.Nc;
+    for (int i = wy; i < D.Nc; i += kTailWarps) {
+      const double* Ai = A + (size_t)i * D.Nc;
+      double acc = 0.0;
+      int j = 0;
+      for (; j + 4 <= D.Nc; j += 4) {
+        double a[4];
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a[u] = Ai[j + u];
+          v[u] = V(D.orc, j + u);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc += a[u] * (double)v[u];
+      }
+      for (; j < D.Nc; ++j) acc += Ai[j] * (double)V(D.orc, j);
+      V(D.ozc, i) = (float)acc;
+    }
+    __syncthreads();
+  }
+  // up: prolongation of the coarser correction, post-smoothing
+  for (int l = D.nl - 1; l >= 0; --l) {
+    const TailLv& L = D.lv[l];
+    int c = cur[l], o = oth[l];
+    transfer(L.Pptr, L.P, L.N, l + 1 < D.nl ? cur[l + 1] : D.ozc, c, true);
+    for (int k = 0; k < L.nu; ++k) {
+      cheb(L, k, c, k >= 1 ? o : -1, o);
+      const int x = c;
+      c = o;
+      o = x;
+    }
+    cur[l] = c;
+  }
+  float* zg = zout + (size_t)t * D.lv[0].N * WM_LANES + lane;
+  for (int i = wy; i < D.lv[0].N; i += kTailWarps) zg[(size_t)i * WM_LANES] = V(cur[0], i);
 }
 
 // inverse of S_c + sigma M_c for each shift by in-place Gauss–Jordan
@@ -1131,6 +1341,73 @@ static int build_cheb_table(const wm_hier* h, WorkSpace& ws, const Batch& bt, cu
   return WM_OK;
 }
 
+// The V-cycle from level l down to the coarse solve and back in one launch of
+// k_vcycle_tail (float), z into level l's za.  *done stays false when the
+// levels do not fit it: a coarser level with a stencil form, more than
+// kTailMax smoothing levels, or vectors beyond a block's shared memory.
+static int vcycle_tail(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const float* rin, cudaStream_t s,
+                       bool* done) {
+  *done = false;
+  const int L = (int)h->lv.size();
+  const int nl = L - 1 - l;
+  if (nl < 1 || nl > kTailMax) return WM_OK;
+  TailDesc D;
+  D.nl = nl;
+  int row = 0, maxn = 0;
+  for (int k = 0; k < nl; ++k) {
+    const wm_level& Lv = h->lv[l + k];
+    if (Lv.sten) return WM_OK;
+    TailLv& tl = D.lv[k];
+    tl.N = Lv.N;
+    tl.W = Lv.W;
+    tl.nu = bt.degree_of(l + k);
+    if (k > 0) {
+      tl.orr = row;
+      row += Lv.N;
+    }
+    tl.oz0 = row;
+    tl.oz1 = row + Lv.N;
+    row += 2 * Lv.N;
+    tl.pk = Lv.d_pk32.p;
+    tl.dS = Lv.d_dS32.p;
+    tl.dM = Lv.d_dM32.p;
+    tl.ctab = ws.cheb32.p + (size_t)(l + k) * bt.nshift * WM_MAX_CHEB;
+    tl.Pptr = Lv.d_Pptr.p;
+    tl.P = Lv.d_P32.p;
+    tl.Rptr = Lv.d_Rptr.p;
+    tl.R = Lv.d_R32.p;
+    maxn = std::max(maxn, Lv.N);
+  }
+  const wm_level& Cv = h->lv[L - 1];
+  D.Nc = Cv.N;
+  D.ores = row;
+  row += maxn;
+  D.orc = row;
+  D.ozc = row + Cv.N;
+  row += 2 * Cv.N;
+  D.ainv = ws.ainv.p;
+  const size_t smem = (size_t)row * WM_LANES * sizeof(float);
+  int dev = 0, cap = 0, per_sm = 0;
+  WM_CUDA(cudaGetDevice(&dev));
+  WM_CUDA(cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  WM_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  if (smem > (size_t)cap) return WM_OK;
+  WM_CUDA(cudaFuncSetAttribute(k_vcycle_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int pct = (int)std::min<size_t>(100, (smem + 1024 + per_sm - 1) * 100 / std::max(per_sm, 1));
+  WM_CUDA(cudaFuncSetAttribute(k_vcycle_tail, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+  WM_LAUNCH(WM_PC_VTAIL, s, k_vcycle_tail<<<bt.tiles, dim3(WM_LANES, kTailWarps), smem, s>>>(
+                                D, ws.sigma.p, ws.sid.p, rin, vb<float>(ws.lvl[l].za), ws.tile_active.p));
+  WM_CUDA(cudaGetLastError());
+  double fl = 2.0 * Cv.N * Cv.N;
+  for (int k = 0; k < nl; ++k) {
+    const wm_level& Lv = h->lv[l + k];
+    fl += (2.0 * bt.degree_of(l + k) + 1.0) * (4.0 * Lv.nnz + 8.0 * Lv.N) + 4.0 * Lv.nnzP;
+  }
+  units(WM_PC_VTAIL, bt, 2.0 * sizeof(float) * h->lv[l].N, fl);
+  *done = true;
+  return WM_OK;
+}
+
 // partial sums the outer CG wants from the V-cycle's last step
 template <typename T>
 struct VDots {
@@ -1171,6 +1448,16 @@ static int vcycle(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, const
     WM_CUDA(cudaGetLastError());
     *zout = za;
     return WM_OK;
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    if (bt.tail_fused && !Lv.sten) {
+      bool done = false;
+      WM_TRY(vcycle_tail(h, ws, bt, l, rin, s, &done));
+      if (done) {
+        *zout = za;
+        return WM_OK;
+      }
+    }
   }
   T* res = vb<T>(B.res);
   const int nu = bt.degree_of(l);

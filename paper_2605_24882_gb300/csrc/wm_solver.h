@@ -48,11 +48,13 @@ struct Batch {
   mutable int active_tiles = 0;  // host copy of the active tile count (for work accounting)
   int vec_rows = 128;     // rows per block of the CG vector kernels
   int vcycle_rows = 16;   // rows per block of the V-cycle row kernels
+  bool tail_fused = true;  // float: the coarse end of the V-cycle in one kernel per tile
   int chunks_for(int N) const;
   int vcycle_chunks(int N) const;
   void schedule(const wm_schedule& s) {
     vec_rows = s.vec_rows;
     vcycle_rows = s.vcycle_rows;
+    tail_fused = s.tail_fused != 0;
   }
 };
 

@@ -2,13 +2,14 @@
 
     python -m paper_2605_24882_gb300.microbench vcycle [--kind sphere] [--p 2]
         [--elems 64] [--levels 6] [--tiles 71] [--tiles-per-shift 1] [--degree 4]
-        [--ratio 12] [--precision mixed] [--reps 3]
+        [--ratio 12] [--precision mixed] [--reps 3] [--schedule knob=value ...]
 
 `vcycle` runs `reps` V-cycles (the preconditioner of the batched solves) on
 `tiles` x 32 seeded random residuals, 32 x `tiles-per-shift` per shift, the
 shifts spread geometrically over [25 + e^-10, 25 + e^10] (sample-major packing
 of a sinc pass puts n_s / 32 consecutive tiles on one shift), and prints the
-mean time per V-cycle.  It is the driver for kernel profiles of the smoother, residual and
+mean time per V-cycle (`--schedule` sets fields of the hierarchy's kernel
+schedule first, e.g. tail_fused=0).  It is the driver for kernel profiles of the smoother, residual and
 transfer kernels.
 
     python -m paper_2605_24882_gb300.microbench sqrt [--kind sphere] [--p 2]
@@ -36,6 +37,8 @@ import paper_2605_24882_gb300 as wm
 
 def vcycle(args):
     hier = wm.Hierarchy(wm.Geometry(args.kind, args.p, args.elems), args.levels)
+    if args.schedule:
+        hier.set_schedule(**{k: int(v) for k, v in (a.split("=") for a in args.schedule)})
     n = hier.num_dofs(0)
     nsh = (args.tiles + args.tiles_per_shift - 1) // args.tiles_per_shift
     sig = np.repeat(np.exp(np.linspace(-10.0, 10.0, nsh)) + 25.0, 32 * args.tiles_per_shift)[:args.tiles * 32]
@@ -60,6 +63,7 @@ def vcycle(args):
                     "gbs": round(v["bytes"] / (v["ms"] * 1e6), 1) if v["ms"] > 0 else None}
                 for k, v in prof.items() if v["timed"] > 0}
     print(json.dumps({"bench": "vcycle", "dofs": n, "systems": args.tiles * 32, "levels": args.levels,
+                      "schedule": hier.schedule(),
                       "tiles_per_shift": args.tiles_per_shift, "categories": cats,
                       "degree": args.degree, "ms_per_vcycle": e0.elapsed_time(e1) / max(1, args.reps),
                       "max_abs_z": float(z.abs().max())}))
@@ -133,6 +137,7 @@ def main():
     ap.add_argument("--samples", type=int, default=64)
     ap.add_argument("--nodes", type=int, default=12)
     ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--schedule", nargs="*", default=[], help="vcycle: schedule fields as knob=value")
     args = ap.parse_args()
     if args.what == "vcycle":
         vcycle(args)

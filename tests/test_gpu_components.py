@@ -166,16 +166,39 @@ def test_schedule_changes_only_rounding(wm):
     hier = wm.Hierarchy(wm.Geometry("sphere", 2, 16), 4)
     kw = dict(kappa=3.0, beta=1.3, sinc_k=0.4, l_lo=-15, l_hi=15, n_samples=40, seed=2, precision="mixed",
               rtol=1e-10)
-    assert hier.schedule() == {"uni_run": 8, "uni_waves": 4, "vec_rows": 128, "vcycle_rows": 16}
+    assert hier.schedule() == {"uni_run": 8, "uni_waves": 4, "vec_rows": 128, "vcycle_rows": 16, "tail_fused": 1}
     u0, _ = hier.sample_fields(**kw)
-    hier.set_schedule(uni_run=2, uni_waves=16, vec_rows=64, vcycle_rows=32)
+    hier.set_schedule(uni_run=2, uni_waves=16, vec_rows=64, vcycle_rows=32, tail_fused=0)
     u1, st = hier.sample_fields(**kw)
     assert st["n_not_converged"] == 0
     d = u1 - u0
     assert float(torch.sqrt((d * hier.apply_mass(d)).sum() / (u0 * hier.apply_mass(u0)).sum())) < 1e-8
     with pytest.raises(wm.WMError):
         hier.set_schedule(uni_run=9)
-    assert hier.set_schedule() == {"uni_run": 8, "uni_waves": 4, "vec_rows": 128, "vcycle_rows": 16}
+    with pytest.raises(wm.WMError):
+        hier.set_schedule(tail_fused=2)
+    assert hier.set_schedule() == {"uni_run": 8, "uni_waves": 4, "vec_rows": 128, "vcycle_rows": 16, "tail_fused": 1}
+
+
+@pytest.mark.parametrize("case", [("sphere", 2, 16, 4), ("sphere", 1, 8, 3), ("sphere", 3, 4, 3), ("sphere", 2, 4, 3)])
+def test_fused_coarse_tail_matches_per_level_launches(wm, case):
+    # the coarse end of the V-cycle in one kernel per tile (levels without a
+    # stencil form and the coarse solve; on the 4 x 4 meshes the whole cycle)
+    # does the per-level kernels' arithmetic in their order: the same z up to
+    # float rounding, on a full and a ragged tile with a shift per system
+    kind, p, n, levels = case
+    hier = wm.Hierarchy(wm.Geometry(kind, p, n), levels)
+    nv = 45
+    sg = np.geomspace(0.05, 1e5, nv)
+    r = torch.tensor(random_vectors(21, nv, hier.num_dofs(0)), device="cuda")
+    for deg in (1, 3):
+        hier.set_schedule(tail_fused=1)
+        z1 = hier.vcycle(r, sg, precision="mixed", smoother_degree=deg).cpu().numpy()
+        hier.set_schedule(tail_fused=0)
+        z0 = hier.vcycle(r, sg, precision="mixed", smoother_degree=deg).cpu().numpy()
+        hier.set_schedule()
+        assert np.isfinite(z1).all() and np.abs(z0).max() > 0
+        np.testing.assert_allclose(z1, z0, rtol=0, atol=2e-6 * np.abs(z0).max())
 
 
 def test_coarse_smoother_degree(wm):
