@@ -775,12 +775,13 @@ __global__ void k_coarse_solve(int N, const double* __restrict__ Ainv, const int
 // each step the arithmetic of the per-level kernels above in their order
 // (k_cheb_first, k_cheb_step, k_residual, k_transfer, k_coarse_solve) with a
 // block barrier in place of a launch boundary.  Vectors are rows of 32 floats
-// at row offsets of the dynamic shared area.
+// at row offsets of the dynamic shared area.  Where they fit (STAGED), the
+// levels' tables (operator rows, diagonals, transfers) are copied behind the
+// vectors at the start, so that no step waits on L1 or L2.
 constexpr int kTailMax = 6;    // smoothing levels of a fused tail
 // One block of 32 warps per SM: each warp walks its rows one at a time, so the
-// rows per warp set the latency of a step, and the shared-memory carve-out is
-// kept to what the block needs so that the level tables (rows, transfers)
-// stay in L1.
+// rows per warp set the latency of a step; without staging the shared-memory
+// carve-out is kept to what the block needs so that the tables stay in L1.
 #ifndef WM_TAIL_WARPS
 #define WM_TAIL_WARPS 32
 #endif
@@ -796,49 +797,120 @@ struct TailLv {
   const PkTr32* P = nullptr;
   const int32_t* Rptr = nullptr;    // r_{l+1} = R res_l, rows of the next level
   const PkTr32* R = nullptr;
+  // staged copies: byte offsets in the table area and element counts
+  int opk = 0, odS = 0, odM = 0, oPp = 0, oP = 0, oRp = 0, oR = 0;
+  int npk = 0, nPp = 0, nP = 0, nRp = 0, nR = 0;
 };
 struct TailDesc {
   int nl = 0, Nc = 0;
   int orc = 0, ozc = 0, ores = 0;   // rows of the coarse r and z, and of the residual scratch
+  int tab0 = 0;                     // byte offset of the table area (STAGED)
   const double* ainv = nullptr;     // [nshift][Nc][Nc]
   TailLv lv[kTailMax];
 };
+template <typename E>
+__device__ __forceinline__ void tail_copy(char* dst, const E* src, int n, int tid, int nt) {
+  static_assert(sizeof(E) % 4 == 0, "word copies");
+  constexpr int NW = (int)(sizeof(E) / 4);
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int w = tid; w < n * NW; w += nt) d[w] = __ldg(s + w);
+}
 
+template <bool STAGED>
 __global__ void __launch_bounds__(WM_LANES * kTailWarps, 1)
     k_vcycle_tail(const TailDesc D, const double* __restrict__ sigma, const int* __restrict__ sid,
                   const float* __restrict__ rin, float* __restrict__ zout, const int* __restrict__ tile_active) {
-  extern __shared__ float sh[];
+  extern __shared__ __align__(16) float sh[];
   const int t = blockIdx.x;
   if (!tile_active[t]) return;  // the whole block
   const int lane = threadIdx.x, wy = threadIdx.y;
   const int g = t * WM_LANES + lane;
   const float sg = (float)sigma[g];
   const int sd = sid[g];
+  char* const tb = reinterpret_cast<char*>(sh) + D.tab0;
+  if constexpr (STAGED) {
+    const int tid = wy * WM_LANES + lane, nt = WM_LANES * kTailWarps;
+    for (int l = 0; l < D.nl; ++l) {
+      const TailLv& L = D.lv[l];
+      tail_copy(tb + L.opk, L.pk, L.npk, tid, nt);
+      tail_copy(tb + L.odS, L.dS, L.N, tid, nt);
+      tail_copy(tb + L.odM, L.dM, L.N, tid, nt);
+      tail_copy(tb + L.oPp, L.Pptr, L.nPp, tid, nt);
+      tail_copy(tb + L.oP, L.P, L.nP, tid, nt);
+      tail_copy(tb + L.oRp, L.Rptr, L.nRp, tid, nt);
+      tail_copy(tb + L.oR, L.R, L.nR, tid, nt);
+    }
+    __syncthreads();
+  }
+  // the level's tables: staged copies or global memory (read-only path)
+  auto row_at = [&](const TailLv& L, int i, int w) -> PkRow32 {
+    if constexpr (STAGED) {
+      const int4 v = *reinterpret_cast<const int4*>(tb + L.opk + ((size_t)i * L.W + w) * sizeof(PkRow32));
+      PkRow32 r;
+      r.col = v.x;
+      r.s = __int_as_float(v.y);
+      r.m = __int_as_float(v.z);
+      r.pad = 0;
+      return r;
+    } else {
+      return ld_row(L.pk + (size_t)i * L.W + w);
+    }
+  };
+  auto dS_at = [&](const TailLv& L, int i) -> float {
+    if constexpr (STAGED)
+      return reinterpret_cast<const float*>(tb + L.odS)[i];
+    else
+      return __ldg(L.dS + i);
+  };
+  auto dM_at = [&](const TailLv& L, int i) -> float {
+    if constexpr (STAGED)
+      return reinterpret_cast<const float*>(tb + L.odM)[i];
+    else
+      return __ldg(L.dM + i);
+  };
+  auto ptr_at = [&](const int32_t* gp, int off, int i) -> int {
+    if constexpr (STAGED)
+      return reinterpret_cast<const int32_t*>(tb + off)[i];
+    else
+      return __ldg(gp + i);
+  };
+  auto tr_at = [&](const PkTr32* gp, int off, int j) -> PkTr32 {
+    if constexpr (STAGED) {
+      const int2 v = reinterpret_cast<const int2*>(tb + off)[j];
+      PkTr32 r;
+      r.col = v.x;
+      r.v = __int_as_float(v.y);
+      return r;
+    } else {
+      return ld_tr(gp + j);
+    }
+  };
   const float* rg = rin + (size_t)t * D.lv[0].N * WM_LANES + lane;
   auto V = [&](int row0, int i) -> float& { return sh[(row0 + i) * WM_LANES + lane]; };
   auto rval = [&](const TailLv& L, int i) { return L.orr < 0 ? rg[(size_t)i * WM_LANES] : V(L.orr, i); };
-  // (the entries of a row are loaded eight at a time, then summed in order:
-  // one block works a row at a time per warp, so the loads must overlap)
+  // (the entries of a row are loaded UR at a time, then summed in order: one
+  // block works a row at a time per warp, so the loads must overlap)
+  constexpr int UR = STAGED ? 4 : 8;
   auto apply_row = [&](const TailLv& L, int zin, int i, float& aS, float& aM) {
     aS = 0.f;
     aM = 0.f;
-    const PkRow32* e = L.pk + (size_t)i * L.W;
     int w = 0;
-    for (; w + 8 <= L.W; w += 8) {
-      PkRow32 en[8];
-      float v[8];
+    for (; w + UR <= L.W; w += UR) {
+      PkRow32 en[UR];
+      float v[UR];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) en[u] = ld_row(e + w + u);
+      for (int u = 0; u < UR; ++u) en[u] = row_at(L, i, w + u);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = V(zin, en[u].col);
+      for (int u = 0; u < UR; ++u) v[u] = V(zin, en[u].col);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < UR; ++u) {
         aS += en[u].s * v[u];
         aM += en[u].m * v[u];
       }
     }
     for (; w < L.W; ++w) {
-      const PkRow32 en = ld_row(e + w);
+      const PkRow32 en = row_at(L, i, w);
       const float v = V(zin, en.col);
       aS += en.s * v;
       aM += en.m * v;
@@ -851,7 +923,7 @@ __global__ void __launch_bounds__(WM_LANES * kTailWarps, 1)
     for (int i = wy; i < L.N; i += kTailWarps) {
       float aS, aM;
       apply_row(L, zin, i, aS, aM);
-      const float ds = L.dS[i], dm = L.dM[i];
+      const float ds = dS_at(L, i), dm = dM_at(L, i);
       const float res = rval(L, i) - (aS + sg * aM);
       const float zc = V(zin, i);
       const float zp = prev >= 0 ? V(prev, i) : 0.f;
@@ -859,23 +931,24 @@ __global__ void __launch_bounds__(WM_LANES * kTailWarps, 1)
     }
     __syncthreads();
   };
-  auto transfer = [&](const int32_t* ptr, const PkTr32* ent, int nout, int in, int out, bool add) {
+  auto transfer = [&](const int32_t* ptr, int optr, const PkTr32* ent, int oent, int nout, int in, int out,
+                      bool add) {
     for (int i = wy; i < nout; i += kTailWarps) {
       float acc = 0.f;
-      const int j1 = ptr[i + 1];
-      int j = ptr[i];
+      const int j1 = ptr_at(ptr, optr, i + 1);
+      int j = ptr_at(ptr, optr, i);
       for (; j + 4 <= j1; j += 4) {
         PkTr32 en[4];
         float v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) en[u] = ld_tr(ent + j + u);
+        for (int u = 0; u < 4; ++u) en[u] = tr_at(ent, oent, j + u);
 #pragma unroll
         for (int u = 0; u < 4; ++u) v[u] = V(in, en[u].col);
 #pragma unroll
         for (int u = 0; u < 4; ++u) acc += en[u].v * v[u];
       }
       for (; j < j1; ++j) {
-        const PkTr32 en = ld_tr(ent + j);
+        const PkTr32 en = tr_at(ent, oent, j);
         acc += en.v * V(in, en.col);
       }
       if (add)
@@ -892,7 +965,7 @@ __global__ void __launch_bounds__(WM_LANES * kTailWarps, 1)
     {
       const float c2 = L.ctab[sd * WM_MAX_CHEB].y;
       for (int i = wy; i < L.N; i += kTailWarps) {
-        const float ds = L.dS[i], dm = L.dM[i];
+        const float ds = dS_at(L, i), dm = dM_at(L, i);
         V(L.oz0, i) = c2 * rval(L, i) / (ds + sg * dm);
       }
       __syncthreads();
@@ -911,7 +984,7 @@ __global__ void __launch_bounds__(WM_LANES * kTailWarps, 1)
     }
     __syncthreads();
     const bool last = l + 1 == D.nl;
-    transfer(L.Rptr, L.R, last ? D.Nc : D.lv[l + 1].N, D.ores, last ? D.orc : D.lv[l + 1].orr, false);
+    transfer(L.Rptr, L.oRp, L.R, L.oR, last ? D.Nc : D.lv[l + 1].N, D.ores, last ? D.orc : D.lv[l + 1].orr, false);
     cur[l] = c;
     oth[l] = o;
   }
@@ -942,7 +1015,7 @@ __global__ void __launch_bounds__(WM_LANES * kTailWarps, 1)
   for (int l = D.nl - 1; l >= 0; --l) {
     const TailLv& L = D.lv[l];
     int c = cur[l], o = oth[l];
-    transfer(L.Pptr, L.P, L.N, l + 1 < D.nl ? cur[l + 1] : D.ozc, c, true);
+    transfer(L.Pptr, L.oPp, L.P, L.oP, L.N, l + 1 < D.nl ? cur[l + 1] : D.ozc, c, true);
     for (int k = 0; k < L.nu; ++k) {
       cheb(L, k, c, k >= 1 ? o : -1, o);
       const int x = c;
@@ -1386,17 +1459,53 @@ static int vcycle_tail(const wm_hier* h, WorkSpace& ws, const Batch& bt, int l, 
   D.ozc = row + Cv.N;
   row += 2 * Cv.N;
   D.ainv = ws.ainv.p;
-  const size_t smem = (size_t)row * WM_LANES * sizeof(float);
+  const size_t vec = (size_t)row * WM_LANES * sizeof(float);
+  // the table area: every array at a 16-byte boundary
+  size_t tab = 0;
+  auto put = [&](int& off, size_t bytes) {
+    off = (int)tab;
+    tab += (bytes + 15) / 16 * 16;
+  };
+  for (int k = 0; k < nl; ++k) {
+    const wm_level& Lv = h->lv[l + k];
+    TailLv& tl = D.lv[k];
+    tl.npk = (int)Lv.d_pk32.n;
+    tl.nPp = (int)Lv.d_Pptr.n;
+    tl.nP = (int)Lv.d_P32.n;
+    tl.nRp = (int)Lv.d_Rptr.n;
+    tl.nR = (int)Lv.d_R32.n;
+    if ((size_t)Lv.N > Lv.d_dS32.n || (size_t)Lv.N > Lv.d_dM32.n || (size_t)Lv.N * Lv.W > Lv.d_pk32.n)
+      return WM_OK;  // (tables smaller than the level: not this path)
+    put(tl.opk, sizeof(PkRow32) * tl.npk);
+    put(tl.odS, sizeof(float) * Lv.N);
+    put(tl.odM, sizeof(float) * Lv.N);
+    put(tl.oPp, sizeof(int32_t) * tl.nPp);
+    put(tl.oP, sizeof(PkTr32) * tl.nP);
+    put(tl.oRp, sizeof(int32_t) * tl.nRp);
+    put(tl.oR, sizeof(PkTr32) * tl.nR);
+  }
+  D.tab0 = (int)vec;
   int dev = 0, cap = 0, per_sm = 0;
   WM_CUDA(cudaGetDevice(&dev));
   WM_CUDA(cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   WM_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-  if (smem > (size_t)cap) return WM_OK;
-  WM_CUDA(cudaFuncSetAttribute(k_vcycle_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const bool staged = vec + tab <= (size_t)cap;
+  if (!staged && vec > (size_t)cap) return WM_OK;
+  const size_t smem = staged ? vec + tab : vec;
   const int pct = (int)std::min<size_t>(100, (smem + 1024 + per_sm - 1) * 100 / std::max(per_sm, 1));
-  WM_CUDA(cudaFuncSetAttribute(k_vcycle_tail, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
-  WM_LAUNCH(WM_PC_VTAIL, s, k_vcycle_tail<<<bt.tiles, dim3(WM_LANES, kTailWarps), smem, s>>>(
-                                D, ws.sigma.p, ws.sid.p, rin, vb<float>(ws.lvl[l].za), ws.tile_active.p));
+  const dim3 blk(WM_LANES, kTailWarps);
+  float* zo = vb<float>(ws.lvl[l].za);
+  if (staged) {
+    WM_CUDA(cudaFuncSetAttribute(k_vcycle_tail<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    WM_CUDA(cudaFuncSetAttribute(k_vcycle_tail<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    WM_LAUNCH(WM_PC_VTAIL, s, k_vcycle_tail<true><<<bt.tiles, blk, smem, s>>>(D, ws.sigma.p, ws.sid.p, rin, zo,
+                                                                                ws.tile_active.p));
+  } else {
+    WM_CUDA(cudaFuncSetAttribute(k_vcycle_tail<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    WM_CUDA(cudaFuncSetAttribute(k_vcycle_tail<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    WM_LAUNCH(WM_PC_VTAIL, s, k_vcycle_tail<false><<<bt.tiles, blk, smem, s>>>(D, ws.sigma.p, ws.sid.p, rin, zo,
+                                                                                 ws.tile_active.p));
+  }
   WM_CUDA(cudaGetLastError());
   double fl = 2.0 * Cv.N * Cv.N;
   for (int k = 0; k < nl; ++k) {
