@@ -344,13 +344,42 @@ __device__ __forceinline__ double sum_parts(const double* part, int chunks, int 
   return s;
 }
 
-__global__ void k_scal_init(int nsys_pad, int chunks, const double* part_rr, const double* part_rz,
-                            const int* src_of, double* bb, double* rho, double* rr, double* rr_ref, int* active,
-                            int* restart, int* flags) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= nsys_pad) return;
-  double b2 = sum_parts(part_rr, chunks, g);
-  double rz = sum_parts(part_rz, chunks, g);
+// The CG's per-system scalars: one block per tile, lane = system.  The
+// chunk partials of a tile's 32 systems (several hundred per system for the
+// stencil kernels' spatial blocks) are summed by the block's warps, warp y
+// taking chunks y, y + kSumWarps, ..., and the warps' sums are added in warp
+// order by warp 0, which then does the system's update: the loads of a long
+// sum are spread over eight warps instead of one chain per system.
+constexpr int kSumWarps = 8;
+const dim3 kSumBlk(WM_LANES, kSumWarps);
+struct SumSm {
+  double v[kSumWarps][WM_LANES];
+};
+// sum of the chunk partials of system (tile blockIdx.x, lane); valid in warp 0.
+// Every thread of the block calls it; `want` false skips the lane's loads (0).
+__device__ __forceinline__ double tile_parts(const double* part, int chunks, bool want, SumSm& sm) {
+  const int t = blockIdx.x, lane = threadIdx.x, y = threadIdx.y;
+  double s = 0.0;
+  if (want)
+    for (int c = y; c < chunks; c += kSumWarps) s += part[((size_t)t * chunks + c) * WM_LANES + lane];
+  sm.v[y][lane] = s;
+  __syncthreads();
+  double r = 0.0;
+  if (y == 0)
+#pragma unroll
+    for (int w = 0; w < kSumWarps; ++w) r += sm.v[w][lane];
+  __syncthreads();  // sm may be reused
+  return r;
+}
+
+__global__ void __launch_bounds__(WM_LANES * kSumWarps)
+    k_scal_init(int chunks, const double* part_rr, const double* part_rz, const int* src_of, double* bb,
+                double* rho, double* rr, double* rr_ref, int* active, int* restart, int* flags) {
+  __shared__ SumSm sm;
+  const double b2 = tile_parts(part_rr, chunks, true, sm);
+  const double rz = tile_parts(part_rz, chunks, true, sm);
+  if (threadIdx.y != 0) return;
+  const int g = blockIdx.x * WM_LANES + threadIdx.x;
   bb[g] = b2;
   rr[g] = b2;
   rr_ref[g] = b2;
@@ -367,13 +396,15 @@ __global__ void k_scal_init(int nsys_pad, int chunks, const double* part_rr, con
   active[g] = a;
 }
 
-__global__ void k_scal_alpha(int nsys_pad, int chunks, const double* part_pq, const double* rho, int* active,
-                             double* alpha, int* flags) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= nsys_pad) return;
+__global__ void __launch_bounds__(WM_LANES * kSumWarps)
+    k_scal_alpha(int chunks, const double* part_pq, const double* rho, int* active, double* alpha, int* flags) {
+  __shared__ SumSm sm;
+  const int g = blockIdx.x * WM_LANES + threadIdx.x;
+  const bool act = active[g] != 0;
+  const double pq = tile_parts(part_pq, chunks, act, sm);
+  if (threadIdx.y != 0) return;
   double a = 0.0;
-  if (active[g]) {
-    double pq = sum_parts(part_pq, chunks, g);
+  if (act) {
     if (pq > 0.0 && isfinite(pq)) {
       a = rho[g] / pq;
     } else {
@@ -386,14 +417,17 @@ __global__ void k_scal_alpha(int nsys_pad, int chunks, const double* part_pq, co
 
 // recursive-residual test: flags systems for a float64 residual replacement;
 // counters: [0] active systems, [1] flagged systems, [2] active tiles, [3] flagged tiles
-__global__ void k_scal_conv(int nsys_pad, int chunks, const double* part_rr, const double* bb, const double* rr_ref,
-                            double rtol2, double drop2, double* rr, int* active, int* rep, int* tile_active,
-                            int* tile_rep, int* counters, int* flags) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= nsys_pad) return;
+__global__ void __launch_bounds__(WM_LANES * kSumWarps)
+    k_scal_conv(int chunks, const double* part_rr, const double* bb, const double* rr_ref, double rtol2,
+                double drop2, double* rr, int* active, int* rep, int* tile_active, int* tile_rep, int* counters,
+                int* flags) {
+  __shared__ SumSm sm;
+  const int g = blockIdx.x * WM_LANES + threadIdx.x;
+  const bool act = active[g] != 0;
+  const double r2 = tile_parts(part_rr, chunks, act, sm);
+  if (threadIdx.y != 0) return;
   int need = 0;
-  if (active[g]) {
-    double r2 = sum_parts(part_rr, chunks, g);
+  if (act) {
     rr[g] = r2;
     if (!isfinite(r2)) {
       atomicOr(&flags[0], 1);
@@ -403,7 +437,7 @@ __global__ void k_scal_conv(int nsys_pad, int chunks, const double* part_rr, con
     }
   }
   rep[g] = need;
-  int t = g / WM_LANES;
+  const int t = blockIdx.x;
   if (active[g]) {
     atomicAdd(&counters[0], 1);
     if (atomicExch(&tile_active[t], 1) == 0) atomicAdd(&counters[2], 1);
@@ -416,13 +450,15 @@ __global__ void k_scal_conv(int nsys_pad, int chunks, const double* part_rr, con
 
 // after a replacement: new reference norm, restart flag, convergence on the
 // true residual; recounts active systems and tiles
-__global__ void k_scal_replace(int nsys_pad, int chunks, const double* part_rr, const double* bb, double rtol2,
-                               const int* rep, double* rr, double* rr_ref, int* active, int* restart, int* tile_active,
-                               int* counters, int* flags) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= nsys_pad) return;
-  if (rep[g] && active[g]) {
-    double r2 = sum_parts(part_rr, chunks, g);
+__global__ void __launch_bounds__(WM_LANES * kSumWarps)
+    k_scal_replace(int chunks, const double* part_rr, const double* bb, double rtol2, const int* rep, double* rr,
+                   double* rr_ref, int* active, int* restart, int* tile_active, int* counters, int* flags) {
+  __shared__ SumSm sm;
+  const int g = blockIdx.x * WM_LANES + threadIdx.x;
+  const bool mine = rep[g] && active[g];
+  const double r2 = tile_parts(part_rr, chunks, mine, sm);
+  if (threadIdx.y != 0) return;
+  if (mine) {
     rr[g] = r2;
     rr_ref[g] = r2;
     restart[g] = 1;
@@ -435,30 +471,35 @@ __global__ void k_scal_replace(int nsys_pad, int chunks, const double* part_rr, 
   }
   if (active[g]) {
     atomicAdd(&counters[0], 1);
-    if (atomicExch(&tile_active[g / WM_LANES], 1) == 0) atomicAdd(&counters[2], 1);
+    if (atomicExch(&tile_active[blockIdx.x], 1) == 0) atomicAdd(&counters[2], 1);
   }
 }
 
 // double-float residual check: counts flagged systems whose rounding-error
 // bound 2^-42 ||B|| exceeds a tenth of the tolerance rtol ||b|| (those
 // residuals are recomputed in float64)
-__global__ void k_df_check(int nsys_pad, int chunks, const double* part_b, const double* bb, double lim2,
-                           const int* rep, int* counter) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= nsys_pad || !rep[g]) return;
-  double b2 = sum_parts(part_b, chunks, g);
+__global__ void __launch_bounds__(WM_LANES * kSumWarps)
+    k_df_check(int chunks, const double* part_b, const double* bb, double lim2, const int* rep, int* counter) {
+  __shared__ SumSm sm;
+  const int g = blockIdx.x * WM_LANES + threadIdx.x;
+  const bool mine = rep[g] != 0;
+  const double b2 = tile_parts(part_b, chunks, mine, sm);
+  if (threadIdx.y != 0 || !mine) return;
   if (!(ldexp(b2, -84) <= lim2 * bb[g])) atomicAdd(counter, 1);
 }
 
-__global__ void k_scal_beta(int nsys_pad, int chunks, const double* part_rz, const double* part_zq,
-                            const double* alpha, const int* active, int* restart, double* rho, double* beta) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= nsys_pad) return;
-  double rz = sum_parts(part_rz, chunks, g);
+__global__ void __launch_bounds__(WM_LANES * kSumWarps)
+    k_scal_beta(int chunks, const double* part_rz, const double* part_zq, const double* alpha, const int* active,
+                int* restart, double* rho, double* beta) {
+  __shared__ SumSm sm;
+  const int g = blockIdx.x * WM_LANES + threadIdx.x;
+  const bool upd = active[g] && !restart[g];
+  const double rz = tile_parts(part_rz, chunks, true, sm);
+  const double zq = tile_parts(part_zq, chunks, upd, sm);
+  if (threadIdx.y != 0) return;
   double b = 0.0;
-  if (active[g] && !restart[g]) {
-    double zq = sum_parts(part_zq, chunks, g);
-    double r0 = rho[g];
+  if (upd) {
+    const double r0 = rho[g];
     // Polak–Ribiere: (z_new, r_new - r_old) / (z_old, r_old) with r_new - r_old = -alpha q
     if (r0 != 0.0) b = -alpha[g] * zq / r0;
   }
@@ -1736,7 +1777,7 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
   WM_LAUNCH(WM_PC_CGVEC, s, k_dots_rz_zq<T><<<grid, kBlk, 0, s>>>(N, ch, tiles, r, z, (const T*)nullptr,
                                                                   ws.tile_active.p, ws.part[1].p, ws.part[2].p,
                                                                   (const int*)nullptr));
-  WM_LAUNCH(WM_PC_SCALAR, s, k_scal_init<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[0].p, ws.part[1].p, ws.src_of.p,
+  WM_LAUNCH(WM_PC_SCALAR, s, k_scal_init<<<tiles, kSumBlk, 0, s>>>(ch, ws.part[0].p, ws.part[1].p, ws.src_of.p,
                                                             ws.bb.p, ws.rho.p, ws.rr.p, ws.rr_ref.p, ws.active.p,
                                                             ws.restart.p, ws.flags.p));
   WM_LAUNCH(WM_PC_SCALAR, s, k_fill_tile_active<<<nblk(tiles, 128), 128, 0, s>>>(tiles, ws.tile_active.p,
@@ -1759,7 +1800,7 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
                                                                        ws.part[0].p));
     }
     units(WM_PC_APPLY64, bt, 2.0 * Tb * N, 4.0 * L0.nnz + 4.0 * N);
-    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_alpha<<<sb, 128, 0, s>>>(nsys_pad, ch_op, ws.part[0].p, ws.rho.p, ws.active.p,
+    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_alpha<<<tiles, kSumBlk, 0, s>>>(ch_op, ws.part[0].p, ws.rho.p, ws.active.p,
                                                                ws.alpha.p, ws.flags.p));
     WM_LAUNCH(WM_PC_CGVEC, s, k_update_xr<T><<<grid, kBlk, 0, s>>>(N, ch, tiles, ws.alpha.p, p, q, ws.x.p, r,
                                                                    ws.tile_active.p, ws.part[0].p));
@@ -1767,7 +1808,7 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
     WM_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(int), s));
     WM_CUDA(cudaMemsetAsync(ws.tile_active.p, 0, tiles * sizeof(int), s));
     WM_CUDA(cudaMemsetAsync(ws.tile_rep.p, 0, tiles * sizeof(int), s));
-    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_conv<<<sb, 128, 0, s>>>(nsys_pad, ch, ws.part[0].p, ws.bb.p, ws.rr_ref.p, rtol2,
+    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_conv<<<tiles, kSumBlk, 0, s>>>(ch, ws.part[0].p, ws.bb.p, ws.rr_ref.p, rtol2,
                                                               drop2, ws.rr.p, ws.active.p, ws.rep.p, ws.tile_active.p,
                                                               ws.tile_rep.p, cnt, ws.flags.p));
     WM_CUDA(cudaGetLastError());
@@ -1787,7 +1828,7 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
             WM_TRY(wm_sten_true_residual_df(L0, h->np, h->p, tiles, uni_of(ws), ws.sigma.p, ws.x.p, rhs_tiled,
                                             ws.src_of.p, ws.rep.p, ws.tile_rep.p, r, ws.part[1].p, ws.part[2].p, s));
             WM_CUDA(cudaMemsetAsync(cnt + 5, 0, sizeof(int), s));
-            WM_LAUNCH(WM_PC_SCALAR, s, k_df_check<<<sb, 128, 0, s>>>(nsys_pad, ch_op, ws.part[2].p, ws.bb.p,
+            WM_LAUNCH(WM_PC_SCALAR, s, k_df_check<<<tiles, kSumBlk, 0, s>>>(ch_op, ws.part[2].p, ws.bb.p,
                                                                      0.01 * rtol2, ws.rep.p, cnt + 5));
             WM_CUDA(cudaGetLastError());
             WM_CUDA(cudaMemcpyAsync(ws.host_small + 8, cnt + 5, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1816,7 +1857,7 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
       }
       WM_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(int), s));
       WM_CUDA(cudaMemsetAsync(ws.tile_active.p, 0, tiles * sizeof(int), s));
-      WM_LAUNCH(WM_PC_SCALAR, s, k_scal_replace<<<sb, 128, 0, s>>>(nsys_pad, ch_op, ws.part[1].p, ws.bb.p, rtol2,
+      WM_LAUNCH(WM_PC_SCALAR, s, k_scal_replace<<<tiles, kSumBlk, 0, s>>>(ch_op, ws.part[1].p, ws.bb.p, rtol2,
                                                                    ws.rep.p, ws.rr.p, ws.rr_ref.p, ws.active.p,
                                                                    ws.restart.p, ws.tile_active.p, cnt, ws.flags.p));
       WM_CUDA(cudaGetLastError());
@@ -1844,7 +1885,7 @@ static int fcg(const wm_hier* h, WorkSpace& ws, const Batch& bt, const double* r
                                     vd.fused ? ws.tile_uni.p : (const int*)nullptr));
       if (!vd.fused) units(WM_PC_CGVEC, bt, 3.0 * Tb * N, 4.0 * N);
     }
-    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_beta<<<sb, 128, 0, s>>>(nsys_pad, ch_dots, ws.part[1].p, ws.part[2].p,
+    WM_LAUNCH(WM_PC_SCALAR, s, k_scal_beta<<<tiles, kSumBlk, 0, s>>>(ch_dots, ws.part[1].p, ws.part[2].p,
                                                               ws.alpha.p, ws.active.p, ws.restart.p, ws.rho.p,
                                                               ws.beta.p));
     WM_LAUNCH(WM_PC_CGVEC, s, k_update_p<T><<<grid, kBlk, 0, s>>>(N, ch, ws.beta.p, z, p, ws.tile_active.p));
