@@ -278,6 +278,22 @@ __global__ void __launch_bounds__(256) k_true_residual(int N, int W, int chunks,
   block_reduce_store<1, kTPW>(acc, parts, chunks, t0, tiles);
 }
 
+// exact widening of a float to float64 by its bits (normal floats and zeros;
+// the others through the conversion instruction), keeping the float64 pipe,
+// which also executes conversions on this part, for the FMA
+__device__ __forceinline__ double to_f64(float f) {
+#ifdef WM_XR_CVT
+  return (double)f;
+#else
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 255u) return (u & 0x7FFFFFFFu) == 0u ? __hiloint2double((int)(u & 0x80000000u), 0) : (double)f;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+#endif
+}
+__device__ __forceinline__ double to_f64(double f) { return f; }
+
 // x += alpha p (float64), r -= alpha q; partial (r, r)
 template <typename T>
 __global__ void k_update_xr(int N, int chunks, int tiles, const double* __restrict__ alpha, const T* __restrict__ p,
@@ -289,9 +305,34 @@ __global__ void k_update_xr(int N, int chunks, int tiles, const double* __restri
   T af = (T)a;
   RowRange rr = chunk_rows(N, chunks);
   Acc<T> acc;
-  for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
+  int i = rr.i0 + threadIdx.y;
+#ifndef WM_XR_ROWS
+#define WM_XR_ROWS 4
+#endif
+  constexpr int UR = WM_XR_ROWS;  // rows of a warp in flight together (the sum keeps row order)
+  for (; i + (UR - 1) * kWarps < rr.i1; i += UR * kWarps) {
+    double xv[UR];
+    T pv[UR], qv[UR], rv[UR];
+#pragma unroll
+    for (int u = 0; u < UR; ++u) {
+      const size_t k = vidx(t, N, i + u * kWarps);
+      xv[u] = x[k];
+      pv[u] = p[k];
+      qv[u] = q[k];
+      rv[u] = r[k];
+    }
+#pragma unroll
+    for (int u = 0; u < UR; ++u) {
+      const size_t k = vidx(t, N, i + u * kWarps);
+      x[k] = xv[u] + a * to_f64(pv[u]);
+      const T rn = rv[u] - af * qv[u];
+      r[k] = rn;
+      acc.add(rn * rn);
+    }
+  }
+  for (; i < rr.i1; i += kWarps) {
     size_t k = vidx(t, N, i);
-    x[k] += a * (double)p[k];
+    x[k] += a * to_f64(p[k]);
     T rv = r[k] - af * q[k];
     r[k] = rv;
     acc.add(rv * rv);
@@ -330,7 +371,20 @@ __global__ void k_update_p(int N, int chunks, const double* __restrict__ beta, c
   if (!tile_active[t]) return;
   T b = (T)beta[t * WM_LANES + threadIdx.x];
   RowRange rr = chunk_rows(N, chunks);
-  for (int i = rr.i0 + threadIdx.y; i < rr.i1; i += kWarps) {
+  constexpr int UR = 4;  // rows of a warp in flight together
+  int i = rr.i0 + threadIdx.y;
+  for (; i + (UR - 1) * kWarps < rr.i1; i += UR * kWarps) {
+    T zv[UR], pv[UR];
+#pragma unroll
+    for (int u = 0; u < UR; ++u) {
+      const size_t k = vidx(t, N, i + u * kWarps);
+      zv[u] = z[k];
+      pv[u] = b == (T)0 ? (T)0 : p[k];
+    }
+#pragma unroll
+    for (int u = 0; u < UR; ++u) p[vidx(t, N, i + u * kWarps)] = b == (T)0 ? zv[u] : zv[u] + b * pv[u];
+  }
+  for (; i < rr.i1; i += kWarps) {
     size_t k = vidx(t, N, i);
     p[k] = b == (T)0 ? z[k] : z[k] + b * p[k];
   }
