@@ -809,22 +809,24 @@ __global__ void __launch_bounds__(256) k_transfer(int Nout, int Nin, int chunks,
       acc[k] = 0;
       old[k] = ADD && ts.act[k] ? out[((size_t)(t0 + k) * Nout + i) * WM_LANES + lane] : (T)0;
     }
-    // entries four at a time: their loads and gathers in flight together,
-    // the products summed in entry order
+    // entries UR at a time: their loads and gathers in flight together, the
+    // products summed in entry order (restriction rows are the longer ones:
+    // (p + 2)^2 entries against at most (p + 1)^2)
+    constexpr int UR = ADD ? 4 : 8;
     const int j1 = ptr[i + 1];
     int j = ptr[i];
-    for (; j + 4 <= j1; j += 4) {
-      typename TrT<T>::type en[4];
-      T v[4][kTPW];
+    for (; j + UR <= j1; j += UR) {
+      typename TrT<T>::type en[UR];
+      T v[UR][kTPW];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) en[u] = ld_tr(ent + j + u);
+      for (int u = 0; u < UR; ++u) en[u] = ld_tr(ent + j + u);
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < UR; ++u)
 #pragma unroll
         for (int k = 0; k < kTPW; ++k)
           v[u][k] = ts.act[k] ? in[((size_t)(t0 + k) * Nin + en[u].col) * WM_LANES + lane] : (T)0;
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < UR; ++u)
 #pragma unroll
         for (int k = 0; k < kTPW; ++k)
           if (ts.act[k]) acc[k] += en[u].v * v[u][k];
