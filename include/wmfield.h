@@ -335,8 +335,10 @@ int wm_noise_loads(wm_hier_t h, uint64_t seed, int n_samples, double* b, void* s
  * WM_ERR_INVALID_ARG without launching anything (so does a b that is not
  * device memory, or a current device other than the hierarchy's).  The first
  * call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it: make that first call before any stream
- * capture.  Every call writes all the scratch it reads, so nothing needs to
+ * (cudaGetSymbolAddress) and caches it; later calls query only the current
+ * device and the pointer attributes of b before their two kernel launches
+ * (with wm_profile_enable on, CUDA events are recorded around them).
+ * Every call writes all the scratch it reads, so nothing needs to
  * start at zero; all calls share the array, so calls whose work overlaps on
  * the GPU (different streams, or different host threads) race.
  * Stream-ordered, no synchronisation.
