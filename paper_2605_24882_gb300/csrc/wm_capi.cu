@@ -176,7 +176,7 @@ static void release_level(wm_level& L) {
   L.d_bu.release(); L.d_du.release(); L.d_bv.release(); L.d_dv.release();
   L.d_Pptr.release(); L.d_Pcol.release(); L.d_Rptr.release(); L.d_Rcol.release();
   L.d_Pval64.release(); L.d_Rval64.release(); L.d_Pval32.release(); L.d_Rval32.release();
-  L.d_ng_ptr.release(); L.d_ng_idx.release(); L.d_Sdense.release(); L.d_Mdense.release();
+  L.d_ng_ptr.release(); L.d_ng_idx.release(); L.d_Sdense.release(); L.d_Mdense.release(); L.d_noise_w.release();
   L.d_pk32.release(); L.d_pk64.release(); L.d_P32.release(); L.d_R32.release(); L.d_P64.release();
   L.d_R64.release();
   L.d_ext.release(); L.d_own.release(); L.d_csm32.release(); L.d_csm64.release(); L.d_csmdf.release();
@@ -234,6 +234,7 @@ static int assemble(wm_hier* h, int n_levels, cudaStream_t s) {
     } else {
       WM_TRY(wm_k_metric(h, L, s));
     }
+    if (l == 0) WM_TRY(wm_k_noise_weights(h, L, s));
     WM_TRY(wm_k_element_matrices(h, L, s));
     WM_TRY(wm_k_assemble_rows(h, L, s));
     WM_TRY(wm_k_pack_rows(L, s));

@@ -151,6 +151,9 @@ struct wm_level {
   DevBuf<float4> d_csmdf;
   // noise gather on this level: DOF i <- sum over (e, k) entries
   DevBuf<int32_t> d_ng_ptr, d_ng_idx;
+  // finest level: sqrt(w_q a_q) of every Gauss point [E][nq*nq], the
+  // sample-independent factor of the noise loads
+  DevBuf<double> d_noise_w;
   // coarse dense operators (coarsest level only): [N][N] row-major
   DevBuf<double> d_Sdense, d_Mdense;
 };
@@ -207,6 +210,8 @@ int wm_k_normals(uint64_t seed, int sample, int stream_id, int64_t q0, int64_t n
 // loads of rows [row0, row0+ns) of a tiled [tiles][N][32] buffer (row v at tile
 // v/32, lane v%32), row row0 + k holding the loads of sample sample_first + k
 // (its Philox counters); `bl` is scratch of E*nk*ns doubles
+// sqrt(w_q a_q) of the level's Gauss points into L.d_noise_w (after its metric)
+int wm_k_noise_weights(const wm_hier* h, wm_level& L, cudaStream_t s);
 int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int sample_first, int row0, int ns, double* b_tiled,
                      double* bl, cudaStream_t s);
 

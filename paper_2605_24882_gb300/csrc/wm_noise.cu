@@ -78,13 +78,29 @@ __global__ void k_normals(uint64_t seed, int sample, int stream, int64_t q0, int
   out[i] = (q & 1) ? z1 : z0;
 }
 
+// sqrt(w_q a_q) of every Gauss point, [E][nq^2] (the factor k_noise_local
+// forms per sample, with the same operations)
+template <int P>
+__global__ void k_noise_weights(int E, int nu, int nv, const double* __restrict__ metric,
+                                const double* __restrict__ gw, double* __restrict__ w) {
+  constexpr int NQ = P + 1, NQ2 = NQ * NQ;
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= (int64_t)E * NQ2) return;
+  const int j = (int)(q % NQ2);
+  const int gv = j / NQ, gu = j % NQ;
+  const double elw = 1.0 / ((double)nu * nv);
+  w[q] = sqrt(gw[gu] * gw[gv] * elw * metric[4 * q]);
+}
+
 // One thread per (element e, sample s0+sl): the (p+1)^2 local load
 // contributions sum_q sqrt(w_q a_q) xi_q phi_k(x_q) of the element, xi the
-// Philox normals of sample s0 + sl.  bl layout [E][nk][ns].
-template <int P>
+// Philox normals of sample s0 + sl.  bl layout [E][nk][ns].  WT: the factors
+// sqrt(w_q a_q) from the table of k_noise_weights instead of per sample.
+template <int P, bool WT = false>
 __global__ void k_noise_local(int E, int nu, int nv, int ns, int s0, uint64_t seed,
                               const double* __restrict__ metric, const double* __restrict__ gw,
-                              const double* __restrict__ bu, const double* __restrict__ bv, double* __restrict__ bl) {
+                              const double* __restrict__ bu, const double* __restrict__ bv, double* __restrict__ bl,
+                              const double* __restrict__ wtab = nullptr) {
   constexpr int NQ = P + 1, NK = (P + 1) * (P + 1), NQ2 = NQ * NQ;
   int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (tid >= (int64_t)E * ns) return;
@@ -103,11 +119,16 @@ __global__ void k_noise_local(int E, int nu, int nv, int ns, int s0, uint64_t se
     if (j0 + 1 < NQ2) xi[j0 + 1] = z1;
   }
   double wq[NQ2];
-  double elw = 1.0 / ((double)nu * nv);
+  if constexpr (WT) {
 #pragma unroll
-  for (int j = 0; j < NQ2; ++j) {
-    int gv = j / NQ, gu = j % NQ;
-    wq[j] = sqrt(gw[gu] * gw[gv] * elw * metric[4 * (q0 + j)]) * xi[j];
+    for (int j = 0; j < NQ2; ++j) wq[j] = wtab[q0 + j] * xi[j];
+  } else {
+    double elw = 1.0 / ((double)nu * nv);
+#pragma unroll
+    for (int j = 0; j < NQ2; ++j) {
+      int gv = j / NQ, gu = j % NQ;
+      wq[j] = sqrt(gw[gu] * gw[gv] * elw * metric[4 * (q0 + j)]) * xi[j];
+    }
   }
   const double* BU = bu + (size_t)eu * (P + 1) * NQ;
   const double* BV = bv + (size_t)ev * (P + 1) * NQ;
@@ -164,9 +185,13 @@ int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int sample_first, int row0
   const wm_level& L = h->lv[0];
   int64_t n1 = (int64_t)L.E * ns;
   unsigned g1 = (unsigned)((n1 + 127) / 128);
-#define WM_NL(PP)                                                                                        \
-  k_noise_local<PP><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, ns, sample_first, seed, L.d_metric.p, h->d_gw.p, L.d_bu.p, \
-                                       L.d_bv.p, bl)
+#define WM_NL(PP)                                                                                              \
+  if (L.d_noise_w.p)                                                                                           \
+    k_noise_local<PP, true><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, ns, sample_first, seed, L.d_metric.p, h->d_gw.p, \
+                                               L.d_bu.p, L.d_bv.p, bl, L.d_noise_w.p);                          \
+  else                                                                                                         \
+    k_noise_local<PP><<<g1, 128, 0, s>>>(L.E, L.nu, L.nv, ns, sample_first, seed, L.d_metric.p, h->d_gw.p,      \
+                                         L.d_bu.p, L.d_bv.p, bl)
   wm_prof_begin(WM_PC_NOISE, s);
   switch (h->p) {
     case 1: WM_NL(1); break;
@@ -181,6 +206,22 @@ int wm_k_noise_tiled(const wm_hier* h, uint64_t seed, int sample_first, int row0
   int64_t n2 = (int64_t)L.N * ns;
   WM_LAUNCH(WM_PC_NOISE, s, k_noise_gather<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(L.N, ns, row0, L.d_ng_ptr.p, L.d_ng_idx.p, bl,
                                                               b_tiled));
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
+int wm_k_noise_weights(const wm_hier* h, wm_level& L, cudaStream_t s) {
+  const int nq2 = h->nq * h->nq;
+  WM_TRY(L.d_noise_w.alloc((size_t)L.E * nq2));
+  const int64_t n = (int64_t)L.E * nq2;
+  const unsigned g = (unsigned)((n + 255) / 256);
+  switch (h->p) {
+    case 1: WM_LAUNCH(WM_PC_ASSEMBLY, s, (k_noise_weights<1><<<g, 256, 0, s>>>(L.E, L.nu, L.nv, L.d_metric.p, h->d_gw.p, L.d_noise_w.p))); break;
+    case 2: WM_LAUNCH(WM_PC_ASSEMBLY, s, (k_noise_weights<2><<<g, 256, 0, s>>>(L.E, L.nu, L.nv, L.d_metric.p, h->d_gw.p, L.d_noise_w.p))); break;
+    case 3: WM_LAUNCH(WM_PC_ASSEMBLY, s, (k_noise_weights<3><<<g, 256, 0, s>>>(L.E, L.nu, L.nv, L.d_metric.p, h->d_gw.p, L.d_noise_w.p))); break;
+    case 4: WM_LAUNCH(WM_PC_ASSEMBLY, s, (k_noise_weights<4><<<g, 256, 0, s>>>(L.E, L.nu, L.nv, L.d_metric.p, h->d_gw.p, L.d_noise_w.p))); break;
+    default: return WM_ERR_UNSUPPORTED;
+  }
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
