@@ -413,16 +413,21 @@ __global__ void __launch_bounds__(BU * 32, sizeof(T) == 4 ? 2 : 1) k_sten(StenGe
 // combined rows
 // A = S + sigma M (with the Chebyshev weights w = c2 / (dS + sigma dM)), so an
 // output costs one FMA per stencil entry and no division.  The group's tiles
-// then stream through one shared-memory stage buffer (cp.async copies of the
-// window and the output rows), four blocks to an SM in float hiding each
-// other's copy latency; two stage buffers (the next tile copied while the
-// current one is computed) measured slower at the two blocks per SM they allow.
+// then stream through shared-memory stage buffers (cp.async copies of the
+// window and the output rows).  Float p = 2 takes two (the next tile copied
+// while the current one is computed) at the three blocks per SM they allow
+// (measured 153.7 against 154.5 ms per bench step with one buffer at four
+// blocks); p = 3 takes one (two would allow only two blocks per SM, which
+// measured slower).
 enum { UNI_CHEB = 0, UNI_RESID = 1, UNI_APPLY = 2, UNI_CHEBDOT = 3, UNI_CHEB1 = 4 };
 // schedule constants of the one-shift kernel: stage buffers in float, output
 // rows per step of a warp (0: two where the register budget allows), partial
 // sums per output
 #ifndef WM_UNI_NST_F32
 #define WM_UNI_NST_F32 1
+#endif
+#ifndef WM_UNI_NST_F32_P2
+#define WM_UNI_NST_F32_P2 2
 #endif
 #ifndef WM_UNI_RPS
 #define WM_UNI_RPS 1
@@ -464,7 +469,7 @@ struct UniLayout {
       (sizeof(T) == 4 && P == 2)
           ? (WM_UNI_TPW == 0 ? ((MODE == UNI_RESID || MODE == UNI_APPLY) ? 2 : 1) : WM_UNI_TPW)
           : 1;
-  static constexpr int NST = TPW == 2 ? 2 : (sizeof(T) == 4 ? WM_UNI_NST_F32 : 1);
+  static constexpr int NST = TPW == 2 ? 2 : (sizeof(T) == 4 ? (P == 2 ? WM_UNI_NST_F32_P2 : WM_UNI_NST_F32) : 1);
   static constexpr size_t win = (size_t)NC * 32 * sizeof(T);  // window of the input vector
   static constexpr size_t rows = (size_t)NR * BU * BV * 32 * sizeof(T);  // staged rows of the outputs
   static constexpr size_t stage = win + rows;
