@@ -32,3 +32,15 @@ def test_committed_cache_entries_are_well_formed():
         sc = e["schedule"]
         assert 1 <= sc["uni_run"] <= 8 and 1 <= sc["uni_waves"] <= 64
         assert 32 <= sc["vec_rows"] <= 4096 and 8 <= sc["vcycle_rows"] <= 1024
+        assert sc.get("tail_fused", 1) in (0, 1)
+
+
+def test_schedule_knobs_are_abi_fields():
+    # every knob the autotuner sweeps (and a cache entry may set) is a field of
+    # the ABI's wm_schedule, so set_schedule cannot silently drop one
+    from paper_2605_24882_gb300 import _capi, autotune
+    fields = [n for n, _ in _capi.Schedule._fields_]
+    assert set(autotune.SCHEDULE_CHOICES) == set(fields)
+    if os.path.exists(autotune.CACHE):
+        for e in json.load(open(autotune.CACHE)).values():
+            assert set(e["schedule"]) <= set(fields)
