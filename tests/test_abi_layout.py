@@ -42,3 +42,16 @@ def test_structs_match_the_header(tmp_path):
         assert got[(ctype, "size")] == C.sizeof(cls), ctype
         for name, _ in cls._fields_:
             assert got[(ctype, name)] == getattr(cls, name).offset, (ctype, name)
+
+
+def test_constants_match_the_header():
+    # every WM_ integer constant of the binding has the header's value
+    import re
+    from paper_2605_24882_gb300 import _capi
+    hdr = open(os.path.join(ROOT, "include", "wmfield.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (WM_[A-Z0-9_]+) \(?(-?\d+)\)?", hdr)}
+    ours = {k: v for k, v in vars(_capi).items() if k.startswith("WM_") and isinstance(v, int)}
+    assert ours, "no constants in the binding"
+    for k, v in ours.items():
+        assert k in defs, k
+        assert defs[k] == v, (k, defs[k], v)
