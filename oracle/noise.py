@@ -38,6 +38,25 @@ def noise_from_xi(space, xi, quad=None):
     return b
 
 
+def noise_adjoint(space, g, quad=None):
+    """B^T g at all global quadrature points (length n_quad): the gradient of a
+    loss with respect to the Gauss-point noise xi, given g = dL/db (b = B xi),
+    (B^T g)_q = sqrt(w_q a_q) sum_i phi_i(x_q) g_i over the glued functions i
+    whose support holds x_q."""
+    surf = space.surf
+    if quad is None:
+        quad = quadrature(surf)
+    phi, _, _ = local_bases(surf)
+    conn = space.connectivity()
+    g = np.asarray(g, dtype=np.float64)
+    out = []
+    for m in range(surf.n_patches):
+        gl = g[conn[m]]  # [n_v, n_u, (p+1)^2]: the element's glued coefficients
+        val = np.einsum("yxkgh,yxk->yxgh", phi, gl)
+        out.append((np.sqrt(quad["W"] * quad["a"][m]) * val).ravel())
+    return np.concatenate(out)
+
+
 def noise_loads(space, seed, n_samples, quad=None):
     """[n_samples, N] load vectors of samples 0..n_samples-1 drawn with ``seed``."""
     q = np.arange(n_quad(space.surf))

@@ -77,6 +77,10 @@ MUTANTS = [
     ("noise_same_sample", "noise.py", "normals(seed, s, q, STREAM_NOISE)", "normals(seed, 0, q, STREAM_NOISE)"),
     ("noise_local_index", "noise.py", 'loc = np.einsum("yxkgh,yxgh->yxk", phi, wq)',
      'loc = np.einsum("yxkgh,yxhg->yxk", phi, wq)'),
+    ("noise_adjoint_no_sqrt", "noise.py", 'out.append((np.sqrt(quad["W"] * quad["a"][m]) * val).ravel())',
+     'out.append((quad["W"] * quad["a"][m] * val).ravel())'),
+    ("noise_adjoint_point_index", "noise.py", 'val = np.einsum("yxkgh,yxk->yxgh", phi, gl)',
+     'val = np.einsum("yxkgh,yxk->yxhg", phi, gl)'),
     ("philox_multiplier", "philox.py", "_M0 = np.uint64(0xD2511F53)", "_M0 = np.uint64(0xD2511F35)"),
     ("philox_weyl", "philox.py", "k1 = (k1 + _W1) & _MASK", "k1 = (k1 + _W0) & _MASK"),
     ("philox_round_words", "philox.py", "c = [hi1 ^ c[1] ^ k0, lo1, hi0 ^ c[3] ^ k1, lo0]",

@@ -6,7 +6,7 @@ import pytest
 
 from oracle import geometry as geo
 from oracle.assembly import assemble, quadrature
-from oracle.noise import n_quad, noise_from_xi, noise_loads
+from oracle.noise import n_quad, noise_adjoint, noise_from_xi, noise_loads
 from oracle.philox import normals, philox4x32_10, uniform53
 from oracle.space import GluedSpace
 
@@ -64,3 +64,29 @@ def test_noise_loads_statistics():
     Md = M.toarray()
     err = np.abs(C - Md).max() / np.abs(Md).max()
     assert err < 0.1
+
+
+@pytest.mark.parametrize("kind,p,nu,nv", [("sphere", 2, 2, 2), ("torus", 3, 8, 4)])
+def test_noise_adjoint_is_the_transpose(kind, p, nu, nv):
+    # <B xi, g> = <xi, B^T g> for random xi and g, and B^T 1 = sqrt(w a) at
+    # every Gauss point (the glued basis is a partition of unity)
+    s = geo.Surface(kind, p, nu, nv)
+    sp_ = GluedSpace(s)
+    q = quadrature(s)
+    nQ = n_quad(s)
+    rng = np.random.default_rng(17)
+    xi = rng.standard_normal(nQ)
+    g = rng.standard_normal(sp_.N)
+    bt = noise_adjoint(sp_, g, q)
+    assert bt.shape == (nQ,)
+    assert noise_from_xi(sp_, xi, q) @ g == pytest.approx(xi @ bt, rel=1e-12)
+    wa = np.concatenate([np.sqrt(q["W"] * a).ravel() for a in q["a"]])
+    np.testing.assert_allclose(noise_adjoint(sp_, np.ones(sp_.N), q), wa, rtol=1e-12)
+    # column j of B^T is the load of unit noise at point j, read at DOF i
+    B = np.stack([noise_from_xi(sp_, np.eye(1, nQ, j).ravel(), q) for j in range(0, nQ, 7)], axis=1)
+    i = rng.integers(0, sp_.N, 5)
+    for ii in i:
+        e = np.zeros(sp_.N)
+        e[ii] = 1.0
+        np.testing.assert_allclose(noise_adjoint(sp_, e, q)[0::7], B[ii], rtol=1e-12, atol=1e-16)
+
